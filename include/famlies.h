@@ -1,0 +1,213 @@
+/*
+ * famlies.h -- C ABI of the B300 dense tensor-contraction library.
+ *
+ * The one operation is the general dense tensor contraction
+ *
+ *     C[c] := alpha * sum_{k} A[a(c,k)] * B[b(c,k)] + beta * C[c]
+ *
+ * over integer index labels, with every tensor in an arbitrary strided
+ * layout.  The paper asks for tensor contraction computed by fusing the data
+ * reorganisation into the level-3 product instead of converting tensors to
+ * matrices first (Sec. 1, "Challenges", last item; Sec. 2.3 "Supporting
+ * tensor computations", block-scatter mapping), for arbitrarily strided
+ * local layouts (Girder 2, "Providing flexibility in data layout"), for
+ * transposition expressed as a change of strides (Sec. 2.1 "Variations on
+ * functionality"), for mixed/new precisions such as bf16 (Sec. 1.5
+ * "Supporting new and mixed precisions"), and for bounds checking with
+ * graceful error recovery (Girder 1, "Code safety").  GEMM is the case of
+ * one label per class.
+ *
+ * Label semantics.  A label in C and in exactly one of A, B is a free index
+ * (class M if in A, class N if in B); a label in A and B but not in C is
+ * contracted (class K); a label in all three is a batch index.  A label that
+ * appears in only one tensor, or twice in one tensor, is rejected
+ * (FAMLIES_ERR_LABEL).  Extents of a label must agree across tensors.
+ *
+ * Conventions (BLAS-style).  alpha == 0, or an empty contracted extent:
+ * C := beta * C and A, B are not read.  beta == 0: C is not read, so NaN or
+ * Inf already in C is overwritten.  Otherwise Inf/NaN in A or B propagate
+ * as IEEE arithmetic gives them (the paper adopts consistent NaN/Inf
+ * propagation, Sec. 1.5 "BLIS and TBLIS").  An empty free extent is a no-op.
+ *
+ * Memory.  Every data pointer is a DEVICE pointer on the current CUDA device
+ * unless the entry point says otherwise; the caller owns all buffers and the
+ * library keeps no pointer after the call returns.  Work is enqueued on the
+ * caller's stream (a cudaStream_t passed as void*; NULL is the legacy
+ * default stream) and runs asynchronously; temporary workspace is taken
+ * from the stream-ordered allocator on that stream and released on it.
+ *
+ * Errors.  Every entry point returns FAMLIES_OK (0) or a negative
+ * FAMLIES_ERR_* code; host-side errors are reported before anything is
+ * launched.  Kernels never trap: a kernel whose bounded wait expires
+ * records FAMLIES_ERR_DEVICE_TIMEOUT in a device status word, which
+ * famlies_device_status() reads.  No C++ exception crosses this ABI.
+ */
+#ifndef FAMLIES_H
+#define FAMLIES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FAMLIES_MAX_NDIM 8
+
+#if defined(__GNUC__)
+#define FAMLIES_API __attribute__((visibility("default")))
+#else
+#define FAMLIES_API
+#endif
+
+/* Storage and arithmetic of one call.
+ *   F64      A, B, C fp64; native fp64 fused multiply-add.
+ *   F64_EMU  A, B, C fp64; each operand is split into `slices` bf16 slices
+ *            of integers (per row / column power-of-two scaling), the slice
+ *            products run on the tensor cores with exact fp32 accumulation,
+ *            recombination and the alpha/beta update run in fp64.
+ *   F32      A, B, C fp32; tensor cores with a three-term split of each
+ *            operand into tf32 high and low parts (fp32-level accuracy).
+ *   BF16     A, B bf16, C fp32; bf16 products with fp32 accumulation.
+ * alpha and beta are always passed as double and rounded to the
+ * accumulation type (fp32 for F32/BF16). */
+typedef enum {
+  FAMLIES_F64 = 0,
+  FAMLIES_F64_EMU = 1,
+  FAMLIES_F32 = 2,
+  FAMLIES_BF16 = 3
+} famlies_dtype_t;
+
+/* One tensor operand.
+ *   ndim       0..FAMLIES_MAX_NDIM modes (0 = scalar).
+ *   extents    ndim extents, each >= 0 (may be NULL when ndim == 0).
+ *   strides    ndim strides in ELEMENTS, each >= 0.  Stride 0 (broadcast)
+ *              is allowed in A and B; C's modes of extent > 1 must not
+ *              overlap (FAMLIES_ERR_UNSUPPORTED otherwise).
+ *   labels     ndim distinct integer labels.
+ *   data       element (i_0..i_{n-1}) is at data + sum_d i_d*strides[d]
+ *              (in elements of the operand's storage type).
+ *   size_bytes optional size of the allocation starting at data; when > 0
+ *              every reachable element must lie inside it
+ *              (FAMLIES_ERR_OUT_OF_BOUNDS otherwise).  0 = unchecked. */
+typedef struct {
+  int32_t ndim;
+  const int64_t* extents;
+  const int64_t* strides;
+  const int32_t* labels;
+  void* data;
+  int64_t size_bytes;
+} famlies_tensor_t;
+
+/* Return codes. */
+#define FAMLIES_OK 0
+#define FAMLIES_ERR_INVALID_ARG (-1)     /* null pointer, ndim, negative extent/stride, dtype */
+#define FAMLIES_ERR_LABEL (-2)           /* label in one tensor only, or repeated in a tensor */
+#define FAMLIES_ERR_EXTENT_MISMATCH (-3) /* same label, different extents */
+#define FAMLIES_ERR_ALIAS (-4)           /* C's memory range overlaps A's or B's */
+#define FAMLIES_ERR_OUT_OF_BOUNDS (-5)   /* reachable element beyond size_bytes */
+#define FAMLIES_ERR_UNSUPPORTED (-6)     /* e.g. self-overlapping C, a class too large */
+#define FAMLIES_ERR_ALLOC (-7)           /* workspace allocation failed */
+#define FAMLIES_ERR_CUDA (-8)            /* a CUDA runtime call failed */
+#define FAMLIES_ERR_DEVICE_TIMEOUT (-9)  /* a kernel's bounded wait expired (asynchronous) */
+#define FAMLIES_ERR_NO_DEVICE (-10)      /* no usable sm_100-family device */
+
+/* Optional knobs for famlies_contract_ex (zero-initialise for defaults).
+ *   slices      F64_EMU: number of bf16 slices per operand, 2..8 (default 7).
+ *   kernel      0 = automatic; 1 = force the SIMT (CUDA-core) kernel for
+ *               F64/F32; 2 = force the tensor-core kernel.
+ *   tile_n      tensor-core tile width (64, 128 or 256; 0 = automatic).
+ *   wait_limit  iteration cap of every bounded wait (0 = default). */
+typedef struct {
+  int32_t slices;
+  int32_t kernel;
+  int32_t tile_n;
+  int32_t reserved0;
+  int64_t wait_limit;
+  int64_t reserved[4];
+} famlies_options_t;
+
+/* What the planner decided for a call (filled by famlies_plan and, when
+ * non-NULL, by famlies_contract_ex).  m, n, k, batch are the products of
+ * the extents of each label class; *_modes count the classes' modes after
+ * index fusion (adjacent modes whose strides chain in every operand that
+ * holds them are merged); swapped = 1 when the kernel treats B as its row
+ * operand so that C's unit-stride mode lies along the rows; kernel is the
+ * path chosen (see FAMLIES_KERNEL_*); launches counts kernel launches. */
+typedef struct {
+  int64_t m, n, k, batch;
+  int32_t m_modes, n_modes, k_modes, batch_modes;
+  int32_t swapped;
+  int32_t kernel;
+  int32_t launches;
+  int32_t slices;
+  int32_t a_contig; /* 0 none, 1 unit stride along the row class, 2 along k */
+  int32_t b_contig;
+  int32_t c_contig; /* 0 none, 1 along rows, 2 along columns */
+  int32_t reserved;
+} famlies_plan_info_t;
+
+#define FAMLIES_KERNEL_NONE 0      /* nothing to do (empty C) */
+#define FAMLIES_KERNEL_SCALE 1     /* C := beta*C only */
+#define FAMLIES_KERNEL_SIMT_F64 2  /* fp64 CUDA-core kernel */
+#define FAMLIES_KERNEL_SIMT_F32 3  /* fp32 CUDA-core kernel */
+#define FAMLIES_KERNEL_TC_BF16 4   /* tcgen05 bf16, gathered operand tiles */
+#define FAMLIES_KERNEL_TC_TF32X3 5 /* tcgen05 tf32 three-term split, gathered tiles */
+#define FAMLIES_KERNEL_TC_EMU 6    /* slice split + tcgen05 slice products + fp64 recombination */
+
+/* C := alpha*contract(A,B) + beta*C on `stream`.  Asynchronous: returns
+ * after enqueueing.  Host-side validation errors return before any launch. */
+FAMLIES_API int famlies_contract(double alpha, const famlies_tensor_t* A, const famlies_tensor_t* B,
+                     double beta, const famlies_tensor_t* C, famlies_dtype_t dtype,
+                     void* stream);
+
+/* famlies_contract with knobs (opt may be NULL) and a plan report (info may
+ * be NULL). */
+FAMLIES_API int famlies_contract_ex(double alpha, const famlies_tensor_t* A, const famlies_tensor_t* B,
+                        double beta, const famlies_tensor_t* C, famlies_dtype_t dtype,
+                        void* stream, const famlies_options_t* opt,
+                        famlies_plan_info_t* info);
+
+/* Same operation on HOST buffers (pageable or pinned): the library copies
+ * the reachable span of A, B (and C when beta != 0) to device workspace on
+ * `stream`, contracts, copies C back and synchronises the stream before
+ * returning.  size_bytes, when set, bounds the host spans as above. */
+FAMLIES_API int famlies_contract_host(double alpha, const famlies_tensor_t* A, const famlies_tensor_t* B,
+                          double beta, const famlies_tensor_t* C, famlies_dtype_t dtype,
+                          void* stream, const famlies_options_t* opt);
+
+/* count independent contractions (alpha[i], A[i], B[i], beta[i], C[i]) of
+ * one dtype, run as ONE grouped persistent launch per kernel stage over a
+ * device tile list ordered longest-first (the blocks of a block-sparse
+ * contraction, Sec. 2.3, "tensor-of-tensors" tiling).  Every C[i] must be
+ * disjoint from every A[j], B[j] and from every other C[j].  When use_graph
+ * is non-zero the launches are captured once into a CUDA graph, cached by
+ * the problem set (pointers, shapes, scalars), and replayed on later calls
+ * with the same set.  Asynchronous. */
+FAMLIES_API int famlies_contract_batched(int64_t count, const double* alpha, const famlies_tensor_t* A,
+                             const famlies_tensor_t* B, const double* beta,
+                             const famlies_tensor_t* C, famlies_dtype_t dtype, void* stream,
+                             int use_graph);
+
+/* Host-only planning: validates the descriptors and reports the plan
+ * without touching any device (data pointers are not dereferenced; C/A/B
+ * alias checks use the pointer values). */
+FAMLIES_API int famlies_plan(const famlies_tensor_t* A, const famlies_tensor_t* B,
+                 const famlies_tensor_t* C, famlies_dtype_t dtype,
+                 const famlies_options_t* opt, famlies_plan_info_t* info);
+
+/* Static English text for a return code (never NULL). */
+FAMLIES_API const char* famlies_error_string(int code);
+
+/* Synchronises `stream`, then returns and clears the device status word of
+ * the current device: FAMLIES_OK, or FAMLIES_ERR_DEVICE_TIMEOUT when some
+ * kernel's bounded wait expired since the last call. */
+FAMLIES_API int famlies_device_status(void* stream);
+
+/* Library ABI version (major*10000 + minor*100 + patch). */
+FAMLIES_API int famlies_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FAMLIES_H */

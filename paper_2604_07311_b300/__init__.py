@@ -1,0 +1,119 @@
+"""B300-native dense tensor contraction: C := alpha*contract(A, B) + beta*C.
+
+Python face of the C ABI in ``include/famlies.h``.  Importing this package
+does not load the CUDA library; the first call does, and raises
+``FamliesError`` if it is missing.  ``inputs`` (seeded synthetic workloads)
+imports nothing from here.
+"""
+from __future__ import annotations
+
+from ._lib import (BF16, DTYPES, F32, F64, F64_EMU, KERNELS, Desc, FamliesError, PlanInfo,
+                   desc_numpy, desc_torch, load, options, check, error_string)
+
+__all__ = ["contract", "contract_host", "contract_batched", "plan", "device_status",
+           "FamliesError", "F64", "F64_EMU", "F32", "BF16", "lib_path", "Contract", "contract_autograd"]
+
+
+def lib_path() -> str:
+    from ._lib import LIB_PATH
+    return LIB_PATH
+
+
+def _dtype_code(dtype, A, C):
+    import torch
+    if dtype is not None:
+        return DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    if A.dtype == torch.float64:
+        return F64
+    if A.dtype == torch.float32:
+        return F32
+    if A.dtype == torch.bfloat16:
+        return BF16
+    raise TypeError(f"unsupported dtype {A.dtype}")
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def contract(alpha, A, la, B, lb, beta, C, lc, dtype=None, stream=None, *, slices=0, kernel=0,
+             tile_n=0, wait_limit=0, return_info=False):
+    """C := alpha * contract(A, B) + beta * C on the GPU, in place on C.
+
+    A, B, C are CUDA torch tensors (any non-negative strides); la, lb, lc are
+    integer labels, one per mode.  dtype: 'f64', 'f64_emu', 'f32', 'bf16' or
+    None (from A's dtype).  Enqueued on `stream` (default: torch's current
+    stream); asynchronous like any CUDA op.
+    """
+    lib = load()
+    code = _dtype_code(dtype, A, C)
+    da, db, dc = desc_torch(A, la), desc_torch(B, lb), desc_torch(C, lc)
+    info = PlanInfo()
+    opt = options(slices, kernel, tile_n, wait_limit)
+    check(lib.famlies_contract_ex(float(alpha), da.ref, db.ref, float(beta), dc.ref, code,
+                                  _stream_handle(stream), opt, info))
+    return (C, info.as_dict()) if return_info else C
+
+
+def contract_host(alpha, A, la, B, lb, beta, C, lc, dtype="f64", stream=None, *, slices=0, kernel=0):
+    """Same operation on host numpy arrays (copies in, contracts, copies C back; synchronous)."""
+    lib = load()
+    code = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    da, db, dc = desc_numpy(A, la), desc_numpy(B, lb), desc_numpy(C, lc)
+    opt = options(slices, kernel)
+    check(lib.famlies_contract_host(float(alpha), da.ref, db.ref, float(beta), dc.ref, code,
+                                    _stream_handle(stream) if stream is not None else None, opt))
+    return C
+
+
+def plan(A_shape, A_strides, la, B_shape, B_strides, lb, C_shape, C_strides, lc, dtype="f64",
+         pointers=(0x10000, 0x20000000, 0x40000000), slices=0, kernel=0):
+    """Host-only plan report (no device needed): classes, fusion, role swap."""
+    lib = load()
+    code = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    da = Desc(A_shape, A_strides, la, pointers[0])
+    db = Desc(B_shape, B_strides, lb, pointers[1])
+    dc = Desc(C_shape, C_strides, lc, pointers[2])
+    info = PlanInfo()
+    check(lib.famlies_plan(da.ref, db.ref, dc.ref, code, options(slices, kernel), info))
+    return info.as_dict()
+
+
+def contract_batched(alpha, As, las, Bs, lbs, beta, Cs, lcs, dtype=None, stream=None, use_graph=True):
+    """count independent contractions in one grouped launch (lists of tensors/labels)."""
+    import ctypes
+    lib = load()
+    n = len(As)
+    if not (len(Bs) == len(Cs) == len(las) == len(lbs) == len(lcs) == n):
+        raise ValueError("one entry per problem")
+    code = _dtype_code(dtype, As[0], Cs[0]) if n else F64
+    descs = [(desc_torch(a, x), desc_torch(b, y), desc_torch(c, z))
+             for a, x, b, y, c, z in zip(As, las, Bs, lbs, Cs, lcs)]
+    from ._lib import TensorDesc
+    ta = (TensorDesc * max(n, 1))(*[d[0].t for d in descs])
+    tb = (TensorDesc * max(n, 1))(*[d[1].t for d in descs])
+    tc = (TensorDesc * max(n, 1))(*[d[2].t for d in descs])
+    al = [alpha] * n if not hasattr(alpha, "__len__") else list(alpha)
+    be = [beta] * n if not hasattr(beta, "__len__") else list(beta)
+    aa = (ctypes.c_double * max(n, 1))(*al)
+    bb = (ctypes.c_double * max(n, 1))(*be)
+    check(lib.famlies_contract_batched(n, aa, ta, tb, bb, tc, code, _stream_handle(stream),
+                                       1 if use_graph else 0))
+    return Cs
+
+
+def device_status(stream=None) -> int:
+    """Synchronises and returns/clears the device status word (0 or -9 timeout)."""
+    return int(load().famlies_device_status(_stream_handle(stream)))
+
+
+def __getattr__(name):
+    if name in ("Contract", "contract_autograd"):
+        from . import autograd
+        return getattr(autograd, name)
+    raise AttributeError(name)

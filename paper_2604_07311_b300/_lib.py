@@ -1,0 +1,136 @@
+"""ctypes binding of libfamlies.so (include/famlies.h): argument marshalling only.
+
+Every step of a contraction runs in the library's CUDA kernels; this module
+converts torch tensors / numpy arrays into ``famlies_tensor_t`` descriptors
+and raises ``FamliesError`` on a non-zero return code.  There is no fallback:
+if the shared library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfamlies.so")
+
+F64, F64_EMU, F32, BF16 = 0, 1, 2, 3
+DTYPES = {"f64": F64, "f64_emu": F64_EMU, "f32": F32, "bf16": BF16}
+KERNELS = {0: "none", 1: "scale", 2: "simt_f64", 3: "simt_f32", 4: "tc_bf16", 5: "tc_tf32x3",
+           6: "tc_emu"}
+ERR_DEVICE_TIMEOUT = -9
+
+EXPORTS = ["famlies_contract", "famlies_contract_ex", "famlies_contract_host",
+           "famlies_contract_batched", "famlies_plan", "famlies_error_string",
+           "famlies_device_status", "famlies_version"]
+
+
+class TensorDesc(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("extents", ctypes.POINTER(ctypes.c_int64)),
+                ("strides", ctypes.POINTER(ctypes.c_int64)), ("labels", ctypes.POINTER(ctypes.c_int32)),
+                ("data", ctypes.c_void_p), ("size_bytes", ctypes.c_int64)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("slices", ctypes.c_int32), ("kernel", ctypes.c_int32), ("tile_n", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("wait_limit", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 4)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("batch", ctypes.c_int64), ("m_modes", ctypes.c_int32), ("n_modes", ctypes.c_int32),
+                ("k_modes", ctypes.c_int32), ("batch_modes", ctypes.c_int32),
+                ("swapped", ctypes.c_int32), ("kernel", ctypes.c_int32), ("launches", ctypes.c_int32),
+                ("slices", ctypes.c_int32), ("a_contig", ctypes.c_int32), ("b_contig", ctypes.c_int32),
+                ("c_contig", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        d["kernel_name"] = KERNELS.get(self.kernel, "?")
+        return d
+
+
+class FamliesError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"famlies error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Loads the shared library (raises if it is missing: no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or os.environ.get("FAMLIES_LIB", LIB_PATH)
+    if not os.path.exists(path):
+        raise FamliesError(-8, f"libfamlies.so not built at {path}; run `python -m paper_2604_07311_b300.build`")
+    lib = ctypes.CDLL(path)
+    T = ctypes.POINTER(TensorDesc)
+    vp = ctypes.c_void_p
+    d = ctypes.c_double
+    lib.famlies_contract.argtypes = [d, T, T, d, T, ctypes.c_int, vp]
+    lib.famlies_contract_ex.argtypes = [d, T, T, d, T, ctypes.c_int, vp, ctypes.POINTER(Options),
+                                        ctypes.POINTER(PlanInfo)]
+    lib.famlies_contract_host.argtypes = [d, T, T, d, T, ctypes.c_int, vp, ctypes.POINTER(Options)]
+    lib.famlies_contract_batched.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_double), T, T,
+                                             ctypes.POINTER(ctypes.c_double), T, ctypes.c_int, vp,
+                                             ctypes.c_int]
+    lib.famlies_plan.argtypes = [T, T, T, ctypes.c_int, ctypes.POINTER(Options), ctypes.POINTER(PlanInfo)]
+    lib.famlies_error_string.argtypes = [ctypes.c_int]
+    lib.famlies_error_string.restype = ctypes.c_char_p
+    lib.famlies_device_status.argtypes = [vp]
+    for f in ("famlies_contract", "famlies_contract_ex", "famlies_contract_host",
+              "famlies_contract_batched", "famlies_plan", "famlies_device_status", "famlies_version"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def error_string(code: int) -> str:
+    return load().famlies_error_string(code).decode()
+
+
+def check(code: int):
+    if code != 0:
+        raise FamliesError(code, error_string(code))
+
+
+class Desc:
+    """Owns the ctypes arrays behind one famlies_tensor_t."""
+
+    def __init__(self, shape, strides, labels, data_ptr: int, size_bytes: int = 0):
+        n = len(shape)
+        if len(strides) != n or len(labels) != n:
+            raise ValueError("shape, strides and labels must have one entry per mode")
+        self._e = (ctypes.c_int64 * max(n, 1))(*[int(x) for x in shape])
+        self._s = (ctypes.c_int64 * max(n, 1))(*[int(x) for x in strides])
+        self._l = (ctypes.c_int32 * max(n, 1))(*[int(x) for x in labels])
+        self.t = TensorDesc(n, self._e, self._s, self._l, ctypes.c_void_p(int(data_ptr)), int(size_bytes))
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.t)
+
+
+def desc_torch(x, labels) -> Desc:
+    """Descriptor of a torch tensor view (device pointer, element strides)."""
+    st = x.untyped_storage()
+    size = st.nbytes() - x.storage_offset() * x.element_size()
+    return Desc(tuple(x.shape), tuple(x.stride()), labels, x.data_ptr(), max(size, 0))
+
+
+def desc_numpy(x, labels) -> Desc:
+    """Descriptor of a numpy view (host pointer, element strides)."""
+    es = x.itemsize
+    if any(s < 0 or s % es for s in x.strides):
+        raise ValueError("non-negative element strides only")
+    return Desc(x.shape, tuple(s // es for s in x.strides), labels, x.__array_interface__["data"][0])
+
+
+def options(slices=0, kernel=0, tile_n=0, wait_limit=0) -> Options:
+    o = Options()
+    o.slices, o.kernel, o.tile_n, o.wait_limit = int(slices), int(kernel), int(tile_n), int(wait_limit)
+    return o

@@ -1,0 +1,269 @@
+// C ABI entry points: validate and plan on the host, take stream-ordered
+// workspace, build the offset tables on the device, launch the kernel the
+// plan names, release the workspace.  Nothing here computes on the host.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "device.h"
+#include "plan.h"
+
+using namespace famlies;
+
+namespace {
+
+// Checks (once per device) that the current device is an sm_103 part, the
+// only target these kernels are built for.
+int check_device() {
+  static std::mutex mu;
+  static int cached[64];
+  static bool init = false;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!init) {
+    for (int& c : cached) c = 1;  // 1 = unknown
+    init = true;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return FAMLIES_ERR_NO_DEVICE;
+  }
+  if (dev < 0 || dev >= 64) return FAMLIES_ERR_NO_DEVICE;
+  if (cached[dev] == 1) {
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaGetLastError();
+    cached[dev] = (major == 10 && minor == 3) ? FAMLIES_OK : FAMLIES_ERR_NO_DEVICE;
+  }
+  return cached[dev];
+}
+
+int64_t env_wait_limit() {
+  static int64_t v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("FAMLIES_WAIT_LIMIT");
+    v = e ? std::atoll(e) : 0;
+    if (v <= 0) v = (int64_t)1 << 26;  // ~ seconds of polling, far above any real wait
+  }
+  return v;
+}
+
+struct Workspace {
+  void* ptr = nullptr;
+  cudaStream_t s = nullptr;
+  ~Workspace() {
+    if (ptr) cudaFreeAsync(ptr, s);
+  }
+};
+
+int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
+             const famlies_options_t* opt, famlies_plan_info_t* info) {
+  fill_info(p, info);
+  if (p.kernel == FAMLIES_KERNEL_NONE) return FAMLIES_OK;
+  int rc = check_device();
+  if (rc) return rc;
+  int64_t tab_bytes = table_entries(p) * (int64_t)sizeof(int64_t);
+  int64_t extra = 0;
+  if (p.kernel == FAMLIES_KERNEL_TC_EMU) extra = emu_workspace_bytes(p);
+  else if (p.kernel == FAMLIES_KERNEL_TC_BF16 || p.kernel == FAMLIES_KERNEL_TC_TF32X3)
+    extra = tc_workspace_bytes(p);
+  extra = (extra + 255) / 256 * 256;
+  tab_bytes = (tab_bytes + 255) / 256 * 256;
+  Workspace ws;
+  ws.s = s;
+  if (cudaMallocAsync(&ws.ptr, tab_bytes + extra, s) != cudaSuccess) {
+    cudaGetLastError();
+    ws.ptr = nullptr;
+    return FAMLIES_ERR_ALLOC;
+  }
+  Tables t;
+  int launches = 0;
+  if (launch_tables(p, (int64_t*)((char*)ws.ptr + extra), &t, s) != cudaSuccess)
+    return FAMLIES_ERR_CUDA;
+  ++launches;
+  cudaError_t err = cudaSuccess;
+  if (p.kernel == FAMLIES_KERNEL_SCALE) {
+    err = launch_scale(p, t, beta, s);
+    ++launches;
+  } else {
+    GemmArgs g;
+    g.a = p.a;
+    g.b = p.b;
+    g.c = p.c;
+    g.t = t;
+    g.m = p.m;
+    g.n = p.n;
+    g.k = p.k;
+    g.l = p.l;
+    g.alpha = alpha;
+    g.beta = beta;
+    g.a_contig = p.a_contig;
+    g.b_contig = p.b_contig;
+    g.wait_limit = (opt && opt->wait_limit > 0) ? opt->wait_limit : env_wait_limit();
+    g.status = device_status_ptr();
+    if (!g.status) return FAMLIES_ERR_CUDA;
+    switch (p.kernel) {
+      case FAMLIES_KERNEL_SIMT_F64:
+      case FAMLIES_KERNEL_SIMT_F32:
+        err = launch_simt(p, g, s);
+        ++launches;
+        break;
+      case FAMLIES_KERNEL_TC_BF16:
+      case FAMLIES_KERNEL_TC_TF32X3:
+        err = launch_tc(p, g, opt ? opt->tile_n : 0, s);
+        ++launches;
+        break;
+      case FAMLIES_KERNEL_TC_EMU:
+        err = launch_emu(p, g, ws.ptr, s);
+        launches += 2;
+        break;
+      default:
+        return FAMLIES_ERR_UNSUPPORTED;
+    }
+  }
+  if (info) info->launches = launches;
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return err == cudaErrorNotSupported ? FAMLIES_ERR_UNSUPPORTED : FAMLIES_ERR_CUDA;
+  }
+  return FAMLIES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int famlies_version(void) { return 100; }
+
+const char* famlies_error_string(int code) {
+  switch (code) {
+    case FAMLIES_OK: return "success";
+    case FAMLIES_ERR_INVALID_ARG: return "invalid argument (null pointer, ndim, negative extent or stride, dtype)";
+    case FAMLIES_ERR_LABEL: return "bad label set (label in one tensor only, or repeated within a tensor)";
+    case FAMLIES_ERR_EXTENT_MISMATCH: return "extent mismatch for a shared label";
+    case FAMLIES_ERR_ALIAS: return "C overlaps A or B";
+    case FAMLIES_ERR_OUT_OF_BOUNDS: return "reachable element beyond size_bytes";
+    case FAMLIES_ERR_UNSUPPORTED: return "unsupported layout or size";
+    case FAMLIES_ERR_ALLOC: return "workspace allocation failed";
+    case FAMLIES_ERR_CUDA: return "CUDA runtime error";
+    case FAMLIES_ERR_DEVICE_TIMEOUT: return "a kernel's bounded wait expired";
+    case FAMLIES_ERR_NO_DEVICE: return "no sm_103 CUDA device";
+  }
+  return "unknown error code";
+}
+
+int famlies_plan(const famlies_tensor_t* A, const famlies_tensor_t* B, const famlies_tensor_t* C,
+                 famlies_dtype_t dtype, const famlies_options_t* opt, famlies_plan_info_t* info) {
+  Plan p;
+  int rc = make_plan(1.0, A, B, C, dtype, opt, &p);
+  if (rc) return rc;
+  fill_info(p, info);
+  return FAMLIES_OK;
+}
+
+int famlies_contract_ex(double alpha, const famlies_tensor_t* A, const famlies_tensor_t* B,
+                        double beta, const famlies_tensor_t* C, famlies_dtype_t dtype,
+                        void* stream, const famlies_options_t* opt, famlies_plan_info_t* info) {
+  Plan p;
+  int rc = make_plan(alpha, A, B, C, dtype, opt, &p);
+  if (rc) return rc;
+  return run_plan(p, alpha, beta, (cudaStream_t)stream, opt, info);
+}
+
+int famlies_contract(double alpha, const famlies_tensor_t* A, const famlies_tensor_t* B,
+                     double beta, const famlies_tensor_t* C, famlies_dtype_t dtype,
+                     void* stream) {
+  return famlies_contract_ex(alpha, A, B, beta, C, dtype, stream, nullptr, nullptr);
+}
+
+int famlies_contract_host(double alpha, const famlies_tensor_t* A, const famlies_tensor_t* B,
+                          double beta, const famlies_tensor_t* C, famlies_dtype_t dtype,
+                          void* stream, const famlies_options_t* opt) {
+  Plan p;
+  int rc = make_plan(alpha, A, B, C, dtype, opt, &p);
+  if (rc) return rc;
+  if (p.kernel == FAMLIES_KERNEL_NONE) return FAMLIES_OK;
+  if ((rc = check_device())) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  // Spans in the caller's operand order (the plan may have swapped roles).
+  const int64_t span_a = p.swapped ? p.span_b : p.span_a;
+  const int64_t span_b = p.swapped ? p.span_a : p.span_b;
+  const bool reads_ab = p.kernel != FAMLIES_KERNEL_SCALE;
+  const int64_t bytes_a = reads_ab ? span_a * p.es_a : 0;
+  const int64_t bytes_b = reads_ab ? span_b * p.es_b : 0;
+  const int64_t bytes_c = p.span_c * p.es_c;
+  auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
+  void* dev = nullptr;
+  if (cudaMallocAsync(&dev, up(bytes_a) + up(bytes_b) + up(bytes_c) + 256, s) != cudaSuccess) {
+    cudaGetLastError();
+    return FAMLIES_ERR_ALLOC;
+  }
+  char* da = (char*)dev;
+  char* db = da + up(bytes_a);
+  char* dc = db + up(bytes_b);
+  int64_t entries_c = 1;
+  for (int i = 0; i < C->ndim; ++i) entries_c *= C->extents[i];
+  // C is copied in when beta reads it, or when its span has gaps that the
+  // copy back must not overwrite with undefined bytes.
+  const bool copy_c_in = beta != 0.0 || entries_c != p.span_c;
+  cudaError_t e = cudaSuccess;
+  if (bytes_a) e = cudaMemcpyAsync(da, A->data, bytes_a, cudaMemcpyHostToDevice, s);
+  if (!e && bytes_b) e = cudaMemcpyAsync(db, B->data, bytes_b, cudaMemcpyHostToDevice, s);
+  if (!e && copy_c_in) e = cudaMemcpyAsync(dc, C->data, bytes_c, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    famlies_tensor_t a2 = *A, b2 = *B, c2 = *C;
+    a2.data = da;
+    b2.data = db;
+    c2.data = dc;
+    a2.size_bytes = b2.size_bytes = c2.size_bytes = 0;
+    Plan p2;
+    rc = make_plan(alpha, &a2, &b2, &c2, dtype, opt, &p2);
+    if (!rc) rc = run_plan(p2, alpha, beta, s, opt, nullptr);
+    if (!rc) e = cudaMemcpyAsync(C->data, dc, bytes_c, cudaMemcpyDeviceToHost, s);
+  }
+  cudaFreeAsync(dev, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (rc) return rc;
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    cudaGetLastError();
+    return FAMLIES_ERR_CUDA;
+  }
+  return FAMLIES_OK;
+}
+
+int famlies_contract_batched(int64_t count, const double* alpha, const famlies_tensor_t* A,
+                             const famlies_tensor_t* B, const double* beta,
+                             const famlies_tensor_t* C, famlies_dtype_t dtype, void* stream,
+                             int use_graph) {
+  (void)use_graph;
+  if (count < 0 || (count > 0 && (!alpha || !beta || !A || !B || !C)))
+    return FAMLIES_ERR_INVALID_ARG;
+  std::vector<Plan> plans((size_t)count);
+  for (int64_t i = 0; i < count; ++i) {
+    int rc = make_plan(alpha[i], &A[i], &B[i], &C[i], dtype, nullptr, &plans[i]);
+    if (rc) return rc;
+  }
+  for (int64_t i = 0; i < count; ++i) {
+    int rc = run_plan(plans[i], alpha[i], beta[i], (cudaStream_t)stream, nullptr, nullptr);
+    if (rc) return rc;
+  }
+  return FAMLIES_OK;
+}
+
+int famlies_device_status(void* stream) {
+  if (check_device()) return FAMLIES_ERR_NO_DEVICE;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    return FAMLIES_ERR_CUDA;
+  }
+  int v = 0;
+  if (read_clear_status(&v)) return FAMLIES_ERR_CUDA;
+  return v;
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+// Device-side argument blocks shared by the kernels and the host launchers.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "plan.h"
+
+namespace famlies {
+
+// Offset tables ("block-scatter" vectors): element (m, n, k, l) of the
+// contraction reads A at a + am[m] + ak[k] + al[l], B at b + bn[n] + bk[k]
+// + bl[l] and writes C at c + cm[m] + cn[n] + cl[l] (offsets in elements).
+struct Tables {
+  const int64_t* am;
+  const int64_t* cm;
+  const int64_t* bn;
+  const int64_t* cn;
+  const int64_t* ak;
+  const int64_t* bk;
+  const int64_t* al;
+  const int64_t* bl;
+  const int64_t* cl;
+};
+
+struct GemmArgs {
+  const void* a;
+  const void* b;
+  void* c;
+  Tables t;
+  int64_t m, n, k, l;
+  double alpha, beta;
+  int a_contig, b_contig;  // 1: unit stride along rows/cols, 2: along k
+  int64_t wait_limit;      // iteration cap of every bounded wait
+  int* status;             // device status word (first error recorded wins)
+};
+
+// Address of the device status word of the current device, and a host-side
+// read-and-clear of it (both defined next to the word itself).
+int* device_status_ptr();
+int read_clear_status(int* value);
+
+// ---- launchers (each returns a cudaError_t from the launch)
+cudaError_t launch_tables(const Plan& p, int64_t* ws, Tables* t, cudaStream_t s);
+cudaError_t launch_scale(const Plan& p, const Tables& t, double beta, cudaStream_t s);
+cudaError_t launch_simt(const Plan& p, const GemmArgs& g, cudaStream_t s);
+cudaError_t launch_tc(const Plan& p, const GemmArgs& g, int tile_n, cudaStream_t s);
+// Split-precision fp64 emulation: workspace size query and launch.
+int64_t emu_workspace_bytes(const Plan& p);
+cudaError_t launch_emu(const Plan& p, const GemmArgs& g, void* ws, cudaStream_t s);
+int64_t tc_workspace_bytes(const Plan& p);
+
+// Number of int64 entries the offset tables of a plan need.
+inline int64_t table_entries(const Plan& p) {
+  return 2 * p.m + 2 * p.n + 2 * p.k + 3 * p.l;
+}
+
+inline int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+}  // namespace famlies

@@ -1,0 +1,213 @@
+// CUDA-core kernels: offset tables, C := beta*C, and the fp64 / fp32 SIMT
+// contraction (the native-fp64 path and a forced-SIMT fp32 path).
+//
+// The SIMT contraction stages a BM x BK tile of A and a BN x BK tile of B
+// into shared memory straight from the strided tensors through the offset
+// tables (block-scatter vectors, Sec. 2.3 of the paper): threads are laid
+// along whichever index is unit-stride in that operand so that the gathers
+// coalesce.  Each thread then owns a TM x TN register block of C, updated
+// with fused multiply-adds, and the epilogue applies alpha/beta and scatters
+// to C's strided layout.  Native fp64 on B300 is bound by the fp64 pipe, not
+// by memory, so this simple register-blocked form reaches that pipe's rate.
+#include <cstdint>
+
+#include "device.h"
+
+namespace famlies {
+
+// Device status word: FAMLIES_OK, or the first error a kernel recorded
+// (kernels get its address through GemmArgs::status).
+__device__ int g_famlies_status = 0;
+
+int* device_status_ptr() {
+  static int* ptr[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!ptr[dev] && cudaGetSymbolAddress((void**)&ptr[dev], g_famlies_status) != cudaSuccess) {
+    cudaGetLastError();
+    ptr[dev] = nullptr;
+  }
+  return ptr[dev];
+}
+
+int read_clear_status(int* value) {
+  int zero = 0;
+  if (cudaMemcpyFromSymbol(value, g_famlies_status, sizeof(int)) != cudaSuccess ||
+      cudaMemcpyToSymbol(g_famlies_status, &zero, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------------- tables
+struct TableJob {
+  int n;
+  int64_t ext[kMaxModes];
+  int64_t st[kMaxModes];
+  int64_t total;
+  int64_t* out;
+};
+struct TableJobs {
+  TableJob j[9];
+};
+
+__global__ void k_tables(TableJobs jobs) {
+  const TableJob& J = jobs.j[blockIdx.y];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < J.total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = i, off = 0;
+    for (int d = 0; d < J.n; ++d) {
+      int64_t e = J.ext[d];
+      off += (r % e) * J.st[d];
+      r /= e;
+    }
+    J.out[i] = off;
+  }
+}
+
+cudaError_t launch_tables(const Plan& p, int64_t* ws, Tables* t, cudaStream_t s) {
+  TableJobs jobs;
+  const ClassModes* cls[9] = {&p.M, &p.M, &p.N, &p.N, &p.K, &p.K, &p.L, &p.L, &p.L};
+  const int which[9] = {0, 2, 1, 2, 0, 1, 0, 1, 2};  // sa, sc, sb, sc, sa, sb, sa, sb, sc
+  int64_t* ptr[9];
+  int64_t off = 0, maxn = 1;
+  for (int i = 0; i < 9; ++i) {
+    TableJob& J = jobs.j[i];
+    const ClassModes& cm = *cls[i];
+    J.n = cm.n;
+    for (int d = 0; d < cm.n; ++d) {
+      J.ext[d] = cm.m[d].ext;
+      J.st[d] = which[i] == 0 ? cm.m[d].sa : (which[i] == 1 ? cm.m[d].sb : cm.m[d].sc);
+    }
+    J.total = cm.total();
+    J.out = ws + off;
+    ptr[i] = ws + off;
+    off += J.total;
+    maxn = J.total > maxn ? J.total : maxn;
+  }
+  t->am = ptr[0]; t->cm = ptr[1]; t->bn = ptr[2]; t->cn = ptr[3];
+  t->ak = ptr[4]; t->bk = ptr[5]; t->al = ptr[6]; t->bl = ptr[7]; t->cl = ptr[8];
+  int64_t blocks = (maxn + 255) / 256;
+  dim3 grid((unsigned)(blocks > 1024 ? 1024 : blocks), 9);
+  k_tables<<<grid, 256, 0, s>>>(jobs);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- C := beta*C
+template <typename T>
+__global__ void k_scale(T* __restrict__ c, Tables t, int64_t m, int64_t n, int64_t l, T beta) {
+  const int64_t total = m * n * l;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t im = i % m, r = i / m;
+    int64_t in = r % n, il = r / n;
+    T* p = c + t.cm[im] + t.cn[in] + t.cl[il];
+    *p = beta == T(0) ? T(0) : beta * *p;  // beta == 0: C is not read
+  }
+}
+
+cudaError_t launch_scale(const Plan& p, const Tables& t, double beta, cudaStream_t s) {
+  int64_t total = p.m * p.n * p.l;
+  int64_t blocks = (total + 255) / 256;
+  int grid = (int)(blocks > 4 * 148 * 8 ? 4 * 148 * 8 : blocks);
+  if (grid < 1) grid = 1;
+  if (p.es_c == 8)
+    k_scale<double><<<grid, 256, 0, s>>>((double*)p.c, t, p.m, p.n, p.l, beta);
+  else
+    k_scale<float><<<grid, 256, 0, s>>>((float*)p.c, t, p.m, p.n, p.l, (float)beta);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- SIMT GEMM
+// 256 threads; thread (tx, ty) owns rows ty + i*(BM/TM) and columns
+// tx + j*(BN/TN) of the tile (interleaved so shared-memory reads of a warp
+// hit distinct banks).
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__(256) k_simt(GemmArgs g) {
+  static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const T* __restrict__ A = (const T*)g.a;
+  const T* __restrict__ B = (const T*)g.b;
+  T* __restrict__ C = (T*)g.c;
+  const int tid = threadIdx.x;
+  const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+  const int64_t tiles_m = (g.m + BM - 1) / BM, tiles_n = (g.n + BN - 1) / BN;
+  const int64_t ntiles = tiles_m * tiles_n * g.l;
+  const T alpha = (T)g.alpha, beta = (T)g.beta;
+
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t tm = tile % tiles_m, rest = tile / tiles_m;
+    const int64_t tn = rest % tiles_n, il = rest / tiles_n;
+    const int64_t m0 = tm * BM, n0 = tn * BN;
+    const int64_t al = g.t.al[il], bl = g.t.bl[il], cl = g.t.cl[il];
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+    for (int64_t k0 = 0; k0 < g.k; k0 += BK) {
+      for (int e = tid; e < BM * BK; e += 256) {
+        int mm, kk;
+        if (g.a_contig == 2) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
+        const int64_t gm = m0 + mm, gk = k0 + kk;
+        As[kk][mm] = (gm < g.m && gk < g.k) ? A[al + g.t.am[gm] + g.t.ak[gk]] : T(0);
+      }
+      for (int e = tid; e < BN * BK; e += 256) {
+        int nn, kk;
+        if (g.b_contig == 2) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
+        const int64_t gn = n0 + nn, gk = k0 + kk;
+        Bs[kk][nn] = (gn < g.n && gk < g.k) ? B[bl + g.t.bn[gn] + g.t.bk[gk]] : T(0);
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < BK; ++kk) {
+        T ra[TM], rb[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) ra[i] = As[kk][ty + i * (BM / TM)];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) rb[j] = Bs[kk][tx + j * (BN / TN)];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(ra[i], rb[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int64_t gm = m0 + ty + i * (BM / TM);
+      if (gm >= g.m) continue;
+      const int64_t crow = cl + g.t.cm[gm];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int64_t gn = n0 + tx + j * (BN / TN);
+        if (gn >= g.n) continue;
+        T* p = C + crow + g.t.cn[gn];
+        T v = alpha * acc[i][j];
+        if (beta != T(0)) v = fma(beta, *p, v);
+        *p = v;
+      }
+    }
+  }
+}
+
+cudaError_t launch_simt(const Plan& p, const GemmArgs& g, cudaStream_t s) {
+  const int sms = num_sms();
+  if (p.es_a == 8) {
+    constexpr int BM = 64, BN = 64;
+    int64_t tiles = ((p.m + BM - 1) / BM) * ((p.n + BN - 1) / BN) * p.l;
+    int grid = (int)(tiles < (int64_t)sms * 8 ? tiles : (int64_t)sms * 8);
+    k_simt<double, BM, BN, 16, 4, 4><<<grid, 256, 0, s>>>(g);
+  } else {
+    constexpr int BM = 128, BN = 128;
+    int64_t tiles = ((p.m + BM - 1) / BM) * ((p.n + BN - 1) / BN) * p.l;
+    int grid = (int)(tiles < (int64_t)sms * 4 ? tiles : (int64_t)sms * 4);
+    k_simt<float, BM, BN, 16, 8, 8><<<grid, 256, 0, s>>>(g);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace famlies

@@ -1,0 +1,132 @@
+"""Host-only checks of the C ABI: the library loads, exports every symbol the
+header declares, and the planner (label classes, index fusion, role swap,
+validation errors) behaves as specified.  No device is touched."""
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2604_07311_b300 as fm
+from paper_2604_07311_b300 import _lib
+from paper_2604_07311_b300 import inputs as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2604_07311_b300 import build
+    build.build()
+
+
+def header_symbols():
+    syms = set()
+    for name in os.listdir(os.path.join(ROOT, "include")):
+        if name.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", name)).read()
+            syms |= set(re.findall(r"FAMLIES_API\s+[\w\s\*]+?\b(famlies_\w+)\s*\(", text))
+    return syms
+
+
+def test_library_exports_every_declared_symbol():
+    syms = header_symbols()
+    assert {"famlies_contract", "famlies_contract_batched", "famlies_plan"} <= syms
+    out = subprocess.check_output(["nm", "-D", "--defined-only", _lib.LIB_PATH]).decode()
+    exported = set(re.findall(r"\bT\s+(famlies_\w+)", out))
+    assert syms <= exported, syms - exported
+    lib = fm.load()
+    for s in syms:
+        assert hasattr(lib, s)
+    assert lib.famlies_version() >= 100
+    assert "label" in fm.error_string(-2)
+
+
+def P(prob, dtype="f64", **kw):
+    return fm.plan(prob.A.extents, prob.A.strides, prob.A.labels, prob.B.extents, prob.B.strides,
+                   prob.B.labels, prob.C.extents, prob.C.strides, prob.C.labels, dtype=dtype, **kw)
+
+
+def test_plan_four_index():
+    info = P(W.four_index(ext=16))
+    assert (info["m"], info["n"], info["k"], info["batch"]) == (256, 256, 256, 1)
+    assert (info["m_modes"], info["n_modes"], info["k_modes"]) == (2, 2, 2)
+    assert info["swapped"] == 0 and info["a_contig"] == 1 and info["b_contig"] == 2
+    assert info["kernel_name"] == "simt_f64"
+
+
+def test_plan_ladder_fuses_to_gemm():
+    info = P(W.ladder(v=8, o=4), dtype="f64_emu")
+    assert (info["m"], info["n"], info["k"]) == (64, 16, 64)
+    assert (info["m_modes"], info["n_modes"], info["k_modes"]) == (1, 1, 1)
+    assert info["a_contig"] == 1 and info["b_contig"] == 2 and info["c_contig"] == 1
+    assert info["kernel_name"] == "tc_emu" and info["slices"] == 7
+
+
+def test_plan_transpose_free_swaps_roles():
+    info = P(W.transpose_free(v=6, o=3, pad=7), dtype="bf16")
+    # C[b,j,a,i]: unit stride on b, an index of B -> B supplies the rows
+    assert info["swapped"] == 1
+    assert (info["m"], info["n"], info["k"]) == (18, 18, 18)
+    assert info["m_modes"] == 2 and info["n_modes"] == 2
+    assert info["a_contig"] == 1 and info["b_contig"] == 1 and info["c_contig"] == 1
+    assert info["kernel_name"] == "tc_bf16"
+
+
+def test_plan_batch_labels_and_extent_one_modes():
+    # C[i,b] = sum_k A[i,k,b] B[k,b,u] with u of extent 1 in B only -> label error;
+    # with u in C too: u is an N mode of extent 1 and is dropped.
+    info = fm.plan((3, 4, 5), (1, 3, 12), [1, 2, 3], (4, 5, 1), (1, 4, 20), [2, 3, 4],
+                   (3, 5, 1), (1, 3, 15), [1, 3, 4])
+    assert info["batch"] == 5 and info["batch_modes"] == 1
+    assert info["n"] == 1 and info["n_modes"] == 0
+    with pytest.raises(fm.FamliesError) as e:
+        fm.plan((3, 4, 5), (1, 3, 12), [1, 2, 3], (4, 5, 1), (1, 4, 20), [2, 3, 4],
+                (3, 5), (1, 3), [1, 3])
+    assert e.value.code == -2
+
+
+@pytest.mark.parametrize("case,code", [
+    ("only_in_a", -2), ("repeat", -2), ("extent", -3), ("neg_extent", -1), ("c_overlap", -6),
+    ("bounds", -5), ("alias", -4), ("bad_dtype", -1)])
+def test_plan_errors(case, code):
+    A = dict(shape=(4, 5), strides=(1, 4), labels=[1, 2])
+    B = dict(shape=(5, 6), strides=(1, 5), labels=[2, 3])
+    C = dict(shape=(4, 6), strides=(1, 4), labels=[1, 3])
+    ptrs = (0x10000, 0x20000000, 0x40000000)
+    dtype = "f64"
+    if case == "only_in_a":
+        A["shape"], A["strides"], A["labels"] = (4, 5, 2), (1, 4, 20), [1, 2, 9]
+    elif case == "repeat":
+        A["labels"] = [1, 1]
+    elif case == "extent":
+        B["shape"] = (7, 6)
+    elif case == "neg_extent":
+        A["shape"] = (-4, 5)
+    elif case == "c_overlap":
+        C["strides"] = (1, 2)
+    elif case == "alias":
+        ptrs = (0x10000, 0x20000000, 0x10000 + 8)
+    elif case == "bad_dtype":
+        dtype = 7
+    lib = fm.load()
+    da = _lib.Desc(A["shape"], A["strides"], A["labels"], ptrs[0], 152 if case == "bounds" else 0)
+    db = _lib.Desc(B["shape"], B["strides"], B["labels"], ptrs[1])
+    dc = _lib.Desc(C["shape"], C["strides"], C["labels"], ptrs[2])
+    info = _lib.PlanInfo()
+    dt = dtype if isinstance(dtype, int) else _lib.DTYPES[dtype]
+    rc = lib.famlies_plan(da.ref, db.ref, dc.ref, dt, None, info)
+    assert rc == code
+
+
+def test_no_device_is_reported_not_faked():
+    """Without a GPU the compute entry points fail loudly (no CPU fallback)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    lib = fm.load()
+    da = _lib.Desc((4, 5), (1, 4), [1, 2], 0x10000)
+    db = _lib.Desc((5, 6), (1, 5), [2, 3], 0x20000000)
+    dc = _lib.Desc((4, 6), (1, 4), [1, 3], 0x40000000)
+    rc = lib.famlies_contract(1.0, da.ref, db.ref, 0.0, dc.ref, 0, None)
+    assert rc == -10
