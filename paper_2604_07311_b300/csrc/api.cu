@@ -115,7 +115,7 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
         break;
       case FAMLIES_KERNEL_TC_BF16:
       case FAMLIES_KERNEL_TC_TF32X3:
-        err = launch_tc(p, g, opt ? opt->tile_n : 0, s);
+        err = launch_tc(p, g, opt ? opt->tile_n : 0, ws.ptr, s);
         ++launches;
         break;
       case FAMLIES_KERNEL_TC_EMU:

@@ -45,7 +45,7 @@ int read_clear_status(int* value);
 cudaError_t launch_tables(const Plan& p, int64_t* ws, Tables* t, cudaStream_t s);
 cudaError_t launch_scale(const Plan& p, const Tables& t, double beta, cudaStream_t s);
 cudaError_t launch_simt(const Plan& p, const GemmArgs& g, cudaStream_t s);
-cudaError_t launch_tc(const Plan& p, const GemmArgs& g, int tile_n, cudaStream_t s);
+cudaError_t launch_tc(const Plan& p, const GemmArgs& g, int tile_n, void* ws, cudaStream_t s);
 // Split-precision fp64 emulation: workspace size query and launch.
 int64_t emu_workspace_bytes(const Plan& p);
 cudaError_t launch_emu(const Plan& p, const GemmArgs& g, void* ws, cudaStream_t s);

@@ -3,10 +3,6 @@
 
 namespace famlies {
 
-int64_t tc_workspace_bytes(const Plan&) { return 0; }
-cudaError_t launch_tc(const Plan&, const GemmArgs&, int, cudaStream_t) {
-  return cudaErrorNotSupported;
-}
 int64_t emu_workspace_bytes(const Plan&) { return 0; }
 cudaError_t launch_emu(const Plan&, const GemmArgs&, void*, cudaStream_t) {
   return cudaErrorNotSupported;
