@@ -113,8 +113,11 @@ typedef struct {
 
 /* Optional knobs for famlies_contract_ex (zero-initialise for defaults).
  *   slices      F64_EMU: number of bf16 slices per operand, 2..8 (default 7).
- *   kernel      0 = automatic; 1 = force the SIMT (CUDA-core) kernel for
- *               F64/F32; 2 = force the tensor-core kernel.
+ *   kernel      0 = automatic; 1 = the SIMT (CUDA-core) kernel (F64, F32);
+ *               2 = the packed TMA tensor-core kernel (F32, BF16, F64_EMU);
+ *               3 = the tensor-core kernel that gathers operand tiles
+ *               straight from the strided tensors (F32, BF16).  A choice
+ *               the dtype has no kernel for returns FAMLIES_ERR_UNSUPPORTED.
  *   tile_n      tensor-core tile width (64, 128 or 256; 0 = automatic).
  *   wait_limit  iteration cap of every bounded wait (0 = default). */
 typedef struct {
@@ -150,9 +153,11 @@ typedef struct {
 #define FAMLIES_KERNEL_SCALE 1     /* C := beta*C only */
 #define FAMLIES_KERNEL_SIMT_F64 2  /* fp64 CUDA-core kernel */
 #define FAMLIES_KERNEL_SIMT_F32 3  /* fp32 CUDA-core kernel */
-#define FAMLIES_KERNEL_TC_BF16 4   /* tcgen05 bf16, gathered operand tiles */
-#define FAMLIES_KERNEL_TC_TF32X3 5 /* tcgen05 tf32 three-term split, gathered tiles */
-#define FAMLIES_KERNEL_TC_EMU 6    /* slice split + tcgen05 slice products + fp64 recombination */
+#define FAMLIES_KERNEL_TC_BF16 4   /* pack + TMA-fed tcgen05 bf16 product */
+#define FAMLIES_KERNEL_TC_TF32X3 5 /* pack (tf32 hi/lo split) + TMA-fed tcgen05 three-term product */
+#define FAMLIES_KERNEL_TC_EMU 6    /* fp64 slice split + tcgen05 slice products + fp64 recombination */
+#define FAMLIES_KERNEL_TC_BF16_GATHER 7   /* tcgen05 bf16, tiles gathered straight from strided A, B */
+#define FAMLIES_KERNEL_TC_TF32X3_GATHER 8 /* tcgen05 three-term tf32, tiles gathered straight */
 
 /* C := alpha*contract(A,B) + beta*C on `stream`.  Asynchronous: returns
  * after enqueueing.  Host-side validation errors return before any launch. */

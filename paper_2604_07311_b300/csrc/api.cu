@@ -69,8 +69,10 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
   if (rc) return rc;
   int64_t tab_bytes = table_entries(p) * (int64_t)sizeof(int64_t);
   int64_t extra = 0;
-  if (p.kernel == FAMLIES_KERNEL_TC_EMU) extra = emu_workspace_bytes(p);
-  else if (p.kernel == FAMLIES_KERNEL_TC_BF16 || p.kernel == FAMLIES_KERNEL_TC_TF32X3)
+  if (p.kernel == FAMLIES_KERNEL_TC_EMU || p.kernel == FAMLIES_KERNEL_TC_BF16 ||
+      p.kernel == FAMLIES_KERNEL_TC_TF32X3)
+    extra = packed_workspace_bytes(p);
+  else if (p.kernel == FAMLIES_KERNEL_TC_BF16_GATHER || p.kernel == FAMLIES_KERNEL_TC_TF32X3_GATHER)
     extra = tc_workspace_bytes(p);
   extra = (extra + 255) / 256 * 256;
   tab_bytes = (tab_bytes + 255) / 256 * 256;
@@ -113,14 +115,19 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
         err = launch_simt(p, g, s);
         ++launches;
         break;
+      case FAMLIES_KERNEL_TC_BF16_GATHER:
+      case FAMLIES_KERNEL_TC_TF32X3_GATHER:
+        err = launch_tc(p, g, p.tile_n, ws.ptr, s);
+        launches += 3;  // two k-stride tables + the product
+        break;
       case FAMLIES_KERNEL_TC_BF16:
       case FAMLIES_KERNEL_TC_TF32X3:
-        err = launch_tc(p, g, opt ? opt->tile_n : 0, ws.ptr, s);
-        ++launches;
+        err = launch_packed(p, g, ws.ptr, s);
+        launches += 2;  // pack + product
         break;
       case FAMLIES_KERNEL_TC_EMU:
-        err = launch_emu(p, g, ws.ptr, s);
-        launches += 2;
+        err = launch_packed(p, g, ws.ptr, s);
+        launches += 4;  // exponents + pack + product + non-finite fix-up
         break;
       default:
         return FAMLIES_ERR_UNSUPPORTED;

@@ -46,10 +46,10 @@ cudaError_t launch_tables(const Plan& p, int64_t* ws, Tables* t, cudaStream_t s)
 cudaError_t launch_scale(const Plan& p, const Tables& t, double beta, cudaStream_t s);
 cudaError_t launch_simt(const Plan& p, const GemmArgs& g, cudaStream_t s);
 cudaError_t launch_tc(const Plan& p, const GemmArgs& g, int tile_n, void* ws, cudaStream_t s);
-// Split-precision fp64 emulation: workspace size query and launch.
-int64_t emu_workspace_bytes(const Plan& p);
-cudaError_t launch_emu(const Plan& p, const GemmArgs& g, void* ws, cudaStream_t s);
 int64_t tc_workspace_bytes(const Plan& p);
+// Packed paths (bf16, tf32 split, fp64 split): workspace size and launch.
+int64_t packed_workspace_bytes(const Plan& p);
+cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream_t s);
 
 // Number of int64 entries the offset tables of a plan need.
 inline int64_t table_entries(const Plan& p) {

@@ -1,0 +1,559 @@
+// Packed tensor-core contraction: one re-layout pass per operand, then a
+// TMA-fed tcgen05 product over pairs of packed "slices".
+//
+// Pack.  Each operand is read once through its offset tables (coalesced
+// along its unit-stride index, transposed through shared memory) and written
+// K-major, one 16-byte chunk per thread, as S slices P[s][l][r][k]:
+//   plain bf16   S = 1, the bf16 values themselves;
+//   tf32 split   S = 2, hi = tf32(x) and lo = tf32(x - hi) (fp32 words);
+//   fp64 split   S = s, integer digits of x scaled by its row's power of two:
+//                x = 2^e_r * sum_i d_i 2^(-b i) + remainder, |d_1| <= 2^b,
+//                |d_i| <= 2^(b-1) for i > 1 (round-to-nearest digits), every
+//                digit exact in bf16.  e_r bounds the row's largest
+//                magnitude (a first, read-only pass).  Rows holding Inf/NaN
+//                are flagged and recomputed natively afterwards.
+// This is the BLIS packing step of Fig. 2 with the tensor re-organisation
+// and the precision split fused into it (Sec. 1 "Challenges"; mixed
+// precision, Sec. 1.5; packing hoisted with data re-organisation, Girder 2).
+//
+// Product.  A persistent, warp-specialised kernel: one thread issues TMA
+// loads of slice tiles into a 4-stage shared-memory ring, one thread issues
+// tcgen05.mma into a double-buffered fp32 accumulator in tensor memory, and
+// eight epilogue warps drain it.  The work of one output tile is a list of
+// "units"; a unit accumulates a set of slice pairs over a k range.
+//   bf16 / tf32: one unit (all pairs, all of K); epilogue C = alpha*acc +
+//                beta*C in fp32.
+//   fp64 split:  the pairs with i + j = d (a "diagonal", weight 2^(-b d))
+//                for d = s+1 down to 2; a unit covers a k range short enough
+//                that the fp32 accumulator stays an exact integer (< 2^24),
+//                the epilogue adds it into int32 running sums, flushes them
+//                into an fp64 tile sum at each diagonal's end, and the last
+//                flush writes C = alpha * 2^(e_m+e_n) * sum + beta * C.
+// The fp32 accumulation is exact because every partial sum is an integer
+// below 2^24; only the diagonal recombination and the alpha/beta update use
+// fp64 arithmetic.
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "device.h"
+#include "packed.h"
+#include "ptx.cuh"
+
+namespace famlies {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 32 * (EPI_WARPS + 2);
+constexpr int STAGES = 4;
+constexpr int MAXD = 10;
+
+enum { KIND_BF16 = 0, KIND_TF32 = 1 };
+enum { MODE_F32OUT = 0, MODE_EMU = 1 };
+
+// The unit schedule of one output tile (identical for every tile).
+struct Sched {
+  int ndiag;
+  int slices;
+  int shift[MAXD];        // diagonal weight 2^-shift (fp64 split)
+  int kcb[MAXD];          // k-blocks per unit
+  int flush_every[MAXD];  // units between flushes of the int32 sums
+  int npairs[MAXD];
+  int8_t pa[MAXD][8], pb[MAXD][8];  // slice index of A and B in each pair
+};
+
+struct PairArgs {
+  GemmArgs g;
+  Sched sc;
+  const int32_t* ea;  // per-row exponents (fp64 split)
+  const int32_t* eb;
+  const int32_t* fa;  // per-row non-finite flags (fp64 split)
+  const int32_t* fb;
+  double* G;          // per-CTA fp64 tile sums (fp64 split)
+};
+
+template <int KIND, int BN>
+struct PCfg {
+  static constexpr int KB = KIND == KIND_BF16 ? 64 : 32;  // k per stage (128-byte rows)
+  static constexpr int MMA_K = KIND == KIND_BF16 ? 16 : 8;
+  static constexpr int KSTEPS = KB / MMA_K;
+  static constexpr int A_BYTES = BM * 128;
+  static constexpr int B_BYTES = BN * 128;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr uint32_t TMEM_COLS = 2 * BN;
+  static constexpr uint32_t IDESC = ptx::idesc_make(BM, BN, KIND == KIND_BF16 ? 1u : 2u);
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+__device__ __forceinline__ void record_timeout(volatile int* abort, int* status) {
+  *abort = 1;
+  atomicCAS(status, 0, FAMLIES_ERR_DEVICE_TIMEOUT);
+}
+
+template <int KIND, int MODE, int BN>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_pair_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                const PairArgs args) {
+  using Cfg = PCfg<KIND, BN>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * Cfg::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* done = tempty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  volatile int* abort = (volatile int*)(tmem_slot + 1);
+
+  const GemmArgs& g = args.g;
+  const Sched& sc = args.sc;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  const int64_t tiles_m = (g.m + BM - 1) / BM, tiles_n = (g.n + BN - 1) / BN;
+  const int64_t ntiles = tiles_m * tiles_n * g.l;
+  const int nkb = (int)((g.k + Cfg::KB - 1) / Cfg::KB);
+  const int64_t lim = g.wait_limit;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(&tfull[b], 1);
+      ptx::mbar_init(&tempty[b], EPI_WARPS);
+    }
+    ptx::mbar_init(done, 1);
+    *abort = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == EPI_WARPS + 1) {
+    ptx::tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == EPI_WARPS) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      ptx::prefetch_tmap(&map_a);
+      ptx::prefetch_tmap(&map_b);
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t pending = 0;  // bit s: stage s holds a copy issued in phase bit (s+8)
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int64_t tn = t % tiles_n, rest = t / tiles_n;
+        const int64_t tm = rest % tiles_m, il = rest / tiles_m;
+        for (int di = 0; di < sc.ndiag && ok; ++di) {
+          const int kcb = sc.kcb[di];
+          for (int kb0 = 0; kb0 < nkb && ok; kb0 += kcb) {
+            const int kb1 = kb0 + kcb < nkb ? kb0 + kcb : nkb;
+            for (int p = 0; p < sc.npairs[di] && ok; ++p) {
+              // slices are stored [slice][batch][rows][k]
+              const int za = sc.pa[di][p] * (int)g.l + (int)il;
+              const int zb = sc.pb[di][p] * (int)g.l + (int)il;
+              for (int kb = kb0; kb < kb1; ++kb) {
+                if (!ptx::mbar_wait(&empty[stage], phase ^ 1, lim, abort)) { ok = false; break; }
+                uint8_t* sa = smem + stage * Cfg::STAGE_BYTES;
+                ptx::mbar_arrive_expect_tx(&full[stage], Cfg::STAGE_BYTES);
+                ptx::tma_load_3d(sa, &map_a, &full[stage], kb * Cfg::KB, (int)(tm * BM), za);
+                ptx::tma_load_3d(sa + Cfg::A_BYTES, &map_b, &full[stage], kb * Cfg::KB,
+                                 (int)(tn * BN), zb);
+                pending = (pending & ~(0x101u << stage)) | (1u << stage) | (phase << (stage + 8));
+                if (++stage == STAGES) { stage = 0; phase ^= 1; }
+              }
+            }
+          }
+        }
+      }
+      if (!ok && !*abort) record_timeout(abort, g.status);
+      // Copies still in flight must land before the CTA leaves: wait (bounded)
+      // for the phase each stage was last filled in.
+      for (int s = 0; s < STAGES; ++s) {
+        if (!(pending & (1u << s))) continue;
+        const uint32_t ph = (pending >> (s + 8)) & 1u;
+        for (int64_t i = 0; i < ((int64_t)1 << 22); ++i)
+          if (ptx::mbar_try_wait(&full[s], ph)) break;
+      }
+    }
+    __syncwarp();
+  } else if (warp == EPI_WARPS + 1) {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, acc = 0, accph = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int di = 0; di < sc.ndiag && ok; ++di) {
+          const int kcb = sc.kcb[di];
+          for (int kb0 = 0; kb0 < nkb && ok; kb0 += kcb) {
+            const int kb1 = kb0 + kcb < nkb ? kb0 + kcb : nkb;
+            if (!ptx::mbar_wait(&tempty[acc], accph ^ 1, lim, abort)) { ok = false; break; }
+            ptx::tc_fence_after();
+            const uint32_t dt = tmem_base + acc * BN;
+            uint32_t accumulate = 0;
+            for (int p = 0; p < sc.npairs[di] && ok; ++p) {
+              for (int kb = kb0; kb < kb1; ++kb) {
+                if (!ptx::mbar_wait(&full[stage], phase, lim, abort)) { ok = false; break; }
+                ptx::tc_fence_after();
+                const uint32_t sa = ptx::smem_u32(smem + stage * Cfg::STAGE_BYTES);
+                const uint64_t da = ptx::sdesc_kmajor_sw128(sa);
+                const uint64_t db = ptx::sdesc_kmajor_sw128(sa + Cfg::A_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < Cfg::KSTEPS; ++kk) {
+                  if (KIND == KIND_BF16)
+                    ptx::mma_f16(dt, da + 2 * kk, db + 2 * kk, Cfg::IDESC, accumulate);
+                  else
+                    ptx::mma_tf32(dt, da + 2 * kk, db + 2 * kk, Cfg::IDESC, accumulate);
+                  accumulate = 1;
+                }
+                ptx::mma_commit(&empty[stage]);
+                if (++stage == STAGES) { stage = 0; phase ^= 1; }
+              }
+            }
+            if (!ok) break;
+            ptx::mma_commit(&tfull[acc]);
+            acc ^= 1;
+            if (acc == 0) accph ^= 1;
+          }
+        }
+      }
+      if (!ok && !*abort) record_timeout(abort, g.status);
+      ptx::mma_commit(done);
+      for (int64_t i = 0; i < ((int64_t)1 << 24); ++i)
+        if (ptx::mbar_try_wait(done, 0)) break;
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    constexpr int CPT = BN / 2;  // columns per thread
+    const int qd = warp & 3, hf = warp >> 2;
+    const uint32_t lane_addr = (uint32_t)(qd * 32) << 16;
+    uint32_t acc = 0, accph = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int64_t tn = t % tiles_n, rest = t / tiles_n;
+      const int64_t tm = rest % tiles_m, il = rest / tiles_m;
+      const int64_t row = tm * BM + qd * 32 + lane;
+      const int64_t col0 = tn * BN + hf * CPT;
+      const bool rv = row < g.m;
+      const int64_t crow = rv ? g.t.cl[il] + g.t.cm[row] : 0;
+      if (MODE == MODE_F32OUT) {
+        if (!ptx::mbar_wait(&tfull[acc], accph, lim, abort)) { ok = false; break; }
+        ptx::tc_fence_after();
+        float* C = (float*)g.c;
+        const float alpha = (float)g.alpha, beta = (float)g.beta;
+#pragma unroll 1
+        for (int q = 0; q < CPT / 32; ++q) {
+          uint32_t r[32];
+          ptx::tmem_ld32(tmem_base + lane_addr + acc * BN + hf * CPT + q * 32, r);
+          ptx::tmem_ld_wait();
+          if (rv) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const int64_t col = col0 + q * 32 + i;
+              if (col < g.n) {
+                float* p = C + crow + g.t.cn[col];
+                float v = alpha * __uint_as_float(r[i]);
+                if (beta != 0.f) v = fmaf(beta, *p, v);
+                *p = v;
+              }
+            }
+          }
+        }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
+        acc ^= 1;
+        if (acc == 0) accph ^= 1;
+      } else {
+        // fp64 split: int32 running sums per diagonal, fp64 tile sums in G.
+        int32_t S[CPT];
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) S[j] = 0;
+        double* Gt = args.G + (size_t)blockIdx.x * BM * BN + (size_t)(hf * CPT) * BM + qd * 32 + lane;
+        bool first_flush = true;
+        for (int di = 0; di < sc.ndiag && ok; ++di) {
+          const int kcb = sc.kcb[di];
+          const int nunits = (nkb + kcb - 1) / kcb;
+          for (int u = 0; u < nunits; ++u) {
+            if (!ptx::mbar_wait(&tfull[acc], accph, lim, abort)) { ok = false; break; }
+            ptx::tc_fence_after();
+#pragma unroll
+            for (int q = 0; q < CPT / 32; ++q) {
+              uint32_t r[32];
+              ptx::tmem_ld32(tmem_base + lane_addr + acc * BN + hf * CPT + q * 32, r);
+              ptx::tmem_ld_wait();
+#pragma unroll
+              for (int i = 0; i < 32; ++i) S[q * 32 + i] += __float2int_rn(__uint_as_float(r[i]));
+            }
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
+            acc ^= 1;
+            if (acc == 0) accph ^= 1;
+            const bool last_unit = (u == nunits - 1);
+            if (!last_unit && ((u + 1) % sc.flush_every[di]) != 0) continue;
+            const double w = ldexp(1.0, -sc.shift[di]);
+            const bool final_flush = last_unit && di == sc.ndiag - 1;
+            if (!final_flush) {
+#pragma unroll
+              for (int j = 0; j < CPT; ++j) {
+                const double prev = first_flush ? 0.0 : Gt[(size_t)j * BM];
+                Gt[(size_t)j * BM] = fma(w, (double)S[j], prev);
+                S[j] = 0;
+              }
+              first_flush = false;
+            } else if (rv && !args.fa[il * g.m + row]) {
+              double* C = (double*)g.c;
+              const double alpha = g.alpha, beta = g.beta;
+              const int er = args.ea[il * g.m + row];
+              const int32_t* ebl = args.eb + il * g.n;
+              const int32_t* fbl = args.fb + il * g.n;
+#pragma unroll
+              for (int j = 0; j < CPT; ++j) {
+                const int64_t col = col0 + j;
+                if (col < g.n && !fbl[col]) {
+                  const double prev = first_flush ? 0.0 : Gt[(size_t)j * BM];
+                  const double sum = fma(w, (double)S[j], prev);
+                  const int e = er + ebl[col];
+                  // 2^e built from its bits when it is a normal number
+                  const double scaled = (e >= -1022 && e <= 1023)
+                                            ? sum * __longlong_as_double((long long)(e + 1023) << 52)
+                                            : ldexp(sum, e);
+                  double* p = C + crow + g.t.cn[col];
+                  double v = alpha * scaled;
+                  if (beta != 0.0) v = fma(beta, *p, v);
+                  *p = v;
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+    if (!ok && !*abort) record_timeout(abort, g.status);
+  }
+
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == EPI_WARPS + 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
+  }
+}
+
+
+// ----------------------------------------------------------------- launch
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                              const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                              const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn get_encode() {
+  static EncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeFn)p;
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// 3-D map over slices [z][rows][kp] (k innermost), box {box_k, box_rows, 1},
+// 128-byte swizzle; out-of-range k and rows read as zeros.
+bool make_map(CUtensorMap* map, void* base, bool f32, int64_t k, int64_t kp, int64_t rows,
+              int64_t z, int box_k, int box_rows) {
+  EncodeFn enc = get_encode();
+  if (!enc) return false;
+  const int es = f32 ? 4 : 2;
+  cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)z};
+  cuuint64_t strides[2] = {(cuuint64_t)(kp * es), (cuuint64_t)(kp * es * rows)};
+  cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, 1u};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  return enc(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+             base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int choose_bn(const Plan& p) {
+  if (p.tile_n == 64 || p.tile_n == 128 || p.tile_n == 256) return p.tile_n;
+  return p.n > 128 ? 256 : (p.n > 64 ? 128 : 64);
+}
+
+int grid_of(const Plan& p, int bn) {
+  const int64_t tiles = ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l;
+  return (int)(tiles < num_sms() ? tiles : num_sms());
+}
+
+struct Layout {
+  size_t a, b, ea, eb, fa, fb, la, lb, G, total;
+};
+
+Layout layout_of(const Plan& p) {
+  const bool emu = p.kernel == FAMLIES_KERNEL_TC_EMU;
+  const bool tf32 = p.kernel == FAMLIES_KERNEL_TC_TF32X3;
+  const int S = emu ? p.slices : (tf32 ? 2 : 1);
+  const int es = tf32 ? 4 : 2;
+  const size_t kp = (size_t)((p.k + 7) / 8 * 8);
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  Layout L{};
+  size_t off = 0;
+  L.a = off; off += up((size_t)S * p.l * p.m * kp * es);
+  L.b = off; off += up((size_t)S * p.l * p.n * kp * es);
+  if (emu) {
+    const int bn = choose_bn(p);
+    L.ea = off; off += up((size_t)p.l * p.m * 4);
+    L.eb = off; off += up((size_t)p.l * p.n * 4);
+    L.fa = off; off += up((size_t)p.l * p.m * 4);
+    L.fb = off; off += up((size_t)p.l * p.n * 4);
+    L.la = off; off += up((size_t)(p.l * p.m + 1) * 4);
+    L.lb = off; off += up((size_t)(p.l * p.n + 1) * 4);
+    L.G = off; off += up((size_t)grid_of(p, bn) * BM * bn * 8);
+  }
+  L.total = off;
+  return L;
+}
+
+// Unit schedule.  fp64 split with s slices of b bits: diagonal q = i + j
+// (0-based slice indices, i + j <= s - 1) has weight 2^(-b (q + 2)); a unit
+// covers kcb 64-wide k blocks so that its exact integer sum stays <= 2^24.
+Sched make_sched(const Plan& p, int bits) {
+  Sched sc;
+  std::memset(&sc, 0, sizeof(sc));
+  if (p.kernel != FAMLIES_KERNEL_TC_EMU) {
+    const bool tf32 = p.kernel == FAMLIES_KERNEL_TC_TF32X3;
+    sc.ndiag = 1;
+    sc.slices = tf32 ? 2 : 1;
+    sc.kcb[0] = 1 << 30;
+    sc.flush_every[0] = 1;
+    if (tf32) {  // lo*hi + hi*lo + hi*hi, hi = slice 0, lo = slice 1
+      sc.npairs[0] = 3;
+      sc.pa[0][0] = 1; sc.pb[0][0] = 0;
+      sc.pa[0][1] = 0; sc.pb[0][1] = 1;
+      sc.pa[0][2] = 0; sc.pb[0][2] = 0;
+    } else {
+      sc.npairs[0] = 1;
+    }
+    return sc;
+  }
+  const int s = p.slices;
+  sc.ndiag = s;
+  sc.slices = s;
+  auto maxd = [&](int i) { return (int64_t)1 << (i == 0 ? bits : bits - 1); };
+  for (int di = 0; di < s; ++di) {
+    const int q = s - 1 - di;  // least significant diagonal first
+    int64_t bound = 0;
+    for (int i = 0; i <= q; ++i) {
+      sc.pa[di][i] = (int8_t)i;
+      sc.pb[di][i] = (int8_t)(q - i);
+      bound += maxd(i) * maxd(q - i);
+    }
+    sc.npairs[di] = q + 1;
+    sc.shift[di] = bits * (q + 2);
+    int64_t kcb = (((int64_t)1 << 24) / bound) / 64;
+    sc.kcb[di] = (int)(kcb < 1 ? 1 : kcb);
+    int64_t fe = (((int64_t)1 << 31) - 1) / (bound * sc.kcb[di] * 64);
+    sc.flush_every[di] = (int)(fe < 1 ? 1 : fe);
+  }
+  return sc;
+}
+
+template <int KIND, int MODE, int BN>
+cudaError_t launch_pair(const CUtensorMap& ma, const CUtensorMap& mb, const PairArgs& a, int grid,
+                        cudaStream_t s) {
+  using Cfg = PCfg<KIND, BN>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_pair_gemm<KIND, MODE, BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_pair_gemm<KIND, MODE, BN><<<grid, THREADS, Cfg::SMEM_BYTES, s>>>(ma, mb, a);
+  return cudaGetLastError();
+}
+
+template <int KIND, int MODE>
+cudaError_t launch_pair_bn(int bn, const CUtensorMap& ma, const CUtensorMap& mb,
+                           const PairArgs& a, int grid, cudaStream_t s) {
+  if (bn == 64) return launch_pair<KIND, MODE, 64>(ma, mb, a, grid, s);
+  if (bn == 128) return launch_pair<KIND, MODE, 128>(ma, mb, a, grid, s);
+  return launch_pair<KIND, MODE, 256>(ma, mb, a, grid, s);
+}
+
+}  // namespace
+
+int64_t packed_workspace_bytes(const Plan& p) { return (int64_t)layout_of(p).total; }
+
+cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream_t s) {
+  const bool emu = p.kernel == FAMLIES_KERNEL_TC_EMU;
+  const bool tf32 = p.kernel == FAMLIES_KERNEL_TC_TF32X3;
+  const int bits = 7;
+  const Layout L = layout_of(p);
+  char* w = (char*)ws;
+  const int64_t kp = (p.k + 7) / 8 * 8;
+  PackArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.k = p.k;
+  pa.kp = kp;
+  pa.l = p.l;
+  pa.slices = emu ? p.slices : (tf32 ? 2 : 1);
+  pa.bits = bits;
+  pa.op[0] = PackOp{g.a, g.t.am, g.t.ak, g.t.al, p.m, p.a_contig, w + L.a, nullptr, nullptr, nullptr};
+  pa.op[1] = PackOp{g.b, g.t.bn, g.t.bk, g.t.bl, p.n, p.b_contig, w + L.b, nullptr, nullptr, nullptr};
+  cudaError_t e;
+  if (emu) {
+    pa.op[0].e = (int32_t*)(w + L.ea);
+    pa.op[1].e = (int32_t*)(w + L.eb);
+    pa.op[0].flag = (int32_t*)(w + L.fa);
+    pa.op[1].flag = (int32_t*)(w + L.fb);
+    pa.op[0].list = (int32_t*)(w + L.la);
+    pa.op[1].list = (int32_t*)(w + L.lb);
+    // exponents start at a large negative value, flags and list counts at 0
+    if ((e = cudaMemsetAsync(w + L.ea, 0x80, L.fa - L.ea, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w + L.fa, 0, L.G - L.fa, s)) != cudaSuccess) return e;
+    if ((e = launch_rowexp(pa, s)) != cudaSuccess) return e;
+  }
+  if ((e = launch_pack(emu ? PACK_F64 : (tf32 ? PACK_TF32 : PACK_BF16), pa, s)) != cudaSuccess)
+    return e;
+  const int bn = choose_bn(p);
+  const int S = pa.slices;
+  const int kbk = tf32 ? 32 : 64;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, w + L.a, tf32, p.k, kp, p.m, (int64_t)S * p.l, kbk, BM) ||
+      !make_map(&mb, w + L.b, tf32, p.k, kp, p.n, (int64_t)S * p.l, kbk, bn))
+    return cudaErrorInvalidValue;
+  PairArgs a;
+  a.g = g;
+  a.sc = make_sched(p, bits);
+  a.ea = pa.op[0].e;
+  a.eb = pa.op[1].e;
+  a.fa = pa.op[0].flag;
+  a.fb = pa.op[1].flag;
+  a.G = emu ? (double*)(w + L.G) : nullptr;
+  const int grid = grid_of(p, bn);
+  if (emu) e = launch_pair_bn<KIND_BF16, MODE_EMU>(bn, ma, mb, a, grid, s);
+  else if (tf32) e = launch_pair_bn<KIND_TF32, MODE_F32OUT>(bn, ma, mb, a, grid, s);
+  else e = launch_pair_bn<KIND_BF16, MODE_F32OUT>(bn, ma, mb, a, grid, s);
+  if (e != cudaSuccess) return e;
+  if (emu) e = launch_fixup(g, pa, s);
+  return e;
+}
+
+}  // namespace famlies

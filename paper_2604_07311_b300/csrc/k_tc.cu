@@ -353,7 +353,7 @@ int64_t tc_workspace_bytes(const Plan& p) {
 }
 
 cudaError_t launch_tc(const Plan& p, const GemmArgs& g, int tile_n, void* ws, cudaStream_t s) {
-  const bool tf32 = p.kernel == FAMLIES_KERNEL_TC_TF32X3;
+  const bool tf32 = p.kernel == FAMLIES_KERNEL_TC_TF32X3_GATHER;
   const int epc = tf32 ? 4 : 8;
   const int64_t nq = (p.k + epc - 1) / epc;
   int64_t* aks = (int64_t*)ws;

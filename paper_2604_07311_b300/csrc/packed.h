@@ -1,0 +1,41 @@
+// Packing kernels that feed the TMA tensor-core product (see k_pack.cu).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "device.h"
+
+namespace famlies {
+
+enum { PACK_BF16 = 0, PACK_TF32 = 1, PACK_F64 = 2 };
+
+// One operand to pack: rows x k (batch l) read through offset tables.
+struct PackOp {
+  const void* x;        // source operand (strided)
+  const int64_t* roff;  // row offsets (rows entries)
+  const int64_t* koff;  // k offsets (k entries)
+  const int64_t* loff;  // batch offsets (l entries)
+  int64_t rows;
+  int contig;           // 1: unit stride along rows, 2: along k, 0: neither
+  void* out;            // slices [S][l][rows][kp]
+  int32_t* e;           // fp64 split: row exponents [l][rows] (pre-set to INT_MIN)
+  int32_t* flag;        // fp64 split: non-finite row flags [l][rows] (pre-set to 0)
+  int32_t* list;        // fp64 split: list[0] = count, list[1..] = flagged l*rows + r
+};
+
+struct PackArgs {
+  PackOp op[2];
+  int64_t k, kp, l;
+  int slices, bits;
+};
+
+// fp64 split, pass 1: row exponent bounds and non-finite flags (both operands).
+cudaError_t launch_rowexp(const PackArgs& pa, cudaStream_t s);
+// Writes the slices of both operands.
+cudaError_t launch_pack(int pmode, const PackArgs& pa, cudaStream_t s);
+// fp64 split: recomputes in native fp64 the outputs of flagged rows/columns.
+cudaError_t launch_fixup(const GemmArgs& g, const PackArgs& pa, cudaStream_t s);
+
+}  // namespace famlies

@@ -242,17 +242,31 @@ int make_plan(double alpha, const famlies_tensor_t* A, const famlies_tensor_t* B
   p.c_contig = unit(p.M, 2) ? 1 : (unit(p.N, 2) ? 2 : 0);
 
   // ---- kernel choice
-  int force = opt ? opt->kernel : 0;
+  const int force = opt ? opt->kernel : 0;
+  if (force < 0 || force > 3) return FAMLIES_ERR_INVALID_ARG;
   if (p.c_empty) p.kernel = FAMLIES_KERNEL_NONE;
   else if (p.scale_only) p.kernel = FAMLIES_KERNEL_SCALE;
   else switch (dtype) {
-    case FAMLIES_F64: p.kernel = FAMLIES_KERNEL_SIMT_F64; break;
-    case FAMLIES_F32:
-      p.kernel = (force == 2) ? FAMLIES_KERNEL_TC_TF32X3 : FAMLIES_KERNEL_SIMT_F32;
+    case FAMLIES_F64:
+      if (force >= 2) return FAMLIES_ERR_UNSUPPORTED;
+      p.kernel = FAMLIES_KERNEL_SIMT_F64;
       break;
-    case FAMLIES_BF16: p.kernel = FAMLIES_KERNEL_TC_BF16; break;
-    case FAMLIES_F64_EMU: p.kernel = FAMLIES_KERNEL_TC_EMU; break;
+    case FAMLIES_F32:
+      p.kernel = force == 1 ? FAMLIES_KERNEL_SIMT_F32
+                            : (force == 3 ? FAMLIES_KERNEL_TC_TF32X3_GATHER : FAMLIES_KERNEL_TC_TF32X3);
+      break;
+    case FAMLIES_BF16:
+      if (force == 1) return FAMLIES_ERR_UNSUPPORTED;
+      p.kernel = force == 3 ? FAMLIES_KERNEL_TC_BF16_GATHER : FAMLIES_KERNEL_TC_BF16;
+      break;
+    case FAMLIES_F64_EMU:
+      if (force == 1 || force == 3) return FAMLIES_ERR_UNSUPPORTED;
+      p.kernel = FAMLIES_KERNEL_TC_EMU;
+      break;
   }
+  p.tile_n = opt ? opt->tile_n : 0;
+  if (p.tile_n != 0 && p.tile_n != 64 && p.tile_n != 128 && p.tile_n != 256)
+    return FAMLIES_ERR_INVALID_ARG;
   int s = opt && opt->slices ? opt->slices : 7;
   if (s < 2 || s > 8) return FAMLIES_ERR_INVALID_ARG;
   p.slices = s;

@@ -50,6 +50,7 @@ struct Plan {
   int64_t span_a = 0, span_b = 0, span_c = 0;  // reachable elements (max offset + 1)
   int kernel = FAMLIES_KERNEL_NONE;
   int slices = 7;
+  int tile_n = 0;  // tensor-core tile width request (0 = automatic)
 };
 
 // Validates and plans; returns FAMLIES_OK or a FAMLIES_ERR_* code.  Never

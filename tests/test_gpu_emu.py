@@ -1,0 +1,154 @@
+"""GPU parity of the split-precision fp64 path (bf16 integer slices on the
+tensor cores, exact fp32 accumulation, fp64 recombination) against the FP64
+oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2604_07311_b300 as fm
+from paper_2604_07311_b300 import inputs as W
+
+from gpu_util import gpu_dense, rel_frob, run_gpu, run_oracle, random_label_problem, to_device
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-13  # relative Frobenius tolerance for fp64 and emulated fp64
+
+
+def _alpha_part(p, want):
+    """alpha*contract(A,B) part of the reference (want - beta*C_in)."""
+    return want - p.beta * np.array(p.C.view())
+
+
+def test_ladder_reduced():
+    p = W.ladder(v=32, o=8)
+    C, info = run_gpu(p, "f64_emu")
+    assert info["kernel_name"] == "tc_emu" and info["slices"] == 7
+    want = run_oracle(p)
+    got = gpu_dense(C)
+    assert rel_frob(got, want) <= TOL
+    # stricter: error relative to the contraction term alone
+    ab = _alpha_part(p, want)
+    assert np.linalg.norm(got - want) / np.linalg.norm(ab) <= 1e-12
+
+
+@pytest.mark.parametrize("tile_n", [64, 128, 256])
+def test_four_index_tiles(tile_n):
+    p = W.four_index(ext=16)
+    C, _ = run_gpu(p, "f64_emu", tile_n=tile_n)
+    assert rel_frob(gpu_dense(C), run_oracle(p)) <= TOL
+
+
+def test_integer_inputs_exact():
+    p = W.four_index(ext=16, integer=True)
+    C, _ = run_gpu(p, "f64_emu")
+    assert np.array_equal(gpu_dense(C), run_oracle(p))
+    rng = np.random.default_rng(400)
+    for _ in range(12):
+        q = random_label_problem(rng, max_ext=6)
+        Cq, info = run_gpu(q, "f64_emu")
+        assert np.array_equal(gpu_dense(Cq), run_oracle(q)), info
+
+
+def test_error_falls_with_slice_count():
+    """Each extra 7-bit slice shrinks the truncation error until fp64 rounding
+    is reached (the split converges to the exact product)."""
+    rng = np.random.default_rng(401)
+    m, n, k = 256, 192, 640
+    A = W.uniform_operand(rng, (m, k), [1, 2])
+    B = W.uniform_operand(rng, (k, n), [2, 3])
+    C = W.zeros_operand((m, n), [1, 3])
+    p = W.Problem("gemm", 1.0, A, B, 0.0, C)
+    want = run_oracle(p)
+    errs = []
+    for s in range(2, 8):
+        Cg, info = run_gpu(p, "f64_emu", slices=s)
+        assert info["slices"] == s
+        errs.append(rel_frob(gpu_dense(Cg), want))
+    for a, b in zip(errs, errs[1:]):
+        assert b <= max(a / 16, 4e-16), errs
+    assert errs[-1] <= TOL
+
+
+def test_nonfinite_rows_follow_ieee():
+    rng = np.random.default_rng(402)
+    m, n, k = 130, 70, 90
+    A = rng.uniform(-1, 1, (m, k))
+    B = rng.uniform(-1, 1, (k, n))
+    A[3, 5] = np.inf
+    A[100, 0] = np.nan
+    B[7, 20] = -np.inf
+    B[:, 33] = 0.0
+    B[2, 33] = np.inf          # inf * 0 in column 33 for every finite row
+    want = np.zeros((m, n))
+    oracle.contract(1.0, A, [1, 2], B, [2, 3], 0.0, want, [1, 3])
+    C = torch.zeros((m, n), dtype=torch.float64, device="cuda")
+    fm.contract(1.0, torch.from_numpy(A).cuda(), [1, 2], torch.from_numpy(B).cuda(), [2, 3], 0.0, C,
+                [1, 3], dtype="f64_emu")
+    got = C.cpu().numpy()
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    assert np.array_equal(np.isposinf(got), np.isposinf(want))
+    assert np.array_equal(np.isneginf(got), np.isneginf(want))
+    fin = np.isfinite(want)
+    assert rel_frob(got[fin], want[fin]) <= TOL
+
+
+def test_wide_exponent_range_per_row_scaling():
+    rng = np.random.default_rng(403)
+    m, n, k = 150, 140, 300
+    A = rng.uniform(-1, 1, (m, k)) * np.exp2(rng.integers(-300, 300, (m, 1)))
+    B = rng.uniform(-1, 1, (k, n)) * np.exp2(rng.integers(-200, 200, (1, n)))
+    want = np.zeros((m, n))
+    oracle.contract(1.0, A, [1, 2], B, [2, 3], 0.0, want, [1, 3])
+    C = torch.zeros((m, n), dtype=torch.float64, device="cuda")
+    fm.contract(1.0, torch.from_numpy(A).cuda(), [1, 2], torch.from_numpy(B).cuda(), [2, 3], 0.0, C,
+                [1, 3], dtype="f64_emu")
+    got = C.cpu().numpy()
+    # every entry carries its own scale 2^(e_m + e_n): compare scale-free
+    scale = np.abs(A).max(1)[:, None] * np.abs(B).max(0)[None, :]
+    assert np.abs((got - want) / scale).max() <= 1e-13 * np.sqrt(k)
+
+
+def test_alpha_beta_conventions():
+    rng = np.random.default_rng(404)
+    A = torch.from_numpy(rng.uniform(-1, 1, (40, 30))).cuda()
+    B = torch.from_numpy(rng.uniform(-1, 1, (30, 20))).cuda()
+    C = torch.full((40, 20), float("nan"), dtype=torch.float64, device="cuda")
+    fm.contract(2.0, A, [1, 2], B, [2, 3], 0.0, C, [1, 3], dtype="f64_emu")
+    want = 2.0 * (A @ B)
+    assert torch.isfinite(C).all()
+    assert (C - want).norm() / want.norm() <= TOL
+    C0 = torch.from_numpy(rng.uniform(-1, 1, (40, 20))).cuda()
+    C = C0.clone()
+    fm.contract(0.0, A * float("nan"), [1, 2], B, [2, 3], 0.5, C, [1, 3], dtype="f64_emu")
+    assert torch.equal(C, 0.5 * C0)
+
+
+def test_batch_labels():
+    rng = np.random.default_rng(405)
+    A = W.uniform_operand(rng, (70, 50, 3), [1, 2, 3])
+    B = W.uniform_operand(rng, (50, 90, 3), [2, 4, 3])
+    C = W.uniform_operand(rng, (70, 90, 3), [1, 4, 3])
+    p = W.Problem("batched", -1.5, A, B, 0.25, C)
+    Cg, info = run_gpu(p, "f64_emu")
+    assert info["batch"] == 3
+    assert rel_frob(gpu_dense(Cg), run_oracle(p)) <= TOL
+
+
+def test_full_ladder_sampled_dot2():
+    """The v=128, o=32 ladder (GEMM 16384 x 1024 x 16384 after fusion) in the
+    benchmark's launch configuration; 4096 sampled entries against the
+    compensated (Dot2) oracle."""
+    p = W.ladder(v=128, o=32)
+    C, info = run_gpu(p, "f64_emu")
+    assert (info["m"], info["n"], info["k"]) == (16384, 1024, 16384)
+    got_all = gpu_dense(C)
+    rng = np.random.default_rng(406)
+    idx = np.stack([rng.integers(0, e, 4096) for e in p.C.extents], axis=1)
+    want = oracle.entries(p.alpha, p.A.view(), p.A.labels, p.B.view(), p.B.labels, p.beta,
+                          p.C.view(), p.C.labels, idx, dot2=True)
+    got = got_all[tuple(idx.T)]
+    assert rel_frob(got, want) <= TOL
+    ab = want - p.beta * p.C.view()[tuple(idx.T)]
+    assert np.linalg.norm(got - want) / np.linalg.norm(ab) <= 1e-12
