@@ -1,0 +1,328 @@
+"""Benchmark: split-precision fp64 tensor contraction on one B300.
+
+Workload (one "step"): the particle-particle ladder contraction
+    C[a,b,i,j] += sum_{c,d} V[a,b,c,d] T[c,d,i,j]      (v = 128, o = 32)
+in fp64 storage, computed by the split-precision path (7 bf16 integer
+slices per operand on the tensor cores, exact fp32 accumulation, fp64
+recombination and beta update): exponent pass + pack + product + fix-up,
+inputs resident in HBM.  The labels fuse to a 16384 x 1024 x 16384
+GEMM-shaped contraction (5.50e11 algorithmic flops).  V alone (2.1 GB)
+exceeds L2, so every step streams its inputs from HBM.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+(test infrastructure, the reference arm here) on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "contraction TFLOP/s, % tensor-pipe peak; split-precision vs FP64 speedup"
+V_EXT, O_EXT, SLICES = 128, 32, 7
+WORKLOAD = "ccsd_ladder_v128_o32_f64_split7"
+
+
+def set_size(v: int, o: int):
+    """Smaller ladders for profiling captures (the default is the benchmark size)."""
+    global V_EXT, O_EXT, WORKLOAD
+    V_EXT, O_EXT = v, o
+    if (v, o) != (128, 32):
+        WORKLOAD = f"ccsd_ladder_v{v}_o{o}_f64_split7"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("bf16_tflops", 1800.0), d.get("bf16_tflops_sustained", 1400.0), "measured"
+    except OSError:
+        return 1800.0, 1400.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.rows, self.proc, self.gpu = [], None, gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        rows = [r for r in self.rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        load = [s for s in sm if mx and s > 0.3 * max(mx)] or sm
+        reasons = sorted({self.NAMES[i] for r in rows for i in range(4)
+                          if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    import torch
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device="cuda", dtype=torch.float64)
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_inputs():
+    from paper_2604_07311_b300 import inputs as W
+    return W.ladder(v=V_EXT, o=O_EXT)
+
+
+def cpu_sample(p, cols: int):
+    """Times the oracle on C[:, :, 0, 0:cols] of the same workload (all host cores)."""
+    import oracle
+    V = p.A.view()
+    T = p.B.view()[:, :, :1, :cols]
+    C = np.array(p.C.view()[:, :, :1, :cols], copy=True)
+    t0 = time.perf_counter()
+    oracle.contract(p.alpha, V, p.A.labels, T, p.B.labels, p.beta, C, p.C.labels)
+    dt = time.perf_counter() - t0
+    flops = 2.0 * V_EXT ** 4 * cols
+    return flops, dt, oracle.default_threads()
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, on a bounded sample."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    p = make_inputs()
+    cols = args.ref_cols
+    for _ in range(args.warmup):
+        cpu_sample(p, cols)
+    times, flops, cores = [], 0.0, 1
+    for _ in range(args.steps):
+        flops, dt, cores = cpu_sample(p, cols)
+        times.append(dt)
+    total = sum(times)
+    value = flops * args.steps / total / 1e12
+    sample = f"C[:, :, 0, 0:{cols}] of the v={V_EXT},o={O_EXT} ladder ({flops:.3g} flop per step)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "v": V_EXT, "o": O_EXT},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import paper_2604_07311_b300 as fm
+    from paper_2604_07311_b300._lib import KERNELS
+
+    rank, world, local = dist_setup()
+    p = make_inputs()
+    flops = float(p.flops)
+    dev = torch.device("cuda")
+
+    def dev_operand(op):
+        buf = torch.from_numpy(op.buf).to(dev)
+        return torch.as_strided(buf, op.extents, op.strides)
+
+    V, T, C0 = dev_operand(p.A), dev_operand(p.B), dev_operand(p.C)
+    C = C0.clone()
+    la, lb, lc = p.A.labels, p.B.labels, p.C.labels
+    stream = torch.cuda.current_stream()
+
+    def step(Cout, **kw):
+        return fm.contract(p.alpha, V, la, T, lb, p.beta, Cout, lc, dtype="f64_emu", slices=SLICES,
+                           return_info=True, **kw)
+
+    _, info = step(C)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        step(C)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps on resident inputs
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        start.record(stream)
+        for _ in range(args.steps):
+            step(C)
+        end.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+    ms = start.elapsed_time(end) / args.steps
+    ms = barrier_max(ms, world)
+    value = world * flops / (ms * 1e-3) / 1e12
+    launches = info["launches"] * args.steps
+
+    # ---- the product kernel alone (events recorded by the library around it)
+    kev = []
+    for _ in range(max(3, min(args.steps, 5))):
+        b, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        step(C, events=(b, e))
+        kev.append((b, e))
+    torch.cuda.synchronize()
+    kms = statistics.mean(b.elapsed_time(e) for b, e in kev)
+    pairs = SLICES * (SLICES + 1) // 2
+    exec_flops = pairs * flops
+    burst, sustained, src = peaks()
+    achieved = exec_flops / (kms * 1e-3) / 1e12
+
+    # ---- native fp64 on the GPU (the speedup denominator) and agreement
+    Ce = C0.clone()
+    step(Ce)
+    Cn = C0.clone()
+    fm.contract(p.alpha, V, la, T, lb, p.beta, Cn, lc, dtype="f64")  # warm-up
+    Cn.copy_(C0)
+    b, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b.record(stream)
+    fm.contract(p.alpha, V, la, T, lb, p.beta, Cn, lc, dtype="f64")
+    e.record(stream)
+    torch.cuda.synchronize()
+    native_ms = b.elapsed_time(e)
+    rel = float((Ce - Cn).norm() / Cn.norm())
+    rel_ab = float((Ce - Cn).norm() / (Cn - p.beta * C0).norm())
+    del Ce, Cn
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        hV = torch.from_numpy(p.A.buf).pin_memory()
+        hT = torch.from_numpy(p.B.buf).pin_memory()
+        hC = torch.from_numpy(p.C.buf).pin_memory()
+        st = lambda h, op: np.lib.stride_tricks.as_strided(h.numpy(), op.extents,
+                                                          tuple(8 * s for s in op.strides))
+        Vn, Tn, Cn_h = st(hV, p.A), st(hT, p.B), st(hC, p.C)
+        fm.contract_host(p.alpha, Vn, la, Tn, lb, p.beta, Cn_h, lc, dtype="f64_emu", slices=SLICES)
+        e2e_steps = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            fm.contract_host(p.alpha, Vn, la, Tn, lb, p.beta, Cn_h, lc, dtype="f64_emu",
+                             slices=SLICES)
+        e2e_s = barrier_max((time.perf_counter() - t0) / e2e_steps, world)
+        e2e = {"value": world * flops / e2e_s / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": 8 * (p.A.span + p.B.span + p.C.span),
+               "d2h_bytes_per_step": 8 * p.C.span, "host_memory": "pinned"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 (bf16 slices, exact fp32 accumulate, fp64 recombine)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "v": V_EXT, "o": O_EXT, "m": info["m"], "n": info["n"],
+                   "k": info["k"], "slices": SLICES, "beta": p.beta, "l2": "inputs larger than L2",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "speedup_vs_native_f64": native_ms / ms,
+        "native_f64": {"ms": native_ms, "tflops": flops / (native_ms * 1e-3) / 1e12},
+        "rel_err_vs_native_f64": rel, "rel_err_vs_native_f64_ab_term": rel_ab,
+        "roofline": {"bound": "tensor", "kernel": "k_pair_gemm<bf16, fp64-split>",
+                     "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
+                     "frac": achieved / sustained, "traffic": None,
+                     "peak_kind": f"bf16 sustained ({src})", "frac_of_burst": achieved / burst,
+                     "kernel_ms": kms, "exec_flops_per_launch": exec_flops},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "kernel_path": KERNELS.get(info["kernel"], "?"),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        cflops, cdt, cores = cpu_sample(p, args.ref_cols)
+        line["cpu_baseline"] = {"value": cflops / cdt / 1e12, "unit": "TFLOP/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"C[:, :, 0, 0:{args.ref_cols}] ({cflops:.3g} flop)"}
+    status = fm.device_status()
+    if status != 0:
+        line["device_status"] = status
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="famlies", choices=["famlies", "reference"])
+    ap.add_argument("--ref-cols", type=int, default=4,
+                    help="output columns (i,j pairs) in the oracle's bounded sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--v", type=int, default=128, help="virtual extent (profiling captures only)")
+    ap.add_argument("--o", type=int, default=32, help="occupied extent (profiling captures only)")
+    args = ap.parse_args()
+    set_size(args.v, args.o)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

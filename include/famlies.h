@@ -119,14 +119,20 @@ typedef struct {
  *               straight from the strided tensors (F32, BF16).  A choice
  *               the dtype has no kernel for returns FAMLIES_ERR_UNSUPPORTED.
  *   tile_n      tensor-core tile width (64, 128 or 256; 0 = automatic).
- *   wait_limit  iteration cap of every bounded wait (0 = default). */
+ *   wait_limit  iteration cap of every bounded wait (0 = default).
+ *   events      optional pair of cudaEvent_t handles created by the caller
+ *               (NULL = none): the library records events[0] on the call's
+ *               stream immediately before the main product kernel and
+ *               events[1] immediately after it, so the caller can time that
+ *               kernel alone.  The library never synchronises on them. */
 typedef struct {
   int32_t slices;
   int32_t kernel;
   int32_t tile_n;
   int32_t reserved0;
   int64_t wait_limit;
-  int64_t reserved[4];
+  void* events[2];
+  int64_t reserved[2];
 } famlies_options_t;
 
 /* What the planner decided for a call (filled by famlies_plan and, when

@@ -35,7 +35,7 @@ class TensorDesc(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("slices", ctypes.c_int32), ("kernel", ctypes.c_int32), ("tile_n", ctypes.c_int32),
                 ("reserved0", ctypes.c_int32), ("wait_limit", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 4)]
+                ("events", ctypes.c_void_p * 2), ("reserved", ctypes.c_int64 * 2)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -132,7 +132,13 @@ def desc_numpy(x, labels) -> Desc:
     return Desc(x.shape, tuple(s // es for s in x.strides), labels, x.__array_interface__["data"][0])
 
 
-def options(slices=0, kernel=0, tile_n=0, wait_limit=0) -> Options:
+def options(slices=0, kernel=0, tile_n=0, wait_limit=0, events=None) -> Options:
+    """events: optional (begin, end) torch.cuda.Event pair recorded around the product kernel."""
     o = Options()
     o.slices, o.kernel, o.tile_n, o.wait_limit = int(slices), int(kernel), int(tile_n), int(wait_limit)
+    if events is not None:
+        for i, ev in enumerate(events):
+            if getattr(ev, "cuda_event", 0) == 0:
+                ev.record()  # materialises the underlying cudaEvent_t
+            o.events[i] = ev.cuda_event
     return o

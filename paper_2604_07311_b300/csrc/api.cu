@@ -109,6 +109,8 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
     g.wait_limit = (opt && opt->wait_limit > 0) ? opt->wait_limit : env_wait_limit();
     g.status = device_status_ptr();
     if (!g.status) return FAMLIES_ERR_CUDA;
+    g.ev_begin = opt ? (cudaEvent_t)opt->events[0] : nullptr;
+    g.ev_end = opt ? (cudaEvent_t)opt->events[1] : nullptr;
     switch (p.kernel) {
       case FAMLIES_KERNEL_SIMT_F64:
       case FAMLIES_KERNEL_SIMT_F32:

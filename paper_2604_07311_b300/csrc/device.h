@@ -34,7 +34,15 @@ struct GemmArgs {
   int a_contig, b_contig;  // 1: unit stride along rows/cols, 2: along k
   int64_t wait_limit;      // iteration cap of every bounded wait
   int* status;             // device status word (first error recorded wins)
+  cudaEvent_t ev_begin, ev_end;  // host only: recorded around the product kernel
 };
+
+inline void mark_begin(const GemmArgs& g, cudaStream_t s) {
+  if (g.ev_begin) cudaEventRecord(g.ev_begin, s);
+}
+inline void mark_end(const GemmArgs& g, cudaStream_t s) {
+  if (g.ev_end) cudaEventRecord(g.ev_end, s);
+}
 
 // Address of the device status word of the current device, and a host-side
 // read-and-clear of it (both defined next to the word itself).

@@ -247,33 +247,45 @@ __global__ void __launch_bounds__(THREADS, 1)
       const bool rv = row < g.m;
       const int64_t crow = rv ? g.t.cl[il] + g.t.cm[row] : 0;
       if (MODE == MODE_F32OUT) {
-        if (!ptx::mbar_wait(&tfull[acc], accph, lim, abort)) { ok = false; break; }
-        ptx::tc_fence_after();
-        float* C = (float*)g.c;
-        const float alpha = (float)g.alpha, beta = (float)g.beta;
-#pragma unroll 1
-        for (int q = 0; q < CPT / 32; ++q) {
-          uint32_t r[32];
-          ptx::tmem_ld32(tmem_base + lane_addr + acc * BN + hf * CPT + q * 32, r);
-          ptx::tmem_ld_wait();
-          if (rv) {
+        // Each unit's tensor-memory sum is added into fp32 registers with
+        // round-to-nearest, which bounds how much rounding any one
+        // accumulator sees over a long k.
+        float S[CPT];
+        const int kcb = sc.kcb[0];
+        const int nunits = (nkb + kcb - 1) / kcb;
+        for (int u = 0; u < nunits; ++u) {
+          if (!ptx::mbar_wait(&tfull[acc], accph, lim, abort)) { ok = false; break; }
+          ptx::tc_fence_after();
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const int64_t col = col0 + q * 32 + i;
-              if (col < g.n) {
-                float* p = C + crow + g.t.cn[col];
-                float v = alpha * __uint_as_float(r[i]);
-                if (beta != 0.f) v = fmaf(beta, *p, v);
-                *p = v;
-              }
+          for (int q = 0; q < CPT / 32; ++q) {
+            uint32_t r[32];
+            ptx::tmem_ld32(tmem_base + lane_addr + acc * BN + hf * CPT + q * 32, r);
+            ptx::tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              S[q * 32 + i] = (u == 0) ? __uint_as_float(r[i]) : S[q * 32 + i] + __uint_as_float(r[i]);
+          }
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
+          acc ^= 1;
+          if (acc == 0) accph ^= 1;
+        }
+        if (!ok) break;
+        if (rv) {
+          float* C = (float*)g.c;
+          const float alpha = (float)g.alpha, beta = (float)g.beta;
+#pragma unroll
+          for (int j = 0; j < CPT; ++j) {
+            const int64_t col = col0 + j;
+            if (col < g.n) {
+              float* p = C + crow + g.t.cn[col];
+              float v = alpha * S[j];
+              if (beta != 0.f) v = fmaf(beta, *p, v);
+              *p = v;
             }
           }
         }
-        ptx::tc_fence_before();
-        __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
-        acc ^= 1;
-        if (acc == 0) accph ^= 1;
       } else {
         // fp64 split: int32 running sums per diagonal, fp64 tile sums in G.
         int32_t S[CPT];
@@ -440,7 +452,7 @@ Sched make_sched(const Plan& p, int bits) {
     const bool tf32 = p.kernel == FAMLIES_KERNEL_TC_TF32X3;
     sc.ndiag = 1;
     sc.slices = tf32 ? 2 : 1;
-    sc.kcb[0] = 1 << 30;
+    sc.kcb[0] = 16;  // units of 1024 (bf16) or 512 (tf32) k
     sc.flush_every[0] = 1;
     if (tf32) {  // lo*hi + hi*lo + hi*hi, hi = slice 0, lo = slice 1
       sc.npairs[0] = 3;
@@ -485,7 +497,9 @@ cudaError_t launch_pair(const CUtensorMap& ma, const CUtensorMap& mb, const Pair
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  mark_begin(a.g, s);
   k_pair_gemm<KIND, MODE, BN><<<grid, THREADS, Cfg::SMEM_BYTES, s>>>(ma, mb, a);
+  mark_end(a.g, s);
   return cudaGetLastError();
 }
 

@@ -200,12 +200,16 @@ cudaError_t launch_simt(const Plan& p, const GemmArgs& g, cudaStream_t s) {
     constexpr int BM = 64, BN = 64;
     int64_t tiles = ((p.m + BM - 1) / BM) * ((p.n + BN - 1) / BN) * p.l;
     int grid = (int)(tiles < (int64_t)sms * 8 ? tiles : (int64_t)sms * 8);
+    mark_begin(g, s);
     k_simt<double, BM, BN, 16, 4, 4><<<grid, 256, 0, s>>>(g);
+    mark_end(g, s);
   } else {
     constexpr int BM = 128, BN = 128;
     int64_t tiles = ((p.m + BM - 1) / BM) * ((p.n + BN - 1) / BN) * p.l;
     int grid = (int)(tiles < (int64_t)sms * 4 ? tiles : (int64_t)sms * 4);
+    mark_begin(g, s);
     k_simt<float, BM, BN, 16, 8, 8><<<grid, 256, 0, s>>>(g);
+    mark_end(g, s);
   }
   return cudaGetLastError();
 }

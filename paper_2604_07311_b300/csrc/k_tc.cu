@@ -342,7 +342,9 @@ cudaError_t launch_one(const TcArgs& a, cudaStream_t s) {
   }
   const int64_t tiles = ((a.g.m + Cfg::BM - 1) / Cfg::BM) * ((a.g.n + BN - 1) / BN) * a.g.l;
   const int grid = (int)(tiles < num_sms() ? tiles : num_sms());
+  mark_begin(a.g, s);
   k_tc<TF32, BN><<<grid, Cfg::THREADS, Cfg::SMEM_BYTES, s>>>(a);
+  mark_end(a.g, s);
   return cudaGetLastError();
 }
 
