@@ -310,7 +310,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="famlies", choices=["famlies", "reference"])
-    ap.add_argument("--ref-cols", type=int, default=4,
+    ap.add_argument("--ref-cols", type=int, default=32,
                     help="output columns (i,j pairs) in the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

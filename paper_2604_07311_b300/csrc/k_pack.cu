@@ -144,24 +144,55 @@ __global__ void __launch_bounds__(256) k_pack(PackArgs pa) {
         pl[0] = make_uint4(lo32[0], lo32[1], lo32[2], lo32[3]);
         pl[1] = make_uint4(lo32[4], lo32[5], lo32[6], lo32[7]);
       } else {
+        // Integer arithmetic only (the fp64 pipe is narrow): with
+        // t = x * 2^-e_r in (-1, 1), F = round(t * 2^(b S)) is taken from
+        // x's significand and exponent bits, then split into balanced base
+        // 2^b digits from the bottom: d_S..d_2 in [-2^(b-1), 2^(b-1)), the
+        // remaining top digit |d_1| <= 2^b.  F = sum_i d_i 2^(b (S - i)), so
+        // |t - sum_i d_i 2^(-b i)| <= 2^(-b S - 1).
         const int64_t ri = il * o.rows + gr;
         const int ex = o.e[ri];
         const bool bad = o.flag[ri] != 0;
-        const double step = (double)(1 << pa.bits);
-        double t[8];
+        const int b = pa.bits, S = pa.slices, bs = b * S;
+        const int64_t half = (int64_t)1 << (b - 1), mask = ((int64_t)1 << b) - 1;
+        int64_t F[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) t[j] = bad ? 0.0 : ldexp(tile[r][c * 8 + j], -ex);
-        for (int s = 0; s < pa.slices; ++s) {
+        for (int j = 0; j < 8; ++j) {
+          const uint64_t bitsx = (uint64_t)__double_as_longlong(tile[r][c * 8 + j]);
+          const int E = (int)((bitsx >> 52) & 0x7FF);
+          const uint64_t mant = (bitsx & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
+          const int sh = max(E, 1) - 1075 - ex + bs;  // F = mant * 2^sh
+          int64_t f = 0;
+          if (!bad && mant != 0) {
+            if (sh >= 0) f = (int64_t)(mant << sh);
+            else if (sh > -63) f = (int64_t)((mant + (1ull << (-sh - 1))) >> (-sh));
+          }
+          F[j] = (bitsx >> 63) ? -f : f;
+        }
+        int32_t dig[8][8];  // [slice][element]
+#pragma unroll
+        for (int s = 7; s >= 1; --s) {
+          if (s >= S) continue;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int64_t d = ((F[j] + half) & mask) - half;
+            F[j] = (F[j] - d) >> b;
+            dig[s][j] = (int32_t)d;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) dig[0][j] = (int32_t)F[j];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          if (s >= S) break;
           uint32_t w[4];
 #pragma unroll
           for (int j = 0; j < 8; j += 2) {
-            const double u0 = t[j] * step, u1 = t[j + 1] * step;
-            const double d0 = rint(u0), d1 = rint(u1);
-            t[j] = u0 - d0;
-            t[j + 1] = u1 - d1;
-            const uint32_t b0 = __bfloat16_as_ushort(__float2bfloat16_rn((float)d0));
-            const uint32_t b1 = __bfloat16_as_ushort(__float2bfloat16_rn((float)d1));
-            w[j / 2] = b0 | (b1 << 16);
+            // small integers are exact in fp32 and bf16: 1.5 * 2^23 + d holds
+            // d in its low significand bits, and the subtraction is exact
+            const float f0 = __int_as_float(0x4B400000 + dig[s][j]) - 12582912.0f;
+            const float f1 = __int_as_float(0x4B400000 + dig[s][j + 1]) - 12582912.0f;
+            w[j / 2] = (__float_as_uint(f0) >> 16) | (__float_as_uint(f1) & 0xFFFF0000u);
           }
           *(uint4*)((uint16_t*)o.out + (size_t)s * slice_stride + rowbase) =
               make_uint4(w[0], w[1], w[2], w[3]);
