@@ -110,6 +110,7 @@ typedef struct {
 #define FAMLIES_ERR_CUDA (-8)            /* a CUDA runtime call failed */
 #define FAMLIES_ERR_DEVICE_TIMEOUT (-9)  /* a kernel's bounded wait expired (asynchronous) */
 #define FAMLIES_ERR_NO_DEVICE (-10)      /* no usable sm_100-family device */
+#define FAMLIES_ERR_SCRATCH (-11)        /* call too large for famlies_contract_noalloc's fixed scratch */
 
 /* Optional knobs for famlies_contract_ex (zero-initialise for defaults).
  *   slices      F64_EMU: number of bf16 slices per operand, 2..8 (default 7).
@@ -216,6 +217,29 @@ FAMLIES_API int famlies_device_status(void* stream);
 
 /* Library ABI version (major*10000 + minor*100 + patch). */
 FAMLIES_API int famlies_version(void);
+
+/* The paper has no counterpart to this entry point: it is a library service
+ * for callers that cannot allocate device memory (a host whose memory pool
+ * owns the whole device, a real-time loop that may not enter the allocator,
+ * an embedding that only hands over its input and output buffers).
+ *
+ * Same operation and conventions as famlies_contract for dtype F64 or F32
+ * (other dtypes: FAMLIES_ERR_UNSUPPORTED), computed by the CUDA-core
+ * kernels; it allocates nothing.  Its only scratch, the offset tables, lives
+ * in a fixed 1 MiB device array built into the library (2^17 int64 entries,
+ * held on every GPU that loads the library until the process exits).  A
+ * call needs 2*(m + n + k) + 3*batch entries, where m, n, k and batch are
+ * the products of the extents of its label classes (famlies_plan reports
+ * them); a larger call returns FAMLIES_ERR_SCRATCH and launches nothing.
+ * Every call on a device shares the array and rewrites the part it reads,
+ * so calls whose kernels may overlap on the GPU (unordered streams) race
+ * and must be ordered by the caller.  The first call on a device looks up
+ * the array's device address with that device current; make it before any
+ * stream capture on that device.  Asynchronous on `stream`. */
+FAMLIES_API int famlies_contract_noalloc(double alpha, const famlies_tensor_t* A,
+                                         const famlies_tensor_t* B, double beta,
+                                         const famlies_tensor_t* C, famlies_dtype_t dtype,
+                                         void* stream);
 
 #ifdef __cplusplus
 }

@@ -107,6 +107,29 @@ def contract_batched(alpha, As, las, Bs, lbs, beta, Cs, lcs, dtype=None, stream=
     return Cs
 
 
+def contract_noalloc(alpha, A, la, B, lb, beta, C, lc, dtype=None, stream=None):
+    """C := alpha * contract(A, B) + beta * C without any device allocation.
+
+    For callers that may not allocate device memory: fp64 or fp32 tensors,
+    computed by the CUDA-core kernels with their offset tables in the
+    library's fixed 1 MiB scratch array (calls needing more raise
+    FamliesError -11).  Calls sharing a device must not overlap on the GPU.
+    """
+    import ctypes
+    lib = load()
+    f = lib.famlies_contract_noalloc
+    T = ctypes.POINTER(_TensorDesc)
+    f.argtypes = [ctypes.c_double, T, T, ctypes.c_double, T, ctypes.c_int, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    code = _dtype_code(dtype, A, C)
+    da, db, dc = desc_torch(A, la), desc_torch(B, lb), desc_torch(C, lc)
+    check(f(float(alpha), da.ref, db.ref, float(beta), dc.ref, code, _stream_handle(stream)))
+    return C
+
+
+from ._lib import TensorDesc as _TensorDesc  # noqa: E402
+
+
 def device_status(stream=None) -> int:
     """Synchronises and returns/clears the device status word (0 or -9 timeout)."""
     return int(load().famlies_device_status(_stream_handle(stream)))

@@ -162,6 +162,7 @@ const char* famlies_error_string(int code) {
     case FAMLIES_ERR_CUDA: return "CUDA runtime error";
     case FAMLIES_ERR_DEVICE_TIMEOUT: return "a kernel's bounded wait expired";
     case FAMLIES_ERR_NO_DEVICE: return "no sm_103 CUDA device";
+    case FAMLIES_ERR_SCRATCH: return "call needs more than the no-allocation entry point's fixed 1 MiB scratch";
   }
   return "unknown error code";
 }
