@@ -29,6 +29,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "contraction TFLOP/s, % tensor-pipe peak; split-precision vs FP64 speedup"
+# DRAM bytes per product-kernel launch from the ncu capture summarised in
+# profiles/k_pair_gemm_ladder.md (v=64 ladder, 1.543 GB, scaled by executed
+# flops to the v=128 launch).  Must go back to None whenever the product
+# kernel changes after that capture.
+PRODUCT_TRAFFIC = {"bytes": 1.543e9, "exec_flops": 9.62072674304e11}
 V_EXT, O_EXT, SLICES = 128, 32, 7
 WORKLOAD = "ccsd_ladder_v128_o32_f64_split7"
 
@@ -282,7 +287,10 @@ def run_gpu(args):
         "rel_err_vs_native_f64": rel, "rel_err_vs_native_f64_ab_term": rel_ab,
         "roofline": {"bound": "tensor", "kernel": "k_pair_gemm<bf16, fp64-split>",
                      "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
-                     "frac": achieved / sustained, "traffic": None,
+                     "frac": achieved / sustained,
+                     "traffic": (PRODUCT_TRAFFIC["bytes"] * exec_flops / PRODUCT_TRAFFIC["exec_flops"]
+                                 if PRODUCT_TRAFFIC else None),
+                     "traffic_note": "ncu dram bytes of the v=64 capture scaled by executed flops",
                      "peak_kind": f"bf16 sustained ({src})", "frac_of_burst": achieved / burst,
                      "kernel_ms": kms, "exec_flops_per_launch": exec_flops},
         "e2e": e2e,
