@@ -250,7 +250,6 @@ int famlies_contract_batched(int64_t count, const double* alpha, const famlies_t
                              const famlies_tensor_t* B, const double* beta,
                              const famlies_tensor_t* C, famlies_dtype_t dtype, void* stream,
                              int use_graph) {
-  (void)use_graph;
   if (count < 0 || (count > 0 && (!alpha || !beta || !A || !B || !C)))
     return FAMLIES_ERR_INVALID_ARG;
   std::vector<Plan> plans((size_t)count);
@@ -258,11 +257,27 @@ int famlies_contract_batched(int64_t count, const double* alpha, const famlies_t
     int rc = make_plan(alpha[i], &A[i], &B[i], &C[i], dtype, nullptr, &plans[i]);
     if (rc) return rc;
   }
+  if (count == 0) return FAMLIES_OK;
+  int rc = check_device();
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  // problems of the packed tensor-core kernels go through one grouped launch
+  // per stage; the rest (empty, scale-only, CUDA-core) one by one
+  std::vector<const Plan*> grouped;
+  std::vector<double> ga, gb;
   for (int64_t i = 0; i < count; ++i) {
-    int rc = run_plan(plans[i], alpha[i], beta[i], (cudaStream_t)stream, nullptr, nullptr);
-    if (rc) return rc;
+    const int k = plans[i].kernel;
+    if (k == FAMLIES_KERNEL_TC_EMU || k == FAMLIES_KERNEL_TC_BF16 || k == FAMLIES_KERNEL_TC_TF32X3) {
+      grouped.push_back(&plans[i]);
+      ga.push_back(alpha[i]);
+      gb.push_back(beta[i]);
+    } else if ((rc = run_plan(plans[i], alpha[i], beta[i], s, nullptr, nullptr))) {
+      return rc;
+    }
   }
-  return FAMLIES_OK;
+  int* status = device_status_ptr();
+  if (!status) return FAMLIES_ERR_CUDA;
+  return run_grouped(grouped, ga, gb, s, use_graph != 0, status, env_wait_limit());
 }
 
 int famlies_device_status(void* stream) {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -43,6 +44,24 @@ inline void mark_begin(const GemmArgs& g, cudaStream_t s) {
 inline void mark_end(const GemmArgs& g, cudaStream_t s) {
   if (g.ev_end) cudaEventRecord(g.ev_end, s);
 }
+
+// One offset table: out[i] = sum_d digit_d(i) * st[d] for the mixed-radix
+// digits of i over ext[0..n).
+struct TableJob {
+  int n;
+  int64_t ext[kMaxModes];
+  int64_t st[kMaxModes];
+  int64_t total;
+  int64_t* out;
+};
+void plan_table_jobs(const Plan& p, int64_t* ws, TableJob jobs[9], Tables* t);
+cudaError_t launch_tables_grouped(const TableJob* jobs, int64_t njobs, int64_t max_total,
+                                  cudaStream_t s);
+
+// Grouped execution of many plans of one packed kernel (csrc/grouped.cu).
+int run_grouped(const std::vector<const Plan*>& ps, const std::vector<double>& alpha,
+                const std::vector<double>& beta, cudaStream_t s, bool use_graph, int* status,
+                int64_t wait_limit);
 
 // Address of the device status word of the current device, and a host-side
 // read-and-clear of it (both defined next to the word itself).

@@ -1,0 +1,541 @@
+// Grouped execution of many independent contractions (the blocks of a
+// block-sparse contraction: the "tensor-of-tensors" tiling of Sec. 2.3, run
+// as a task list in the spirit of the algorithms-by-blocks runtimes of
+// Sec. 2.4 with no dependencies between tasks).
+//
+// One call = one launch per stage, whatever the number of problems:
+//   offset tables -> [fp64 split: row exponents] -> pack -> product -> [fix-up]
+// Every problem's descriptors (offset-table jobs, pack arguments, TMA maps,
+// epilogue descriptor) travel to the device in one copy; the product kernel
+// walks a device tile list sorted longest-first, so the persistent CTAs
+// balance the uneven blocks.  With use_graph the launches are captured once
+// into a CUDA graph per problem set and replayed.  The tile width of the
+// product is picked by timing the candidates on the first call for a given
+// shape class (the autotuner) and remembered for the process.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <list>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "device.h"
+#include "packed.h"
+#include "pair_gemm.h"
+#include "plan.h"
+
+namespace famlies {
+
+namespace {
+
+constexpr int kBits = 7;
+auto up256 = [](size_t x) { return (x + 255) / 256 * 256; };
+
+struct ProbLayout {
+  size_t tab, a, b;    // in the per-problem region
+  size_t ea, eb;       // in the exponent region
+  size_t fa, fb, la, lb;  // in the flag region
+};
+
+struct GroupSetup {
+  int n = 0;
+  int kernel = 0, kind = 0, mode = 0, slices = 1;
+  size_t ws_main = 0, ws_exp = 0, ws_flag = 0, ws_g = 0, ws_total = 0;
+  std::vector<ProbLayout> lay;
+  int64_t ntiles = 0, max_table = 1, max_rowexp_blocks = 1, max_pack_blocks = 1;
+  size_t blob_probs = 0, blob_gargs = 0, blob_pargs = 0, blob_jobs = 0, blob_tiles = 0,
+         blob_maps = 0, blob_bytes = 0;
+  size_t c_bytes = 0;  // sum of C spans (autotuning scratch)
+};
+
+GroupSetup layout_group(const std::vector<const Plan*>& ps, int bn_max) {
+  GroupSetup G;
+  G.n = (int)ps.size();
+  G.kernel = ps[0]->kernel;
+  const bool emu = G.kernel == FAMLIES_KERNEL_TC_EMU;
+  const bool tf32 = G.kernel == FAMLIES_KERNEL_TC_TF32X3;
+  G.kind = tf32 ? PAIR_KIND_TF32 : PAIR_KIND_BF16;
+  G.mode = emu ? PAIR_MODE_EMU : PAIR_MODE_F32OUT;
+  G.slices = emu ? ps[0]->slices : (tf32 ? 2 : 1);
+  const int es = tf32 ? 4 : 2;
+  G.lay.resize(G.n);
+  for (int i = 0; i < G.n; ++i) {
+    const Plan& p = *ps[i];
+    ProbLayout& L = G.lay[i];
+    const size_t kp = (size_t)((p.k + 7) / 8 * 8);
+    L.tab = G.ws_main; G.ws_main += up256((size_t)table_entries(p) * 8);
+    L.a = G.ws_main; G.ws_main += up256((size_t)G.slices * p.l * p.m * kp * es);
+    L.b = G.ws_main; G.ws_main += up256((size_t)G.slices * p.l * p.n * kp * es);
+    if (emu) {
+      L.ea = G.ws_exp; G.ws_exp += up256((size_t)p.l * p.m * 4);
+      L.eb = G.ws_exp; G.ws_exp += up256((size_t)p.l * p.n * 4);
+      L.fa = G.ws_flag; G.ws_flag += up256((size_t)p.l * p.m * 4);
+      L.fb = G.ws_flag; G.ws_flag += up256((size_t)p.l * p.n * 4);
+      L.la = G.ws_flag; G.ws_flag += up256((size_t)(p.l * p.m + 1) * 4);
+      L.lb = G.ws_flag; G.ws_flag += up256((size_t)(p.l * p.n + 1) * 4);
+    }
+    int64_t tmax = std::max(std::max(p.m, p.n), std::max(p.k, p.l));
+    G.max_table = std::max(G.max_table, tmax);
+    const int64_t rb = ((std::max(p.m, p.n) + 63) / 64) * ((p.k + 1023) / 1024) * p.l;
+    const int64_t pb = ((std::max(p.m, p.n) + 63) / 64) * ((p.k + 63) / 64) * p.l;
+    G.max_rowexp_blocks = std::max(G.max_rowexp_blocks, rb);
+    G.max_pack_blocks = std::max(G.max_pack_blocks, pb);
+    G.c_bytes += up256((size_t)p.span_c * p.es_c);
+  }
+  if (emu) G.ws_g = up256((size_t)num_sms() * kPairBM * bn_max * 8);
+  G.ws_total = G.ws_main + G.ws_exp + G.ws_flag + G.ws_g;
+  return G;
+}
+
+int64_t tile_count_for(const Plan& p, int bn) {
+  return ((p.m + kPairBM - 1) / kPairBM) * ((p.n + bn - 1) / bn) * p.l;
+}
+
+// Fills the host image of the descriptor blob whose device copy starts at
+// d_blob, for workspace d_ws and product tile width bn.  Returns false if a
+// TMA map cannot be encoded.
+bool build_blob(const std::vector<const Plan*>& ps, const double* alpha, const double* beta,
+                GroupSetup& G, int bn, char* d_ws, char* d_blob, int* status, int64_t wait_limit,
+                std::vector<char>& blob) {
+  const int n = G.n;
+  std::vector<TileEntry> tiles;
+  std::vector<int64_t> cost;
+  for (int i = 0; i < n; ++i) {
+    const Plan& p = *ps[i];
+    const int64_t tm_n = (p.m + kPairBM - 1) / kPairBM, tn_n = (p.n + bn - 1) / bn;
+    const int64_t c = (p.k + 63) / 64;
+    for (int64_t il = 0; il < p.l; ++il)
+      for (int64_t tm = 0; tm < tm_n; ++tm)
+        for (int64_t tn = 0; tn < tn_n; ++tn) {
+          tiles.push_back(TileEntry{i, (int32_t)tm, (int32_t)tn, (int32_t)il});
+          cost.push_back(c);
+        }
+  }
+  // longest first: the persistent CTAs then take the remaining tiles
+  // greedily, which bounds the imbalance by the shortest tile
+  std::vector<size_t> order(tiles.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+  G.ntiles = (int64_t)tiles.size();
+
+  size_t off = 0;
+  G.blob_probs = off; off += up256(sizeof(Prob) * n);
+  G.blob_gargs = off; off += up256(sizeof(GemmArgs) * n);
+  G.blob_pargs = off; off += up256(sizeof(PackArgs) * n);
+  G.blob_jobs = off; off += up256(sizeof(TableJob) * 9 * n);
+  G.blob_tiles = off; off += up256(sizeof(TileEntry) * tiles.size());
+  G.blob_maps = off; off += up256(sizeof(CUtensorMap) * 2 * n);
+  G.blob_bytes = off;
+  blob.assign(off, 0);
+
+  Prob* probs = (Prob*)(blob.data() + G.blob_probs);
+  GemmArgs* gargs = (GemmArgs*)(blob.data() + G.blob_gargs);
+  PackArgs* pargs = (PackArgs*)(blob.data() + G.blob_pargs);
+  TableJob* jobs = (TableJob*)(blob.data() + G.blob_jobs);
+  TileEntry* tl = (TileEntry*)(blob.data() + G.blob_tiles);
+  CUtensorMap* maps = (CUtensorMap*)(blob.data() + G.blob_maps);
+  const CUtensorMap* d_maps = (const CUtensorMap*)(d_blob + G.blob_maps);
+  char* d_exp = d_ws + G.ws_main;
+  char* d_flag = d_exp + G.ws_exp;
+  const bool emu = G.mode == PAIR_MODE_EMU;
+  const bool tf32 = G.kind == PAIR_KIND_TF32;
+  for (int i = 0; i < n; ++i) {
+    const Plan& p = *ps[i];
+    const ProbLayout& L = G.lay[i];
+    Tables t;
+    plan_table_jobs(p, (int64_t*)(d_ws + L.tab), jobs + 9 * i, &t);
+    GemmArgs& g = gargs[i];
+    std::memset(&g, 0, sizeof(g));
+    g.a = p.a; g.b = p.b; g.c = p.c; g.t = t;
+    g.m = p.m; g.n = p.n; g.k = p.k; g.l = p.l;
+    g.alpha = alpha[i]; g.beta = beta[i];
+    g.a_contig = p.a_contig; g.b_contig = p.b_contig;
+    g.wait_limit = wait_limit; g.status = status;
+    PackArgs& pa = pargs[i];
+    std::memset(&pa, 0, sizeof(pa));
+    const int64_t kp = (p.k + 7) / 8 * 8;
+    pa.k = p.k; pa.kp = kp; pa.l = p.l; pa.slices = G.slices; pa.bits = kBits;
+    pa.op[0] = PackOp{p.a, t.am, t.ak, t.al, p.m, p.a_contig, d_ws + L.a, nullptr, nullptr, nullptr};
+    pa.op[1] = PackOp{p.b, t.bn, t.bk, t.bl, p.n, p.b_contig, d_ws + L.b, nullptr, nullptr, nullptr};
+    if (emu) {
+      pa.op[0].e = (int32_t*)(d_exp + L.ea);
+      pa.op[1].e = (int32_t*)(d_exp + L.eb);
+      pa.op[0].flag = (int32_t*)(d_flag + L.fa);
+      pa.op[1].flag = (int32_t*)(d_flag + L.fb);
+      pa.op[0].list = (int32_t*)(d_flag + L.la);
+      pa.op[1].list = (int32_t*)(d_flag + L.lb);
+    }
+    const int kbk = pair_stage_k(G.kind);
+    if (!make_slice_map(&maps[2 * i], d_ws + L.a, tf32, p.k, kp, p.m, (int64_t)G.slices * p.l, kbk,
+                        kPairBM) ||
+        !make_slice_map(&maps[2 * i + 1], d_ws + L.b, tf32, p.k, kp, p.n,
+                        (int64_t)G.slices * p.l, kbk, bn))
+      return false;
+    probs[i] = Prob{d_maps + 2 * i, d_maps + 2 * i + 1, p.c, t.cm, t.cn, t.cl, pa.op[0].e,
+                    pa.op[1].e, pa.op[0].flag, pa.op[1].flag, p.m, p.n, p.k, p.l,
+                    alpha[i], beta[i]};
+  }
+  for (size_t i = 0; i < order.size(); ++i) tl[i] = tiles[order[i]];
+  return true;
+}
+
+struct DevPtrs {
+  const Prob* probs;
+  const GemmArgs* gargs;
+  const PackArgs* pargs;
+  const TableJob* jobs;
+  const TileEntry* tiles;
+};
+
+DevPtrs dev_ptrs(const GroupSetup& G, char* d_blob) {
+  return DevPtrs{(const Prob*)(d_blob + G.blob_probs), (const GemmArgs*)(d_blob + G.blob_gargs),
+                 (const PackArgs*)(d_blob + G.blob_pargs), (const TableJob*)(d_blob + G.blob_jobs),
+                 (const TileEntry*)(d_blob + G.blob_tiles)};
+}
+
+cudaError_t enqueue_prepare(const GroupSetup& G, char* d_ws, const DevPtrs& d, cudaStream_t s) {
+  cudaError_t e;
+  char* d_exp = d_ws + G.ws_main;
+  char* d_flag = d_exp + G.ws_exp;
+  const bool emu = G.mode == PAIR_MODE_EMU;
+  if (emu) {
+    if ((e = cudaMemsetAsync(d_exp, 0x80, G.ws_exp, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(d_flag, 0, G.ws_flag, s)) != cudaSuccess) return e;
+  }
+  if ((e = launch_tables_grouped(d.jobs, 9 * (int64_t)G.n, G.max_table, s)) != cudaSuccess) return e;
+  if (emu && (e = launch_rowexp_grouped(d.pargs, G.n, G.max_rowexp_blocks, s)) != cudaSuccess)
+    return e;
+  const int pmode = emu ? PACK_F64 : (G.kind == PAIR_KIND_TF32 ? PACK_TF32 : PACK_BF16);
+  return launch_pack_grouped(pmode, d.pargs, G.n, G.max_pack_blocks, s);
+}
+
+cudaError_t enqueue_product(const GroupSetup& G, int bn, const Prob* probs, const TileEntry* tiles,
+                            char* d_ws, int* status, int64_t wait_limit, cudaStream_t s) {
+  const int grid = (int)std::min<int64_t>(G.ntiles, num_sms());
+  const Sched sc = make_pair_sched(G.kernel, G.slices, kBits);
+  double* Gsum = G.mode == PAIR_MODE_EMU ? (double*)(d_ws + G.ws_main + G.ws_exp + G.ws_flag) : nullptr;
+  return launch_pair_grouped(G.kind, G.mode, bn, probs, tiles, G.ntiles, sc, Gsum, grid, status,
+                             wait_limit, s);
+}
+
+cudaError_t enqueue_finish(const GroupSetup& G, const DevPtrs& d, cudaStream_t s) {
+  if (G.mode != PAIR_MODE_EMU) return cudaSuccess;
+  return launch_fixup_grouped(d.gargs, d.pargs, G.n, s);
+}
+
+// ------------------------------------------------------------ autotuner
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+
+std::string tune_key(const std::vector<const Plan*>& ps) {
+  std::vector<int64_t> m, n, k;
+  for (const Plan* p : ps) { m.push_back(p->m); n.push_back(p->n); k.push_back(p->k); }
+  auto med = [](std::vector<int64_t>& v) {
+    std::nth_element(v.begin(), v.begin() + v.size() / 2, v.end());
+    return v[v.size() / 2];
+  };
+  auto lg = [](int64_t x) { int b = 0; while ((int64_t)1 << (b + 1) <= x) ++b; return b; };
+  char buf[160];
+  std::snprintf(buf, sizeof(buf), "k%d s%d m%d n%d k%d c%d", ps[0]->kernel, ps[0]->slices,
+                lg(med(m)), lg(med(n)), lg(med(k)), lg((int64_t)ps.size()));
+  return buf;
+}
+
+int heuristic_bn(const std::vector<const Plan*>& ps) {
+  std::vector<int64_t> n;
+  for (const Plan* p : ps) n.push_back(p->n);
+  std::nth_element(n.begin(), n.begin() + n.size() / 2, n.end());
+  return pair_bn_for(n[n.size() / 2], 0);
+}
+
+bool autotune_enabled() {
+  const char* e = std::getenv("FAMLIES_AUTOTUNE");
+  return !(e && e[0] == '0');
+}
+
+// Times each candidate width on the packed problems with C redirected to
+// scratch, so the caller's C is untouched; returns the fastest.
+int tune_bn(const std::vector<const Plan*>& ps, const double* alpha, const double* beta,
+            GroupSetup& G, char* d_ws, int* status, int64_t wait_limit, cudaStream_t s) {
+  const int cands[3] = {64, 128, 256};
+  int best = heuristic_bn(ps);
+  float best_ms = 1e30f;
+  char* scratch = nullptr;
+  if (cudaMallocAsync((void**)&scratch, G.c_bytes + 256, s) != cudaSuccess) {
+    cudaGetLastError();
+    return best;
+  }
+  cudaMemsetAsync(scratch, 0, G.c_bytes + 256, s);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int bn : cands) {
+    // a width beyond twice the widest problem only adds empty columns
+    int64_t maxn = 0;
+    for (const Plan* p : ps) maxn = std::max(maxn, p->n);
+    if (bn > 64 && bn / 2 >= maxn) continue;
+    std::vector<char> blob;
+    char* d_blob = nullptr;
+    GroupSetup Gb = G;
+    // first pass sizes the descriptors, the second writes device addresses
+    if (!build_blob(ps, alpha, beta, Gb, bn, d_ws, nullptr, status, wait_limit, blob)) continue;
+    if (cudaMallocAsync((void**)&d_blob, Gb.blob_bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      break;
+    }
+    build_blob(ps, alpha, beta, Gb, bn, d_ws, d_blob, status, wait_limit, blob);
+    Prob* probs = (Prob*)(blob.data() + Gb.blob_probs);
+    size_t coff = 0;
+    for (int i = 0; i < Gb.n; ++i) {  // redirect C to scratch (same offsets)
+      probs[i].c = scratch + coff;
+      coff += up256((size_t)ps[i]->span_c * ps[i]->es_c);
+    }
+    cudaMemcpyAsync(d_blob, blob.data(), Gb.blob_bytes, cudaMemcpyHostToDevice, s);
+    const DevPtrs d = dev_ptrs(Gb, d_blob);
+    cudaEventRecord(e0, s);
+    cudaError_t err = enqueue_product(Gb, bn, d.probs, d.tiles, d_ws, status, wait_limit, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+      best_ms = ms;
+      best = bn;
+    }
+    cudaGetLastError();
+    cudaFreeAsync(d_blob, s);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(scratch, s);
+  return best;
+}
+
+int pick_bn(const std::vector<const Plan*>& ps, const double* alpha, const double* beta,
+            GroupSetup& G, char* d_ws, int* status, int64_t wait_limit, cudaStream_t s,
+            bool can_tune) {
+  const std::string key = tune_key(ps);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  if (!can_tune || !autotune_enabled()) return heuristic_bn(ps);
+  const int bn = tune_bn(ps, alpha, beta, G, d_ws, status, wait_limit, s);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = bn;
+  return bn;
+}
+
+// ------------------------------------------------------------ graph cache
+struct GraphEntry {
+  uint64_t key;
+  char* ws;
+  char* blob;
+  cudaGraphExec_t exec;
+};
+std::mutex g_graph_mu;
+std::list<GraphEntry> g_graphs;  // most recent first
+constexpr size_t kGraphCap = 4;
+
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = (const unsigned char*)p;
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+
+uint64_t set_key(const std::vector<const Plan*>& ps, const double* alpha, const double* beta,
+                 int dev) {
+  uint64_t h = 1469598103934665603ull;
+  h = fnv(h, &dev, sizeof(dev));
+  for (size_t i = 0; i < ps.size(); ++i) {
+    const Plan& p = *ps[i];
+    h = fnv(h, &p.kernel, sizeof(p.kernel));
+    h = fnv(h, &p.slices, sizeof(p.slices));
+    h = fnv(h, &p.a, sizeof(p.a));
+    h = fnv(h, &p.b, sizeof(p.b));
+    h = fnv(h, &p.c, sizeof(p.c));
+    for (const ClassModes* cm : {&p.M, &p.N, &p.K, &p.L}) {
+      h = fnv(h, &cm->n, sizeof(cm->n));
+      h = fnv(h, cm->m, sizeof(Mode) * cm->n);
+    }
+    h = fnv(h, &alpha[i], sizeof(double));
+    h = fnv(h, &beta[i], sizeof(double));
+  }
+  return h;
+}
+
+int run_chunk(const std::vector<const Plan*>& ps, const double* alpha, const double* beta,
+              cudaStream_t s, bool use_graph, int* status, int64_t wait_limit) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  GroupSetup G = layout_group(ps, 256);
+  if (use_graph) {
+    const uint64_t key = set_key(ps, alpha, beta, dev);
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {
+      if (it->key != key) continue;
+      g_graphs.splice(g_graphs.begin(), g_graphs, it);
+      return cudaGraphLaunch(g_graphs.front().exec, s) == cudaSuccess ? FAMLIES_OK : FAMLIES_ERR_CUDA;
+    }
+    // build: persistent workspace and descriptors, tune, capture, replay
+    char *ws = nullptr, *d_blob = nullptr;
+    if (cudaMalloc((void**)&ws, G.ws_total + 256) != cudaSuccess) {
+      cudaGetLastError();
+      return FAMLIES_ERR_ALLOC;
+    }
+    std::vector<char> blob;
+    if (!build_blob(ps, alpha, beta, G, 256, ws, nullptr, status, wait_limit, blob)) {
+      cudaFree(ws);
+      return FAMLIES_ERR_CUDA;
+    }
+    // prepare once on the caller's stream so that the tuner can time the product
+    const size_t max_blob = G.blob_bytes;
+    if (cudaMalloc((void**)&d_blob, max_blob + 65536) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(ws);
+      return FAMLIES_ERR_ALLOC;
+    }
+    build_blob(ps, alpha, beta, G, 256, ws, d_blob, status, wait_limit, blob);
+    cudaMemcpyAsync(d_blob, blob.data(), G.blob_bytes, cudaMemcpyHostToDevice, s);
+    DevPtrs d = dev_ptrs(G, d_blob);
+    if (enqueue_prepare(G, ws, d, s) != cudaSuccess) {
+      cudaGetLastError();
+      cudaStreamSynchronize(s);
+      cudaFree(ws);
+      cudaFree(d_blob);
+      return FAMLIES_ERR_CUDA;
+    }
+    const int bn = pick_bn(ps, alpha, beta, G, ws, status, wait_limit, s, true);
+    // the final descriptors for the chosen width (tile list depends on it)
+    GroupSetup Gf = G;
+    build_blob(ps, alpha, beta, Gf, bn, ws, d_blob, status, wait_limit, blob);
+    if (Gf.blob_bytes > max_blob + 65536) {
+      cudaStreamSynchronize(s);
+      cudaFree(d_blob);
+      if (cudaMalloc((void**)&d_blob, Gf.blob_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ws);
+        return FAMLIES_ERR_ALLOC;
+      }
+      build_blob(ps, alpha, beta, Gf, bn, ws, d_blob, status, wait_limit, blob);
+    }
+    cudaStreamSynchronize(s);
+    cudaMemcpy(d_blob, blob.data(), Gf.blob_bytes, cudaMemcpyHostToDevice);
+    d = dev_ptrs(Gf, d_blob);
+    cudaStream_t cs;
+    cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = enqueue_prepare(Gf, ws, d, cs);
+      cudaError_t e2 = enqueue_product(Gf, bn, d.probs, d.tiles, ws, status, wait_limit, cs);
+      cudaError_t e3 = enqueue_finish(Gf, d, cs);
+      e = cudaStreamEndCapture(cs, &graph);
+      if (e == cudaSuccess && (e1 || e2 || e3)) e = e1 ? e1 : (e2 ? e2 : e3);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(ws);
+      cudaFree(d_blob);
+      return FAMLIES_ERR_CUDA;
+    }
+    if (g_graphs.size() >= kGraphCap) {
+      cudaDeviceSynchronize();  // an evicted graph may still run on some stream
+      GraphEntry& old = g_graphs.back();
+      cudaGraphExecDestroy(old.exec);
+      cudaFree(old.ws);
+      cudaFree(old.blob);
+      g_graphs.pop_back();
+    }
+    g_graphs.push_front(GraphEntry{key, ws, d_blob, exec});
+    return cudaGraphLaunch(exec, s) == cudaSuccess ? FAMLIES_OK : FAMLIES_ERR_CUDA;
+  }
+
+  // no graph: stream-ordered workspace, one descriptor copy, five launches
+  char *ws = nullptr, *d_blob = nullptr;
+  if (cudaMallocAsync((void**)&ws, G.ws_total + 256, s) != cudaSuccess) {
+    cudaGetLastError();
+    return FAMLIES_ERR_ALLOC;
+  }
+  std::vector<char> blob;
+  if (!build_blob(ps, alpha, beta, G, 256, ws, nullptr, status, wait_limit, blob)) {
+    cudaFreeAsync(ws, s);
+    return FAMLIES_ERR_CUDA;
+  }
+  // descriptors sized for the narrowest width (the largest tile list)
+  GroupSetup G64 = G;
+  build_blob(ps, alpha, beta, G64, 64, ws, nullptr, status, wait_limit, blob);
+  const size_t cap = std::max(G.blob_bytes, G64.blob_bytes);
+  if (cudaMallocAsync((void**)&d_blob, cap, s) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeAsync(ws, s);
+    return FAMLIES_ERR_ALLOC;
+  }
+  build_blob(ps, alpha, beta, G, 256, ws, d_blob, status, wait_limit, blob);
+  cudaMemcpyAsync(d_blob, blob.data(), G.blob_bytes, cudaMemcpyHostToDevice, s);
+  DevPtrs d = dev_ptrs(G, d_blob);
+  cudaError_t e = enqueue_prepare(G, ws, d, s);
+  int bn = 256;
+  if (e == cudaSuccess) {
+    bn = pick_bn(ps, alpha, beta, G, ws, status, wait_limit, s, true);
+    if (bn != 256) {
+      build_blob(ps, alpha, beta, G, bn, ws, d_blob, status, wait_limit, blob);
+      cudaMemcpyAsync(d_blob, blob.data(), G.blob_bytes, cudaMemcpyHostToDevice, s);
+      d = dev_ptrs(G, d_blob);
+    }
+    e = enqueue_product(G, bn, d.probs, d.tiles, ws, status, wait_limit, s);
+  }
+  if (e == cudaSuccess) e = enqueue_finish(G, d, s);
+  // the host image must outlive the (pageable, staged) copies: they complete
+  // before cudaMemcpyAsync returns for pageable memory
+  cudaFreeAsync(d_blob, s);
+  cudaFreeAsync(ws, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return FAMLIES_ERR_CUDA;
+  }
+  return FAMLIES_OK;
+}
+
+}  // namespace
+
+int run_grouped(const std::vector<const Plan*>& ps, const std::vector<double>& alpha,
+                const std::vector<double>& beta, cudaStream_t s, bool use_graph, int* status,
+                int64_t wait_limit) {
+  if (ps.empty()) return FAMLIES_OK;
+  // split into chunks whose workspace fits half of the free device memory
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    free_b = (size_t)16 << 30;
+  }
+  const char* env = std::getenv("FAMLIES_BATCH_WORKSPACE_MB");
+  size_t budget = env ? (size_t)std::atoll(env) << 20 : free_b / 2;
+  if (budget < ((size_t)64 << 20)) budget = (size_t)64 << 20;
+  size_t i0 = 0;
+  while (i0 < ps.size()) {
+    size_t i1 = i0 + 1;
+    std::vector<const Plan*> chunk{ps[i0]};
+    while (i1 < ps.size()) {
+      chunk.push_back(ps[i1]);
+      if (layout_group(chunk, 256).ws_total > budget) { chunk.pop_back(); break; }
+      ++i1;
+    }
+    int rc = run_chunk(chunk, alpha.data() + i0, beta.data() + i0, s, use_graph, status, wait_limit);
+    if (rc) return rc;
+    i0 = i1;
+  }
+  return FAMLIES_OK;
+}
+
+}  // namespace famlies

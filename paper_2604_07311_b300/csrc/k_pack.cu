@@ -35,8 +35,7 @@ __device__ __forceinline__ void exp_update(double v, int& mx, int& bad) {
   else mx = max(mx, max(E, 1) - 1022);
 }
 
-__global__ void __launch_bounds__(256) k_rowexp(PackArgs pa) {
-  const PackOp& o = pa.op[blockIdx.z];
+__device__ __forceinline__ void rowexp_body(const PackArgs& pa, const PackOp& o) {
   const double* __restrict__ X = (const double*)o.x;
   const int64_t tiles_r = (o.rows + PR - 1) / PR, tiles_k = (pa.k + KCH - 1) / KCH;
   __shared__ int smx[4][PR], sbad[4][PR];
@@ -97,10 +96,9 @@ __device__ __forceinline__ uint32_t tf32_bits(float x) {
 }
 
 template <int PMODE>
-__global__ void __launch_bounds__(256) k_pack(PackArgs pa) {
+__device__ __forceinline__ void pack_body(const PackArgs& pa, const PackOp& o) {
   using T = typename PackT<PMODE>::T;
   __shared__ T tile[PR][PK + 1];
-  const PackOp& o = pa.op[blockIdx.z];
   const T* __restrict__ X = (const T*)o.x;
   const int64_t tiles_r = (o.rows + PR - 1) / PR, tiles_k = (pa.k + PK - 1) / PK;
   const size_t slice_stride = (size_t)pa.l * o.rows * pa.kp;  // elements per slice
@@ -203,9 +201,9 @@ __global__ void __launch_bounds__(256) k_pack(PackArgs pa) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_fixup(GemmArgs g, const int32_t* __restrict__ list_a,
-                                               const int32_t* __restrict__ list_b,
-                                               const int32_t* __restrict__ flag_a) {
+__device__ __forceinline__ void fixup_body(const GemmArgs& g, const int32_t* __restrict__ list_a,
+                                           const int32_t* __restrict__ list_b,
+                                           const int32_t* __restrict__ flag_a) {
   const int64_t na = list_a[0], nb = list_b[0];
   if (na == 0 && nb == 0) return;
   const double* __restrict__ A = (const double*)g.a;
@@ -243,7 +241,66 @@ int grid_for(int64_t blocks) {
   return (int)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
 }
 
+// One problem per launch: blockIdx.z picks the operand.
+__global__ void __launch_bounds__(256) k_rowexp(PackArgs pa) { rowexp_body(pa, pa.op[blockIdx.z]); }
+
+template <int PMODE>
+__global__ void __launch_bounds__(256) k_pack(PackArgs pa) { pack_body<PMODE>(pa, pa.op[blockIdx.z]); }
+
+__global__ void __launch_bounds__(256) k_fixup(GemmArgs g, const int32_t* list_a,
+                                               const int32_t* list_b, const int32_t* flag_a) {
+  fixup_body(g, list_a, list_b, flag_a);
+}
+
+// Many problems per launch: blockIdx.y walks the problems.
+__global__ void __launch_bounds__(256) k_rowexp_grouped(const PackArgs* __restrict__ pas, int n) {
+  for (int p = blockIdx.y; p < n; p += gridDim.y) rowexp_body(pas[p], pas[p].op[blockIdx.z]);
+}
+
+template <int PMODE>
+__global__ void __launch_bounds__(256) k_pack_grouped(const PackArgs* __restrict__ pas, int n) {
+  for (int p = blockIdx.y; p < n; p += gridDim.y) pack_body<PMODE>(pas[p], pas[p].op[blockIdx.z]);
+}
+
+__global__ void __launch_bounds__(256) k_fixup_grouped(const GemmArgs* __restrict__ gs,
+                                                       const PackArgs* __restrict__ pas, int n) {
+  for (int p = blockIdx.y; p < n; p += gridDim.y)
+    fixup_body(gs[p], pas[p].op[0].list, pas[p].op[1].list, pas[p].op[0].flag);
+}
+
 }  // namespace
+
+// Blocks per problem: enough for ~8 blocks per SM in total, at most what the
+// largest problem can use.
+static int64_t grouped_gx(int n, int64_t max_blocks) {
+  int64_t gx = ((int64_t)num_sms() * 8 + n - 1) / n;
+  if (gx > max_blocks) gx = max_blocks;
+  return gx < 1 ? 1 : (gx > 65535 ? 65535 : gx);
+}
+
+cudaError_t launch_rowexp_grouped(const PackArgs* pas, int n, int64_t max_blocks, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)grouped_gx(n, max_blocks), (unsigned)(n > 32768 ? 32768 : n), 2);
+  k_rowexp_grouped<<<grid, 256, 0, s>>>(pas, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_grouped(int pmode, const PackArgs* pas, int n, int64_t max_blocks,
+                                cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)grouped_gx(n, max_blocks), (unsigned)(n > 32768 ? 32768 : n), 2);
+  if (pmode == PACK_BF16) k_pack_grouped<PACK_BF16><<<grid, 256, 0, s>>>(pas, n);
+  else if (pmode == PACK_TF32) k_pack_grouped<PACK_TF32><<<grid, 256, 0, s>>>(pas, n);
+  else k_pack_grouped<PACK_F64><<<grid, 256, 0, s>>>(pas, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fixup_grouped(const GemmArgs* gs, const PackArgs* pas, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const dim3 grid(4, (unsigned)(n > 32768 ? 32768 : n));
+  k_fixup_grouped<<<grid, 256, 0, s>>>(gs, pas, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_rowexp(const PackArgs& pa, cudaStream_t s) {
   int64_t blocks = 0;

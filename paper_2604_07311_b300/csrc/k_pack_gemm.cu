@@ -32,6 +32,11 @@
 // The fp32 accumulation is exact because every partial sum is an integer
 // below 2^24; only the diagonal recombination and the alpha/beta update use
 // fp64 arithmetic.
+//
+// Grouped launches (many independent problems, e.g. the blocks of a
+// block-sparse contraction) run the same kernel over a device tile list:
+// each entry names its problem, whose descriptor (TMA maps in global memory,
+// C's offset tables, scalars) the roles read per tile.
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -41,52 +46,39 @@
 
 #include "device.h"
 #include "packed.h"
+#include "pair_gemm.h"
 #include "ptx.cuh"
 
 namespace famlies {
 
 namespace {
 
-constexpr int BM = 128;
+constexpr int BM = kPairBM;
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 32 * (EPI_WARPS + 2);
 constexpr int STAGES = 4;
-constexpr int MAXD = 10;
-
-enum { KIND_BF16 = 0, KIND_TF32 = 1 };
-enum { MODE_F32OUT = 0, MODE_EMU = 1 };
-
-// The unit schedule of one output tile (identical for every tile).
-struct Sched {
-  int ndiag;
-  int slices;
-  int shift[MAXD];        // diagonal weight 2^-shift (fp64 split)
-  int kcb[MAXD];          // k-blocks per unit
-  int flush_every[MAXD];  // units between flushes of the int32 sums
-  int npairs[MAXD];
-  int8_t pa[MAXD][8], pb[MAXD][8];  // slice index of A and B in each pair
-};
 
 struct PairArgs {
-  GemmArgs g;
+  Prob single;           // the problem of a single-problem launch
+  const Prob* probs;     // grouped: problem descriptors (device)
+  const TileEntry* tiles;  // grouped: tile list (device)
+  int64_t ntiles;        // grouped: tile count
   Sched sc;
-  const int32_t* ea;  // per-row exponents (fp64 split)
-  const int32_t* eb;
-  const int32_t* fa;  // per-row non-finite flags (fp64 split)
-  const int32_t* fb;
-  double* G;          // per-CTA fp64 tile sums (fp64 split)
+  double* G;             // fp64 split: per-CTA fp64 tile sums
+  int* status;
+  int64_t wait_limit;
 };
 
 template <int KIND, int BN>
 struct PCfg {
-  static constexpr int KB = KIND == KIND_BF16 ? 64 : 32;  // k per stage (128-byte rows)
-  static constexpr int MMA_K = KIND == KIND_BF16 ? 16 : 8;
+  static constexpr int KB = pair_stage_k(KIND);            // k per stage (128-byte rows)
+  static constexpr int MMA_K = KIND == PAIR_KIND_BF16 ? 16 : 8;
   static constexpr int KSTEPS = KB / MMA_K;
   static constexpr int A_BYTES = BM * 128;
   static constexpr int B_BYTES = BN * 128;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr uint32_t TMEM_COLS = 2 * BN;
-  static constexpr uint32_t IDESC = ptx::idesc_make(BM, BN, KIND == KIND_BF16 ? 1u : 2u);
+  static constexpr uint32_t IDESC = ptx::idesc_make(BM, BN, KIND == PAIR_KIND_BF16 ? 1u : 2u);
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 };
 
@@ -95,10 +87,36 @@ __device__ __forceinline__ void record_timeout(volatile int* abort, int* status)
   atomicCAS(status, 0, FAMLIES_ERR_DEVICE_TIMEOUT);
 }
 
-template <int KIND, int MODE, int BN>
+struct TileRef {
+  const Prob* P;
+  int64_t tm, tn, il;
+};
+
+template <int BN, bool GROUPED>
+__device__ __forceinline__ int64_t tile_count(const PairArgs& a) {
+  if (GROUPED) return a.ntiles;
+  const Prob& P = a.single;
+  return ((P.m + BM - 1) / BM) * ((P.n + BN - 1) / BN) * P.l;
+}
+
+// Tile t of the launch.  Single problems walk column tiles fastest, so the
+// CTAs running at the same time share A tiles through L2.
+template <int BN, bool GROUPED>
+__device__ __forceinline__ TileRef tile_at(const PairArgs& a, int64_t t) {
+  if (GROUPED) {
+    const TileEntry e = a.tiles[t];
+    return TileRef{a.probs + e.p, e.tm, e.tn, e.il};
+  }
+  const Prob& P = a.single;
+  const int64_t tiles_m = (P.m + BM - 1) / BM, tiles_n = (P.n + BN - 1) / BN;
+  const int64_t tn = t % tiles_n, rest = t / tiles_n;
+  return TileRef{&a.single, rest % tiles_m, tn, rest / tiles_m};
+}
+
+template <int KIND, int MODE, int BN, bool GROUPED>
 __global__ void __launch_bounds__(THREADS, 1)
     k_pair_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
-                const PairArgs args) {
+                const __grid_constant__ PairArgs args) {
   using Cfg = PCfg<KIND, BN>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -110,13 +128,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort = (volatile int*)(tmem_slot + 1);
 
-  const GemmArgs& g = args.g;
   const Sched& sc = args.sc;
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-  const int64_t tiles_m = (g.m + BM - 1) / BM, tiles_n = (g.n + BN - 1) / BN;
-  const int64_t ntiles = tiles_m * tiles_n * g.l;
-  const int nkb = (int)((g.k + Cfg::KB - 1) / Cfg::KB);
-  const int64_t lim = g.wait_limit;
+  const int64_t ntiles = tile_count<BN, GROUPED>(args);
+  const int64_t lim = args.wait_limit;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -143,30 +158,35 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == EPI_WARPS) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      ptx::prefetch_tmap(&map_a);
-      ptx::prefetch_tmap(&map_b);
+      if (!GROUPED) {
+        ptx::prefetch_tmap(&map_a);
+        ptx::prefetch_tmap(&map_b);
+      }
       int stage = 0;
       uint32_t phase = 0;
       uint32_t pending = 0;  // bit s: stage s holds a copy issued in phase bit (s+8)
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int64_t tn = t % tiles_n, rest = t / tiles_n;
-        const int64_t tm = rest % tiles_m, il = rest / tiles_m;
+        const TileRef T = tile_at<BN, GROUPED>(args, t);
+        const CUtensorMap* ma = GROUPED ? T.P->map_a : &map_a;
+        const CUtensorMap* mb = GROUPED ? T.P->map_b : &map_b;
+        const int nkb = (int)((T.P->k + Cfg::KB - 1) / Cfg::KB);
+        const int l = (int)T.P->l;
         for (int di = 0; di < sc.ndiag && ok; ++di) {
           const int kcb = sc.kcb[di];
           for (int kb0 = 0; kb0 < nkb && ok; kb0 += kcb) {
             const int kb1 = kb0 + kcb < nkb ? kb0 + kcb : nkb;
             for (int p = 0; p < sc.npairs[di] && ok; ++p) {
               // slices are stored [slice][batch][rows][k]
-              const int za = sc.pa[di][p] * (int)g.l + (int)il;
-              const int zb = sc.pb[di][p] * (int)g.l + (int)il;
+              const int za = sc.pa[di][p] * l + (int)T.il;
+              const int zb = sc.pb[di][p] * l + (int)T.il;
               for (int kb = kb0; kb < kb1; ++kb) {
                 if (!ptx::mbar_wait(&empty[stage], phase ^ 1, lim, abort)) { ok = false; break; }
                 uint8_t* sa = smem + stage * Cfg::STAGE_BYTES;
                 ptx::mbar_arrive_expect_tx(&full[stage], Cfg::STAGE_BYTES);
-                ptx::tma_load_3d(sa, &map_a, &full[stage], kb * Cfg::KB, (int)(tm * BM), za);
-                ptx::tma_load_3d(sa + Cfg::A_BYTES, &map_b, &full[stage], kb * Cfg::KB,
-                                 (int)(tn * BN), zb);
+                ptx::tma_load_3d(sa, ma, &full[stage], kb * Cfg::KB, (int)(T.tm * BM), za);
+                ptx::tma_load_3d(sa + Cfg::A_BYTES, mb, &full[stage], kb * Cfg::KB,
+                                 (int)(T.tn * BN), zb);
                 pending = (pending & ~(0x101u << stage)) | (1u << stage) | (phase << (stage + 8));
                 if (++stage == STAGES) { stage = 0; phase ^= 1; }
               }
@@ -174,7 +194,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
       }
-      if (!ok && !*abort) record_timeout(abort, g.status);
+      if (!ok && !*abort) record_timeout(abort, args.status);
       // Copies still in flight must land before the CTA leaves: wait (bounded)
       // for the phase each stage was last filled in.
       for (int s = 0; s < STAGES; ++s) {
@@ -192,6 +212,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t phase = 0, acc = 0, accph = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const TileRef T = tile_at<BN, GROUPED>(args, t);
+        const int nkb = (int)((T.P->k + Cfg::KB - 1) / Cfg::KB);
         for (int di = 0; di < sc.ndiag && ok; ++di) {
           const int kcb = sc.kcb[di];
           for (int kb0 = 0; kb0 < nkb && ok; kb0 += kcb) {
@@ -209,7 +231,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const uint64_t db = ptx::sdesc_kmajor_sw128(sa + Cfg::A_BYTES);
 #pragma unroll
                 for (int kk = 0; kk < Cfg::KSTEPS; ++kk) {
-                  if (KIND == KIND_BF16)
+                  if (KIND == PAIR_KIND_BF16)
                     ptx::mma_f16(dt, da + 2 * kk, db + 2 * kk, Cfg::IDESC, accumulate);
                   else
                     ptx::mma_tf32(dt, da + 2 * kk, db + 2 * kk, Cfg::IDESC, accumulate);
@@ -226,7 +248,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
       }
-      if (!ok && !*abort) record_timeout(abort, g.status);
+      if (!ok && !*abort) record_timeout(abort, args.status);
       ptx::mma_commit(done);
       for (int64_t i = 0; i < ((int64_t)1 << 24); ++i)
         if (ptx::mbar_try_wait(done, 0)) break;
@@ -240,13 +262,15 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t acc = 0, accph = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const int64_t tn = t % tiles_n, rest = t / tiles_n;
-      const int64_t tm = rest % tiles_m, il = rest / tiles_m;
-      const int64_t row = tm * BM + qd * 32 + lane;
-      const int64_t col0 = tn * BN + hf * CPT;
-      const bool rv = row < g.m;
-      const int64_t crow = rv ? g.t.cl[il] + g.t.cm[row] : 0;
-      if (MODE == MODE_F32OUT) {
+      const TileRef T = tile_at<BN, GROUPED>(args, t);
+      const Prob& P = *T.P;
+      const int nkb = (int)((P.k + Cfg::KB - 1) / Cfg::KB);
+      const int64_t il = T.il;
+      const int64_t row = T.tm * BM + qd * 32 + lane;
+      const int64_t col0 = T.tn * BN + hf * CPT;
+      const bool rv = row < P.m;
+      const int64_t crow = rv ? P.cl[il] + P.cm[row] : 0;
+      if (MODE == PAIR_MODE_F32OUT) {
         // Each unit's tensor-memory sum is added into fp32 registers with
         // round-to-nearest, which bounds how much rounding any one
         // accumulator sees over a long k.
@@ -273,13 +297,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         if (!ok) break;
         if (rv) {
-          float* C = (float*)g.c;
-          const float alpha = (float)g.alpha, beta = (float)g.beta;
+          float* C = (float*)P.c;
+          const float alpha = (float)P.alpha, beta = (float)P.beta;
 #pragma unroll
           for (int j = 0; j < CPT; ++j) {
             const int64_t col = col0 + j;
-            if (col < g.n) {
-              float* p = C + crow + g.t.cn[col];
+            if (col < P.n) {
+              float* p = C + crow + P.cn[col];
               float v = alpha * S[j];
               if (beta != 0.f) v = fmaf(beta, *p, v);
               *p = v;
@@ -324,16 +348,16 @@ __global__ void __launch_bounds__(THREADS, 1)
                 S[j] = 0;
               }
               first_flush = false;
-            } else if (rv && !args.fa[il * g.m + row]) {
-              double* C = (double*)g.c;
-              const double alpha = g.alpha, beta = g.beta;
-              const int er = args.ea[il * g.m + row];
-              const int32_t* ebl = args.eb + il * g.n;
-              const int32_t* fbl = args.fb + il * g.n;
+            } else if (rv && !P.fa[il * P.m + row]) {
+              double* C = (double*)P.c;
+              const double alpha = P.alpha, beta = P.beta;
+              const int er = P.ea[il * P.m + row];
+              const int32_t* ebl = P.eb + il * P.n;
+              const int32_t* fbl = P.fb + il * P.n;
 #pragma unroll
               for (int j = 0; j < CPT; ++j) {
                 const int64_t col = col0 + j;
-                if (col < g.n && !fbl[col]) {
+                if (col < P.n && !fbl[col]) {
                   const double prev = first_flush ? 0.0 : Gt[(size_t)j * BM];
                   const double sum = fma(w, (double)S[j], prev);
                   const int e = er + ebl[col];
@@ -341,7 +365,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                   const double scaled = (e >= -1022 && e <= 1023)
                                             ? sum * __longlong_as_double((long long)(e + 1023) << 52)
                                             : ldexp(sum, e);
-                  double* p = C + crow + g.t.cn[col];
+                  double* p = C + crow + P.cn[col];
                   double v = alpha * scaled;
                   if (beta != 0.0) v = fma(beta, *p, v);
                   *p = v;
@@ -352,7 +376,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
     }
-    if (!ok && !*abort) record_timeout(abort, g.status);
+    if (!ok && !*abort) record_timeout(abort, args.status);
   }
 
   ptx::tc_fence_before();
@@ -362,7 +386,6 @@ __global__ void __launch_bounds__(THREADS, 1)
     ptx::tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
   }
 }
-
 
 // ----------------------------------------------------------------- launch
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -386,28 +409,6 @@ EncodeFn get_encode() {
   return fn;
 }
 
-// 3-D map over slices [z][rows][kp] (k innermost), box {box_k, box_rows, 1},
-// 128-byte swizzle; out-of-range k and rows read as zeros.
-bool make_map(CUtensorMap* map, void* base, bool f32, int64_t k, int64_t kp, int64_t rows,
-              int64_t z, int box_k, int box_rows) {
-  EncodeFn enc = get_encode();
-  if (!enc) return false;
-  const int es = f32 ? 4 : 2;
-  cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)z};
-  cuuint64_t strides[2] = {(cuuint64_t)(kp * es), (cuuint64_t)(kp * es * rows)};
-  cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, 1u};
-  cuuint32_t estr[3] = {1u, 1u, 1u};
-  return enc(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
-             base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-int choose_bn(const Plan& p) {
-  if (p.tile_n == 64 || p.tile_n == 128 || p.tile_n == 256) return p.tile_n;
-  return p.n > 128 ? 256 : (p.n > 64 ? 128 : 64);
-}
-
 int grid_of(const Plan& p, int bn) {
   const int64_t tiles = ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l;
   return (int)(tiles < num_sms() ? tiles : num_sms());
@@ -429,7 +430,7 @@ Layout layout_of(const Plan& p) {
   L.a = off; off += up((size_t)S * p.l * p.m * kp * es);
   L.b = off; off += up((size_t)S * p.l * p.n * kp * es);
   if (emu) {
-    const int bn = choose_bn(p);
+    const int bn = pair_bn_for(p.n, p.tile_n);
     L.ea = off; off += up((size_t)p.l * p.m * 4);
     L.eb = off; off += up((size_t)p.l * p.n * 4);
     L.fa = off; off += up((size_t)p.l * p.m * 4);
@@ -442,14 +443,68 @@ Layout layout_of(const Plan& p) {
   return L;
 }
 
+template <int KIND, int MODE, int BN, bool GROUPED>
+cudaError_t launch_pair(const CUtensorMap& ma, const CUtensorMap& mb, const PairArgs& a, int grid,
+                        cudaStream_t s) {
+  using Cfg = PCfg<KIND, BN>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_pair_gemm<KIND, MODE, BN, GROUPED>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_pair_gemm<KIND, MODE, BN, GROUPED><<<grid, THREADS, Cfg::SMEM_BYTES, s>>>(ma, mb, a);
+  return cudaGetLastError();
+}
+
+template <int KIND, int MODE, bool GROUPED>
+cudaError_t launch_pair_bn(int bn, const CUtensorMap& ma, const CUtensorMap& mb,
+                           const PairArgs& a, int grid, cudaStream_t s) {
+  if (bn == 64) return launch_pair<KIND, MODE, 64, GROUPED>(ma, mb, a, grid, s);
+  if (bn == 128) return launch_pair<KIND, MODE, 128, GROUPED>(ma, mb, a, grid, s);
+  return launch_pair<KIND, MODE, 256, GROUPED>(ma, mb, a, grid, s);
+}
+
+template <bool GROUPED>
+cudaError_t launch_pair_any(int kind, int mode, int bn, const CUtensorMap& ma,
+                            const CUtensorMap& mb, const PairArgs& a, int grid, cudaStream_t s) {
+  if (mode == PAIR_MODE_EMU) return launch_pair_bn<PAIR_KIND_BF16, PAIR_MODE_EMU, GROUPED>(bn, ma, mb, a, grid, s);
+  if (kind == PAIR_KIND_TF32)
+    return launch_pair_bn<PAIR_KIND_TF32, PAIR_MODE_F32OUT, GROUPED>(bn, ma, mb, a, grid, s);
+  return launch_pair_bn<PAIR_KIND_BF16, PAIR_MODE_F32OUT, GROUPED>(bn, ma, mb, a, grid, s);
+}
+
+}  // namespace
+
+bool make_slice_map(CUtensorMap* map, void* base, bool f32, int64_t k, int64_t kp, int64_t rows,
+                    int64_t z, int box_k, int box_rows) {
+  EncodeFn enc = get_encode();
+  if (!enc) return false;
+  const int es = f32 ? 4 : 2;
+  cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)z};
+  cuuint64_t strides[2] = {(cuuint64_t)(kp * es), (cuuint64_t)(kp * es * rows)};
+  cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, 1u};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  return enc(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+             base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int pair_bn_for(int64_t n, int request) {
+  if (request == 64 || request == 128 || request == 256) return request;
+  return n > 128 ? 256 : (n > 64 ? 128 : 64);
+}
+
 // Unit schedule.  fp64 split with s slices of b bits: diagonal q = i + j
 // (0-based slice indices, i + j <= s - 1) has weight 2^(-b (q + 2)); a unit
 // covers kcb 64-wide k blocks so that its exact integer sum stays <= 2^24.
-Sched make_sched(const Plan& p, int bits) {
+Sched make_pair_sched(int kernel, int slices, int bits) {
   Sched sc;
   std::memset(&sc, 0, sizeof(sc));
-  if (p.kernel != FAMLIES_KERNEL_TC_EMU) {
-    const bool tf32 = p.kernel == FAMLIES_KERNEL_TC_TF32X3;
+  if (kernel != FAMLIES_KERNEL_TC_EMU) {
+    const bool tf32 = kernel == FAMLIES_KERNEL_TC_TF32X3;
     sc.ndiag = 1;
     sc.slices = tf32 ? 2 : 1;
     sc.kcb[0] = 16;  // units of 1024 (bf16) or 512 (tf32) k
@@ -464,7 +519,7 @@ Sched make_sched(const Plan& p, int bits) {
     }
     return sc;
   }
-  const int s = p.slices;
+  const int s = slices;
   sc.ndiag = s;
   sc.slices = s;
   auto maxd = [&](int i) { return (int64_t)1 << (i == 0 ? bits : bits - 1); };
@@ -486,32 +541,23 @@ Sched make_sched(const Plan& p, int bits) {
   return sc;
 }
 
-template <int KIND, int MODE, int BN>
-cudaError_t launch_pair(const CUtensorMap& ma, const CUtensorMap& mb, const PairArgs& a, int grid,
-                        cudaStream_t s) {
-  using Cfg = PCfg<KIND, BN>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_pair_gemm<KIND, MODE, BN>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  mark_begin(a.g, s);
-  k_pair_gemm<KIND, MODE, BN><<<grid, THREADS, Cfg::SMEM_BYTES, s>>>(ma, mb, a);
-  mark_end(a.g, s);
-  return cudaGetLastError();
+cudaError_t launch_pair_grouped(int kind, int mode, int bn, const Prob* probs,
+                                const TileEntry* tiles, int64_t ntiles, const Sched& sc,
+                                double* G, int grid, int* status, int64_t wait_limit,
+                                cudaStream_t s) {
+  PairArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.probs = probs;
+  a.tiles = tiles;
+  a.ntiles = ntiles;
+  a.sc = sc;
+  a.G = G;
+  a.status = status;
+  a.wait_limit = wait_limit;
+  CUtensorMap unused;
+  std::memset(&unused, 0, sizeof(unused));
+  return launch_pair_any<true>(kind, mode, bn, unused, unused, a, grid, s);
 }
-
-template <int KIND, int MODE>
-cudaError_t launch_pair_bn(int bn, const CUtensorMap& ma, const CUtensorMap& mb,
-                           const PairArgs& a, int grid, cudaStream_t s) {
-  if (bn == 64) return launch_pair<KIND, MODE, 64>(ma, mb, a, grid, s);
-  if (bn == 128) return launch_pair<KIND, MODE, 128>(ma, mb, a, grid, s);
-  return launch_pair<KIND, MODE, 256>(ma, mb, a, grid, s);
-}
-
-}  // namespace
 
 int64_t packed_workspace_bytes(const Plan& p) { return (int64_t)layout_of(p).total; }
 
@@ -546,25 +592,26 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   }
   if ((e = launch_pack(emu ? PACK_F64 : (tf32 ? PACK_TF32 : PACK_BF16), pa, s)) != cudaSuccess)
     return e;
-  const int bn = choose_bn(p);
+  const int bn = pair_bn_for(p.n, p.tile_n);
   const int S = pa.slices;
-  const int kbk = tf32 ? 32 : 64;
+  const int kind = tf32 ? PAIR_KIND_TF32 : PAIR_KIND_BF16;
+  const int kbk = pair_stage_k(kind);
   CUtensorMap ma, mb;
-  if (!make_map(&ma, w + L.a, tf32, p.k, kp, p.m, (int64_t)S * p.l, kbk, BM) ||
-      !make_map(&mb, w + L.b, tf32, p.k, kp, p.n, (int64_t)S * p.l, kbk, bn))
+  if (!make_slice_map(&ma, w + L.a, tf32, p.k, kp, p.m, (int64_t)S * p.l, kbk, BM) ||
+      !make_slice_map(&mb, w + L.b, tf32, p.k, kp, p.n, (int64_t)S * p.l, kbk, bn))
     return cudaErrorInvalidValue;
   PairArgs a;
-  a.g = g;
-  a.sc = make_sched(p, bits);
-  a.ea = pa.op[0].e;
-  a.eb = pa.op[1].e;
-  a.fa = pa.op[0].flag;
-  a.fb = pa.op[1].flag;
+  std::memset(&a, 0, sizeof(a));
+  a.single = Prob{nullptr, nullptr, g.c, g.t.cm, g.t.cn, g.t.cl, pa.op[0].e, pa.op[1].e,
+                  pa.op[0].flag, pa.op[1].flag, p.m, p.n, p.k, p.l, g.alpha, g.beta};
+  a.sc = make_pair_sched(p.kernel, p.slices, bits);
   a.G = emu ? (double*)(w + L.G) : nullptr;
+  a.status = g.status;
+  a.wait_limit = g.wait_limit;
   const int grid = grid_of(p, bn);
-  if (emu) e = launch_pair_bn<KIND_BF16, MODE_EMU>(bn, ma, mb, a, grid, s);
-  else if (tf32) e = launch_pair_bn<KIND_TF32, MODE_F32OUT>(bn, ma, mb, a, grid, s);
-  else e = launch_pair_bn<KIND_BF16, MODE_F32OUT>(bn, ma, mb, a, grid, s);
+  mark_begin(g, s);
+  e = launch_pair_any<false>(kind, emu ? PAIR_MODE_EMU : PAIR_MODE_F32OUT, bn, ma, mb, a, grid, s);
+  mark_end(g, s);
   if (e != cudaSuccess) return e;
   if (emu) e = launch_fixup(g, pa, s);
   return e;

@@ -41,13 +41,6 @@ int read_clear_status(int* value) {
 }
 
 // ---------------------------------------------------------------- tables
-struct TableJob {
-  int n;
-  int64_t ext[kMaxModes];
-  int64_t st[kMaxModes];
-  int64_t total;
-  int64_t* out;
-};
 struct TableJobs {
   TableJob j[9];
 };
@@ -91,6 +84,57 @@ cudaError_t launch_tables(const Plan& p, int64_t* ws, Tables* t, cudaStream_t s)
   int64_t blocks = (maxn + 255) / 256;
   dim3 grid((unsigned)(blocks > 1024 ? 1024 : blocks), 9);
   k_tables<<<grid, 256, 0, s>>>(jobs);
+  return cudaGetLastError();
+}
+
+// The nine table jobs of one plan, writing into ws (same order and
+// placement as launch_tables); fills *t with the table addresses.
+void plan_table_jobs(const Plan& p, int64_t* ws, TableJob jobs[9], Tables* t) {
+  const ClassModes* cls[9] = {&p.M, &p.M, &p.N, &p.N, &p.K, &p.K, &p.L, &p.L, &p.L};
+  const int which[9] = {0, 2, 1, 2, 0, 1, 0, 1, 2};
+  int64_t* ptr[9];
+  int64_t off = 0;
+  for (int i = 0; i < 9; ++i) {
+    TableJob& J = jobs[i];
+    const ClassModes& cm = *cls[i];
+    J.n = cm.n;
+    for (int d = 0; d < cm.n; ++d) {
+      J.ext[d] = cm.m[d].ext;
+      J.st[d] = which[i] == 0 ? cm.m[d].sa : (which[i] == 1 ? cm.m[d].sb : cm.m[d].sc);
+    }
+    J.total = cm.total();
+    J.out = ws + off;
+    ptr[i] = ws + off;
+    off += J.total;
+  }
+  t->am = ptr[0]; t->cm = ptr[1]; t->bn = ptr[2]; t->cn = ptr[3];
+  t->ak = ptr[4]; t->bk = ptr[5]; t->al = ptr[6]; t->bl = ptr[7]; t->cl = ptr[8];
+}
+
+// Many problems' tables in one launch: blockIdx.y walks the job list.
+__global__ void k_tables_grouped(const TableJob* __restrict__ jobs, int64_t njobs) {
+  for (int64_t j = blockIdx.y; j < njobs; j += gridDim.y) {
+    const TableJob J = jobs[j];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < J.total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      int64_t r = i, off = 0;
+      for (int d = 0; d < J.n; ++d) {
+        int64_t e = J.ext[d];
+        off += (r % e) * J.st[d];
+        r /= e;
+      }
+      J.out[i] = off;
+    }
+  }
+}
+
+cudaError_t launch_tables_grouped(const TableJob* jobs, int64_t njobs, int64_t max_total,
+                                  cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  const int64_t bx = (max_total + 255) / 256;
+  dim3 grid((unsigned)(bx > 64 ? 64 : (bx < 1 ? 1 : bx)),
+            (unsigned)(njobs > 32768 ? 32768 : njobs));
+  k_tables_grouped<<<grid, 256, 0, s>>>(jobs, njobs);
   return cudaGetLastError();
 }
 

@@ -38,4 +38,11 @@ cudaError_t launch_pack(int pmode, const PackArgs& pa, cudaStream_t s);
 // fp64 split: recomputes in native fp64 the outputs of flagged rows/columns.
 cudaError_t launch_fixup(const GemmArgs& g, const PackArgs& pa, cudaStream_t s);
 
+// Grouped forms: n problems' PackArgs / GemmArgs in device memory, one launch
+// each; max_blocks bounds the tiles of the largest problem.
+cudaError_t launch_rowexp_grouped(const PackArgs* pas, int n, int64_t max_blocks, cudaStream_t s);
+cudaError_t launch_pack_grouped(int pmode, const PackArgs* pas, int n, int64_t max_blocks,
+                                cudaStream_t s);
+cudaError_t launch_fixup_grouped(const GemmArgs* gs, const PackArgs* pas, int n, cudaStream_t s);
+
 }  // namespace famlies

@@ -1,0 +1,65 @@
+// The packed tensor-core product (k_pair_gemm, csrc/k_pack_gemm.cu): the
+// per-problem descriptor, the unit schedule, and the launchers shared by the
+// single-problem path and the grouped (many-problem) path.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "device.h"
+
+namespace famlies {
+
+constexpr int kPairBM = 128;      // rows of an output tile
+constexpr int kPairMaxDiag = 10;
+
+enum { PAIR_KIND_BF16 = 0, PAIR_KIND_TF32 = 1 };
+enum { PAIR_MODE_F32OUT = 0, PAIR_MODE_EMU = 1 };
+
+// The unit schedule of one output tile (identical for every tile of a launch).
+struct Sched {
+  int ndiag;
+  int slices;
+  int shift[kPairMaxDiag];        // diagonal weight 2^-shift (fp64 split)
+  int kcb[kPairMaxDiag];          // k-blocks per unit
+  int flush_every[kPairMaxDiag];  // units between flushes of the int32 sums
+  int npairs[kPairMaxDiag];
+  int8_t pa[kPairMaxDiag][8], pb[kPairMaxDiag][8];  // slice of A and B in each pair
+};
+
+// What the product needs to know about one problem.
+struct Prob {
+  const CUtensorMap* map_a;  // grouped launches: maps in global memory (64-byte aligned)
+  const CUtensorMap* map_b;
+  void* c;
+  const int64_t* cm;
+  const int64_t* cn;
+  const int64_t* cl;
+  const int32_t* ea;  // fp64 split: row exponents and non-finite flags
+  const int32_t* eb;
+  const int32_t* fa;
+  const int32_t* fb;
+  int64_t m, n, k, l;
+  double alpha, beta;
+};
+
+// One entry of a grouped launch's tile list: problem, row tile, column tile, batch.
+struct TileEntry {
+  int32_t p, tm, tn, il;
+};
+
+Sched make_pair_sched(int kernel, int slices, int bits);
+int pair_bn_for(int64_t n, int request);
+// 3-D map over slices [z][rows][kp] (k innermost), box {box_k, box_rows, 1}.
+bool make_slice_map(CUtensorMap* map, void* base, bool f32, int64_t k, int64_t kp, int64_t rows,
+                    int64_t z, int box_k, int box_rows);
+// Grouped product over a device tile list; probs/tiles are device arrays.
+cudaError_t launch_pair_grouped(int kind, int mode, int bn, const Prob* probs,
+                                const TileEntry* tiles, int64_t ntiles, const Sched& sc,
+                                double* G, int grid, int* status, int64_t wait_limit,
+                                cudaStream_t s);
+constexpr int pair_stage_k(int kind) { return kind == PAIR_KIND_BF16 ? 64 : 32; }
+
+}  // namespace famlies
