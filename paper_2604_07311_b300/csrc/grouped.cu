@@ -48,9 +48,9 @@ struct GroupSetup {
   int kernel = 0, kind = 0, mode = 0, slices = 1;
   size_t ws_main = 0, ws_exp = 0, ws_flag = 0, ws_g = 0, ws_total = 0;
   std::vector<ProbLayout> lay;
-  int64_t ntiles = 0, max_table = 1, max_rowexp_blocks = 1, max_pack_blocks = 1;
+  int64_t ntiles = 0, max_table = 1, rowexp_total = 0, pack_total = 0;
   size_t blob_probs = 0, blob_gargs = 0, blob_pargs = 0, blob_jobs = 0, blob_tiles = 0,
-         blob_maps = 0, blob_bytes = 0;
+         blob_maps = 0, blob_offr = 0, blob_offp = 0, blob_bytes = 0;
   size_t c_bytes = 0;  // sum of C spans (autotuning scratch)
 };
 
@@ -82,10 +82,8 @@ GroupSetup layout_group(const std::vector<const Plan*>& ps, int bn_max) {
     }
     int64_t tmax = std::max(std::max(p.m, p.n), std::max(p.k, p.l));
     G.max_table = std::max(G.max_table, tmax);
-    const int64_t rb = ((std::max(p.m, p.n) + 63) / 64) * ((p.k + 1023) / 1024) * p.l;
-    const int64_t pb = ((std::max(p.m, p.n) + 63) / 64) * ((p.k + 63) / 64) * p.l;
-    G.max_rowexp_blocks = std::max(G.max_rowexp_blocks, rb);
-    G.max_pack_blocks = std::max(G.max_pack_blocks, pb);
+    G.rowexp_total += rowexp_tiles(p.m, p.k, p.l) + rowexp_tiles(p.n, p.k, p.l);
+    G.pack_total += pack_tiles(p.m, p.k, p.l) + pack_tiles(p.n, p.k, p.l);
     G.c_bytes += up256((size_t)p.span_c * p.es_c);
   }
   if (emu) G.ws_g = up256((size_t)num_sms() * kPairBM * bn_max * 8);
@@ -93,9 +91,9 @@ GroupSetup layout_group(const std::vector<const Plan*>& ps, int bn_max) {
   return G;
 }
 
-int64_t tile_count_for(const Plan& p, int bn) {
-  return ((p.m + kPairBM - 1) / kPairBM) * ((p.n + bn - 1) / bn) * p.l;
-}
+// Tile width of one problem in a launch whose widest tile is cap: the
+// narrowest of 64/128/256 that covers the problem's columns, at most cap.
+int width_for(const Plan& p, int cap) { return std::min(pair_bn_for(p.n, 0), cap); }
 
 // Fills the host image of the descriptor blob whose device copy starts at
 // d_blob, for workspace d_ws and product tile width bn.  Returns false if a
@@ -108,8 +106,9 @@ bool build_blob(const std::vector<const Plan*>& ps, const double* alpha, const d
   std::vector<int64_t> cost;
   for (int i = 0; i < n; ++i) {
     const Plan& p = *ps[i];
-    const int64_t tm_n = (p.m + kPairBM - 1) / kPairBM, tn_n = (p.n + bn - 1) / bn;
-    const int64_t c = (p.k + 63) / 64;
+    const int bw = width_for(p, bn);
+    const int64_t tm_n = (p.m + kPairBM - 1) / kPairBM, tn_n = (p.n + bw - 1) / bw;
+    const int64_t c = (p.k + 63) / 64 * (bw / 64);  // work of one tile
     for (int64_t il = 0; il < p.l; ++il)
       for (int64_t tm = 0; tm < tm_n; ++tm)
         for (int64_t tn = 0; tn < tn_n; ++tn) {
@@ -131,6 +130,8 @@ bool build_blob(const std::vector<const Plan*>& ps, const double* alpha, const d
   G.blob_jobs = off; off += up256(sizeof(TableJob) * 9 * n);
   G.blob_tiles = off; off += up256(sizeof(TileEntry) * tiles.size());
   G.blob_maps = off; off += up256(sizeof(CUtensorMap) * 2 * n);
+  G.blob_offr = off; off += up256(sizeof(int64_t) * (2 * n + 1));
+  G.blob_offp = off; off += up256(sizeof(int64_t) * (2 * n + 1));
   G.blob_bytes = off;
   blob.assign(off, 0);
 
@@ -175,13 +176,24 @@ bool build_blob(const std::vector<const Plan*>& ps, const double* alpha, const d
     if (!make_slice_map(&maps[2 * i], d_ws + L.a, tf32, p.k, kp, p.m, (int64_t)G.slices * p.l, kbk,
                         kPairBM) ||
         !make_slice_map(&maps[2 * i + 1], d_ws + L.b, tf32, p.k, kp, p.n,
-                        (int64_t)G.slices * p.l, kbk, bn))
+                        (int64_t)G.slices * p.l, kbk, width_for(p, bn)))
       return false;
     probs[i] = Prob{d_maps + 2 * i, d_maps + 2 * i + 1, p.c, t.cm, t.cn, t.cl, pa.op[0].e,
                     pa.op[1].e, pa.op[0].flag, pa.op[1].flag, p.m, p.n, p.k, p.l,
-                    alpha[i], beta[i]};
+                    alpha[i], beta[i], width_for(p, bn)};
   }
   for (size_t i = 0; i < order.size(); ++i) tl[i] = tiles[order[i]];
+  // flat tile numbering of the exponent and pack passes, per (problem, operand)
+  int64_t* offr = (int64_t*)(blob.data() + G.blob_offr);
+  int64_t* offp = (int64_t*)(blob.data() + G.blob_offp);
+  offr[0] = offp[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    const Plan& p = *ps[i];
+    offr[2 * i + 1] = offr[2 * i] + rowexp_tiles(p.m, p.k, p.l);
+    offr[2 * i + 2] = offr[2 * i + 1] + rowexp_tiles(p.n, p.k, p.l);
+    offp[2 * i + 1] = offp[2 * i] + pack_tiles(p.m, p.k, p.l);
+    offp[2 * i + 2] = offp[2 * i + 1] + pack_tiles(p.n, p.k, p.l);
+  }
   return true;
 }
 
@@ -191,12 +203,15 @@ struct DevPtrs {
   const PackArgs* pargs;
   const TableJob* jobs;
   const TileEntry* tiles;
+  const int64_t* offr;
+  const int64_t* offp;
 };
 
 DevPtrs dev_ptrs(const GroupSetup& G, char* d_blob) {
   return DevPtrs{(const Prob*)(d_blob + G.blob_probs), (const GemmArgs*)(d_blob + G.blob_gargs),
                  (const PackArgs*)(d_blob + G.blob_pargs), (const TableJob*)(d_blob + G.blob_jobs),
-                 (const TileEntry*)(d_blob + G.blob_tiles)};
+                 (const TileEntry*)(d_blob + G.blob_tiles), (const int64_t*)(d_blob + G.blob_offr),
+                 (const int64_t*)(d_blob + G.blob_offp)};
 }
 
 cudaError_t enqueue_prepare(const GroupSetup& G, char* d_ws, const DevPtrs& d, cudaStream_t s) {
@@ -209,10 +224,10 @@ cudaError_t enqueue_prepare(const GroupSetup& G, char* d_ws, const DevPtrs& d, c
     if ((e = cudaMemsetAsync(d_flag, 0, G.ws_flag, s)) != cudaSuccess) return e;
   }
   if ((e = launch_tables_grouped(d.jobs, 9 * (int64_t)G.n, G.max_table, s)) != cudaSuccess) return e;
-  if (emu && (e = launch_rowexp_grouped(d.pargs, G.n, G.max_rowexp_blocks, s)) != cudaSuccess)
+  if (emu && (e = launch_rowexp_grouped(d.pargs, d.offr, G.n, G.rowexp_total, s)) != cudaSuccess)
     return e;
   const int pmode = emu ? PACK_F64 : (G.kind == PAIR_KIND_TF32 ? PACK_TF32 : PACK_BF16);
-  return launch_pack_grouped(pmode, d.pargs, G.n, G.max_pack_blocks, s);
+  return launch_pack_grouped(pmode, d.pargs, d.offp, G.n, G.pack_total, s);
 }
 
 cudaError_t enqueue_product(const GroupSetup& G, int bn, const Prob* probs, const TileEntry* tiles,
@@ -247,11 +262,11 @@ std::string tune_key(const std::vector<const Plan*>& ps) {
   return buf;
 }
 
+// Without tuning: the cap that lets every problem use its own best width.
 int heuristic_bn(const std::vector<const Plan*>& ps) {
-  std::vector<int64_t> n;
-  for (const Plan* p : ps) n.push_back(p->n);
-  std::nth_element(n.begin(), n.begin() + n.size() / 2, n.end());
-  return pair_bn_for(n[n.size() / 2], 0);
+  int cap = 64;
+  for (const Plan* p : ps) cap = std::max(cap, pair_bn_for(p->n, 0));
+  return cap;
 }
 
 bool autotune_enabled() {
@@ -335,8 +350,8 @@ int pick_bn(const std::vector<const Plan*>& ps, const double* alpha, const doubl
 // ------------------------------------------------------------ graph cache
 struct GraphEntry {
   uint64_t key;
-  char* ws;
-  char* blob;
+  char* ws;                  // persistent workspace of the captured set
+  std::vector<char*> blobs;  // persistent descriptor blocks, one per chunk
   cudaGraphExec_t exec;
 };
 std::mutex g_graph_mu;
@@ -370,172 +385,200 @@ uint64_t set_key(const std::vector<const Plan*>& ps, const double* alpha, const 
   return h;
 }
 
-int run_chunk(const std::vector<const Plan*>& ps, const double* alpha, const double* beta,
-              cudaStream_t s, bool use_graph, int* status, int64_t wait_limit) {
+// Problems in call order, cut into chunks whose workspace stays within
+// the budget (a problem larger than the budget forms its own chunk).
+// Small chunks keep the packed slices within TLB reach and close in time to
+// their use; every chunk still runs as one launch per stage.
+std::vector<std::pair<size_t, size_t>> make_chunks(const std::vector<const Plan*>& ps) {
+  const char* env = std::getenv("FAMLIES_BATCH_WORKSPACE_MB");
+  size_t budget = env ? (size_t)std::atoll(env) << 20 : (size_t)4096 << 20;
+  if (budget < ((size_t)16 << 20)) budget = (size_t)16 << 20;
+  std::vector<std::pair<size_t, size_t>> out;
+  size_t i0 = 0;
+  while (i0 < ps.size()) {
+    size_t i1 = i0 + 1, used = layout_group({ps[i0]}, 256).ws_total;
+    while (i1 < ps.size()) {
+      const GroupSetup one = layout_group({ps[i1]}, 256);
+      const size_t w = one.ws_total - one.ws_g;  // the per-CTA sums are shared
+      if (used + w > budget) break;
+      used += w;
+      ++i1;
+    }
+    out.emplace_back(i0, i1);
+    i0 = i1;
+  }
+  return out;
+}
+
+struct ChunkRun {
+  std::vector<const Plan*> ps;
+  const double* alpha;
+  const double* beta;
+  GroupSetup G;
+  int bn = 256;
+  std::vector<char> blob;
+  char* d_blob = nullptr;
+  size_t blob_cap = 0;
+};
+
+// Descriptor capacity: the narrowest width gives the longest tile list.
+size_t blob_capacity(ChunkRun& c, char* ws, int* status, int64_t wait_limit) {
+  GroupSetup G64 = c.G;
+  std::vector<char> tmp;
+  build_blob(c.ps, c.alpha, c.beta, G64, 64, ws, nullptr, status, wait_limit, tmp);
+  return G64.blob_bytes;
+}
+
+}  // namespace
+
+int run_grouped(const std::vector<const Plan*>& all, const std::vector<double>& alpha,
+                const std::vector<double>& beta, cudaStream_t s, bool use_graph, int* status,
+                int64_t wait_limit) {
+  if (all.empty()) return FAMLIES_OK;
   int dev = 0;
   cudaGetDevice(&dev);
-  GroupSetup G = layout_group(ps, 256);
+  const auto ranges = make_chunks(all);
+  std::vector<ChunkRun> chunks(ranges.size());
+  size_t ws_max = 0;
+  for (size_t c = 0; c < ranges.size(); ++c) {
+    ChunkRun& r = chunks[c];
+    r.ps.assign(all.begin() + ranges[c].first, all.begin() + ranges[c].second);
+    r.alpha = alpha.data() + ranges[c].first;
+    r.beta = beta.data() + ranges[c].first;
+    r.G = layout_group(r.ps, 256);
+    ws_max = std::max(ws_max, r.G.ws_total);
+  }
+  uint64_t key = 0;
   if (use_graph) {
-    const uint64_t key = set_key(ps, alpha, beta, dev);
+    key = set_key(all, alpha.data(), beta.data(), dev);
     std::lock_guard<std::mutex> lk(g_graph_mu);
     for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {
       if (it->key != key) continue;
       g_graphs.splice(g_graphs.begin(), g_graphs, it);
       return cudaGraphLaunch(g_graphs.front().exec, s) == cudaSuccess ? FAMLIES_OK : FAMLIES_ERR_CUDA;
     }
-    // build: persistent workspace and descriptors, tune, capture, replay
-    char *ws = nullptr, *d_blob = nullptr;
-    if (cudaMalloc((void**)&ws, G.ws_total + 256) != cudaSuccess) {
-      cudaGetLastError();
-      return FAMLIES_ERR_ALLOC;
-    }
-    std::vector<char> blob;
-    if (!build_blob(ps, alpha, beta, G, 256, ws, nullptr, status, wait_limit, blob)) {
-      cudaFree(ws);
-      return FAMLIES_ERR_CUDA;
-    }
-    // prepare once on the caller's stream so that the tuner can time the product
-    const size_t max_blob = G.blob_bytes;
-    if (cudaMalloc((void**)&d_blob, max_blob + 65536) != cudaSuccess) {
-      cudaGetLastError();
-      cudaFree(ws);
-      return FAMLIES_ERR_ALLOC;
-    }
-    build_blob(ps, alpha, beta, G, 256, ws, d_blob, status, wait_limit, blob);
-    cudaMemcpyAsync(d_blob, blob.data(), G.blob_bytes, cudaMemcpyHostToDevice, s);
-    DevPtrs d = dev_ptrs(G, d_blob);
-    if (enqueue_prepare(G, ws, d, s) != cudaSuccess) {
-      cudaGetLastError();
-      cudaStreamSynchronize(s);
-      cudaFree(ws);
-      cudaFree(d_blob);
-      return FAMLIES_ERR_CUDA;
-    }
-    const int bn = pick_bn(ps, alpha, beta, G, ws, status, wait_limit, s, true);
-    // the final descriptors for the chosen width (tile list depends on it)
-    GroupSetup Gf = G;
-    build_blob(ps, alpha, beta, Gf, bn, ws, d_blob, status, wait_limit, blob);
-    if (Gf.blob_bytes > max_blob + 65536) {
-      cudaStreamSynchronize(s);
-      cudaFree(d_blob);
-      if (cudaMalloc((void**)&d_blob, Gf.blob_bytes) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(ws);
-        return FAMLIES_ERR_ALLOC;
-      }
-      build_blob(ps, alpha, beta, Gf, bn, ws, d_blob, status, wait_limit, blob);
-    }
-    cudaStreamSynchronize(s);
-    cudaMemcpy(d_blob, blob.data(), Gf.blob_bytes, cudaMemcpyHostToDevice);
-    d = dev_ptrs(Gf, d_blob);
-    cudaStream_t cs;
-    cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      cudaError_t e1 = enqueue_prepare(Gf, ws, d, cs);
-      cudaError_t e2 = enqueue_product(Gf, bn, d.probs, d.tiles, ws, status, wait_limit, cs);
-      cudaError_t e3 = enqueue_finish(Gf, d, cs);
-      e = cudaStreamEndCapture(cs, &graph);
-      if (e == cudaSuccess && (e1 || e2 || e3)) e = e1 ? e1 : (e2 ? e2 : e3);
-    }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-    if (graph) cudaGraphDestroy(graph);
-    cudaStreamDestroy(cs);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      cudaFree(ws);
-      cudaFree(d_blob);
-      return FAMLIES_ERR_CUDA;
-    }
-    if (g_graphs.size() >= kGraphCap) {
-      cudaDeviceSynchronize();  // an evicted graph may still run on some stream
-      GraphEntry& old = g_graphs.back();
-      cudaGraphExecDestroy(old.exec);
-      cudaFree(old.ws);
-      cudaFree(old.blob);
-      g_graphs.pop_back();
-    }
-    g_graphs.push_front(GraphEntry{key, ws, d_blob, exec});
-    return cudaGraphLaunch(exec, s) == cudaSuccess ? FAMLIES_OK : FAMLIES_ERR_CUDA;
   }
-
-  // no graph: stream-ordered workspace, one descriptor copy, five launches
-  char *ws = nullptr, *d_blob = nullptr;
-  if (cudaMallocAsync((void**)&ws, G.ws_total + 256, s) != cudaSuccess) {
-    cudaGetLastError();
-    return FAMLIES_ERR_ALLOC;
-  }
-  std::vector<char> blob;
-  if (!build_blob(ps, alpha, beta, G, 256, ws, nullptr, status, wait_limit, blob)) {
-    cudaFreeAsync(ws, s);
-    return FAMLIES_ERR_CUDA;
-  }
-  // descriptors sized for the narrowest width (the largest tile list)
-  GroupSetup G64 = G;
-  build_blob(ps, alpha, beta, G64, 64, ws, nullptr, status, wait_limit, blob);
-  const size_t cap = std::max(G.blob_bytes, G64.blob_bytes);
-  if (cudaMallocAsync((void**)&d_blob, cap, s) != cudaSuccess) {
-    cudaGetLastError();
-    cudaFreeAsync(ws, s);
-    return FAMLIES_ERR_ALLOC;
-  }
-  build_blob(ps, alpha, beta, G, 256, ws, d_blob, status, wait_limit, blob);
-  cudaMemcpyAsync(d_blob, blob.data(), G.blob_bytes, cudaMemcpyHostToDevice, s);
-  DevPtrs d = dev_ptrs(G, d_blob);
-  cudaError_t e = enqueue_prepare(G, ws, d, s);
-  int bn = 256;
-  if (e == cudaSuccess) {
-    bn = pick_bn(ps, alpha, beta, G, ws, status, wait_limit, s, true);
-    if (bn != 256) {
-      build_blob(ps, alpha, beta, G, bn, ws, d_blob, status, wait_limit, blob);
-      cudaMemcpyAsync(d_blob, blob.data(), G.blob_bytes, cudaMemcpyHostToDevice, s);
-      d = dev_ptrs(G, d_blob);
-    }
-    e = enqueue_product(G, bn, d.probs, d.tiles, ws, status, wait_limit, s);
-  }
-  if (e == cudaSuccess) e = enqueue_finish(G, d, s);
-  // the host image must outlive the (pageable, staged) copies: they complete
-  // before cudaMemcpyAsync returns for pageable memory
-  cudaFreeAsync(d_blob, s);
-  cudaFreeAsync(ws, s);
+  // workspace (one, reused by the chunks in turn) and descriptor blocks
+  char* ws = nullptr;
+  cudaError_t e = use_graph ? cudaMalloc((void**)&ws, ws_max + 256)
+                            : cudaMallocAsync((void**)&ws, ws_max + 256, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    return FAMLIES_ERR_ALLOC;
+  }
+  auto release = [&]() {
+    for (ChunkRun& r : chunks) {
+      if (!r.d_blob) continue;
+      if (use_graph) cudaFree(r.d_blob); else cudaFreeAsync(r.d_blob, s);
+      r.d_blob = nullptr;
+    }
+    if (use_graph) cudaFree(ws); else cudaFreeAsync(ws, s);
+  };
+  for (ChunkRun& r : chunks) {
+    r.blob_cap = blob_capacity(r, ws, status, wait_limit);
+    e = use_graph ? cudaMalloc((void**)&r.d_blob, r.blob_cap)
+                  : cudaMallocAsync((void**)&r.d_blob, r.blob_cap, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      r.d_blob = nullptr;
+      if (use_graph) cudaStreamSynchronize(s);
+      release();
+      return FAMLIES_ERR_ALLOC;
+    }
+  }
+  // Eager part on the caller's stream.  Without a graph: every stage of
+  // every chunk.  With a graph: only what the tuner needs (the packed slices
+  // of a chunk whose shape class has no tuned width yet); the graph below
+  // then computes the result exactly once.
+  int rc = FAMLIES_OK;
+  for (ChunkRun& r : chunks) {
+    const std::string tk = tune_key(r.ps);
+    bool tuned;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(tk);
+      tuned = it != g_tune.end();
+      r.bn = tuned ? it->second : heuristic_bn(r.ps);
+    }
+    const bool need_prepare = !use_graph || !tuned;
+    if (!need_prepare) continue;
+    if (!build_blob(r.ps, r.alpha, r.beta, r.G, r.bn, ws, r.d_blob, status, wait_limit, r.blob)) {
+      rc = FAMLIES_ERR_CUDA;
+      break;
+    }
+    cudaMemcpyAsync(r.d_blob, r.blob.data(), r.G.blob_bytes, cudaMemcpyHostToDevice, s);
+    DevPtrs d = dev_ptrs(r.G, r.d_blob);
+    if (enqueue_prepare(r.G, ws, d, s) != cudaSuccess) { rc = FAMLIES_ERR_CUDA; break; }
+    if (!tuned) {
+      const int bn = pick_bn(r.ps, r.alpha, r.beta, r.G, ws, status, wait_limit, s, true);
+      if (bn != r.bn) {
+        r.bn = bn;
+        build_blob(r.ps, r.alpha, r.beta, r.G, r.bn, ws, r.d_blob, status, wait_limit, r.blob);
+        cudaMemcpyAsync(r.d_blob, r.blob.data(), r.G.blob_bytes, cudaMemcpyHostToDevice, s);
+        d = dev_ptrs(r.G, r.d_blob);
+      }
+    }
+    if (!use_graph) {
+      if (enqueue_product(r.G, r.bn, d.probs, d.tiles, ws, status, wait_limit, s) != cudaSuccess ||
+          enqueue_finish(r.G, d, s) != cudaSuccess) {
+        rc = FAMLIES_ERR_CUDA;
+        break;
+      }
+    }
+  }
+  if (rc != FAMLIES_OK || !use_graph) {
+    cudaGetLastError();
+    release();
+    return rc;
+  }
+
+  // Graph: final descriptors of every chunk, then one capture of all stages
+  // of all chunks in order (they share the workspace), instantiate, replay.
+  cudaStreamSynchronize(s);
+  for (ChunkRun& r : chunks) {
+    build_blob(r.ps, r.alpha, r.beta, r.G, r.bn, ws, r.d_blob, status, wait_limit, r.blob);
+    cudaMemcpy(r.d_blob, r.blob.data(), r.G.blob_bytes, cudaMemcpyHostToDevice);
+  }
+  cudaStream_t cs;
+  cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t ek = cudaSuccess;
+    for (ChunkRun& r : chunks) {
+      const DevPtrs d = dev_ptrs(r.G, r.d_blob);
+      if (ek == cudaSuccess) ek = enqueue_prepare(r.G, ws, d, cs);
+      if (ek == cudaSuccess) ek = enqueue_product(r.G, r.bn, d.probs, d.tiles, ws, status, wait_limit, cs);
+      if (ek == cudaSuccess) ek = enqueue_finish(r.G, d, cs);
+    }
+    e = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess && ek != cudaSuccess) e = ek;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    release();
     return FAMLIES_ERR_CUDA;
   }
-  return FAMLIES_OK;
-}
-
-}  // namespace
-
-int run_grouped(const std::vector<const Plan*>& ps, const std::vector<double>& alpha,
-                const std::vector<double>& beta, cudaStream_t s, bool use_graph, int* status,
-                int64_t wait_limit) {
-  if (ps.empty()) return FAMLIES_OK;
-  // split into chunks whose workspace fits half of the free device memory
-  size_t free_b = 0, total_b = 0;
-  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
-    cudaGetLastError();
-    free_b = (size_t)16 << 30;
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  if (g_graphs.size() >= kGraphCap) {
+    cudaDeviceSynchronize();  // an evicted graph may still run on some stream
+    GraphEntry& old = g_graphs.back();
+    cudaGraphExecDestroy(old.exec);
+    for (char* b : old.blobs) cudaFree(b);
+    cudaFree(old.ws);
+    g_graphs.pop_back();
   }
-  const char* env = std::getenv("FAMLIES_BATCH_WORKSPACE_MB");
-  size_t budget = env ? (size_t)std::atoll(env) << 20 : free_b / 2;
-  if (budget < ((size_t)64 << 20)) budget = (size_t)64 << 20;
-  size_t i0 = 0;
-  while (i0 < ps.size()) {
-    size_t i1 = i0 + 1;
-    std::vector<const Plan*> chunk{ps[i0]};
-    while (i1 < ps.size()) {
-      chunk.push_back(ps[i1]);
-      if (layout_group(chunk, 256).ws_total > budget) { chunk.pop_back(); break; }
-      ++i1;
-    }
-    int rc = run_chunk(chunk, alpha.data() + i0, beta.data() + i0, s, use_graph, status, wait_limit);
-    if (rc) return rc;
-    i0 = i1;
-  }
-  return FAMLIES_OK;
+  GraphEntry ge;
+  ge.key = key;
+  ge.ws = ws;
+  ge.exec = exec;
+  for (ChunkRun& r : chunks) ge.blobs.push_back(r.d_blob);
+  g_graphs.push_front(ge);
+  return cudaGraphLaunch(exec, s) == cudaSuccess ? FAMLIES_OK : FAMLIES_ERR_CUDA;
 }
 
 }  // namespace famlies

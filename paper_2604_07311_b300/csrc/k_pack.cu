@@ -35,12 +35,14 @@ __device__ __forceinline__ void exp_update(double v, int& mx, int& bad) {
   else mx = max(mx, max(E, 1) - 1022);
 }
 
-__device__ __forceinline__ void rowexp_body(const PackArgs& pa, const PackOp& o) {
+// Processes tiles b0, b0 + bstep, ... of one operand.
+__device__ __forceinline__ void rowexp_body(const PackArgs& pa, const PackOp& o, int64_t b0,
+                                            int64_t bstep) {
   const double* __restrict__ X = (const double*)o.x;
   const int64_t tiles_r = (o.rows + PR - 1) / PR, tiles_k = (pa.k + KCH - 1) / KCH;
   __shared__ int smx[4][PR], sbad[4][PR];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int64_t b = blockIdx.x; b < tiles_r * tiles_k * pa.l; b += gridDim.x) {
+  for (int64_t b = b0; b < tiles_r * tiles_k * pa.l; b += bstep) {
     const int64_t tr = b % tiles_r, rest = b / tiles_r;
     const int64_t tk = rest % tiles_k, il = rest / tiles_k;
     const int64_t lo = o.loff[il];
@@ -96,14 +98,15 @@ __device__ __forceinline__ uint32_t tf32_bits(float x) {
 }
 
 template <int PMODE>
-__device__ __forceinline__ void pack_body(const PackArgs& pa, const PackOp& o) {
+__device__ __forceinline__ void pack_body(const PackArgs& pa, const PackOp& o, int64_t b0,
+                                          int64_t bstep) {
   using T = typename PackT<PMODE>::T;
   __shared__ T tile[PR][PK + 1];
   const T* __restrict__ X = (const T*)o.x;
   const int64_t tiles_r = (o.rows + PR - 1) / PR, tiles_k = (pa.k + PK - 1) / PK;
   const size_t slice_stride = (size_t)pa.l * o.rows * pa.kp;  // elements per slice
   const int tid = threadIdx.x;
-  for (int64_t b = blockIdx.x; b < tiles_r * tiles_k * pa.l; b += gridDim.x) {
+  for (int64_t b = b0; b < tiles_r * tiles_k * pa.l; b += bstep) {
     const int64_t tr = b % tiles_r, rest = b / tiles_r;
     const int64_t tk = rest % tiles_k, il = rest / tiles_k;
     const int64_t lo = o.loff[il];
@@ -242,24 +245,54 @@ int grid_for(int64_t blocks) {
 }
 
 // One problem per launch: blockIdx.z picks the operand.
-__global__ void __launch_bounds__(256) k_rowexp(PackArgs pa) { rowexp_body(pa, pa.op[blockIdx.z]); }
+__global__ void __launch_bounds__(256) k_rowexp(PackArgs pa) {
+  rowexp_body(pa, pa.op[blockIdx.z], blockIdx.x, gridDim.x);
+}
 
 template <int PMODE>
-__global__ void __launch_bounds__(256) k_pack(PackArgs pa) { pack_body<PMODE>(pa, pa.op[blockIdx.z]); }
+__global__ void __launch_bounds__(256) k_pack(PackArgs pa) {
+  pack_body<PMODE>(pa, pa.op[blockIdx.z], blockIdx.x, gridDim.x);
+}
 
 __global__ void __launch_bounds__(256) k_fixup(GemmArgs g, const int32_t* list_a,
                                                const int32_t* list_b, const int32_t* flag_a) {
   fixup_body(g, list_a, list_b, flag_a);
 }
 
-// Many problems per launch: blockIdx.y walks the problems.
-__global__ void __launch_bounds__(256) k_rowexp_grouped(const PackArgs* __restrict__ pas, int n) {
-  for (int p = blockIdx.y; p < n; p += gridDim.y) rowexp_body(pas[p], pas[p].op[blockIdx.z]);
+// Many problems per launch.  The tiles of every (problem, operand) segment
+// are numbered consecutively (off[s] = first tile of segment s = 2p + op,
+// off[nseg] = total); the blocks stride over that flat range, so large and
+// small problems share the grid evenly.
+__device__ __forceinline__ int segment_of(const int64_t* off, int nseg, int64_t g) {
+  int lo = 0, hi = nseg;  // largest s with off[s] <= g
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= g) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int64_t kOneTile = (int64_t)1 << 62;  // a step that ends a body's loop after one tile
+
+__global__ void __launch_bounds__(256) k_rowexp_grouped(const PackArgs* __restrict__ pas,
+                                                        const int64_t* __restrict__ off, int nseg) {
+  const int64_t total = off[nseg];
+  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+    const int s = segment_of(off, nseg, g);
+    const PackArgs& pa = pas[s >> 1];
+    rowexp_body(pa, pa.op[s & 1], g - off[s], kOneTile);
+  }
 }
 
 template <int PMODE>
-__global__ void __launch_bounds__(256) k_pack_grouped(const PackArgs* __restrict__ pas, int n) {
-  for (int p = blockIdx.y; p < n; p += gridDim.y) pack_body<PMODE>(pas[p], pas[p].op[blockIdx.z]);
+__global__ void __launch_bounds__(256) k_pack_grouped(const PackArgs* __restrict__ pas,
+                                                      const int64_t* __restrict__ off, int nseg) {
+  const int64_t total = off[nseg];
+  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+    const int s = segment_of(off, nseg, g);
+    const PackArgs& pa = pas[s >> 1];
+    pack_body<PMODE>(pa, pa.op[s & 1], g - off[s], kOneTile);
+  }
 }
 
 __global__ void __launch_bounds__(256) k_fixup_grouped(const GemmArgs* __restrict__ gs,
@@ -270,28 +303,27 @@ __global__ void __launch_bounds__(256) k_fixup_grouped(const GemmArgs* __restric
 
 }  // namespace
 
-// Blocks per problem: enough for ~8 blocks per SM in total, at most what the
-// largest problem can use.
-static int64_t grouped_gx(int n, int64_t max_blocks) {
-  int64_t gx = ((int64_t)num_sms() * 8 + n - 1) / n;
-  if (gx > max_blocks) gx = max_blocks;
-  return gx < 1 ? 1 : (gx > 65535 ? 65535 : gx);
+int64_t rowexp_tiles(int64_t rows, int64_t k, int64_t l) {
+  return ((rows + PR - 1) / PR) * ((k + KCH - 1) / KCH) * l;
+}
+int64_t pack_tiles(int64_t rows, int64_t k, int64_t l) {
+  return ((rows + PR - 1) / PR) * ((k + PK - 1) / PK) * l;
 }
 
-cudaError_t launch_rowexp_grouped(const PackArgs* pas, int n, int64_t max_blocks, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const dim3 grid((unsigned)grouped_gx(n, max_blocks), (unsigned)(n > 32768 ? 32768 : n), 2);
-  k_rowexp_grouped<<<grid, 256, 0, s>>>(pas, n);
+cudaError_t launch_rowexp_grouped(const PackArgs* pas, const int64_t* off, int n, int64_t total,
+                                  cudaStream_t s) {
+  if (n <= 0 || total <= 0) return cudaSuccess;
+  k_rowexp_grouped<<<grid_for(total), 256, 0, s>>>(pas, off, 2 * n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_grouped(int pmode, const PackArgs* pas, int n, int64_t max_blocks,
-                                cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const dim3 grid((unsigned)grouped_gx(n, max_blocks), (unsigned)(n > 32768 ? 32768 : n), 2);
-  if (pmode == PACK_BF16) k_pack_grouped<PACK_BF16><<<grid, 256, 0, s>>>(pas, n);
-  else if (pmode == PACK_TF32) k_pack_grouped<PACK_TF32><<<grid, 256, 0, s>>>(pas, n);
-  else k_pack_grouped<PACK_F64><<<grid, 256, 0, s>>>(pas, n);
+cudaError_t launch_pack_grouped(int pmode, const PackArgs* pas, const int64_t* off, int n,
+                                int64_t total, cudaStream_t s) {
+  if (n <= 0 || total <= 0) return cudaSuccess;
+  const int grid = grid_for(total);
+  if (pmode == PACK_BF16) k_pack_grouped<PACK_BF16><<<grid, 256, 0, s>>>(pas, off, 2 * n);
+  else if (pmode == PACK_TF32) k_pack_grouped<PACK_TF32><<<grid, 256, 0, s>>>(pas, off, 2 * n);
+  else k_pack_grouped<PACK_F64><<<grid, 256, 0, s>>>(pas, off, 2 * n);
   return cudaGetLastError();
 }
 

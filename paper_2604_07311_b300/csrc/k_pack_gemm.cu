@@ -172,6 +172,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         const CUtensorMap* mb = GROUPED ? T.P->map_b : &map_b;
         const int nkb = (int)((T.P->k + Cfg::KB - 1) / Cfg::KB);
         const int l = (int)T.P->l;
+        const int bnp = GROUPED ? T.P->bn : BN;  // this tile's width
+        const uint32_t stage_tx = (uint32_t)(Cfg::A_BYTES + bnp * 128);
         for (int di = 0; di < sc.ndiag && ok; ++di) {
           const int kcb = sc.kcb[di];
           for (int kb0 = 0; kb0 < nkb && ok; kb0 += kcb) {
@@ -183,10 +185,10 @@ __global__ void __launch_bounds__(THREADS, 1)
               for (int kb = kb0; kb < kb1; ++kb) {
                 if (!ptx::mbar_wait(&empty[stage], phase ^ 1, lim, abort)) { ok = false; break; }
                 uint8_t* sa = smem + stage * Cfg::STAGE_BYTES;
-                ptx::mbar_arrive_expect_tx(&full[stage], Cfg::STAGE_BYTES);
+                ptx::mbar_arrive_expect_tx(&full[stage], stage_tx);
                 ptx::tma_load_3d(sa, ma, &full[stage], kb * Cfg::KB, (int)(T.tm * BM), za);
                 ptx::tma_load_3d(sa + Cfg::A_BYTES, mb, &full[stage], kb * Cfg::KB,
-                                 (int)(T.tn * BN), zb);
+                                 (int)(T.tn * bnp), zb);
                 pending = (pending & ~(0x101u << stage)) | (1u << stage) | (phase << (stage + 8));
                 if (++stage == STAGES) { stage = 0; phase ^= 1; }
               }
@@ -214,6 +216,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const TileRef T = tile_at<BN, GROUPED>(args, t);
         const int nkb = (int)((T.P->k + Cfg::KB - 1) / Cfg::KB);
+        // the MMA's N is this tile's width (the instruction descriptor's N field)
+        const uint32_t idesc =
+            GROUPED ? ptx::idesc_make(BM, T.P->bn, KIND == PAIR_KIND_BF16 ? 1u : 2u) : Cfg::IDESC;
         for (int di = 0; di < sc.ndiag && ok; ++di) {
           const int kcb = sc.kcb[di];
           for (int kb0 = 0; kb0 < nkb && ok; kb0 += kcb) {
@@ -232,9 +237,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                 for (int kk = 0; kk < Cfg::KSTEPS; ++kk) {
                   if (KIND == PAIR_KIND_BF16)
-                    ptx::mma_f16(dt, da + 2 * kk, db + 2 * kk, Cfg::IDESC, accumulate);
+                    ptx::mma_f16(dt, da + 2 * kk, db + 2 * kk, idesc, accumulate);
                   else
-                    ptx::mma_tf32(dt, da + 2 * kk, db + 2 * kk, Cfg::IDESC, accumulate);
+                    ptx::mma_tf32(dt, da + 2 * kk, db + 2 * kk, idesc, accumulate);
                   accumulate = 1;
                 }
                 ptx::mma_commit(&empty[stage]);
@@ -267,7 +272,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int nkb = (int)((P.k + Cfg::KB - 1) / Cfg::KB);
       const int64_t il = T.il;
       const int64_t row = T.tm * BM + qd * 32 + lane;
-      const int64_t col0 = T.tn * BN + hf * CPT;
+      const int bnp = GROUPED ? P.bn : BN;  // this tile's width
+      const int lc0 = hf * CPT;             // first tile-local column of this thread
+      const int64_t col0 = T.tn * bnp + lc0;
       const bool rv = row < P.m;
       const int64_t crow = rv ? P.cl[il] + P.cm[row] : 0;
       if (MODE == PAIR_MODE_F32OUT) {
@@ -282,6 +289,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           ptx::tc_fence_after();
 #pragma unroll
           for (int q = 0; q < CPT / 32; ++q) {
+            if (lc0 + q * 32 >= bnp) continue;  // beyond this tile's width (warp-uniform)
             uint32_t r[32];
             ptx::tmem_ld32(tmem_base + lane_addr + acc * BN + hf * CPT + q * 32, r);
             ptx::tmem_ld_wait();
@@ -302,7 +310,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int j = 0; j < CPT; ++j) {
             const int64_t col = col0 + j;
-            if (col < P.n) {
+            if (lc0 + j < bnp && col < P.n) {
               float* p = C + crow + P.cn[col];
               float v = alpha * S[j];
               if (beta != 0.f) v = fmaf(beta, *p, v);
@@ -325,6 +333,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             ptx::tc_fence_after();
 #pragma unroll
             for (int q = 0; q < CPT / 32; ++q) {
+              if (lc0 + q * 32 >= bnp) continue;  // beyond this tile's width (warp-uniform)
               uint32_t r[32];
               ptx::tmem_ld32(tmem_base + lane_addr + acc * BN + hf * CPT + q * 32, r);
               ptx::tmem_ld_wait();
@@ -357,7 +366,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
               for (int j = 0; j < CPT; ++j) {
                 const int64_t col = col0 + j;
-                if (col < P.n && !fbl[col]) {
+                if (lc0 + j < bnp && col < P.n && !fbl[col]) {
                   const double prev = first_flush ? 0.0 : Gt[(size_t)j * BM];
                   const double sum = fma(w, (double)S[j], prev);
                   const int e = er + ebl[col];
@@ -603,7 +612,7 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   PairArgs a;
   std::memset(&a, 0, sizeof(a));
   a.single = Prob{nullptr, nullptr, g.c, g.t.cm, g.t.cn, g.t.cl, pa.op[0].e, pa.op[1].e,
-                  pa.op[0].flag, pa.op[1].flag, p.m, p.n, p.k, p.l, g.alpha, g.beta};
+                  pa.op[0].flag, pa.op[1].flag, p.m, p.n, p.k, p.l, g.alpha, g.beta, bn};
   a.sc = make_pair_sched(p.kernel, p.slices, bits);
   a.G = emu ? (double*)(w + L.G) : nullptr;
   a.status = g.status;

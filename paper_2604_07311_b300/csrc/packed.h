@@ -39,10 +39,15 @@ cudaError_t launch_pack(int pmode, const PackArgs& pa, cudaStream_t s);
 cudaError_t launch_fixup(const GemmArgs& g, const PackArgs& pa, cudaStream_t s);
 
 // Grouped forms: n problems' PackArgs / GemmArgs in device memory, one launch
-// each; max_blocks bounds the tiles of the largest problem.
-cudaError_t launch_rowexp_grouped(const PackArgs* pas, int n, int64_t max_blocks, cudaStream_t s);
-cudaError_t launch_pack_grouped(int pmode, const PackArgs* pas, int n, int64_t max_blocks,
-                                cudaStream_t s);
+// each.  off[2n+1] (device) numbers the tiles of segment s = 2*problem +
+// operand from off[s]; off[2n] = total.  The tile counts per segment come
+// from rowexp_tiles / pack_tiles.
+int64_t rowexp_tiles(int64_t rows, int64_t k, int64_t l);
+int64_t pack_tiles(int64_t rows, int64_t k, int64_t l);
+cudaError_t launch_rowexp_grouped(const PackArgs* pas, const int64_t* off, int n, int64_t total,
+                                  cudaStream_t s);
+cudaError_t launch_pack_grouped(int pmode, const PackArgs* pas, const int64_t* off, int n,
+                                int64_t total, cudaStream_t s);
 cudaError_t launch_fixup_grouped(const GemmArgs* gs, const PackArgs* pas, int n, cudaStream_t s);
 
 }  // namespace famlies

@@ -43,6 +43,7 @@ struct Prob {
   const int32_t* fb;
   int64_t m, n, k, l;
   double alpha, beta;
+  int bn;  // grouped launches: this problem's tile width (64, 128 or 256, <= the launch's)
 };
 
 // One entry of a grouped launch's tile list: problem, row tile, column tile, batch.
