@@ -39,6 +39,17 @@ int check_device() {
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
     cudaGetLastError();
     cached[dev] = (major == 10 && minor == 3) ? FAMLIES_OK : FAMLIES_ERR_NO_DEVICE;
+    if (cached[dev] == FAMLIES_OK) {
+      // Keep freed stream-ordered workspace mapped in the device's default
+      // pool between calls instead of returning it at every synchronisation
+      // (re-mapping gigabytes of slices each call costs milliseconds).
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      }
+      cudaGetLastError();
+    }
   }
   return cached[dev];
 }

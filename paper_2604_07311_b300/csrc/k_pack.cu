@@ -170,19 +170,24 @@ __device__ __forceinline__ void pack_body(const PackArgs& pa, const PackOp& o, i
           }
           F[j] = (bitsx >> 63) ? -f : f;
         }
-        int32_t dig[8][8];  // [slice][element]
+        // Peeling the digits from the bottom (d = ((F + h) & mask) - h,
+        // F = (F - d) >> b) is the same as adding the bias
+        // h * (1 + 2^b + ... + 2^(b(S-2))) once and reading the lower S-1
+        // digits as b-bit fields minus h; the top digit is what remains
+        // above them (arithmetic shift).  No digit then waits on another.
+        int64_t bias = 0;
+        for (int s = 0; s < S - 1; ++s) bias += half << (b * s);
+        int32_t dig[8][8];  // [slice][element], slice 0 most significant
 #pragma unroll
-        for (int s = 7; s >= 1; --s) {
-          if (s >= S) continue;
+        for (int j = 0; j < 8; ++j) {
+          const int64_t G = F[j] + bias;
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int64_t d = ((F[j] + half) & mask) - half;
-            F[j] = (F[j] - d) >> b;
-            dig[s][j] = (int32_t)d;
+          for (int s = 1; s < 8; ++s) {
+            if (s >= S) break;
+            dig[s][j] = (int32_t)((G >> (b * (S - 1 - s))) & mask) - (int32_t)half;
           }
+          dig[0][j] = (int32_t)(G >> (b * (S - 1)));
         }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) dig[0][j] = (int32_t)F[j];
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
           if (s >= S) break;
