@@ -123,14 +123,23 @@ def dist_setup():
 
 
 def barrier_max(x: float, world: int) -> float:
+    """Max of x over the ranks (after a barrier); x itself on one rank."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], device="cuda", dtype=torch.float64)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
     dist.barrier()
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(local_ms: float, flops_per_rank: float, world: int):
+    """Whole-job (ms, TFLOP/s): every replica does the same work, the slowest
+    rank's time counts."""
+    ms = barrier_max(local_ms, world)
+    return ms, world * flops_per_rank / (ms * 1e-3) / 1e12
 
 
 def make_inputs():
@@ -220,9 +229,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
-    ms = start.elapsed_time(end) / args.steps
-    ms = barrier_max(ms, world)
-    value = world * flops / (ms * 1e-3) / 1e12
+    ms, value = replica_throughput(start.elapsed_time(end) / args.steps, flops, world)
     launches = info["launches"] * args.steps
 
     # ---- the product kernel alone (events recorded by the library around it)
