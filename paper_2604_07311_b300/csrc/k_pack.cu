@@ -177,27 +177,23 @@ __device__ __forceinline__ void pack_body(const PackArgs& pa, const PackOp& o, i
         // above them (arithmetic shift).  No digit then waits on another.
         int64_t bias = 0;
         for (int s = 0; s < S - 1; ++s) bias += half << (b * s);
-        int32_t dig[8][8];  // [slice][element], slice 0 most significant
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int64_t G = F[j] + bias;
-#pragma unroll
-          for (int s = 1; s < 8; ++s) {
-            if (s >= S) break;
-            dig[s][j] = (int32_t)((G >> (b * (S - 1 - s))) & mask) - (int32_t)half;
-          }
-          dig[0][j] = (int32_t)(G >> (b * (S - 1)));
-        }
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-          if (s >= S) break;
+        for (int j = 0; j < 8; ++j) F[j] += bias;
+        // slice 0 (most significant) first; each slice's digits are read
+        // straight from the biased values, so only those stay in registers
+        for (int s = 0; s < S; ++s) {
+          const int sh2 = b * (S - 1 - s);
           uint32_t w[4];
 #pragma unroll
           for (int j = 0; j < 8; j += 2) {
+            const int32_t d0 = s == 0 ? (int32_t)(F[j] >> sh2)
+                                      : (int32_t)((F[j] >> sh2) & mask) - (int32_t)half;
+            const int32_t d1 = s == 0 ? (int32_t)(F[j + 1] >> sh2)
+                                      : (int32_t)((F[j + 1] >> sh2) & mask) - (int32_t)half;
             // small integers are exact in fp32 and bf16: 1.5 * 2^23 + d holds
             // d in its low significand bits, and the subtraction is exact
-            const float f0 = __int_as_float(0x4B400000 + dig[s][j]) - 12582912.0f;
-            const float f1 = __int_as_float(0x4B400000 + dig[s][j + 1]) - 12582912.0f;
+            const float f0 = __int_as_float(0x4B400000 + d0) - 12582912.0f;
+            const float f1 = __int_as_float(0x4B400000 + d1) - 12582912.0f;
             w[j / 2] = (__float_as_uint(f0) >> 16) | (__float_as_uint(f1) & 0xFFFF0000u);
           }
           *(uint4*)((uint16_t*)o.out + (size_t)s * slice_stride + rowbase) =
@@ -308,6 +304,8 @@ __global__ void __launch_bounds__(256) k_fixup_grouped(const GemmArgs* __restric
 
 }  // namespace
 
+static void prefer_shared_carveout();
+
 int64_t rowexp_tiles(int64_t rows, int64_t k, int64_t l) {
   return ((rows + PR - 1) / PR) * ((k + KCH - 1) / KCH) * l;
 }
@@ -325,6 +323,7 @@ cudaError_t launch_rowexp_grouped(const PackArgs* pas, const int64_t* off, int n
 cudaError_t launch_pack_grouped(int pmode, const PackArgs* pas, const int64_t* off, int n,
                                 int64_t total, cudaStream_t s) {
   if (n <= 0 || total <= 0) return cudaSuccess;
+  prefer_shared_carveout();
   const int grid = grid_for(total);
   if (pmode == PACK_BF16) k_pack_grouped<PACK_BF16><<<grid, 256, 0, s>>>(pas, off, 2 * n);
   else if (pmode == PACK_TF32) k_pack_grouped<PACK_TF32><<<grid, 256, 0, s>>>(pas, off, 2 * n);
@@ -349,7 +348,25 @@ cudaError_t launch_rowexp(const PackArgs& pa, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The pack kernels stage 64 x 64 tiles in shared memory (33 KB for fp64):
+// ask for the largest shared-memory carveout so that several blocks fit
+// per SM and keep enough loads in flight.
+static void prefer_shared_carveout() {
+  static bool done = false;
+  if (done) return;
+  const int c = cudaSharedmemCarveoutMaxShared;
+  cudaFuncSetAttribute(k_pack<PACK_BF16>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+  cudaFuncSetAttribute(k_pack<PACK_TF32>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+  cudaFuncSetAttribute(k_pack<PACK_F64>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+  cudaFuncSetAttribute(k_pack_grouped<PACK_BF16>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+  cudaFuncSetAttribute(k_pack_grouped<PACK_TF32>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+  cudaFuncSetAttribute(k_pack_grouped<PACK_F64>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+  cudaGetLastError();
+  done = true;
+}
+
 cudaError_t launch_pack(int pmode, const PackArgs& pa, cudaStream_t s) {
+  prefer_shared_carveout();
   int64_t blocks = 0;
   for (int i = 0; i < 2; ++i) {
     const int64_t b = ((pa.op[i].rows + PR - 1) / PR) * ((pa.k + PK - 1) / PK) * pa.l;
