@@ -319,8 +319,108 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+def _cuda_ms(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(steps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / steps
+
+
+def _product_ms(fn, n=5):
+    import torch
+    evs = []
+    for _ in range(n):
+        b, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn(events=(b, e))
+        evs.append((b, e))
+    torch.cuda.synchronize()
+    return statistics.mean(b.elapsed_time(e) for b, e in evs)
+
+
+def run_other(args):
+    """Secondary workloads (one JSON line each): not the headline metric."""
+    import torch
+    import paper_2604_07311_b300 as fm
+    from paper_2604_07311_b300 import inputs as W
+    torch.cuda.set_device(0)
+    burst, sustained, src = peaks()
+
+    def put(op, dt):
+        buf = torch.from_numpy(op.buf).to(device="cuda", dtype=dt)
+        return torch.as_strided(buf, op.extents, op.strides)
+
+    if args.workload == "transpose_free":
+        p = W.transpose_free(v=96, o=48, pad=7)
+        for dt, kind, pairs in (("bf16", 2, 1), ("bf16", 3, 1), ("f32", 2, 3), ("f32", 3, 3), ("f32", 1, 1)):
+            tin = torch.bfloat16 if dt == "bf16" else torch.float32
+            A, B, C = put(p.A, tin), put(p.B, tin), put(p.C, torch.float32)
+            f = lambda **kw: fm.contract(1.0, A, p.A.labels, B, p.B.labels, 0.0, C, p.C.labels,
+                                         dtype=dt, kernel=kind, **kw)
+            ms = _cuda_ms(f, args.steps, args.warmup)
+            kms = _product_ms(f)
+            print(json.dumps({"workload": "transpose_free_v96_o48_pad7", "dtype": dt,
+                              "path": {1: "cuda_cores", 2: "packed_tma", 3: "direct_gather"}[kind],
+                              "ms_per_step": ms, "tflops": p.flops / ms / 1e9, "product_ms": kms,
+                              "product_exec_tflops": pairs * p.flops / kms / 1e9,
+                              "bf16_peak_sustained": sustained, "peak_source": src}), flush=True)
+    elif args.workload == "autograd":
+        from paper_2604_07311_b300.autograd import contract_autograd
+        d = W.autograd_problem()
+        A = torch.from_numpy(d["A"].astype(np.float32)).cuda().requires_grad_()
+        B = torch.from_numpy(d["B"].astype(np.float32)).cuda().requires_grad_()
+        T = torch.from_numpy(d["T"].astype(np.float32)).cuda()
+
+        def fb():
+            A.grad = B.grad = None
+            ((contract_autograd(A, d["la"], B, d["lb"], d["lc"]) - T) ** 2).sum().backward()
+        ms = _cuda_ms(fb, args.steps, args.warmup)
+        fl = 3 * 2 * 64 * 64 * 64 * 48 * 48
+        print(json.dumps({"workload": "autograd_i64_k48_fwd_bwd_fp32", "ms_per_step": ms,
+                          "tflops": fl / ms / 1e9}), flush=True)
+    elif args.workload == "block_sparse":
+        for nblocks, choices in ((2000, [8, 16, 24, 32]), (500, None)):
+            ext = W.block_sparse_extents(nblocks=nblocks, choices=choices)
+            gen = torch.Generator(device="cuda")
+            gen.manual_seed(3)
+            As, Bs, Cs, la, lb, lc, flops = [], [], [], [], [], [], 0
+            for a, b, c, i, j, k in (map(int, e) for e in ext):
+                As.append(torch.rand((k, i, c, a), device="cuda", dtype=torch.float64,
+                                     generator=gen).permute(3, 2, 1, 0))
+                Bs.append(torch.rand((j, b, k, c), device="cuda", dtype=torch.float64,
+                                     generator=gen).permute(3, 2, 1, 0))
+                Cs.append(torch.zeros((j, i, b, a), device="cuda", dtype=torch.float64).permute(3, 2, 1, 0))
+                la.append(W.L("acik")); lb.append(W.L("ckbj")); lc.append(W.L("abij"))
+                flops += 2 * a * b * c * i * j * k
+            res = {}
+            for name, graph in (("grouped_graph", True), ("grouped_nograph", False)):
+                f = lambda: fm.contract_batched(1.0, As, la, Bs, lb, 0.0, Cs, lc, dtype="f64_emu",
+                                                use_graph=graph)
+                ms = _cuda_ms(f, max(1, min(args.steps, 3)), 1)
+                res[name] = {"ms": ms, "tflops": flops / ms / 1e9}
+
+            def loop():
+                for x in zip(As, la, Bs, lb, Cs, lc):
+                    fm.contract(1.0, x[0], x[1], x[2], x[3], 0.0, x[4], x[5], dtype="f64_emu")
+            ms = _cuda_ms(loop, max(1, min(args.steps, 3)), 1)
+            res["one_call_per_block"] = {"ms": ms, "tflops": flops / ms / 1e9}
+            print(json.dumps({"workload": f"block_sparse_{nblocks}_ext_"
+                              f"{'8-32' if choices else '8-96'}_f64_split7", "flops": flops, **res}),
+                  flush=True)
+    print(json.dumps({"device_status": fm.device_status()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="ladder",
+                    choices=["ladder", "transpose_free", "block_sparse", "autograd"],
+                    help="ladder is the benchmark line; the others print secondary measurements")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
@@ -333,7 +433,9 @@ def main():
     ap.add_argument("--o", type=int, default=32, help="occupied extent (profiling captures only)")
     args = ap.parse_args()
     set_size(args.v, args.o)
-    if args.impl == "reference":
+    if args.workload != "ladder":
+        run_other(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
