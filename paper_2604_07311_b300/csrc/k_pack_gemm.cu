@@ -501,6 +501,40 @@ bool make_slice_map(CUtensorMap* map, void* base, bool f32, int64_t k, int64_t k
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// A bf16 operand that TMA can read as it stands: its contracted modes fused
+// to one unit-stride mode, at most one row mode and one batch mode, every
+// stride a multiple of 16 bytes and the base 16-byte aligned.  which: 0 for
+// the row operand (strides sa), 1 for the column operand (sb).
+struct DirectView {
+  const void* base;
+  int64_t row_stride, batch_stride;  // elements
+};
+
+static bool direct_view(const ClassModes& R, const ClassModes& K, const ClassModes& Lb, int which,
+                        const void* base, DirectView* v) {
+  auto st = [&](const Mode& m) { return which == 0 ? m.sa : m.sb; };
+  if (K.n != 1 || st(K.m[0]) != 1 || R.n > 1 || Lb.n > 1) return false;
+  if (((uintptr_t)base & 15) != 0) return false;
+  v->base = base;
+  v->row_stride = R.n ? st(R.m[0]) : 8;
+  v->batch_stride = Lb.n ? st(Lb.m[0]) : 8;
+  return v->row_stride % 8 == 0 && v->batch_stride % 8 == 0 && v->row_stride > 0 &&
+         v->batch_stride > 0;
+}
+
+static bool make_view_map(CUtensorMap* map, const DirectView& v, int64_t k, int64_t rows, int64_t l,
+                          int box_k, int box_rows) {
+  EncodeFn enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)l};
+  cuuint64_t strides[2] = {(cuuint64_t)(v.row_stride * 2), (cuuint64_t)(v.batch_stride * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, 1u};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(v.base), dims, strides,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int pair_bn_for(int64_t n, int request) {
   if (request == 64 || request == 128 || request == 256) return request;
   return n > 128 ? 256 : (n > 64 ? 128 : 64);
@@ -599,16 +633,27 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     if ((e = cudaMemsetAsync(w + L.fa, 0, L.G - L.fa, s)) != cudaSuccess) return e;
     if ((e = launch_rowexp(pa, s)) != cudaSuccess) return e;
   }
-  if ((e = launch_pack(emu ? PACK_F64 : (tf32 ? PACK_TF32 : PACK_BF16), pa, s)) != cudaSuccess)
-    return e;
   const int bn = pair_bn_for(p.n, p.tile_n);
   const int S = pa.slices;
   const int kind = tf32 ? PAIR_KIND_TF32 : PAIR_KIND_BF16;
   const int kbk = pair_stage_k(kind);
   CUtensorMap ma, mb;
-  if (!make_slice_map(&ma, w + L.a, tf32, p.k, kp, p.m, (int64_t)S * p.l, kbk, BM) ||
-      !make_slice_map(&mb, w + L.b, tf32, p.k, kp, p.n, (int64_t)S * p.l, kbk, bn))
-    return cudaErrorInvalidValue;
+  // bf16 operands already laid out like a slice (k unit-stride, aligned
+  // rows and batches) are read by TMA straight from the caller's tensor;
+  // only the others are packed.
+  DirectView va, vb;
+  const bool da = !emu && !tf32 && direct_view(p.M, p.K, p.L, 0, p.a, &va);
+  const bool db = !emu && !tf32 && direct_view(p.N, p.K, p.L, 1, p.b, &vb);
+  if (da) pa.op[0].rows = 0;  // nothing to pack
+  if (db) pa.op[1].rows = 0;
+  if ((!da || !db) &&
+      (e = launch_pack(emu ? PACK_F64 : (tf32 ? PACK_TF32 : PACK_BF16), pa, s)) != cudaSuccess)
+    return e;
+  const bool ok_a = da ? make_view_map(&ma, va, p.k, p.m, p.l, kbk, BM)
+                       : make_slice_map(&ma, w + L.a, tf32, p.k, kp, p.m, (int64_t)S * p.l, kbk, BM);
+  const bool ok_b = db ? make_view_map(&mb, vb, p.k, p.n, p.l, kbk, bn)
+                       : make_slice_map(&mb, w + L.b, tf32, p.k, kp, p.n, (int64_t)S * p.l, kbk, bn);
+  if (!ok_a || !ok_b) return cudaErrorInvalidValue;
   PairArgs a;
   std::memset(&a, 0, sizeof(a));
   a.single = Prob{nullptr, nullptr, g.c, g.t.cm, g.t.cn, g.t.cl, pa.op[0].e, pa.op[1].e,

@@ -77,6 +77,22 @@ def test_bf16_k_major_operands(path):
     assert rel_frob(gpu_dense(Cg), run_oracle(p, in_dtype=torch.bfloat16)) <= 1e-5
 
 
+@pytest.mark.parametrize("kext", [64, 200, 37])
+def test_bf16_k_unit_stride_batched_read_in_place(kext):
+    """Operands whose contracted index is unit-stride (and, for k = 64 and
+    200, whose rows start on 16-byte boundaries) are read by TMA straight from
+    the caller's tensors; k = 37 takes the pack.  C[i,j,b] = sum_k A[k,i,b] B[k,j,b]."""
+    rng = np.random.default_rng(305)
+    A = W.uniform_operand(rng, (kext, 150, 3), [2, 1, 3])
+    B = W.uniform_operand(rng, (kext, 90, 3), [2, 4, 3])
+    C = W.uniform_operand(rng, (150, 90, 3), [1, 4, 3])
+    p = W.Problem("kmajor_batched", 1.5, A, B, -0.5, C)
+    Cg, info = run_gpu(p, "bf16")
+    assert info["a_contig"] == 2 and info["b_contig"] == 2 and info["batch"] == 3
+    want = run_oracle(p, in_dtype=torch.bfloat16, out_dtype=torch.float32)
+    assert rel_frob(gpu_dense(Cg), want) <= 1e-5
+
+
 def test_bf16_batch_labels():
     """A label in A, B and C (batch): C[i,j,b] = sum_k A[i,k,b] B[k,j,b]."""
     rng = np.random.default_rng(304)
