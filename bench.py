@@ -30,10 +30,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "contraction TFLOP/s, % tensor-pipe peak; split-precision vs FP64 speedup"
 # DRAM bytes per product-kernel launch from the ncu capture summarised in
-# profiles/k_pair_gemm_ladder.md (v=64 ladder, 1.543 GB, scaled by executed
+# profiles/k_pair_gemm_ladder.md (v=64 ladder, 1.549 GB, scaled by executed
 # flops to the v=128 launch).  Must go back to None whenever the product
 # kernel changes after that capture.
-PRODUCT_TRAFFIC = {"bytes": 1.543e9, "exec_flops": 9.62072674304e11}
+PRODUCT_TRAFFIC = {"bytes": 1.549e9, "exec_flops": 9.62072674304e11}
 V_EXT, O_EXT, SLICES = 128, 32, 7
 WORKLOAD = "ccsd_ladder_v128_o32_f64_split7"
 
