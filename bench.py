@@ -165,7 +165,10 @@ def run_reference(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return
     p = make_inputs()
-    cols = args.ref_cols
+    # size each step's sample so that the whole run stays near two minutes
+    _, t1, _ = cpu_sample(p, 1)
+    budget_s = 120.0
+    cols = max(1, min(args.ref_cols, int(budget_s / max(t1, 1e-3) / (args.steps + args.warmup))))
     for _ in range(args.warmup):
         cpu_sample(p, cols)
     times, flops, cores = [], 0.0, 1
