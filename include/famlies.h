@@ -188,13 +188,23 @@ FAMLIES_API int famlies_contract_host(double alpha, const famlies_tensor_t* A, c
                           void* stream, const famlies_options_t* opt);
 
 /* count independent contractions (alpha[i], A[i], B[i], beta[i], C[i]) of
- * one dtype, run as ONE grouped persistent launch per kernel stage over a
- * device tile list ordered longest-first (the blocks of a block-sparse
- * contraction, Sec. 2.3, "tensor-of-tensors" tiling).  Every C[i] must be
- * disjoint from every A[j], B[j] and from every other C[j].  When use_graph
- * is non-zero the launches are captured once into a CUDA graph, cached by
- * the problem set (pointers, shapes, scalars), and replayed on later calls
- * with the same set.  Asynchronous. */
+ * one dtype (the blocks of a block-sparse contraction, Sec. 2.3,
+ * "tensor-of-tensors" tiling).  Problems of the tensor-core dtypes (F64_EMU,
+ * BF16, F32) run as one grouped persistent launch per kernel stage over a
+ * device tile list ordered longest-first, each problem with its own tile
+ * width; the set is cut, in order, into chunks of at most 4 GB of slice
+ * workspace (environment FAMLIES_BATCH_WORKSPACE_MB overrides), which run
+ * one after the other.  F64 problems, and problems with alpha == 0 or an
+ * empty contracted extent, run one by one.  The tile width is tuned on the
+ * first call for a shape class by timing the candidates with C redirected
+ * to scratch (FAMLIES_AUTOTUNE=0 disables this).  Every C[i] must be
+ * disjoint from every A[j], B[j] and from every other C[j] (not checked
+ * across problems).  When use_graph is non-zero the whole call is captured
+ * once into a CUDA graph, cached by the problem set (device, pointers,
+ * shapes, strides, scalars) and replayed on later calls with the same set;
+ * each cached set keeps its workspace allocated (at most four sets, least
+ * recently used evicted), and replays read the operands' current contents.
+ * Asynchronous. */
 FAMLIES_API int famlies_contract_batched(int64_t count, const double* alpha, const famlies_tensor_t* A,
                              const famlies_tensor_t* B, const double* beta,
                              const famlies_tensor_t* C, famlies_dtype_t dtype, void* stream,

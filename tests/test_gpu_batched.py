@@ -95,3 +95,44 @@ def test_mixed_batch_scale_only_and_empty():
     # the fp64 CUDA-core path runs block by block inside the same call
     _, _, Cs = run_batch(blocks[1:6], "f64", False)
     check(blocks[1:6], Cs, "f64")
+
+
+def _gemm_block(rng, m, n, k, batch, name):
+    """C[i,j(,z)] = sum_k A[i,k(,z)] B[k,j(,z)] with an optional batch label z."""
+    lz = [9] if batch else []
+    ez = (batch,) if batch else ()
+    A = W.uniform_operand(rng, (m, k) + ez, [1, 2] + lz)
+    B = W.uniform_operand(rng, (k, n) + ez, [2, 3] + lz)
+    C = W.uniform_operand(rng, (m, n) + ez, [1, 3] + lz)
+    return W.Problem(name, 1.25, A, B, -0.75, C)
+
+
+@pytest.mark.parametrize("dtype", ["f64_emu", "bf16"])
+def test_mixed_widths_and_batch_labels_in_one_group(dtype):
+    """Blocks whose column counts call for tile widths 64, 128 and 256 share
+    one grouped launch; some carry a batch label."""
+    rng = np.random.default_rng(952)
+    shapes = [(130, 40, 70, 0), (257, 100, 33, 3), (64, 300, 129, 0), (9, 17, 5, 2),
+              (200, 256, 64, 0), (140, 129, 200, 4)]
+    blocks = [_gemm_block(rng, m, n, k, z, f"g{i}") for i, (m, n, k, z) in enumerate(shapes)]
+    _, _, Cs = run_batch(blocks, dtype, False)
+    for b, C in zip(blocks, Cs):
+        want = run_oracle(b, in_dtype=TORCH_DT[dtype], out_dtype=OUT_DT[dtype])
+        assert rel_frob(gpu_dense(C), want) <= TOL[dtype], b.name
+
+
+def test_graph_cache_rekeys_on_new_pointers():
+    """A different problem set (new output buffers) builds its own graph; the
+    cached one keeps working for the original set."""
+    rng = np.random.default_rng(953)
+    blocks = [_gemm_block(rng, 96, 80, 48, 0, f"h{i}") for i in range(5)]
+    As, Bs, Cs = run_batch(blocks, "f64_emu", True)
+    check(blocks, Cs, "f64_emu")
+    Cs2 = [to_device(b.C, torch.float64) for b in blocks]
+    batched_call(blocks, As, Bs, Cs2, "f64_emu", True)
+    check(blocks, Cs2, "f64_emu")
+    Cs3 = [to_device(b.C, torch.float64) for b in blocks]
+    for C3, C in zip(Cs3, Cs):
+        C.copy_(C3)
+    batched_call(blocks, As, Bs, Cs, "f64_emu", True)  # the first set again: replay
+    check(blocks, Cs, "f64_emu")
