@@ -34,7 +34,6 @@ namespace famlies {
 
 namespace {
 
-constexpr int kBits = 7;
 auto up256 = [](size_t x) { return (x + 255) / 256 * 256; };
 
 struct ProbLayout {
@@ -161,9 +160,11 @@ bool build_blob(const std::vector<const Plan*>& ps, const double* alpha, const d
     PackArgs& pa = pargs[i];
     std::memset(&pa, 0, sizeof(pa));
     const int64_t kp = (p.k + 7) / 8 * 8;
-    pa.k = p.k; pa.kp = kp; pa.l = p.l; pa.slices = G.slices; pa.bits = kBits;
+    pa.k = p.k; pa.kp = kp; pa.l = p.l; pa.slices = G.slices;
     pa.op[0] = PackOp{p.a, t.am, t.ak, t.al, p.m, p.a_contig, d_ws + L.a, nullptr, nullptr, nullptr};
     pa.op[1] = PackOp{p.b, t.bn, t.bk, t.bl, p.n, p.b_contig, d_ws + L.b, nullptr, nullptr, nullptr};
+    set_affine(pa.op[0], p.M, p.K, 0);
+    set_affine(pa.op[1], p.N, p.K, 1);
     if (emu) {
       pa.op[0].e = (int32_t*)(d_exp + L.ea);
       pa.op[1].e = (int32_t*)(d_exp + L.eb);
@@ -233,7 +234,7 @@ cudaError_t enqueue_prepare(const GroupSetup& G, char* d_ws, const DevPtrs& d, c
 cudaError_t enqueue_product(const GroupSetup& G, int bn, const Prob* probs, const TileEntry* tiles,
                             char* d_ws, int* status, int64_t wait_limit, cudaStream_t s) {
   const int grid = (int)std::min<int64_t>(G.ntiles, num_sms());
-  const Sched sc = make_pair_sched(G.kernel, G.slices, kBits);
+  const Sched sc = make_pair_sched(G.kernel, G.slices, kSplitBits);
   double* Gsum = G.mode == PAIR_MODE_EMU ? (double*)(d_ws + G.ws_main + G.ws_exp + G.ws_flag) : nullptr;
   return launch_pair_grouped(G.kind, G.mode, bn, probs, tiles, G.ntiles, sc, Gsum, grid, status,
                              wait_limit, s);

@@ -20,11 +20,24 @@ constexpr int PR = 64;      // rows per pack tile
 constexpr int PK = 64;      // k per pack tile
 constexpr int KCH = 1024;   // k per block in the exponent pass
 
+__host__ __device__ inline int64_t n_pack_tiles(int64_t rows, int64_t k, int64_t l) {
+  return ((rows + PR - 1) / PR) * ((k + PK - 1) / PK) * l;
+}
+
 __device__ __forceinline__ void mark_row(const PackOp& o, int64_t idx) {
   if (atomicExch(&o.flag[idx], 1) == 0) {
     const int pos = atomicAdd(&o.list[0], 1);
     o.list[1 + pos] = (int32_t)idx;
   }
+}
+
+// Offsets of row r and contracted index k of an operand: affine when the
+// class fused to one mode, otherwise read from the offset tables.
+__device__ __forceinline__ int64_t row_off(const PackOp& o, int64_t r) {
+  return (o.affine & 1) ? r * o.rs : o.roff[r];
+}
+__device__ __forceinline__ int64_t k_off(const PackOp& o, int64_t k) {
+  return (o.affine & 2) ? k * o.ks : o.koff[k];
 }
 
 // Exponent bound of one fp64 value: |x| < 2^(max(E,1) - 1022) for its biased
@@ -52,9 +65,9 @@ __device__ __forceinline__ void rowexp_body(const PackArgs& pa, const PackOp& o,
       for (int j = 0; j < PR / 8; ++j) {
         const int64_t gr = tr * PR + warp + 8 * j;
         if (gr >= o.rows) break;
-        const int64_t base = lo + o.roff[gr];
+        const int64_t base = lo + row_off(o, gr);
         int mx = -1100, bad = 0;
-        for (int64_t k = k0 + lane; k < k1; k += 32) exp_update(__ldg(X + base + o.koff[k]), mx, bad);
+        for (int64_t k = k0 + lane; k < k1; k += 32) exp_update(__ldg(X + base + k_off(o, k)), mx, bad);
         mx = __reduce_max_sync(0xffffffffu, mx);
         bad = __reduce_or_sync(0xffffffffu, bad);
         if (lane == 0) {
@@ -68,8 +81,8 @@ __device__ __forceinline__ void rowexp_body(const PackArgs& pa, const PackOp& o,
       const int64_t gr = tr * PR + r;
       int mx = -1100, bad = 0;
       if (gr < o.rows) {
-        const int64_t base = lo + o.roff[gr];
-        for (int64_t k = k0 + kl; k < k1; k += 4) exp_update(__ldg(X + base + o.koff[k]), mx, bad);
+        const int64_t base = lo + row_off(o, gr);
+        for (int64_t k = k0 + kl; k < k1; k += 4) exp_update(__ldg(X + base + k_off(o, k)), mx, bad);
       }
       smx[kl][r] = mx;
       sbad[kl][r] = bad;
@@ -97,111 +110,241 @@ __device__ __forceinline__ uint32_t tf32_bits(float x) {
   return r;
 }
 
-template <int PMODE>
-__device__ __forceinline__ void pack_body(const PackArgs& pa, const PackOp& o, int64_t b0,
-                                          int64_t bstep) {
-  using T = typename PackT<PMODE>::T;
-  __shared__ T tile[PR][PK + 1];
-  const T* __restrict__ X = (const T*)o.x;
-  const int64_t tiles_r = (o.rows + PR - 1) / PR, tiles_k = (pa.k + PK - 1) / PK;
-  const size_t slice_stride = (size_t)pa.l * o.rows * pa.kp;  // elements per slice
-  const int tid = threadIdx.x;
-  for (int64_t b = b0; b < tiles_r * tiles_k * pa.l; b += bstep) {
-    const int64_t tr = b % tiles_r, rest = b / tiles_r;
-    const int64_t tk = rest % tiles_k, il = rest / tiles_k;
-    const int64_t lo = o.loff[il];
-    for (int e = tid; e < PR * PK; e += 256) {
-      int r, kk;
-      if (o.contig == 2) { kk = e % PK; r = e / PK; } else { r = e % PR; kk = e / PR; }
-      const int64_t gr = tr * PR + r, gk = tk * PK + kk;
-      T v = T(0);
-      if (gr < o.rows && gk < pa.k) v = __ldg(X + lo + o.roff[gr] + o.koff[gk]);
-      tile[r][kk] = v;
+// fp64 split of 8 consecutive values of one row into S slices of
+// kSplitBits = 7-bit digits, in integer arithmetic only (the fp64 pipe is
+// narrow).  With t = x * 2^-e_r in (-1, 1), F = round(t * 2^(7 S)) is taken
+// from x's significand and exponent bits, then split into balanced base-2^7
+// digits: d_S..d_2 in [-64, 64), the remaining top digit |d_1| <= 128, and
+// F = sum_i d_i 2^(7 (S - i)), so |t - sum_i d_i 2^(-7 i)| <= 2^(-7 S - 1).
+// S is a template argument so that every digit shift is a constant.
+template <int S>
+__device__ __forceinline__ void split8(const double* v, int ex, bool bad, uint16_t* out,
+                                       size_t slice_stride) {
+  constexpr int b = kSplitBits, bs = b * S, top = b * (S - 1);
+  if (bad) {  // recomputed natively afterwards: zero slices
+#pragma unroll
+    for (int s = 0; s < S; ++s) *(uint4*)(out + (size_t)s * slice_stride) = make_uint4(0, 0, 0, 0);
+    return;
+  }
+  // Peeling the digits from the bottom (d = ((F + h) & mask) - h,
+  // F = (F - d) >> b, h = 2^(b-1)) is the same as adding the bias
+  // h * (1 + 2^b + ... + 2^(b(S-2))) once and reading the lower S-1 digits
+  // as b-bit fields minus h; the top digit is what remains above them
+  // (arithmetic shift).  No digit then waits on another.
+  constexpr int64_t bias = [] {
+    int64_t t = 0;
+    for (int s = 0; s < S - 1; ++s) t += ((int64_t)1 << (b - 1)) << (b * s);
+    return t;
+  }();
+  int64_t F[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint64_t u = (uint64_t)__double_as_longlong(v[j]);
+    const int E = (int)(((uint32_t)(u >> 32) >> 20) & 0x7FF);
+    const uint64_t mant = (u & 0xFFFFFFFFFFFFFull) | ((uint64_t)(E != 0) << 52);
+    // F = mant * 2^-n; |x| < 2^ex bounds n below by 53 - bs
+    const int n = ex + (1075 - bs) - max(E, 1);
+    uint64_t f;
+    if constexpr (bs > 53) {
+      f = n <= 0 ? mant << (-n) : (n <= 54 ? (mant + (1ull << (n - 1))) >> n : 0);
+    } else {
+      f = n <= 54 ? (mant + (1ull << (n - 1))) >> n : 0;
     }
-    __syncthreads();
-    for (int it = tid; it < PR * 8; it += 256) {
-      const int r = it >> 3, c = it & 7;
-      const int64_t gr = tr * PR + r, gk0 = tk * PK + c * 8;
-      if (gr >= o.rows || gk0 >= pa.k) continue;
-      const size_t rowbase = ((size_t)il * o.rows + gr) * pa.kp + gk0;
-      if constexpr (PMODE == PACK_BF16) {
-        uint32_t w[4];
+    F[j] = ((int64_t)u < 0 ? -(int64_t)f : (int64_t)f) + bias;
+  }
+  // slice 0 (most significant) first.  Small integers are exact in fp32
+  // and bf16: the float with bits 0x4B400000 + d is 1.5 * 2^23 + d, so
+  // subtracting 1.5 * 2^23 gives d exactly; a lower digit's field u is
+  // or-ed into those bits and 64 more is subtracted.
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          w[j] = (uint32_t)tile[r][c * 8 + 2 * j] | ((uint32_t)tile[r][c * 8 + 2 * j + 1] << 16);
-        *(uint4*)((uint16_t*)o.out + rowbase) = make_uint4(w[0], w[1], w[2], w[3]);
-      } else if constexpr (PMODE == PACK_TF32) {
-        uint32_t hi[8], lo32[8];
+  for (int s = 0; s < S; ++s) {
+    const int sh2 = top - b * s;
+    float f[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float x = tile[r][c * 8 + j];
-          hi[j] = tf32_bits(x);
-          lo32[j] = tf32_bits(x - __uint_as_float(hi[j]));
-        }
-        uint4* ph = (uint4*)((float*)o.out + rowbase);
-        uint4* pl = (uint4*)((float*)o.out + slice_stride + rowbase);
-        ph[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        ph[1] = make_uint4(hi[4], hi[5], hi[6], hi[7]);
-        pl[0] = make_uint4(lo32[0], lo32[1], lo32[2], lo32[3]);
-        pl[1] = make_uint4(lo32[4], lo32[5], lo32[6], lo32[7]);
+    for (int j = 0; j < 8; ++j) {
+      if (s == 0) {
+        f[j] = __int_as_float(0x4B400000 + (int32_t)(F[j] >> top)) - 12582912.0f;
       } else {
-        // Integer arithmetic only (the fp64 pipe is narrow): with
-        // t = x * 2^-e_r in (-1, 1), F = round(t * 2^(b S)) is taken from
-        // x's significand and exponent bits, then split into balanced base
-        // 2^b digits from the bottom: d_S..d_2 in [-2^(b-1), 2^(b-1)), the
-        // remaining top digit |d_1| <= 2^b.  F = sum_i d_i 2^(b (S - i)), so
-        // |t - sum_i d_i 2^(-b i)| <= 2^(-b S - 1).
-        const int64_t ri = il * o.rows + gr;
-        const int ex = o.e[ri];
-        const bool bad = o.flag[ri] != 0;
-        const int b = pa.bits, S = pa.slices, bs = b * S;
-        const int64_t half = (int64_t)1 << (b - 1), mask = ((int64_t)1 << b) - 1;
-        int64_t F[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const uint64_t bitsx = (uint64_t)__double_as_longlong(tile[r][c * 8 + j]);
-          const int E = (int)((bitsx >> 52) & 0x7FF);
-          const uint64_t mant = (bitsx & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
-          const int sh = max(E, 1) - 1075 - ex + bs;  // F = mant * 2^sh
-          int64_t f = 0;
-          if (!bad && mant != 0) {
-            if (sh >= 0) f = (int64_t)(mant << sh);
-            else if (sh > -63) f = (int64_t)((mant + (1ull << (-sh - 1))) >> (-sh));
-          }
-          F[j] = (bitsx >> 63) ? -f : f;
-        }
-        // Peeling the digits from the bottom (d = ((F + h) & mask) - h,
-        // F = (F - d) >> b) is the same as adding the bias
-        // h * (1 + 2^b + ... + 2^(b(S-2))) once and reading the lower S-1
-        // digits as b-bit fields minus h; the top digit is what remains
-        // above them (arithmetic shift).  No digit then waits on another.
-        int64_t bias = 0;
-        for (int s = 0; s < S - 1; ++s) bias += half << (b * s);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) F[j] += bias;
-        // slice 0 (most significant) first; each slice's digits are read
-        // straight from the biased values, so only those stay in registers
-        for (int s = 0; s < S; ++s) {
-          const int sh2 = b * (S - 1 - s);
-          uint32_t w[4];
-#pragma unroll
-          for (int j = 0; j < 8; j += 2) {
-            const int32_t d0 = s == 0 ? (int32_t)(F[j] >> sh2)
-                                      : (int32_t)((F[j] >> sh2) & mask) - (int32_t)half;
-            const int32_t d1 = s == 0 ? (int32_t)(F[j + 1] >> sh2)
-                                      : (int32_t)((F[j + 1] >> sh2) & mask) - (int32_t)half;
-            // small integers are exact in fp32 and bf16: 1.5 * 2^23 + d holds
-            // d in its low significand bits, and the subtraction is exact
-            const float f0 = __int_as_float(0x4B400000 + d0) - 12582912.0f;
-            const float f1 = __int_as_float(0x4B400000 + d1) - 12582912.0f;
-            w[j / 2] = (__float_as_uint(f0) >> 16) | (__float_as_uint(f1) & 0xFFFF0000u);
-          }
-          *(uint4*)((uint16_t*)o.out + (size_t)s * slice_stride + rowbase) =
-              make_uint4(w[0], w[1], w[2], w[3]);
-        }
+        const uint32_t field = (uint32_t)((uint64_t)F[j] >> sh2) & ((1u << b) - 1);
+        f[j] = __uint_as_float(field | 0x4B400000u) - (12582912.0f + (float)(1 << (b - 1)));
       }
     }
-    __syncthreads();
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      w[j] = __byte_perm(__float_as_uint(f[2 * j]), __float_as_uint(f[2 * j + 1]), 0x7632);
+    *(uint4*)(out + (size_t)s * slice_stride) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// One tile of one operand to pack: tile b of pa.op[...] = *o.
+struct PackTile {
+  const PackArgs* pa;
+  const PackOp* o;
+  int64_t b;
+};
+
+// Asynchronous global -> shared copy of one element, zero-filled when
+// `valid` is false (no bytes are then read), so that the next tile's loads
+// are in flight while the current tile is split and stored.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src, bool valid) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(BYTES),
+               "r"(valid ? BYTES : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int TLD = PK + 1;  // shared tile row length (padded against bank conflicts)
+
+// Stages a PR x PK tile of the operand in shared memory (buf[r][kk]),
+// reading along the operand's unit-stride index: with unit stride along k
+// the threads of a warp take consecutive k of one row, otherwise
+// consecutive rows at one k.  Entries past the operand's edge are zero.
+template <int PMODE>
+__device__ __forceinline__ void load_tile(const PackTile& t, typename PackT<PMODE>::T* buf) {
+  using T = typename PackT<PMODE>::T;
+  constexpr int NT = 256;
+  const PackArgs& pa = *t.pa;
+  const PackOp& o = *t.o;
+  const T* __restrict__ X = (const T*)o.x;
+  const int64_t tiles_r = (o.rows + PR - 1) / PR, tiles_k = (pa.k + PK - 1) / PK;
+  const int64_t tr = t.b % tiles_r, rest = t.b / tiles_r;
+  const int64_t tk = rest % tiles_k, il = rest / tiles_k;
+  const int64_t r0 = tr * PR, k0 = tk * PK;
+  const int rmax = (int)min((int64_t)PR, o.rows - r0), kmax = (int)min((int64_t)PK, pa.k - k0);
+  const T* const base = X + o.loff[il];
+  auto put = [&](T* dst, const T* src, bool ok) {
+    if constexpr (sizeof(T) >= 4) cp_async_elem<sizeof(T)>(dst, ok ? src : X, ok);
+    else *dst = ok ? __ldg(src) : T(0);
+  };
+  if (o.contig == 2) {
+    const int kk = threadIdx.x % PK;
+    const bool kok = kk < kmax;
+    const T* src = base + (kok ? k_off(o, k0 + kk) : 0);
+    T* dst = buf + kk;
+    if (o.affine & 1) {
+      const int64_t step = (NT / PK) * o.rs;
+      int r = threadIdx.x / PK;
+      src += (r0 + r) * o.rs;
+      for (; r < PR; r += NT / PK, src += step) put(dst + r * TLD, src, kok && r < rmax);
+    } else {
+      for (int r = threadIdx.x / PK; r < PR; r += NT / PK) {
+        const bool ok = kok && r < rmax;
+        put(dst + r * TLD, src + (ok ? o.roff[r0 + r] : 0), ok);
+      }
+    }
+  } else {
+    const int r = threadIdx.x % PR;
+    const bool rok = r < rmax;
+    const T* src = base + (rok ? row_off(o, r0 + r) : 0);
+    T* dst = buf + r * TLD;
+    if (o.affine & 2) {
+      const int64_t step = (NT / PR) * o.ks;
+      int kk = threadIdx.x / PR;
+      src += (k0 + kk) * o.ks;
+      for (; kk < PK; kk += NT / PR, src += step) put(dst + kk, src, rok && kk < kmax);
+    } else {
+      for (int kk = threadIdx.x / PR; kk < PK; kk += NT / PR) {
+        const bool ok = rok && kk < kmax;
+        put(dst + kk, src + (ok ? o.koff[k0 + kk] : 0), ok);
+      }
+    }
+  }
+}
+
+// Converts a staged tile and writes it as 16-byte K-major chunks of every
+// slice.
+template <int PMODE>
+__device__ __forceinline__ void emit_tile(const PackTile& t, const typename PackT<PMODE>::T* buf) {
+  const PackArgs& pa = *t.pa;
+  const PackOp& o = *t.o;
+  const int64_t tiles_r = (o.rows + PR - 1) / PR, tiles_k = (pa.k + PK - 1) / PK;
+  const int64_t tr = t.b % tiles_r, rest = t.b / tiles_r;
+  const int64_t tk = rest % tiles_k, il = rest / tiles_k;
+  const size_t slice_stride = (size_t)pa.l * o.rows * pa.kp;  // elements per slice
+  for (int it = threadIdx.x; it < PR * 8; it += 256) {
+    const int r = it >> 3, c = it & 7;
+    const int64_t gr = tr * PR + r, gk0 = tk * PK + c * 8;
+    if (gr >= o.rows || gk0 >= pa.k) continue;
+    const size_t rowbase = ((size_t)il * o.rows + gr) * pa.kp + gk0;
+    const auto* v = buf + r * TLD + c * 8;
+    if constexpr (PMODE == PACK_BF16) {
+      uint32_t w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[j] = (uint32_t)v[2 * j] | ((uint32_t)v[2 * j + 1] << 16);
+      *(uint4*)((uint16_t*)o.out + rowbase) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else if constexpr (PMODE == PACK_TF32) {
+      uint32_t hi[8], lo32[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float x = v[j];
+        hi[j] = tf32_bits(x);
+        lo32[j] = tf32_bits(x - __uint_as_float(hi[j]));
+      }
+      uint4* ph = (uint4*)((float*)o.out + rowbase);
+      uint4* pl = (uint4*)((float*)o.out + slice_stride + rowbase);
+      ph[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      ph[1] = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+      pl[0] = make_uint4(lo32[0], lo32[1], lo32[2], lo32[3]);
+      pl[1] = make_uint4(lo32[4], lo32[5], lo32[6], lo32[7]);
+    } else {
+      const int64_t ri = il * o.rows + gr;
+      uint16_t* out = (uint16_t*)o.out + rowbase;
+      const int ex = o.e[ri];
+      const bool bad = o.flag[ri] != 0;
+      switch (pa.slices) {
+        case 2: split8<2>(v, ex, bad, out, slice_stride); break;
+        case 3: split8<3>(v, ex, bad, out, slice_stride); break;
+        case 4: split8<4>(v, ex, bad, out, slice_stride); break;
+        case 5: split8<5>(v, ex, bad, out, slice_stride); break;
+        case 6: split8<6>(v, ex, bad, out, slice_stride); break;
+        case 7: split8<7>(v, ex, bad, out, slice_stride); break;
+        default: split8<8>(v, ex, bad, out, slice_stride); break;
+      }
+    }
+  }
+}
+
+// Dynamic shared memory of the pack kernels: two staged tiles.
+template <int PMODE>
+constexpr int pack_smem_bytes() {
+  return 2 * PR * TLD * (int)sizeof(typename PackT<PMODE>::T);
+}
+
+// Packs tiles g0, g0 + gstep, ... < total (loc maps a flat index to its
+// tile) with two shared-memory buffers: the loads of the next tile are
+// issued before the current one is converted.
+template <int PMODE, class Locate>
+__device__ __forceinline__ void pack_pipeline(int64_t g0, int64_t gstep, int64_t total, Locate loc) {
+  using T = typename PackT<PMODE>::T;
+  extern __shared__ __align__(16) unsigned char pack_smem[];
+  T* const buf0 = (T*)pack_smem;
+  auto buf = [&](int j) { return buf0 + (j & 1) * (PR * TLD); };
+  if (g0 >= total) return;
+  PackTile cur = loc(g0);
+  load_tile<PMODE>(cur, buf(0));
+  cp_async_commit();
+  int i = 0;
+  for (int64_t g = g0; g < total; g += gstep, ++i) {
+    PackTile nxt = cur;
+    if (g + gstep < total) {
+      nxt = loc(g + gstep);
+      load_tile<PMODE>(nxt, buf(i + 1));
+    }
+    cp_async_commit();
+    cp_async_wait<1>();  // this thread's copies of the current tile have landed
+    __syncthreads();     // ... and everyone else's
+    emit_tile<PMODE>(cur, buf(i));
+    __syncthreads();     // the buffer is free for the tile after next
+    cur = nxt;
   }
 }
 
@@ -251,8 +394,10 @@ __global__ void __launch_bounds__(256) k_rowexp(PackArgs pa) {
 }
 
 template <int PMODE>
-__global__ void __launch_bounds__(256) k_pack(PackArgs pa) {
-  pack_body<PMODE>(pa, pa.op[blockIdx.z], blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(256, 3) k_pack(const __grid_constant__ PackArgs pa) {
+  const PackOp* o = &pa.op[blockIdx.z];
+  pack_pipeline<PMODE>(blockIdx.x, gridDim.x, n_pack_tiles(o->rows, pa.k, pa.l),
+                       [&](int64_t g) { return PackTile{&pa, o, g}; });
 }
 
 __global__ void __launch_bounds__(256) k_fixup(GemmArgs g, const int32_t* list_a,
@@ -286,14 +431,13 @@ __global__ void __launch_bounds__(256) k_rowexp_grouped(const PackArgs* __restri
 }
 
 template <int PMODE>
-__global__ void __launch_bounds__(256) k_pack_grouped(const PackArgs* __restrict__ pas,
+__global__ void __launch_bounds__(256, 3) k_pack_grouped(const PackArgs* __restrict__ pas,
                                                       const int64_t* __restrict__ off, int nseg) {
-  const int64_t total = off[nseg];
-  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+  pack_pipeline<PMODE>(blockIdx.x, gridDim.x, off[nseg], [&](int64_t g) {
     const int s = segment_of(off, nseg, g);
-    const PackArgs& pa = pas[s >> 1];
-    pack_body<PMODE>(pa, pa.op[s & 1], g - off[s], kOneTile);
-  }
+    const PackArgs* pa = pas + (s >> 1);
+    return PackTile{pa, &pa->op[s & 1], g - off[s]};
+  });
 }
 
 __global__ void __launch_bounds__(256) k_fixup_grouped(const GemmArgs* __restrict__ gs,
@@ -304,14 +448,20 @@ __global__ void __launch_bounds__(256) k_fixup_grouped(const GemmArgs* __restric
 
 }  // namespace
 
-static void prefer_shared_carveout();
+static cudaError_t configure_pack_kernels();
+
+void set_affine(PackOp& o, const ClassModes& R, const ClassModes& K, int which) {
+  auto st = [&](const Mode& m) { return which == 0 ? m.sa : m.sb; };
+  o.affine = 0;
+  o.rs = o.ks = 0;
+  if (R.n <= 1) { o.affine |= 1; o.rs = R.n ? st(R.m[0]) : 0; }
+  if (K.n <= 1) { o.affine |= 2; o.ks = K.n ? st(K.m[0]) : 0; }
+}
 
 int64_t rowexp_tiles(int64_t rows, int64_t k, int64_t l) {
   return ((rows + PR - 1) / PR) * ((k + KCH - 1) / KCH) * l;
 }
-int64_t pack_tiles(int64_t rows, int64_t k, int64_t l) {
-  return ((rows + PR - 1) / PR) * ((k + PK - 1) / PK) * l;
-}
+int64_t pack_tiles(int64_t rows, int64_t k, int64_t l) { return n_pack_tiles(rows, k, l); }
 
 cudaError_t launch_rowexp_grouped(const PackArgs* pas, const int64_t* off, int n, int64_t total,
                                   cudaStream_t s) {
@@ -323,11 +473,14 @@ cudaError_t launch_rowexp_grouped(const PackArgs* pas, const int64_t* off, int n
 cudaError_t launch_pack_grouped(int pmode, const PackArgs* pas, const int64_t* off, int n,
                                 int64_t total, cudaStream_t s) {
   if (n <= 0 || total <= 0) return cudaSuccess;
-  prefer_shared_carveout();
+  if (cudaError_t e = configure_pack_kernels(); e != cudaSuccess) return e;
   const int grid = grid_for(total);
-  if (pmode == PACK_BF16) k_pack_grouped<PACK_BF16><<<grid, 256, 0, s>>>(pas, off, 2 * n);
-  else if (pmode == PACK_TF32) k_pack_grouped<PACK_TF32><<<grid, 256, 0, s>>>(pas, off, 2 * n);
-  else k_pack_grouped<PACK_F64><<<grid, 256, 0, s>>>(pas, off, 2 * n);
+  if (pmode == PACK_BF16)
+    k_pack_grouped<PACK_BF16><<<grid, 256, pack_smem_bytes<PACK_BF16>(), s>>>(pas, off, 2 * n);
+  else if (pmode == PACK_TF32)
+    k_pack_grouped<PACK_TF32><<<grid, 256, pack_smem_bytes<PACK_TF32>(), s>>>(pas, off, 2 * n);
+  else
+    k_pack_grouped<PACK_F64><<<grid, 256, pack_smem_bytes<PACK_F64>(), s>>>(pas, off, 2 * n);
   return cudaGetLastError();
 }
 
@@ -348,34 +501,48 @@ cudaError_t launch_rowexp(const PackArgs& pa, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// The pack kernels stage 64 x 64 tiles in shared memory (33 KB for fp64):
-// ask for the largest shared-memory carveout so that several blocks fit
-// per SM and keep enough loads in flight.
-static void prefer_shared_carveout() {
-  static bool done = false;
-  if (done) return;
-  const int c = cudaSharedmemCarveoutMaxShared;
-  cudaFuncSetAttribute(k_pack<PACK_BF16>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-  cudaFuncSetAttribute(k_pack<PACK_TF32>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-  cudaFuncSetAttribute(k_pack<PACK_F64>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-  cudaFuncSetAttribute(k_pack_grouped<PACK_BF16>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-  cudaFuncSetAttribute(k_pack_grouped<PACK_TF32>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-  cudaFuncSetAttribute(k_pack_grouped<PACK_F64>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-  cudaGetLastError();
-  done = true;
+// The pack kernels stage two 64 x 64 tiles in dynamic shared memory (65 KB
+// for fp64): allow that size and ask for the largest shared-memory carveout
+// so that several blocks fit per SM.  Once per device.
+template <class Kernel>
+static void configure(Kernel kernel, int smem) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+}
+
+static cudaError_t configure_pack_kernels() {
+  constexpr int kMaxDev = 64;
+  static bool done[kMaxDev] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < kMaxDev && done[dev]) return cudaSuccess;
+  configure(k_pack<PACK_BF16>, pack_smem_bytes<PACK_BF16>());
+  configure(k_pack<PACK_TF32>, pack_smem_bytes<PACK_TF32>());
+  configure(k_pack<PACK_F64>, pack_smem_bytes<PACK_F64>());
+  configure(k_pack_grouped<PACK_BF16>, pack_smem_bytes<PACK_BF16>());
+  configure(k_pack_grouped<PACK_TF32>, pack_smem_bytes<PACK_TF32>());
+  configure(k_pack_grouped<PACK_F64>, pack_smem_bytes<PACK_F64>());
+  e = cudaGetLastError();
+  if (e == cudaSuccess && dev < kMaxDev) done[dev] = true;
+  return e;
 }
 
 cudaError_t launch_pack(int pmode, const PackArgs& pa, cudaStream_t s) {
-  prefer_shared_carveout();
+  if (cudaError_t e = configure_pack_kernels(); e != cudaSuccess) return e;
   int64_t blocks = 0;
   for (int i = 0; i < 2; ++i) {
     const int64_t b = ((pa.op[i].rows + PR - 1) / PR) * ((pa.k + PK - 1) / PK) * pa.l;
     blocks = b > blocks ? b : blocks;
   }
   const dim3 grid(grid_for(blocks), 1, 2);
-  if (pmode == PACK_BF16) k_pack<PACK_BF16><<<grid, 256, 0, s>>>(pa);
-  else if (pmode == PACK_TF32) k_pack<PACK_TF32><<<grid, 256, 0, s>>>(pa);
-  else k_pack<PACK_F64><<<grid, 256, 0, s>>>(pa);
+  if (pmode == PACK_BF16)
+    k_pack<PACK_BF16><<<grid, 256, pack_smem_bytes<PACK_BF16>(), s>>>(pa);
+  else if (pmode == PACK_TF32)
+    k_pack<PACK_TF32><<<grid, 256, pack_smem_bytes<PACK_TF32>(), s>>>(pa);
+  else
+    k_pack<PACK_F64><<<grid, 256, pack_smem_bytes<PACK_F64>(), s>>>(pa);
   return cudaGetLastError();
 }
 

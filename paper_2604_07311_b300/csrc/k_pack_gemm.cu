@@ -607,7 +607,7 @@ int64_t packed_workspace_bytes(const Plan& p) { return (int64_t)layout_of(p).tot
 cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream_t s) {
   const bool emu = p.kernel == FAMLIES_KERNEL_TC_EMU;
   const bool tf32 = p.kernel == FAMLIES_KERNEL_TC_TF32X3;
-  const int bits = 7;
+  const int bits = kSplitBits;
   const Layout L = layout_of(p);
   char* w = (char*)ws;
   const int64_t kp = (p.k + 7) / 8 * 8;
@@ -617,9 +617,10 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   pa.kp = kp;
   pa.l = p.l;
   pa.slices = emu ? p.slices : (tf32 ? 2 : 1);
-  pa.bits = bits;
   pa.op[0] = PackOp{g.a, g.t.am, g.t.ak, g.t.al, p.m, p.a_contig, w + L.a, nullptr, nullptr, nullptr};
   pa.op[1] = PackOp{g.b, g.t.bn, g.t.bk, g.t.bl, p.n, p.b_contig, w + L.b, nullptr, nullptr, nullptr};
+  set_affine(pa.op[0], p.M, p.K, 0);
+  set_affine(pa.op[1], p.N, p.K, 1);
   cudaError_t e;
   if (emu) {
     pa.op[0].e = (int32_t*)(w + L.ea);

@@ -11,6 +11,10 @@ namespace famlies {
 
 enum { PACK_BF16 = 0, PACK_TF32 = 1, PACK_F64 = 2 };
 
+// Digit width b of the fp64 split (emulated precision, Sec. 1.5): each
+// slice holds b-bit balanced digits, exact in bf16.
+constexpr int kSplitBits = 7;
+
 // One operand to pack: rows x k (batch l) read through offset tables.
 struct PackOp {
   const void* x;        // source operand (strided)
@@ -23,12 +27,21 @@ struct PackOp {
   int32_t* e;           // fp64 split: row exponents [l][rows] (pre-set to INT_MIN)
   int32_t* flag;        // fp64 split: non-finite row flags [l][rows] (pre-set to 0)
   int32_t* list;        // fp64 split: list[0] = count, list[1..] = flagged l*rows + r
+  // When a class fused to at most one mode its offsets are affine:
+  // affine bit 0 -> row offset = r * rs, bit 1 -> k offset = k * ks
+  // (the tables are then not read).
+  int affine;
+  int64_t rs, ks;
 };
+
+// Sets the affine fields of a pack operand from its row and k classes
+// (which: 0 = the plan's row operand, 1 = its column operand).
+void set_affine(PackOp& o, const ClassModes& R, const ClassModes& K, int which);
 
 struct PackArgs {
   PackOp op[2];
   int64_t k, kp, l;
-  int slices, bits;
+  int slices;
 };
 
 // fp64 split, pass 1: row exponent bounds and non-finite flags (both operands).
