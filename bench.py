@@ -33,9 +33,9 @@ METRIC = "contraction TFLOP/s, % tensor-pipe peak; split-precision vs FP64 speed
 # profiles/k_pair_gemm_ladder.md (v=64 ladder, 1.549 GB, scaled by executed
 # flops to the v=128 launch).  Must go back to None whenever the product
 # kernel changes after that capture.
-PRODUCT_TRAFFIC = {"bytes": 1.549e9, "exec_flops": 9.62072674304e11}
-V_EXT, O_EXT, SLICES = 128, 32, 7
-WORKLOAD = "ccsd_ladder_v128_o32_f64_split7"
+PRODUCT_TRAFFIC = None  # re-captured after each product change
+V_EXT, O_EXT, SLICES = 128, 32, 6
+WORKLOAD = f"ccsd_ladder_v128_o32_f64_split{SLICES}"
 
 
 def set_size(v: int, o: int):
@@ -43,7 +43,7 @@ def set_size(v: int, o: int):
     global V_EXT, O_EXT, WORKLOAD
     V_EXT, O_EXT = v, o
     if (v, o) != (128, 32):
-        WORKLOAD = f"ccsd_ladder_v{v}_o{o}_f64_split7"
+        WORKLOAD = f"ccsd_ladder_v{v}_o{o}_f64_split{SLICES}"
 
 
 def peaks():
@@ -414,7 +414,7 @@ def run_other(args):
             ms = _cuda_ms(loop, max(1, min(args.steps, 3)), 1)
             res["one_call_per_block"] = {"ms": ms, "tflops": flops / ms / 1e9}
             print(json.dumps({"workload": f"block_sparse_{nblocks}_ext_"
-                              f"{'8-32' if choices else '8-96'}_f64_split7", "flops": flops, **res}),
+                              f"{'8-32' if choices else '8-96'}_f64_split{SLICES}", "flops": flops, **res}),
                   flush=True)
     print(json.dumps({"device_status": fm.device_status()}), flush=True)
 

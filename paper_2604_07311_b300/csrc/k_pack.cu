@@ -111,32 +111,35 @@ __device__ __forceinline__ uint32_t tf32_bits(float x) {
 }
 
 // fp64 split of 8 consecutive values of one row into S slices of
-// kSplitBits = 7-bit digits, in integer arithmetic only (the fp64 pipe is
-// narrow).  With t = x * 2^-e_r in (-1, 1), F = round(t * 2^(7 S)) is taken
-// from x's significand and exponent bits, then split into balanced base-2^7
-// digits: d_S..d_2 in [-64, 64), the remaining top digit |d_1| <= 128, and
-// F = sum_i d_i 2^(7 (S - i)), so |t - sum_i d_i 2^(-7 i)| <= 2^(-7 S - 1).
-// S is a template argument so that every digit shift is a constant.
+// kSplitBits = 8-bit digits, in integer arithmetic only (the fp64 pipe is
+// narrow).  With t = x * 2^-e_r in (-1, 1), F = round(t * 2^(8 S)) is taken
+// from x's significand and exponent bits, then split into balanced base-256
+// digits: d_S..d_2 in [-128, 128), the remaining top digit |d_1| <= 256
+// (all exact in bf16's 8-bit significand), and F = sum_i d_i 2^(8 (S - i)),
+// so |t - sum_i d_i 2^(-8 i)| <= 2^(-8 S - 1).  S is a template argument so
+// that every digit is a fixed byte of F.
 template <int S>
 __device__ __forceinline__ void split8(const double* v, int ex, bool bad, uint16_t* out,
                                        size_t slice_stride) {
-  constexpr int b = kSplitBits, bs = b * S, top = b * (S - 1);
+  static_assert(kSplitBits == 8, "digits are read as bytes");
+  static_assert(S >= 2 && S <= kMaxSplitSlices, "F must fit in 63 bits");
+  constexpr int bs = 8 * S, top = 8 * (S - 1);
   if (bad) {  // recomputed natively afterwards: zero slices
 #pragma unroll
     for (int s = 0; s < S; ++s) *(uint4*)(out + (size_t)s * slice_stride) = make_uint4(0, 0, 0, 0);
     return;
   }
-  // Peeling the digits from the bottom (d = ((F + h) & mask) - h,
-  // F = (F - d) >> b, h = 2^(b-1)) is the same as adding the bias
-  // h * (1 + 2^b + ... + 2^(b(S-2))) once and reading the lower S-1 digits
-  // as b-bit fields minus h; the top digit is what remains above them
-  // (arithmetic shift).  No digit then waits on another.
+  // Peeling the digits from the bottom (d = ((F + 128) & 255) - 128,
+  // F = (F - d) >> 8) is the same as adding the bias 0x80 in each of the
+  // lower S-1 bytes once and reading those bytes minus 128; the top digit
+  // is what remains above them (arithmetic shift).  No digit then waits on
+  // another.
   constexpr int64_t bias = [] {
     int64_t t = 0;
-    for (int s = 0; s < S - 1; ++s) t += ((int64_t)1 << (b - 1)) << (b * s);
+    for (int s = 0; s < S - 1; ++s) t |= (int64_t)0x80 << (8 * s);
     return t;
   }();
-  int64_t F[8];
+  uint32_t lo[8], hi[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const uint64_t u = (uint64_t)__double_as_longlong(v[j]);
@@ -150,23 +153,27 @@ __device__ __forceinline__ void split8(const double* v, int ex, bool bad, uint16
     } else {
       f = n <= 54 ? (mant + (1ull << (n - 1))) >> n : 0;
     }
-    F[j] = ((int64_t)u < 0 ? -(int64_t)f : (int64_t)f) + bias;
+    const uint64_t F = (uint64_t)(((int64_t)u < 0 ? -(int64_t)f : (int64_t)f) + bias);
+    lo[j] = (uint32_t)F;
+    hi[j] = (uint32_t)(F >> 32);
   }
   // slice 0 (most significant) first.  Small integers are exact in fp32
   // and bf16: the float with bits 0x4B400000 + d is 1.5 * 2^23 + d, so
-  // subtracting 1.5 * 2^23 gives d exactly; a lower digit's field u is
-  // or-ed into those bits and 64 more is subtracted.
+  // subtracting 1.5 * 2^23 gives d exactly.  A lower digit's byte is
+  // permuted straight into those bits and 128 more is subtracted.
 #pragma unroll
   for (int s = 0; s < S; ++s) {
-    const int sh2 = top - b * s;
     float f[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       if (s == 0) {
-        f[j] = __int_as_float(0x4B400000 + (int32_t)(F[j] >> top)) - 12582912.0f;
+        const int32_t d = (int32_t)(((int64_t)hi[j] << 32 | lo[j]) >> top);
+        f[j] = __int_as_float(0x4B400000 + d) - 12582912.0f;
       } else {
-        const uint32_t field = (uint32_t)((uint64_t)F[j] >> sh2) & ((1u << b) - 1);
-        f[j] = __uint_as_float(field | 0x4B400000u) - (12582912.0f + (float)(1 << (b - 1)));
+        const int byte = S - 1 - s;  // digit s sits in byte `byte` of F
+        const uint32_t word = byte < 4 ? lo[j] : hi[j];
+        const uint32_t w = __byte_perm(word, 0x4B400000u, 0x7650 | (byte & 3));
+        f[j] = __uint_as_float(w) - (12582912.0f + 128.0f);
       }
     }
     uint32_t w[4];
@@ -306,8 +313,7 @@ __device__ __forceinline__ void emit_tile(const PackTile& t, const typename Pack
         case 4: split8<4>(v, ex, bad, out, slice_stride); break;
         case 5: split8<5>(v, ex, bad, out, slice_stride); break;
         case 6: split8<6>(v, ex, bad, out, slice_stride); break;
-        case 7: split8<7>(v, ex, bad, out, slice_stride); break;
-        default: split8<8>(v, ex, bad, out, slice_stride); break;
+        default: split8<7>(v, ex, bad, out, slice_stride); break;
       }
     }
   }

@@ -12,8 +12,10 @@ namespace famlies {
 enum { PACK_BF16 = 0, PACK_TF32 = 1, PACK_F64 = 2 };
 
 // Digit width b of the fp64 split (emulated precision, Sec. 1.5): each
-// slice holds b-bit balanced digits, exact in bf16.
-constexpr int kSplitBits = 7;
+// slice holds b-bit balanced digits, exact in bf16 (8 significant bits).
+// At most 7 slices: the scaled integer F < 2^(b s) must fit in int64.
+constexpr int kSplitBits = 8;
+constexpr int kMaxSplitSlices = 7;
 
 // One operand to pack: rows x k (batch l) read through offset tables.
 struct PackOp {

@@ -267,8 +267,8 @@ int make_plan(double alpha, const famlies_tensor_t* A, const famlies_tensor_t* B
   p.tile_n = opt ? opt->tile_n : 0;
   if (p.tile_n != 0 && p.tile_n != 64 && p.tile_n != 128 && p.tile_n != 256)
     return FAMLIES_ERR_INVALID_ARG;
-  int s = opt && opt->slices ? opt->slices : 7;
-  if (s < 2 || s > 8) return FAMLIES_ERR_INVALID_ARG;
+  int s = opt && opt->slices ? opt->slices : 6;
+  if (s < 2 || s > 7) return FAMLIES_ERR_INVALID_ARG;
   p.slices = s;
   *out = p;
   return FAMLIES_OK;

@@ -49,7 +49,7 @@ struct Plan {
   int a_contig = 0, b_contig = 0, c_contig = 0;
   int64_t span_a = 0, span_b = 0, span_c = 0;  // reachable elements (max offset + 1)
   int kernel = FAMLIES_KERNEL_NONE;
-  int slices = 7;
+  int slices = 6;
   int tile_n = 0;  // tensor-core tile width request (0 = automatic)
 };
 

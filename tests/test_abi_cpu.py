@@ -60,7 +60,7 @@ def test_plan_ladder_fuses_to_gemm():
     assert (info["m"], info["n"], info["k"]) == (64, 16, 64)
     assert (info["m_modes"], info["n_modes"], info["k_modes"]) == (1, 1, 1)
     assert info["a_contig"] == 1 and info["b_contig"] == 2 and info["c_contig"] == 1
-    assert info["kernel_name"] == "tc_emu" and info["slices"] == 7
+    assert info["kernel_name"] == "tc_emu" and info["slices"] == 6
 
 
 def test_plan_transpose_free_swaps_roles():

@@ -24,7 +24,7 @@ def _alpha_part(p, want):
 def test_ladder_reduced():
     p = W.ladder(v=32, o=8)
     C, info = run_gpu(p, "f64_emu")
-    assert info["kernel_name"] == "tc_emu" and info["slices"] == 7
+    assert info["kernel_name"] == "tc_emu" and info["slices"] == 6
     want = run_oracle(p)
     got = gpu_dense(C)
     assert rel_frob(got, want) <= TOL
@@ -52,7 +52,7 @@ def test_integer_inputs_exact():
 
 
 def test_error_falls_with_slice_count():
-    """Each extra 7-bit slice shrinks the truncation error until fp64 rounding
+    """Each extra 8-bit slice shrinks the truncation error until fp64 rounding
     is reached (the split converges to the exact product)."""
     rng = np.random.default_rng(401)
     m, n, k = 256, 192, 640
@@ -67,7 +67,7 @@ def test_error_falls_with_slice_count():
         assert info["slices"] == s
         errs.append(rel_frob(gpu_dense(Cg), want))
     for a, b in zip(errs, errs[1:]):
-        assert b <= max(a / 16, 4e-16), errs
+        assert b <= max(a / 16, 1e-15), errs  # 1e-15: fp64 rounding floor
     assert errs[-1] <= TOL
 
 
