@@ -56,7 +56,6 @@ namespace {
 constexpr int BM = kPairBM;
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 32 * (EPI_WARPS + 2);
-constexpr int STAGES = 4;
 
 struct PairArgs {
   Prob single;           // the problem of a single-problem launch
@@ -77,6 +76,8 @@ struct PCfg {
   static constexpr int A_BYTES = BM * 128;
   static constexpr int B_BYTES = BN * 128;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  // as many ring stages as ~200 KB of shared memory holds (at most 8)
+  static constexpr int STAGES = (200 * 1024) / STAGE_BYTES > 8 ? 8 : (200 * 1024) / STAGE_BYTES;
   static constexpr uint32_t TMEM_COLS = 2 * BN;
   static constexpr uint32_t IDESC = ptx::idesc_make(BM, BN, KIND == PAIR_KIND_BF16 ? 1u : 2u);
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
@@ -113,6 +114,50 @@ __device__ __forceinline__ TileRef tile_at(const PairArgs& a, int64_t t) {
   return TileRef{&a.single, rest % tiles_m, tn, rest / tiles_m};
 }
 
+// The end of an fp64-split tile: C = alpha * 2^(e_m + e_n) * G + beta * C
+// for this thread's row and CPT columns, in groups of columns whose table
+// entries, G and C are loaded together.  Not inlined: it runs once per tile
+// and keeps its registers out of the drain loop's budget.
+template <int CPT>
+__device__ __noinline__ void finish_tile(const Prob& P, const double* Gt, int64_t il, int64_t row,
+                                         int64_t crow, int64_t col0, int lc0, int bnp) {
+  double* C = (double*)P.c;
+  const double alpha = P.alpha, beta = P.beta;
+  const int er = P.ea[il * P.m + row];
+  const int32_t* ebl = P.eb + il * P.n;
+  const int32_t* fbl = P.fb + il * P.n;
+  constexpr int FG = 8;
+#pragma unroll 1
+  for (int j0 = 0; j0 < CPT; j0 += FG) {
+    bool use[FG];
+    int ecol[FG];
+    int64_t coff[FG];
+    double g[FG], cold[FG];
+#pragma unroll
+    for (int j = 0; j < FG; ++j) {
+      const int64_t col = col0 + j0 + j;
+      use[j] = lc0 + j0 + j < bnp && col < P.n;
+      ecol[j] = use[j] ? ebl[col] : 0;
+      coff[j] = use[j] ? P.cn[col] : 0;
+      use[j] = use[j] && !fbl[col];
+      g[j] = Gt[(size_t)(j0 + j) * BM];
+    }
+#pragma unroll
+    for (int j = 0; j < FG; ++j) cold[j] = (use[j] && beta != 0.0) ? C[crow + coff[j]] : 0.0;
+#pragma unroll
+    for (int j = 0; j < FG; ++j) {
+      const int e = er + ecol[j];
+      // 2^e built from its bits when it is a normal number
+      const double scaled = (e >= -1022 && e <= 1023)
+                                ? g[j] * __longlong_as_double((long long)(e + 1023) << 52)
+                                : ldexp(g[j], e);
+      double v = alpha * scaled;
+      if (beta != 0.0) v = fma(beta, cold[j], v);
+      if (use[j]) C[crow + coff[j]] = v;
+    }
+  }
+}
+
 template <int KIND, int MODE, int BN, bool GROUPED>
 __global__ void __launch_bounds__(THREADS, 1)
     k_pair_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
@@ -120,9 +165,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   using Cfg = PCfg<KIND, BN>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + STAGES * Cfg::STAGE_BYTES);
-  uint64_t* empty = full + STAGES;
-  uint64_t* tfull = empty + STAGES;
+  uint64_t* full = (uint64_t*)(smem + Cfg::STAGES * Cfg::STAGE_BYTES);
+  uint64_t* empty = full + Cfg::STAGES;
+  uint64_t* tfull = empty + Cfg::STAGES;
   uint64_t* tempty = tfull + 2;
   uint64_t* done = tempty + 2;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
@@ -134,7 +179,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int64_t lim = args.wait_limit;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < Cfg::STAGES; ++s) {
       ptx::mbar_init(&full[s], 1);
       ptx::mbar_init(&empty[s], 1);
     }
@@ -190,7 +235,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 ptx::tma_load_3d(sa + Cfg::A_BYTES, mb, &full[stage], kb * Cfg::KB,
                                  (int)(T.tn * bnp), zb);
                 pending = (pending & ~(0x101u << stage)) | (1u << stage) | (phase << (stage + 8));
-                if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                if (++stage == Cfg::STAGES) { stage = 0; phase ^= 1; }
               }
             }
           }
@@ -199,7 +244,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (!ok && !*abort) record_timeout(abort, args.status);
       // Copies still in flight must land before the CTA leaves: wait (bounded)
       // for the phase each stage was last filled in.
-      for (int s = 0; s < STAGES; ++s) {
+      for (int s = 0; s < Cfg::STAGES; ++s) {
         if (!(pending & (1u << s))) continue;
         const uint32_t ph = (pending >> (s + 8)) & 1u;
         for (int64_t i = 0; i < ((int64_t)1 << 22); ++i)
@@ -243,7 +288,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                   accumulate = 1;
                 }
                 ptx::mma_commit(&empty[stage]);
-                if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                if (++stage == Cfg::STAGES) { stage = 0; phase ^= 1; }
               }
             }
             if (!ok) break;
@@ -331,6 +376,14 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int u = 0; u < nunits; ++u) {
             if (!ptx::mbar_wait(&tfull[acc], accph, lim, abort)) { ok = false; break; }
             ptx::tc_fence_after();
+            const bool last_unit = (u == nunits - 1);
+            const bool flush = last_unit || ((u + 1) % sc.flush_every[di]) == 0;
+            // a flush reads this thread's fp64 tile sums: bring them towards
+            // the SM while the unit drains
+            if (flush && !first_flush) {
+#pragma unroll
+              for (int j = 0; j < CPT; ++j) ptx::prefetch_l2(Gt + (size_t)j * BM);
+            }
 #pragma unroll
             for (int q = 0; q < CPT / 32; ++q) {
               if (lc0 + q * 32 >= bnp) continue;  // beyond this tile's width (warp-uniform)
@@ -345,42 +398,27 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
             acc ^= 1;
             if (acc == 0) accph ^= 1;
-            const bool last_unit = (u == nunits - 1);
-            if (!last_unit && ((u + 1) % sc.flush_every[di]) != 0) continue;
+            if (!flush) continue;
+            // G += 2^-shift * S, the loads issued in groups ahead of the
+            // stores (a few memory round trips per flush, not one per column)
             const double w = ldexp(1.0, -sc.shift[di]);
-            const bool final_flush = last_unit && di == sc.ndiag - 1;
-            if (!final_flush) {
+            {
+              constexpr int FG = 4;
 #pragma unroll
-              for (int j = 0; j < CPT; ++j) {
-                const double prev = first_flush ? 0.0 : Gt[(size_t)j * BM];
-                Gt[(size_t)j * BM] = fma(w, (double)S[j], prev);
-                S[j] = 0;
-              }
-              first_flush = false;
-            } else if (rv && !P.fa[il * P.m + row]) {
-              double* C = (double*)P.c;
-              const double alpha = P.alpha, beta = P.beta;
-              const int er = P.ea[il * P.m + row];
-              const int32_t* ebl = P.eb + il * P.n;
-              const int32_t* fbl = P.fb + il * P.n;
+              for (int j0 = 0; j0 < CPT; j0 += FG) {
+                double prev[FG];
 #pragma unroll
-              for (int j = 0; j < CPT; ++j) {
-                const int64_t col = col0 + j;
-                if (lc0 + j < bnp && col < P.n && !fbl[col]) {
-                  const double prev = first_flush ? 0.0 : Gt[(size_t)j * BM];
-                  const double sum = fma(w, (double)S[j], prev);
-                  const int e = er + ebl[col];
-                  // 2^e built from its bits when it is a normal number
-                  const double scaled = (e >= -1022 && e <= 1023)
-                                            ? sum * __longlong_as_double((long long)(e + 1023) << 52)
-                                            : ldexp(sum, e);
-                  double* p = C + crow + P.cn[col];
-                  double v = alpha * scaled;
-                  if (beta != 0.0) v = fma(beta, *p, v);
-                  *p = v;
+                for (int j = 0; j < FG; ++j) prev[j] = first_flush ? 0.0 : Gt[(size_t)(j0 + j) * BM];
+#pragma unroll
+                for (int j = 0; j < FG; ++j) {
+                  Gt[(size_t)(j0 + j) * BM] = fma(w, (double)S[j0 + j], prev[j]);
+                  S[j0 + j] = 0;
                 }
               }
+              first_flush = false;
             }
+            if (!(last_unit && di == sc.ndiag - 1) || !rv || P.fa[il * P.m + row]) continue;
+            finish_tile<CPT>(P, Gt, il, row, crow, col0, lc0, bnp);
           }
         }
       }
