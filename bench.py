@@ -30,10 +30,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "contraction TFLOP/s, % tensor-pipe peak; split-precision vs FP64 speedup"
 # DRAM bytes per product-kernel launch from the ncu capture summarised in
-# profiles/k_pair_gemm_ladder.md (v=64 ladder, 1.549 GB, scaled by executed
+# profiles/k_pair_gemm_ladder.md (v=96 ladder, 5.30 GB, scaled by executed
 # flops to the v=128 launch).  Must go back to None whenever the product
 # kernel changes after that capture.
-PRODUCT_TRAFFIC = None  # re-captured after each product change
+PRODUCT_TRAFFIC = {"bytes": 5.300521e9, "exec_flops": 3.652869685248e12}
 V_EXT, O_EXT, SLICES = 128, 32, 6
 WORKLOAD = f"ccsd_ladder_v128_o32_f64_split{SLICES}"
 
@@ -300,7 +300,7 @@ def run_gpu(args):
                      "frac": achieved / sustained,
                      "traffic": (PRODUCT_TRAFFIC["bytes"] * exec_flops / PRODUCT_TRAFFIC["exec_flops"]
                                  if PRODUCT_TRAFFIC else None),
-                     "traffic_note": "ncu dram bytes of the v=64 capture scaled by executed flops",
+                     "traffic_note": "ncu dram bytes of the v=96 capture scaled by executed flops",
                      "peak_kind": f"bf16 sustained ({src})", "frac_of_burst": achieved / burst,
                      "kernel_ms": kms, "exec_flops_per_launch": exec_flops},
         "e2e": e2e,
