@@ -47,7 +47,7 @@ struct GroupSetup {
   int kernel = 0, kind = 0, mode = 0, slices = 1;
   size_t ws_main = 0, ws_exp = 0, ws_flag = 0, ws_g = 0, ws_total = 0;
   std::vector<ProbLayout> lay;
-  int64_t ntiles = 0, max_table = 1, rowexp_total = 0, pack_total = 0;
+  int64_t ntiles = 0, max_table = 1, rowexp_total = 0, pack_total = 0, kmax = 1;
   size_t blob_probs = 0, blob_gargs = 0, blob_pargs = 0, blob_jobs = 0, blob_tiles = 0,
          blob_maps = 0, blob_offr = 0, blob_offp = 0, blob_bytes = 0;
   size_t c_bytes = 0;  // sum of C spans (autotuning scratch)
@@ -81,6 +81,7 @@ GroupSetup layout_group(const std::vector<const Plan*>& ps, int bn_max) {
     }
     int64_t tmax = std::max(std::max(p.m, p.n), std::max(p.k, p.l));
     G.max_table = std::max(G.max_table, tmax);
+    G.kmax = std::max(G.kmax, p.k);
     G.rowexp_total += rowexp_tiles(p.m, p.k, p.l) + rowexp_tiles(p.n, p.k, p.l);
     G.pack_total += pack_tiles(p.m, p.k, p.l) + pack_tiles(p.n, p.k, p.l);
     G.c_bytes += up256((size_t)p.span_c * p.es_c);
@@ -234,7 +235,7 @@ cudaError_t enqueue_prepare(const GroupSetup& G, char* d_ws, const DevPtrs& d, c
 cudaError_t enqueue_product(const GroupSetup& G, int bn, const Prob* probs, const TileEntry* tiles,
                             char* d_ws, int* status, int64_t wait_limit, cudaStream_t s) {
   const int grid = (int)std::min<int64_t>(G.ntiles, num_sms());
-  const Sched sc = make_pair_sched(G.kernel, G.slices, kSplitBits);
+  const Sched sc = make_pair_sched(G.kernel, G.slices, kSplitBits, G.kmax);
   double* Gsum = G.mode == PAIR_MODE_EMU ? (double*)(d_ws + G.ws_main + G.ws_exp + G.ws_flag) : nullptr;
   return launch_pair_grouped(G.kind, G.mode, bn, probs, tiles, G.ntiles, sc, Gsum, grid, status,
                              wait_limit, s);

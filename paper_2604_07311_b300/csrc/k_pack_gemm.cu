@@ -17,7 +17,7 @@
 // precision, Sec. 1.5; packing hoisted with data re-organisation, Girder 2).
 //
 // Product.  A persistent, warp-specialised kernel: one thread issues TMA
-// loads of slice tiles into a 4-stage shared-memory ring, one thread issues
+// loads of slice tiles into a shared-memory ring, one thread issues
 // tcgen05.mma into a double-buffered fp32 accumulator in tensor memory, and
 // eight epilogue warps drain it.  The work of one output tile is a list of
 // "units"; a unit accumulates a set of slice pairs over a k range.
@@ -26,17 +26,21 @@
 //   fp64 split:  the pairs with i + j = d (a "diagonal", weight 2^(-b d))
 //                for d = s+1 down to 2; a unit covers a k range short enough
 //                that the fp32 accumulator stays an exact integer (< 2^24),
-//                the epilogue adds it into int32 running sums, flushes them
-//                into an fp64 tile sum at each diagonal's end, and the last
-//                flush writes C = alpha * 2^(e_m+e_n) * sum + beta * C.
+//                the epilogue adds it into int32 running sums and, at each
+//                diagonal's end, adds them (scaled by the diagonal's weight)
+//                into an int64 tile sum with reductions performed at L2; the
+//                tile's end converts the sum once to fp64 and writes
+//                C = alpha * 2^(e_m+e_n) * sum + beta * C.
 // The fp32 accumulation is exact because every partial sum is an integer
-// below 2^24; only the diagonal recombination and the alpha/beta update use
-// fp64 arithmetic.
+// below 2^24, and so is the int64 recombination down to the finest weight K
+// allows; only the final scaling and the alpha/beta update use fp64
+// arithmetic (B300's fp64 pipe is narrow).
 //
 // Grouped launches (many independent problems, e.g. the blocks of a
 // block-sparse contraction) run the same kernel over a device tile list:
 // each entry names its problem, whose descriptor (TMA maps in global memory,
 // C's offset tables, scalars) the roles read per tile.
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -114,16 +118,17 @@ __device__ __forceinline__ TileRef tile_at(const PairArgs& a, int64_t t) {
   return TileRef{&a.single, rest % tiles_m, tn, rest / tiles_m};
 }
 
-// The end of an fp64-split tile: C = alpha * 2^(e_m + e_n) * G + beta * C
-// for this thread's row and CPT columns, in groups of columns whose table
-// entries, G and C are loaded together.  Not inlined: it runs once per tile
-// and keeps its registers out of the drain loop's budget.
+// The end of an fp64-split tile: C = alpha * 2^(e_m + e_n - xunit) * X + beta
+// * C for this thread's row and CPT columns (X: the int64 tile sums), in
+// groups of columns whose table entries, X and C are loaded together.  X is
+// read from L2 (the reductions that built it ran there).  Not inlined: it
+// runs once per tile and keeps its registers out of the drain loop's budget.
 template <int CPT>
-__device__ __noinline__ void finish_tile(const Prob& P, const double* Gt, int64_t il, int64_t row,
-                                         int64_t crow, int64_t col0, int lc0, int bnp) {
+__device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, int xunit, int64_t il,
+                                         int64_t row, int64_t crow, int64_t col0, int lc0, int bnp) {
   double* C = (double*)P.c;
   const double alpha = P.alpha, beta = P.beta;
-  const int er = P.ea[il * P.m + row];
+  const int er = P.ea[il * P.m + row] - xunit;
   const int32_t* ebl = P.eb + il * P.n;
   const int32_t* fbl = P.fb + il * P.n;
   constexpr int FG = 8;
@@ -132,7 +137,8 @@ __device__ __noinline__ void finish_tile(const Prob& P, const double* Gt, int64_
     bool use[FG];
     int ecol[FG];
     int64_t coff[FG];
-    double g[FG], cold[FG];
+    int64_t g[FG];
+    double cold[FG];
 #pragma unroll
     for (int j = 0; j < FG; ++j) {
       const int64_t col = col0 + j0 + j;
@@ -140,7 +146,7 @@ __device__ __noinline__ void finish_tile(const Prob& P, const double* Gt, int64_
       ecol[j] = use[j] ? ebl[col] : 0;
       coff[j] = use[j] ? P.cn[col] : 0;
       use[j] = use[j] && !fbl[col];
-      g[j] = Gt[(size_t)(j0 + j) * BM];
+      g[j] = __ldcg(Xt + (size_t)(j0 + j) * BM);
     }
 #pragma unroll
     for (int j = 0; j < FG; ++j) cold[j] = (use[j] && beta != 0.0) ? C[crow + coff[j]] : 0.0;
@@ -148,9 +154,10 @@ __device__ __noinline__ void finish_tile(const Prob& P, const double* Gt, int64_
     for (int j = 0; j < FG; ++j) {
       const int e = er + ecol[j];
       // 2^e built from its bits when it is a normal number
+      const double x = (double)g[j];
       const double scaled = (e >= -1022 && e <= 1023)
-                                ? g[j] * __longlong_as_double((long long)(e + 1023) << 52)
-                                : ldexp(g[j], e);
+                                ? x * __longlong_as_double((long long)(e + 1023) << 52)
+                                : ldexp(x, e);
       double v = alpha * scaled;
       if (beta != 0.0) v = fma(beta, cold[j], v);
       if (use[j]) C[crow + coff[j]] = v;
@@ -368,7 +375,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         int32_t S[CPT];
 #pragma unroll
         for (int j = 0; j < CPT; ++j) S[j] = 0;
-        double* Gt = args.G + (size_t)blockIdx.x * BM * BN + (size_t)(hf * CPT) * BM + qd * 32 + lane;
+        int64_t* Xt = (int64_t*)args.G + (size_t)blockIdx.x * BM * BN + (size_t)(hf * CPT) * BM + qd * 32 + lane;
         bool first_flush = true;
         for (int di = 0; di < sc.ndiag && ok; ++di) {
           const int kcb = sc.kcb[di];
@@ -378,12 +385,6 @@ __global__ void __launch_bounds__(THREADS, 1)
             ptx::tc_fence_after();
             const bool last_unit = (u == nunits - 1);
             const bool flush = last_unit || ((u + 1) % sc.flush_every[di]) == 0;
-            // a flush reads this thread's fp64 tile sums: bring them towards
-            // the SM while the unit drains
-            if (flush && !first_flush) {
-#pragma unroll
-              for (int j = 0; j < CPT; ++j) ptx::prefetch_l2(Gt + (size_t)j * BM);
-            }
 #pragma unroll
             for (int q = 0; q < CPT / 32; ++q) {
               if (lc0 + q * 32 >= bnp) continue;  // beyond this tile's width (warp-uniform)
@@ -399,26 +400,23 @@ __global__ void __launch_bounds__(THREADS, 1)
             acc ^= 1;
             if (acc == 0) accph ^= 1;
             if (!flush) continue;
-            // G += 2^-shift * S, the loads issued in groups ahead of the
-            // stores (a few memory round trips per flush, not one per column)
-            const double w = ldexp(1.0, -sc.shift[di]);
+            // X += S * 2^xshift in int64 (exact, order-free): the first
+            // flush of a tile stores, later ones are fire-and-forget
+            // reductions performed at L2, so no flush waits on memory.
             {
-              constexpr int FG = 4;
+              const int xs = sc.xshift[di];
 #pragma unroll
-              for (int j0 = 0; j0 < CPT; j0 += FG) {
-                double prev[FG];
-#pragma unroll
-                for (int j = 0; j < FG; ++j) prev[j] = first_flush ? 0.0 : Gt[(size_t)(j0 + j) * BM];
-#pragma unroll
-                for (int j = 0; j < FG; ++j) {
-                  Gt[(size_t)(j0 + j) * BM] = fma(w, (double)S[j0 + j], prev[j]);
-                  S[j0 + j] = 0;
-                }
+              for (int j = 0; j < CPT; ++j) {
+                int64_t v = (int64_t)S[j];
+                v = xs >= 0 ? (int64_t)((uint64_t)v << xs) : ((v + ((int64_t)1 << (-xs - 1))) >> (-xs));
+                if (first_flush) Xt[(size_t)j * BM] = v;
+                else atomicAdd((unsigned long long*)(Xt + (size_t)j * BM), (unsigned long long)v);
+                S[j] = 0;
               }
               first_flush = false;
             }
             if (!(last_unit && di == sc.ndiag - 1) || !rv || P.fa[il * P.m + row]) continue;
-            finish_tile<CPT>(P, Gt, il, row, crow, col0, lc0, bnp);
+            finish_tile<CPT>(P, Xt, sc.xunit, il, row, crow, col0, lc0, bnp);
           }
         }
       }
@@ -581,7 +579,7 @@ int pair_bn_for(int64_t n, int request) {
 // Unit schedule.  fp64 split with s slices of b bits: diagonal q = i + j
 // (0-based slice indices, i + j <= s - 1) has weight 2^(-b (q + 2)); a unit
 // covers kcb 64-wide k blocks so that its exact integer sum stays <= 2^24.
-Sched make_pair_sched(int kernel, int slices, int bits) {
+Sched make_pair_sched(int kernel, int slices, int bits, int64_t k) {
   Sched sc;
   std::memset(&sc, 0, sizeof(sc));
   if (kernel != FAMLIES_KERNEL_TC_EMU) {
@@ -619,6 +617,20 @@ Sched make_pair_sched(int kernel, int slices, int bits) {
     int64_t fe = (((int64_t)1 << 31) - 1) / (bound * sc.kcb[di] * 64);
     sc.flush_every[di] = (int)(fe < 1 ? 1 : fe);
   }
+  // |tile sum| <= sum over diagonals of k * bound * 2^-shift (in units of 1);
+  // in units of 2^-xunit it must stay below 2^62.  No finer than the least
+  // significant diagonal's weight (that is already exact).
+  double T = 0.0;
+  for (int di = 0; di < s; ++di) {
+    const int q = s - 1 - di;
+    int64_t bound = 0;
+    for (int i = 0; i <= q; ++i) bound += maxd(i) * maxd(q - i);
+    T += std::ldexp((double)(k < 1 ? 1 : k) * (double)bound, -sc.shift[di]);
+  }
+  int xunit = (int)std::floor(62.0 - std::log2(T)) - 1;
+  if (xunit > sc.shift[0]) xunit = sc.shift[0];  // di = 0 is the least significant diagonal
+  sc.xunit = xunit;
+  for (int di = 0; di < s; ++di) sc.xshift[di] = xunit - sc.shift[di];
   return sc;
 }
 
@@ -697,7 +709,7 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   std::memset(&a, 0, sizeof(a));
   a.single = Prob{nullptr, nullptr, g.c, g.t.cm, g.t.cn, g.t.cl, pa.op[0].e, pa.op[1].e,
                   pa.op[0].flag, pa.op[1].flag, p.m, p.n, p.k, p.l, g.alpha, g.beta, bn};
-  a.sc = make_pair_sched(p.kernel, p.slices, bits);
+  a.sc = make_pair_sched(p.kernel, p.slices, bits, p.k);
   a.G = emu ? (double*)(w + L.G) : nullptr;
   a.status = g.status;
   a.wait_limit = g.wait_limit;

@@ -27,6 +27,11 @@ struct Sched {
   int flush_every[kPairMaxDiag];  // units between flushes of the int32 sums
   int npairs[kPairMaxDiag];
   int8_t pa[kPairMaxDiag][8], pb[kPairMaxDiag][8];  // slice of A and B in each pair
+  // fp64 split: the tile sums are int64 in units of 2^-xunit; a diagonal's
+  // int32 sums enter them shifted by xshift (a right shift, rounded, when
+  // negative).  xunit is as fine as K allows without int64 overflow.
+  int xunit;
+  int xshift[kPairMaxDiag];
 };
 
 // What the product needs to know about one problem.
@@ -51,7 +56,8 @@ struct TileEntry {
   int32_t p, tm, tn, il;
 };
 
-Sched make_pair_sched(int kernel, int slices, int bits);
+// k: the largest contracted extent the schedule serves (bounds the tile sums).
+Sched make_pair_sched(int kernel, int slices, int bits, int64_t k);
 int pair_bn_for(int64_t n, int request);
 // 3-D map over slices [z][rows][kp] (k innermost), box {box_k, box_rows, 1}.
 bool make_slice_map(CUtensorMap* map, void* base, bool f32, int64_t k, int64_t kp, int64_t rows,
