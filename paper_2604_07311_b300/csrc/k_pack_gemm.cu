@@ -59,7 +59,7 @@ namespace {
 
 constexpr int BM = kPairBM;
 constexpr int EPI_WARPS = 8;
-constexpr int THREADS = 32 * (EPI_WARPS + 3);  // + A producer, MMA issuer, B producer
+constexpr int THREADS = 32 * (EPI_WARPS + 2);  // + TMA producer, MMA issuer
 
 struct PairArgs {
   Prob single;           // the problem of a single-problem launch
@@ -72,25 +72,21 @@ struct PairArgs {
   int64_t wait_limit;
 };
 
-template <int KIND, int BN, bool SPLIT>
+template <int KIND, int BN>
 struct PCfg {
   static constexpr int KB = pair_stage_k(KIND);            // k per stage (128-byte rows)
   static constexpr int MMA_K = KIND == PAIR_KIND_BF16 ? 16 : 8;
   static constexpr int KSTEPS = KB / MMA_K;
   static constexpr int A_BYTES = BM * 128;
   static constexpr int B_BYTES = BN * 128;
-  // SPLIT: separate rings for the two operands, each fed by its own
-  // producer, the row operand's ring the deeper one (bf16 / tf32 products).
-  // Otherwise one producer fills both rings stage by stage and one barrier
-  // pair guards each stage (fp64 split: measured faster there).
-  static constexpr int JOINT = (200 * 1024) / (A_BYTES + B_BYTES) > 8 ? 8 : (200 * 1024) / (A_BYTES + B_BYTES);
-  static constexpr int SB = !SPLIT ? JOINT : (BN == 64 ? 6 : 4);
-  static constexpr int SA = !SPLIT ? JOINT
-                                   : ((224 * 1024 - SB * B_BYTES) / A_BYTES > 8
-                                          ? 8
-                                          : (224 * 1024 - SB * B_BYTES) / A_BYTES);
-  static constexpr int B_OFF = SA * A_BYTES;
-  static constexpr int BAR_OFF = B_OFF + SB * B_BYTES;
+  // Ring stages (as many as ~200 KB holds, at most 8).  The row operand's
+  // tiles fill one region and the column operand's another, stage s of each
+  // guarded by one barrier pair.  (Separate producers and rings of different
+  // depth per operand measured slower on both the fp64 split and bf16.)
+  static constexpr int STAGES =
+      (200 * 1024) / (A_BYTES + B_BYTES) > 8 ? 8 : (200 * 1024) / (A_BYTES + B_BYTES);
+  static constexpr int B_OFF = STAGES * A_BYTES;
+  static constexpr int BAR_OFF = B_OFF + STAGES * B_BYTES;
   static constexpr uint32_t TMEM_COLS = 2 * BN;
   static constexpr uint32_t IDESC = ptx::idesc_make(BM, BN, KIND == PAIR_KIND_BF16 ? 1u : 2u);
   static constexpr int SMEM_BYTES = BAR_OFF + 1024 + 512;
@@ -174,23 +170,20 @@ __device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, int x
   }
 }
 
-// One operand's TMA producer: walks the CTA's unit sequence (tiles,
-// diagonals, units, pairs, k blocks, exactly as the MMA issuer consumes it)
-// and fills its ring.  On a timeout it sets the abort flag; before returning
-// it waits (bounded) for its copies still in flight.
-// WHICH: 0 = the row operand only, 1 = the column operand only, 2 = both
-// into the same stage of their rings, signalled on the row ring's barriers.
-template <class Cfg, int BN, bool GROUPED, int WHICH>
+// The TMA producer: walks the CTA's unit sequence (tiles, diagonals, units,
+// pairs, k blocks, exactly as the MMA issuer consumes it) and fills stage s
+// of both operand regions per k block.  On a timeout it sets the abort flag;
+// before returning it waits (bounded) for its copies still in flight.
+template <class Cfg, int BN, bool GROUPED>
 __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap* map_a,
                                         const CUtensorMap* map_b, uint8_t* ring_a, uint8_t* ring_b,
                                         uint64_t* full, uint64_t* empty, int64_t ntiles,
                                         int64_t lim, volatile int* abort) {
-  constexpr bool IS_A = WHICH != 1;
-  constexpr int S = IS_A ? Cfg::SA : Cfg::SB;
+  constexpr int S = Cfg::STAGES;
   const Sched& sc = args.sc;
   if (!GROUPED) {
-    if (WHICH != 1) ptx::prefetch_tmap(map_a);
-    if (WHICH != 0) ptx::prefetch_tmap(map_b);
+    ptx::prefetch_tmap(map_a);
+    ptx::prefetch_tmap(map_b);
   }
   int stage = 0;
   uint32_t phase = 0;
@@ -203,7 +196,7 @@ __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap*
     const int nkb = (int)((T.P->k + Cfg::KB - 1) / Cfg::KB);
     const int l = (int)T.P->l;
     const int bnp = GROUPED ? T.P->bn : BN;  // this tile's width
-    const uint32_t bytes = (WHICH != 1 ? (uint32_t)Cfg::A_BYTES : 0u) + (WHICH != 0 ? (uint32_t)(bnp * 128) : 0u);
+    const uint32_t bytes = (uint32_t)(Cfg::A_BYTES + bnp * 128);
     const int row_a = (int)(T.tm * BM), row_b = (int)(T.tn * bnp);
     for (int di = 0; di < sc.ndiag && ok; ++di) {
       const int kcb = sc.kcb[di];
@@ -216,10 +209,8 @@ __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap*
           for (int kb = kb0; kb < kb1; ++kb) {
             if (!ptx::mbar_wait(&empty[stage], phase ^ 1, lim, abort)) { ok = false; break; }
             ptx::mbar_arrive_expect_tx(&full[stage], bytes);
-            if (WHICH != 1)
-              ptx::tma_load_3d(ring_a + stage * Cfg::A_BYTES, ma, &full[stage], kb * Cfg::KB, row_a, za);
-            if (WHICH != 0)
-              ptx::tma_load_3d(ring_b + stage * Cfg::B_BYTES, mb, &full[stage], kb * Cfg::KB, row_b, zb);
+            ptx::tma_load_3d(ring_a + stage * Cfg::A_BYTES, ma, &full[stage], kb * Cfg::KB, row_a, za);
+            ptx::tma_load_3d(ring_b + stage * Cfg::B_BYTES, mb, &full[stage], kb * Cfg::KB, row_b, zb);
             pending = (pending & ~(0x101u << stage)) | (1u << stage) | (phase << (stage + 8));
             if (++stage == S) { stage = 0; phase ^= 1; }
           }
@@ -242,15 +233,12 @@ template <int KIND, int MODE, int BN, bool GROUPED>
 __global__ void __launch_bounds__(THREADS, 1)
     k_pair_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                 const __grid_constant__ PairArgs args) {
-  constexpr bool SPLIT = MODE == PAIR_MODE_F32OUT;
-  using Cfg = PCfg<KIND, BN, SPLIT>;
+  using Cfg = PCfg<KIND, BN>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full_a = (uint64_t*)(smem + Cfg::BAR_OFF);
-  uint64_t* empty_a = full_a + Cfg::SA;
-  uint64_t* full_b = empty_a + Cfg::SA;
-  uint64_t* empty_b = full_b + Cfg::SB;
-  uint64_t* tfull = empty_b + Cfg::SB;
+  uint64_t* full = (uint64_t*)(smem + Cfg::BAR_OFF);
+  uint64_t* empty = full + Cfg::STAGES;
+  uint64_t* tfull = empty + Cfg::STAGES;
   uint64_t* tempty = tfull + 2;
   uint64_t* done = tempty + 2;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
@@ -262,13 +250,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int64_t lim = args.wait_limit;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < Cfg::SA; ++s) {
-      ptx::mbar_init(&full_a[s], 1);
-      ptx::mbar_init(&empty_a[s], 1);
-    }
-    for (int s = 0; s < Cfg::SB; ++s) {
-      ptx::mbar_init(&full_b[s], 1);
-      ptx::mbar_init(&empty_b[s], 1);
+    for (int s = 0; s < Cfg::STAGES; ++s) {
+      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(&tfull[b], 1);
@@ -287,28 +271,17 @@ __global__ void __launch_bounds__(THREADS, 1)
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  if (warp == EPI_WARPS || warp == EPI_WARPS + 2) {
-    // ------------------------------------------------------------ TMA producers
-    if (lane == 0) {
-      uint8_t* ring_b = smem + Cfg::B_OFF;
-      if (!SPLIT) {
-        if (warp == EPI_WARPS)
-          produce<Cfg, BN, GROUPED, 2>(args, &map_a, &map_b, smem, ring_b, full_a, empty_a, ntiles, lim,
-                                       abort);
-      } else if (warp == EPI_WARPS) {
-        produce<Cfg, BN, GROUPED, 0>(args, &map_a, &map_b, smem, ring_b, full_a, empty_a, ntiles, lim,
-                                     abort);
-      } else {
-        produce<Cfg, BN, GROUPED, 1>(args, &map_a, &map_b, smem, ring_b, full_b, empty_b, ntiles, lim,
-                                     abort);
-      }
-    }
+  if (warp == EPI_WARPS) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0)
+      produce<Cfg, BN, GROUPED>(args, &map_a, &map_b, smem, smem + Cfg::B_OFF, full, empty, ntiles,
+                                lim, abort);
     __syncwarp();
   } else if (warp == EPI_WARPS + 1) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
-      int sa_ = 0, sb_ = 0;
-      uint32_t pha = 0, phb = 0, acc = 0, accph = 0;
+      int stage = 0;
+      uint32_t phase = 0, acc = 0, accph = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const TileRef T = tile_at<BN, GROUPED>(args, t);
@@ -326,15 +299,11 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint32_t accumulate = 0;
             for (int p = 0; p < sc.npairs[di] && ok; ++p) {
               for (int kb = kb0; kb < kb1; ++kb) {
-                if (!ptx::mbar_wait(&full_a[sa_], pha, lim, abort) ||
-                    (SPLIT && !ptx::mbar_wait(&full_b[sb_], phb, lim, abort))) {
-                  ok = false;
-                  break;
-                }
+                if (!ptx::mbar_wait(&full[stage], phase, lim, abort)) { ok = false; break; }
                 ptx::tc_fence_after();
-                const uint64_t da = ptx::sdesc_kmajor_sw128(ptx::smem_u32(smem + sa_ * Cfg::A_BYTES));
+                const uint64_t da = ptx::sdesc_kmajor_sw128(ptx::smem_u32(smem + stage * Cfg::A_BYTES));
                 const uint64_t db =
-                    ptx::sdesc_kmajor_sw128(ptx::smem_u32(smem + Cfg::B_OFF + sb_ * Cfg::B_BYTES));
+                    ptx::sdesc_kmajor_sw128(ptx::smem_u32(smem + Cfg::B_OFF + stage * Cfg::B_BYTES));
 #pragma unroll
                 for (int kk = 0; kk < Cfg::KSTEPS; ++kk) {
                   if (KIND == PAIR_KIND_BF16)
@@ -343,10 +312,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                     ptx::mma_tf32(dt, da + 2 * kk, db + 2 * kk, idesc, accumulate);
                   accumulate = 1;
                 }
-                ptx::mma_commit(&empty_a[sa_]);
-                if (SPLIT) ptx::mma_commit(&empty_b[sb_]);
-                if (++sa_ == Cfg::SA) { sa_ = 0; pha ^= 1; }
-                if (++sb_ == Cfg::SB) { sb_ = 0; phb ^= 1; }
+                ptx::mma_commit(&empty[stage]);
+                if (++stage == Cfg::STAGES) { stage = 0; phase ^= 1; }
               }
             }
             if (!ok) break;
@@ -542,7 +509,7 @@ Layout layout_of(const Plan& p) {
 template <int KIND, int MODE, int BN, bool GROUPED>
 cudaError_t launch_pair(const CUtensorMap& ma, const CUtensorMap& mb, const PairArgs& a, int grid,
                         cudaStream_t s) {
-  using Cfg = PCfg<KIND, BN, MODE == PAIR_MODE_F32OUT>;
+  using Cfg = PCfg<KIND, BN>;
   constexpr int kMaxDev = 64;
   static bool attr[kMaxDev] = {};  // per device: function attributes are per context
   int dev = 0;
