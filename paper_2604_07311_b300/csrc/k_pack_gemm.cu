@@ -159,12 +159,16 @@ __device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, int x
     for (int j = 0; j < FG; ++j) {
       const int e = er + ecol[j];
       // 2^e built from its bits when it is a normal number
+      // x * 2^e by adding e to x's exponent field (integer arithmetic: the
+      // fp64 pipe is narrow) when the result stays a normal number
       const double x = (double)g[j];
-      const double scaled = (e >= -1022 && e <= 1023)
-                                ? x * __longlong_as_double((long long)(e + 1023) << 52)
+      const long long xb = __double_as_longlong(x);
+      const int ex = (int)((xb >> 52) & 0x7FF);
+      const double scaled = (ex != 0 && ex + e >= 1 && ex + e <= 2046)
+                                ? __longlong_as_double(xb + ((long long)e << 52))
                                 : ldexp(x, e);
-      double v = alpha * scaled;
-      if (beta != 0.0) v = fma(beta, cold[j], v);
+      double v = alpha == 1.0 ? scaled : alpha * scaled;
+      if (beta != 0.0) v = beta == 1.0 ? v + cold[j] : fma(beta, cold[j], v);
       if (use[j]) C[crow + coff[j]] = v;
     }
   }
