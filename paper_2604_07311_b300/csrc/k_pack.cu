@@ -48,6 +48,28 @@ __device__ __forceinline__ void exp_update(double v, int& mx, int& bad) {
   else mx = max(mx, max(E, 1) - 1022);
 }
 
+// Exponent bound and non-finite flag over X[base + k_off(k)] for k = k0,
+// k0 + step, ... < k1, with U independent loads in flight per thread (the
+// offsets may come from a table: one more dependent load each).
+template <int U>
+__device__ __forceinline__ void scan_row(const PackOp& o, const double* __restrict__ X, int64_t base,
+                                         int64_t k0, int64_t k1, int step, int& mx, int& bad) {
+  if (o.affine & 2) {  // affine offsets: the plain loop measures faster
+    for (int64_t k = k0; k < k1; k += step) exp_update(__ldg(X + base + k * o.ks), mx, bad);
+    return;
+  }
+  for (int64_t k = k0; k < k1; k += (int64_t)U * step) {
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t kk = k + (int64_t)u * step;
+      v[u] = kk < k1 ? __ldg(X + base + k_off(o, kk)) : 0.0;  // a zero bounds nothing
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) exp_update(v[u], mx, bad);
+  }
+}
+
 // Processes tiles b0, b0 + bstep, ... of one operand.
 __device__ __forceinline__ void rowexp_body(const PackArgs& pa, const PackOp& o, int64_t b0,
                                             int64_t bstep) {
@@ -67,7 +89,7 @@ __device__ __forceinline__ void rowexp_body(const PackArgs& pa, const PackOp& o,
         if (gr >= o.rows) break;
         const int64_t base = lo + row_off(o, gr);
         int mx = -1100, bad = 0;
-        for (int64_t k = k0 + lane; k < k1; k += 32) exp_update(__ldg(X + base + k_off(o, k)), mx, bad);
+        scan_row<8>(o, X, base, k0 + lane, k1, 32, mx, bad);
         mx = __reduce_max_sync(0xffffffffu, mx);
         bad = __reduce_or_sync(0xffffffffu, bad);
         if (lane == 0) {
@@ -82,7 +104,7 @@ __device__ __forceinline__ void rowexp_body(const PackArgs& pa, const PackOp& o,
       int mx = -1100, bad = 0;
       if (gr < o.rows) {
         const int64_t base = lo + row_off(o, gr);
-        for (int64_t k = k0 + kl; k < k1; k += 4) exp_update(__ldg(X + base + k_off(o, k)), mx, bad);
+        scan_row<8>(o, X, base, k0 + kl, k1, 4, mx, bad);
       }
       smx[kl][r] = mx;
       sbad[kl][r] = bad;
@@ -243,9 +265,18 @@ __device__ __forceinline__ void load_tile(const PackTile& t, typename PackT<PMOD
       src += (r0 + r) * o.rs;
       for (; r < PR; r += NT / PK, src += step) put(dst + r * TLD, src, kok && r < rmax);
     } else {
-      for (int r = threadIdx.x / PK; r < PR; r += NT / PK) {
-        const bool ok = kok && r < rmax;
-        put(dst + r * TLD, src + (ok ? o.roff[r0 + r] : 0), ok);
+      // the table reads first, all in flight together, then the copies
+      constexpr int NI = PR / (NT / PK);
+      int64_t off[NI];
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        const int r = threadIdx.x / PK + i * (NT / PK);
+        off[i] = kok && r < rmax ? o.roff[r0 + r] : -1;
+      }
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        const int r = threadIdx.x / PK + i * (NT / PK);
+        put(dst + r * TLD, src + (off[i] >= 0 ? off[i] : 0), off[i] >= 0);
       }
     }
   } else {
@@ -259,9 +290,17 @@ __device__ __forceinline__ void load_tile(const PackTile& t, typename PackT<PMOD
       src += (k0 + kk) * o.ks;
       for (; kk < PK; kk += NT / PR, src += step) put(dst + kk, src, rok && kk < kmax);
     } else {
-      for (int kk = threadIdx.x / PR; kk < PK; kk += NT / PR) {
-        const bool ok = rok && kk < kmax;
-        put(dst + kk, src + (ok ? o.koff[k0 + kk] : 0), ok);
+      constexpr int NI = PK / (NT / PR);
+      int64_t off[NI];
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        const int kk = threadIdx.x / PR + i * (NT / PR);
+        off[i] = rok && kk < kmax ? o.koff[k0 + kk] : -1;
+      }
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        const int kk = threadIdx.x / PR + i * (NT / PR);
+        put(dst + kk, src + (off[i] >= 0 ? off[i] : 0), off[i] >= 0);
       }
     }
   }
