@@ -62,8 +62,10 @@ __device__ __forceinline__ void scan_row(const PackOp& o, const double* __restri
     double v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int64_t kk = k + (int64_t)u * step;
-      v[u] = kk < k1 ? __ldg(X + base + k_off(o, kk)) : 0.0;  // a zero bounds nothing
+      // past the end: the last element again (it changes neither result),
+      // so that no load is predicated
+      const int64_t kk = min(k + (int64_t)u * step, k1 - 1);
+      v[u] = __ldg(X + base + k_off(o, kk));
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) exp_update(v[u], mx, bad);
@@ -89,7 +91,7 @@ __device__ __forceinline__ void rowexp_body(const PackArgs& pa, const PackOp& o,
         if (gr >= o.rows) break;
         const int64_t base = lo + row_off(o, gr);
         int mx = -1100, bad = 0;
-        scan_row<8>(o, X, base, k0 + lane, k1, 32, mx, bad);
+        scan_row<4>(o, X, base, k0 + lane, k1, 32, mx, bad);
         mx = __reduce_max_sync(0xffffffffu, mx);
         bad = __reduce_or_sync(0xffffffffu, bad);
         if (lane == 0) {
@@ -104,7 +106,7 @@ __device__ __forceinline__ void rowexp_body(const PackArgs& pa, const PackOp& o,
       int mx = -1100, bad = 0;
       if (gr < o.rows) {
         const int64_t base = lo + row_off(o, gr);
-        scan_row<8>(o, X, base, k0 + kl, k1, 4, mx, bad);
+        scan_row<4>(o, X, base, k0 + kl, k1, 4, mx, bad);
       }
       smx[kl][r] = mx;
       sbad[kl][r] = bad;
