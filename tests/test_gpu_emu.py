@@ -152,3 +152,21 @@ def test_full_ladder_sampled_dot2():
     assert rel_frob(got, want) <= TOL
     ab = want - p.beta * p.C.view()[tuple(idx.T)]
     assert np.linalg.norm(got - want) / np.linalg.norm(ab) <= 1e-12
+
+
+def test_long_k_tile_sums_stay_accurate():
+    """K = 2^20: the int64 tile sums take a coarser unit (their bound grows
+    with K) and round the least significant diagonals; sampled entries still
+    meet the fp64 bound against the oracle's compensated dot products."""
+    rng = np.random.default_rng(405)
+    m, n, k = 130, 66, 1 << 20
+    A = W.uniform_operand(rng, (m, k), [1, 2])
+    B = W.uniform_operand(rng, (k, n), [2, 3])
+    C = W.uniform_operand(rng, (m, n), [1, 3])
+    p = W.Problem("long_k", 1.0, A, B, 0.5, C)
+    Cg, _ = run_gpu(p, "f64_emu")
+    got = gpu_dense(Cg)
+    idx = np.stack([rng.integers(0, m, 64), rng.integers(0, n, 64)], axis=1)
+    want = oracle.entries(p.alpha, A.view(), A.labels, B.view(), B.labels, p.beta, C.view(),
+                          C.labels, idx, dot2=True)
+    assert rel_frob(got[idx[:, 0], idx[:, 1]], want) <= TOL
