@@ -56,21 +56,24 @@ def peaks():
 
 
 class Clocks:
-    """Samples nvidia-smi every 200 ms while the timed region runs."""
+    """Samples nvidia-smi every 25 ms around the timed region; the summary keeps
+    the samples whose own timestamps fall between mark_start() and mark_end()
+    (all samples if none do, and says so)."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, gpu_index: int):
         self.rows, self.proc, self.gpu = [], None, gpu_index
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "25"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -82,6 +85,23 @@ class Clocks:
     def _read(self):
         for line in self.proc.stdout:
             self.rows.append([x.strip() for x in line.split(",")])
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+        time.sleep(0.06)  # let the sampler emit the samples taken up to now
+
+    @staticmethod
+    def _when(stamp):
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(stamp, fmt).timestamp()
+            except ValueError:
+                pass
+        return None
 
     def __exit__(self, *exc):
         if self.proc:
@@ -97,16 +117,22 @@ class Clocks:
                 return float(x)
             except ValueError:
                 return None
-        rows = [r for r in self.rows if len(r) >= 9]
+        rows = [r for r in self.rows if len(r) >= 10]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
-        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        inside = rows
+        if self.t0 is not None and self.t1 is not None:
+            inside = [r for r in rows if (w := self._when(r[0])) is not None and self.t0 <= w <= self.t1]
+        window = "timed region" if inside else "around the timed region"
+        rows = inside or rows
+        sm = [num(r[2]) for r in rows if num(r[2]) is not None]
+        mx = [num(r[3]) for r in rows if num(r[3]) is not None]
         load = [s for s in sm if mx and s > 0.3 * max(mx)] or sm
         reasons = sorted({self.NAMES[i] for r in rows for i in range(4)
-                          if r[5 + i].strip().lower() == "active"})
+                          if r[6 + i].strip().lower() == "active"})
         return {"sm_mhz": statistics.median(load) if load else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "window": window}
 
 
 def dist_setup():
@@ -225,11 +251,13 @@ def run_gpu(args):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+        clk.mark_start()
         start.record(stream)
         for _ in range(args.steps):
             step(C)
         end.record(stream)
         torch.cuda.synchronize()
+        clk.mark_end()
         if world > 1:
             torch.distributed.barrier()
     ms, value = replica_throughput(start.elapsed_time(end) / args.steps, flops, world)
