@@ -135,12 +135,9 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
         break;
       case FAMLIES_KERNEL_TC_BF16:
       case FAMLIES_KERNEL_TC_TF32X3:
-        err = launch_packed(p, g, ws.ptr, s);
-        launches += 2;  // pack + product
-        break;
       case FAMLIES_KERNEL_TC_EMU:
         err = launch_packed(p, g, ws.ptr, s);
-        launches += 4;  // exponents + pack + product + non-finite fix-up
+        launches += packed_launches(p);
         break;
       default:
         return FAMLIES_ERR_UNSUPPORTED;

@@ -77,6 +77,8 @@ int64_t tc_workspace_bytes(const Plan& p);
 // Packed paths (bf16, tf32 split, fp64 split): workspace size and launch.
 int64_t packed_workspace_bytes(const Plan& p);
 cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream_t s);
+// Kernel launches launch_packed makes for plan p.
+int packed_launches(const Plan& p);
 
 // Number of int64 entries the offset tables of a plan need.
 inline int64_t table_entries(const Plan& p) {

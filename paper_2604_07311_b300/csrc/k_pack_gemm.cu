@@ -68,6 +68,8 @@ struct PairArgs {
   int64_t ntiles;        // grouped: tile count
   Sched sc;
   double* G;             // fp64 split: per-CTA fp64 tile sums
+  int splits;            // fp32 output, single problem: K split across CTAs (1: off)
+  float* part;           // splits > 1: fp32 partial tiles [split][tile][BN][BM]
   int* status;
   int64_t wait_limit;
 };
@@ -97,30 +99,54 @@ __device__ __forceinline__ void record_timeout(volatile int* abort, int* status)
   atomicCAS(status, 0, FAMLIES_ERR_DEVICE_TIMEOUT);
 }
 
+// One work item: an output tile (tm, tn, il) of problem P and, with split K,
+// the part of its k blocks [kb_lo, kb_hi) this item covers.
 struct TileRef {
   const Prob* P;
   int64_t tm, tn, il;
+  int64_t tile;  // single problems: the tile's number
+  int split;
+  int kb_lo, kb_hi;
 };
 
-template <int BN, bool GROUPED>
+template <int BN, bool GROUPED, bool SPLITK>
 __device__ __forceinline__ int64_t tile_count(const PairArgs& a) {
   if (GROUPED) return a.ntiles;
   const Prob& P = a.single;
-  return ((P.m + BM - 1) / BM) * ((P.n + BN - 1) / BN) * P.l;
+  return ((P.m + BM - 1) / BM) * ((P.n + BN - 1) / BN) * P.l * (SPLITK ? a.splits : 1);
 }
 
-// Tile t of the launch.  Single problems walk column tiles fastest, so the
-// CTAs running at the same time share A tiles through L2.
-template <int BN, bool GROUPED>
+// Item t of the launch.  Single problems walk column tiles fastest, so the
+// CTAs running at the same time share A tiles through L2; with split K the
+// splits are the slowest index (concurrent CTAs read the same k range).  A
+// split covers whole units of the schedule's first k-block count.
+template <int BN, bool GROUPED, int KB, bool SPLITK>
 __device__ __forceinline__ TileRef tile_at(const PairArgs& a, int64_t t) {
   if (GROUPED) {
     const TileEntry e = a.tiles[t];
-    return TileRef{a.probs + e.p, e.tm, e.tn, e.il};
+    const Prob* P = a.probs + e.p;
+    return TileRef{P, e.tm, e.tn, e.il, 0, 0, 0, (int)((P->k + KB - 1) / KB)};
   }
   const Prob& P = a.single;
   const int64_t tiles_m = (P.m + BM - 1) / BM, tiles_n = (P.n + BN - 1) / BN;
-  const int64_t tn = t % tiles_n, rest = t / tiles_n;
-  return TileRef{&a.single, rest % tiles_m, tn, rest / tiles_m};
+  const int nkb = (int)((P.k + KB - 1) / KB);
+  if (!SPLITK) {
+    const int64_t tn = t % tiles_n, rest = t / tiles_n;
+    return TileRef{&a.single, rest % tiles_m, tn, rest / tiles_m, t, 0, 0, nkb};
+  }
+  const int64_t ntile = tiles_m * tiles_n * P.l;
+  const int64_t tile = t % ntile;
+  const int split = (int)(t / ntile);
+  const int64_t tn = tile % tiles_n, rest = tile / tiles_n;
+  int lo = 0, hi = nkb;
+  {
+    const int kcb = a.sc.kcb[0];
+    const int64_t units = (nkb + kcb - 1) / kcb;
+    lo = (int)(units * split / a.splits) * kcb;
+    hi = (int)(units * (split + 1) / a.splits) * kcb;
+    hi = hi < nkb ? hi : nkb;
+  }
+  return TileRef{&a.single, rest % tiles_m, tn, rest / tiles_m, tile, split, lo, hi};
 }
 
 // The end of an fp64-split tile: C = alpha * 2^(e_m + e_n - xunit) * X + beta
@@ -178,7 +204,7 @@ __device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, int x
 // pairs, k blocks, exactly as the MMA issuer consumes it) and fills stage s
 // of both operand regions per k block.  On a timeout it sets the abort flag;
 // before returning it waits (bounded) for its copies still in flight.
-template <class Cfg, int BN, bool GROUPED>
+template <class Cfg, int BN, bool GROUPED, bool SPLITK>
 __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap* map_a,
                                         const CUtensorMap* map_b, uint8_t* ring_a, uint8_t* ring_b,
                                         uint64_t* full, uint64_t* empty, int64_t ntiles,
@@ -194,18 +220,17 @@ __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap*
   uint32_t pending = 0;  // bit s: stage s holds a copy issued in phase bit (s+8)
   bool ok = true;
   for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-    const TileRef T = tile_at<BN, GROUPED>(args, t);
+    const TileRef T = tile_at<BN, GROUPED, Cfg::KB, SPLITK>(args, t);
     const CUtensorMap* ma = GROUPED ? T.P->map_a : map_a;
     const CUtensorMap* mb = GROUPED ? T.P->map_b : map_b;
-    const int nkb = (int)((T.P->k + Cfg::KB - 1) / Cfg::KB);
     const int l = (int)T.P->l;
     const int bnp = GROUPED ? T.P->bn : BN;  // this tile's width
     const uint32_t bytes = (uint32_t)(Cfg::A_BYTES + bnp * 128);
     const int row_a = (int)(T.tm * BM), row_b = (int)(T.tn * bnp);
     for (int di = 0; di < sc.ndiag && ok; ++di) {
       const int kcb = sc.kcb[di];
-      for (int kb0 = 0; kb0 < nkb && ok; kb0 += kcb) {
-        const int kb1 = kb0 + kcb < nkb ? kb0 + kcb : nkb;
+      for (int kb0 = T.kb_lo; kb0 < T.kb_hi && ok; kb0 += kcb) {
+        const int kb1 = kb0 + kcb < T.kb_hi ? kb0 + kcb : T.kb_hi;
         for (int p = 0; p < sc.npairs[di] && ok; ++p) {
           // slices are stored [slice][batch][rows][k]
           const int za = sc.pa[di][p] * l + (int)T.il;
@@ -233,7 +258,7 @@ __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap*
   }
 }
 
-template <int KIND, int MODE, int BN, bool GROUPED>
+template <int KIND, int MODE, int BN, bool GROUPED, bool SPLITK>
 __global__ void __launch_bounds__(THREADS, 1)
     k_pair_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                 const __grid_constant__ PairArgs args) {
@@ -250,7 +275,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const Sched& sc = args.sc;
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-  const int64_t ntiles = tile_count<BN, GROUPED>(args);
+  const int64_t ntiles = tile_count<BN, GROUPED, SPLITK>(args);
   const int64_t lim = args.wait_limit;
 
   if (threadIdx.x == 0) {
@@ -278,7 +303,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == EPI_WARPS) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0)
-      produce<Cfg, BN, GROUPED>(args, &map_a, &map_b, smem, smem + Cfg::B_OFF, full, empty, ntiles,
+      produce<Cfg, BN, GROUPED, SPLITK>(args, &map_a, &map_b, smem, smem + Cfg::B_OFF, full, empty, ntiles,
                                 lim, abort);
     __syncwarp();
   } else if (warp == EPI_WARPS + 1) {
@@ -288,15 +313,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t phase = 0, acc = 0, accph = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const TileRef T = tile_at<BN, GROUPED>(args, t);
-        const int nkb = (int)((T.P->k + Cfg::KB - 1) / Cfg::KB);
+        const TileRef T = tile_at<BN, GROUPED, Cfg::KB, SPLITK>(args, t);
         // the MMA's N is this tile's width (the instruction descriptor's N field)
         const uint32_t idesc =
             GROUPED ? ptx::idesc_make(BM, T.P->bn, KIND == PAIR_KIND_BF16 ? 1u : 2u) : Cfg::IDESC;
         for (int di = 0; di < sc.ndiag && ok; ++di) {
           const int kcb = sc.kcb[di];
-          for (int kb0 = 0; kb0 < nkb && ok; kb0 += kcb) {
-            const int kb1 = kb0 + kcb < nkb ? kb0 + kcb : nkb;
+          for (int kb0 = T.kb_lo; kb0 < T.kb_hi && ok; kb0 += kcb) {
+            const int kb1 = kb0 + kcb < T.kb_hi ? kb0 + kcb : T.kb_hi;
             if (!ptx::mbar_wait(&tempty[acc], accph ^ 1, lim, abort)) { ok = false; break; }
             ptx::tc_fence_after();
             const uint32_t dt = tmem_base + acc * BN;
@@ -341,9 +365,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t acc = 0, accph = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const TileRef T = tile_at<BN, GROUPED>(args, t);
+      const TileRef T = tile_at<BN, GROUPED, Cfg::KB, SPLITK>(args, t);
       const Prob& P = *T.P;
-      const int nkb = (int)((P.k + Cfg::KB - 1) / Cfg::KB);
+      const int nkb = T.kb_hi - T.kb_lo;  // k blocks of this item
       const int64_t il = T.il;
       const int64_t row = T.tm * BM + qd * 32 + lane;
       const int bnp = GROUPED ? P.bn : BN;  // this tile's width
@@ -378,7 +402,13 @@ __global__ void __launch_bounds__(THREADS, 1)
           if (acc == 0) accph ^= 1;
         }
         if (!ok) break;
-        if (rv) {
+        if (SPLITK) {
+          // split K: this item's partial tile, reduced (with alpha, beta) later
+          float* Pt = args.part + ((size_t)T.split * (size_t)(tile_count<BN, GROUPED, SPLITK>(args) / args.splits) +
+                                   (size_t)T.tile) * BM * BN + (size_t)lc0 * BM + qd * 32 + lane;
+#pragma unroll
+          for (int j = 0; j < CPT; ++j) Pt[(size_t)j * BM] = S[j];
+        } else if (rv) {
           float* C = (float*)P.c;
           const float alpha = (float)P.alpha, beta = (float)P.beta;
 #pragma unroll
@@ -454,6 +484,32 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+// Split K: C = alpha * (sum of the splits' partial tiles, in split order) +
+// beta * C, for every element of every tile (tile numbering as tile_at's).
+__global__ void __launch_bounds__(256) k_split_reduce(const float* __restrict__ part, int splits,
+                                                     int bn, Prob P) {
+  const int64_t tiles_m = (P.m + BM - 1) / BM, tiles_n = (P.n + bn - 1) / bn;
+  const int64_t ntile = tiles_m * tiles_n * P.l;
+  const int64_t per = (int64_t)BM * bn, total = ntile * per;
+  float* C = (float*)P.c;
+  const float alpha = (float)P.alpha, beta = (float)P.beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t tile = i / per, rem = i % per;
+    const int64_t lc = rem / BM, lr = rem % BM;
+    const int64_t tn = tile % tiles_n, rest = tile / tiles_n;
+    const int64_t tm = rest % tiles_m, il = rest / tiles_m;
+    const int64_t row = tm * BM + lr, col = tn * bn + lc;
+    if (row >= P.m || col >= P.n) continue;
+    float sum = 0.f;
+    for (int sp = 0; sp < splits; ++sp) sum += part[(size_t)sp * total + i];
+    float* p = C + P.cl[il] + P.cm[row] + P.cn[col];
+    float v = alpha * sum;
+    if (beta != 0.f) v = fmaf(beta, *p, v);
+    *p = v;
+  }
+}
+
 // ----------------------------------------------------------------- launch
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                               const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -476,13 +532,30 @@ EncodeFn get_encode() {
   return fn;
 }
 
-int grid_of(const Plan& p, int bn) {
+// K splits of a single fp32-output product: when its tiles would fill at
+// most half of the SMs, the k range is split (in whole units of the
+// schedule) across CTAs so that more SMs take part; the partial tiles are
+// summed in split order by k_split_reduce.
+int split_count(const Plan& p, int bn) {
+  if (p.kernel == FAMLIES_KERNEL_TC_EMU) return 1;
   const int64_t tiles = ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l;
+  const int sms = num_sms();
+  if (tiles * 2 > sms) return 1;
+  const int kb = pair_stage_k(p.kernel == FAMLIES_KERNEL_TC_TF32X3 ? PAIR_KIND_TF32 : PAIR_KIND_BF16);
+  const int64_t units = ((p.k + kb - 1) / kb + 15) / 16;  // the fp32-output schedule's units
+  int64_t sp = sms / tiles;
+  sp = sp < units ? sp : units;
+  sp = sp < 16 ? sp : 16;
+  return (int)(sp < 1 ? 1 : sp);
+}
+
+int grid_of(const Plan& p, int bn) {
+  const int64_t tiles = ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l * split_count(p, bn);
   return (int)(tiles < num_sms() ? tiles : num_sms());
 }
 
 struct Layout {
-  size_t a, b, ea, eb, fa, fb, la, lb, G, total;
+  size_t a, b, ea, eb, fa, fb, la, lb, G, part, total;
 };
 
 Layout layout_of(const Plan& p) {
@@ -505,27 +578,45 @@ Layout layout_of(const Plan& p) {
     L.la = off; off += up((size_t)(p.l * p.m + 1) * 4);
     L.lb = off; off += up((size_t)(p.l * p.n + 1) * 4);
     L.G = off; off += up((size_t)grid_of(p, bn) * BM * bn * 8);
+  } else {
+    const int bn = pair_bn_for(p.n, p.tile_n);
+    const int sp = split_count(p, bn);
+    if (sp > 1) {
+      const size_t tiles = (size_t)((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l;
+      L.part = off; off += up((size_t)sp * tiles * BM * bn * 4);
+    }
   }
   L.total = off;
   return L;
 }
 
-template <int KIND, int MODE, int BN, bool GROUPED>
-cudaError_t launch_pair(const CUtensorMap& ma, const CUtensorMap& mb, const PairArgs& a, int grid,
-                        cudaStream_t s) {
+template <int KIND, int MODE, int BN, bool GROUPED, bool SPLITK>
+cudaError_t launch_pair_k(const CUtensorMap& ma, const CUtensorMap& mb, const PairArgs& a, int grid,
+                          cudaStream_t s) {
   using Cfg = PCfg<KIND, BN>;
   constexpr int kMaxDev = 64;
   static bool attr[kMaxDev] = {};  // per device: function attributes are per context
   int dev = 0;
   if (cudaError_t e = cudaGetDevice(&dev); e != cudaSuccess) return e;
   if (dev >= kMaxDev || !attr[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_pair_gemm<KIND, MODE, BN, GROUPED>,
+    cudaError_t e = cudaFuncSetAttribute(k_pair_gemm<KIND, MODE, BN, GROUPED, SPLITK>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     if (dev < kMaxDev) attr[dev] = true;
   }
-  k_pair_gemm<KIND, MODE, BN, GROUPED><<<grid, THREADS, Cfg::SMEM_BYTES, s>>>(ma, mb, a);
+  k_pair_gemm<KIND, MODE, BN, GROUPED, SPLITK><<<grid, THREADS, Cfg::SMEM_BYTES, s>>>(ma, mb, a);
   return cudaGetLastError();
+}
+
+template <int KIND, int MODE, int BN, bool GROUPED>
+cudaError_t launch_pair(const CUtensorMap& ma, const CUtensorMap& mb, const PairArgs& a, int grid,
+                        cudaStream_t s) {
+  // split K only for single fp32-output problems (a separate instantiation,
+  // so that the common kernel carries none of its bookkeeping)
+  if constexpr (MODE == PAIR_MODE_F32OUT && !GROUPED) {
+    if (a.splits > 1) return launch_pair_k<KIND, MODE, BN, GROUPED, true>(ma, mb, a, grid, s);
+  }
+  return launch_pair_k<KIND, MODE, BN, GROUPED, false>(ma, mb, a, grid, s);
 }
 
 template <int KIND, int MODE, bool GROUPED>
@@ -679,6 +770,15 @@ cudaError_t launch_pair_grouped(int kind, int mode, int bn, const Prob* probs,
 
 int64_t packed_workspace_bytes(const Plan& p) { return (int64_t)layout_of(p).total; }
 
+int packed_launches(const Plan& p) {
+  if (p.kernel == FAMLIES_KERNEL_TC_EMU) return 4;  // exponents + pack + product + fix-up
+  DirectView v;
+  const bool tf32 = p.kernel == FAMLIES_KERNEL_TC_TF32X3;
+  const bool da = !tf32 && direct_view(p.M, p.K, p.L, 0, p.a, &v);
+  const bool db = !tf32 && direct_view(p.N, p.K, p.L, 1, p.b, &v);
+  return ((da && db) ? 0 : 1) + 1 + (split_count(p, pair_bn_for(p.n, p.tile_n)) > 1 ? 1 : 0);
+}
+
 cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream_t s) {
   const bool emu = p.kernel == FAMLIES_KERNEL_TC_EMU;
   const bool tf32 = p.kernel == FAMLIES_KERNEL_TC_TF32X3;
@@ -736,11 +836,20 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
                   pa.op[0].flag, pa.op[1].flag, p.m, p.n, p.k, p.l, g.alpha, g.beta, bn};
   a.sc = make_pair_sched(p.kernel, p.slices, bits, p.k);
   a.G = emu ? (double*)(w + L.G) : nullptr;
+  a.splits = split_count(p, bn);
+  a.part = a.splits > 1 ? (float*)(w + L.part) : nullptr;
   a.status = g.status;
   a.wait_limit = g.wait_limit;
   const int grid = grid_of(p, bn);
   mark_begin(g, s);
   e = launch_pair_any<false>(kind, emu ? PAIR_MODE_EMU : PAIR_MODE_F32OUT, bn, ma, mb, a, grid, s);
+  if (e == cudaSuccess && a.splits > 1) {
+    const int64_t total = ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l * BM * bn;
+    const int64_t blocks = (total + 255) / 256;
+    const int cap = num_sms() * 8;
+    k_split_reduce<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(a.part, a.splits, bn, a.single);
+    e = cudaGetLastError();
+  }
   mark_end(g, s);
   if (e != cudaSuccess) return e;
   if (emu) e = launch_fixup(g, pa, s);

@@ -172,3 +172,35 @@ def test_bounded_wait_timeout_reports_status_and_context_survives(path):
     C, _ = run_gpu(p, "bf16", kernel=path)
     assert rel_frob(gpu_dense(C), run_oracle(p, in_dtype=torch.bfloat16)) <= 1e-5
     assert fm.device_status() == 0
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+def test_split_k_few_tiles(dtype):
+    """Two output tiles and a long K: the packed kernel splits K across CTAs
+    and sums the partial tiles (with alpha, beta) afterwards; the launch
+    count reports the extra reduction."""
+    rng = np.random.default_rng(640)
+    m, n, k = 200, 64, 8192
+    A = W.uniform_operand(rng, (m, k), [1, 2])
+    B = W.uniform_operand(rng, (k, n), [2, 3])
+    C = W.uniform_operand(rng, (m, n), [1, 3])
+    p = W.Problem("split_k", 0.75, A, B, -1.5, C)
+    Cg, info = run_gpu(p, dtype, kernel=KERNEL_PACKED)
+    assert info["launches"] == 4  # tables + pack + product + split reduction
+    tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
+    want = run_oracle(p, in_dtype=tdt, out_dtype=torch.float32)
+    assert rel_frob(gpu_dense(Cg), want) <= (1e-5 if dtype == "bf16" else TOL_F32)
+
+
+def test_split_k_integer_exact():
+    """Integer-valued bf16 inputs: every partial sum is exact, so splitting K
+    changes nothing."""
+    rng = np.random.default_rng(641)
+    m, n, k = 130, 70, 4096
+    A = W.integer_operand(rng, (m, k), [1, 2])
+    B = W.integer_operand(rng, (k, n), [2, 3])
+    C = W.zeros_operand((m, n), [1, 3])
+    p = W.Problem("split_k_int", 1.0, A, B, 0.0, C)
+    Cg, info = run_gpu(p, "bf16", kernel=KERNEL_PACKED)
+    assert info["launches"] == 4
+    assert np.array_equal(gpu_dense(Cg), run_oracle(p))
