@@ -40,6 +40,7 @@
 // block-sparse contraction) run the same kernel over a device tile list:
 // each entry names its problem, whose descriptor (TMA maps in global memory,
 // C's offset tables, scalars) the roles read per tile.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -140,7 +141,9 @@ __device__ __forceinline__ TileRef tile_at(const PairArgs& a, int64_t t) {
   const int64_t tn = tile % tiles_n, rest = tile / tiles_n;
   int lo = 0, hi = nkb;
   {
-    const int kcb = a.sc.kcb[0];
+    // fp32 output: whole units of its schedule; fp64 split: any k block
+    // (each diagonal forms its units inside the range)
+    const int kcb = a.sc.ndiag > 1 ? 1 : a.sc.kcb[0];
     const int64_t units = (nkb + kcb - 1) / kcb;
     lo = (int)(units * split / a.splits) * kcb;
     hi = (int)(units * (split + 1) / a.splits) * kcb;
@@ -427,7 +430,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         int32_t S[CPT];
 #pragma unroll
         for (int j = 0; j < CPT; ++j) S[j] = 0;
-        int64_t* Xt = (int64_t*)args.G + (size_t)blockIdx.x * BM * BN + (size_t)(hf * CPT) * BM + qd * 32 + lane;
+        // tile sums: per CTA, or (split K) per tile, shared by the tile's
+        // splits through the reductions and finished by k_split_finish
+        const size_t xslot = SPLITK ? (size_t)T.tile : (size_t)blockIdx.x;
+        int64_t* Xt = (int64_t*)args.G + xslot * BM * BN + (size_t)(hf * CPT) * BM + qd * 32 + lane;
         bool first_flush = true;
         for (int di = 0; di < sc.ndiag && ok; ++di) {
           const int kcb = sc.kcb[di];
@@ -461,13 +467,13 @@ __global__ void __launch_bounds__(THREADS, 1)
               for (int j = 0; j < CPT; ++j) {
                 int64_t v = (int64_t)S[j];
                 v = xs >= 0 ? (int64_t)((uint64_t)v << xs) : ((v + ((int64_t)1 << (-xs - 1))) >> (-xs));
-                if (first_flush) Xt[(size_t)j * BM] = v;
+                if (first_flush && !SPLITK) Xt[(size_t)j * BM] = v;
                 else atomicAdd((unsigned long long*)(Xt + (size_t)j * BM), (unsigned long long)v);
                 S[j] = 0;
               }
               first_flush = false;
             }
-            if (!(last_unit && di == sc.ndiag - 1) || !rv || P.fa[il * P.m + row]) continue;
+            if (SPLITK || !(last_unit && di == sc.ndiag - 1) || !rv || P.fa[il * P.m + row]) continue;
             finish_tile<CPT>(P, Xt, sc.xunit, il, row, crow, col0, lc0, bnp);
           }
         }
@@ -510,6 +516,37 @@ __global__ void __launch_bounds__(256) k_split_reduce(const float* __restrict__ 
   }
 }
 
+// Split K, fp64 split: the splits of a tile added their int64 sums into one
+// slot; C = alpha * 2^(e_m + e_n - xunit) * sum + beta * C for every element
+// (rows and columns holding Inf/NaN are left to the native fix-up).
+__global__ void __launch_bounds__(256) k_split_finish(const int64_t* __restrict__ X, int bn,
+                                                     int xunit, Prob P) {
+  const int64_t tiles_m = (P.m + BM - 1) / BM, tiles_n = (P.n + bn - 1) / bn;
+  const int64_t per = (int64_t)BM * bn, total = tiles_m * tiles_n * P.l * per;
+  double* C = (double*)P.c;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t tile = i / per, rem = i % per;
+    const int64_t lc = rem / BM, lr = rem % BM;
+    const int64_t tn = tile % tiles_n, rest = tile / tiles_n;
+    const int64_t tm = rest % tiles_m, il = rest / tiles_m;
+    const int64_t row = tm * BM + lr, col = tn * bn + lc;
+    if (row >= P.m || col >= P.n) continue;
+    if (P.fa[il * P.m + row] || P.fb[il * P.n + col]) continue;
+    const double x = (double)X[i];
+    const int e = P.ea[il * P.m + row] + P.eb[il * P.n + col] - xunit;
+    const long long xb = __double_as_longlong(x);
+    const int ex = (int)((xb >> 52) & 0x7FF);
+    const double scaled = (ex != 0 && ex + e >= 1 && ex + e <= 2046)
+                              ? __longlong_as_double(xb + ((long long)e << 52))
+                              : ldexp(x, e);
+    double* p = C + P.cl[il] + P.cm[row] + P.cn[col];
+    double v = P.alpha == 1.0 ? scaled : P.alpha * scaled;
+    if (P.beta != 0.0) v = P.beta == 1.0 ? v + *p : fma(P.beta, *p, v);
+    *p = v;
+  }
+}
+
 // ----------------------------------------------------------------- launch
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                               const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -537,12 +574,14 @@ EncodeFn get_encode() {
 // schedule) across CTAs so that more SMs take part; the partial tiles are
 // summed in split order by k_split_reduce.
 int split_count(const Plan& p, int bn) {
-  if (p.kernel == FAMLIES_KERNEL_TC_EMU) return 1;
   const int64_t tiles = ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l;
   const int sms = num_sms();
   if (tiles * 2 > sms) return 1;
   const int kb = pair_stage_k(p.kernel == FAMLIES_KERNEL_TC_TF32X3 ? PAIR_KIND_TF32 : PAIR_KIND_BF16);
-  const int64_t units = ((p.k + kb - 1) / kb + 15) / 16;  // the fp32-output schedule's units
+  // pieces a split may take: fp32 output, the schedule's units (16 k blocks);
+  // fp64 split, 8 k blocks at least (its units form inside each range)
+  const int64_t units = p.kernel == FAMLIES_KERNEL_TC_EMU ? ((p.k + kb - 1) / kb) / 8
+                                                          : ((p.k + kb - 1) / kb + 15) / 16;
   int64_t sp = sms / tiles;
   sp = sp < units ? sp : units;
   sp = sp < 16 ? sp : 16;
@@ -577,7 +616,10 @@ Layout layout_of(const Plan& p) {
     L.fb = off; off += up((size_t)p.l * p.n * 4);
     L.la = off; off += up((size_t)(p.l * p.m + 1) * 4);
     L.lb = off; off += up((size_t)(p.l * p.n + 1) * 4);
-    L.G = off; off += up((size_t)grid_of(p, bn) * BM * bn * 8);
+    // per-CTA tile sums, or (split K) one per tile
+    const size_t ntile = (size_t)((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l;
+    const size_t slots = split_count(p, bn) > 1 ? ntile : (size_t)grid_of(p, bn);
+    L.G = off; off += up(slots * BM * bn * 8);
   } else {
     const int bn = pair_bn_for(p.n, p.tile_n);
     const int sp = split_count(p, bn);
@@ -611,9 +653,9 @@ cudaError_t launch_pair_k(const CUtensorMap& ma, const CUtensorMap& mb, const Pa
 template <int KIND, int MODE, int BN, bool GROUPED>
 cudaError_t launch_pair(const CUtensorMap& ma, const CUtensorMap& mb, const PairArgs& a, int grid,
                         cudaStream_t s) {
-  // split K only for single fp32-output problems (a separate instantiation,
-  // so that the common kernel carries none of its bookkeeping)
-  if constexpr (MODE == PAIR_MODE_F32OUT && !GROUPED) {
+  // split K only for single problems (a separate instantiation, so that the
+  // common kernel carries none of its bookkeeping)
+  if constexpr (!GROUPED) {
     if (a.splits > 1) return launch_pair_k<KIND, MODE, BN, GROUPED, true>(ma, mb, a, grid, s);
   }
   return launch_pair_k<KIND, MODE, BN, GROUPED, false>(ma, mb, a, grid, s);
@@ -771,7 +813,8 @@ cudaError_t launch_pair_grouped(int kind, int mode, int bn, const Prob* probs,
 int64_t packed_workspace_bytes(const Plan& p) { return (int64_t)layout_of(p).total; }
 
 int packed_launches(const Plan& p) {
-  if (p.kernel == FAMLIES_KERNEL_TC_EMU) return 4;  // exponents + pack + product + fix-up
+  if (p.kernel == FAMLIES_KERNEL_TC_EMU)  // exponents + pack + product (+ split finish) + fix-up
+    return 4 + (split_count(p, pair_bn_for(p.n, p.tile_n)) > 1 ? 1 : 0);
   DirectView v;
   const bool tf32 = p.kernel == FAMLIES_KERNEL_TC_TF32X3;
   const bool da = !tf32 && direct_view(p.M, p.K, p.L, 0, p.a, &v);
@@ -841,13 +884,18 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   a.status = g.status;
   a.wait_limit = g.wait_limit;
   const int grid = grid_of(p, bn);
+  const int64_t split_elems = ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l * BM * bn;
+  const int split_grid = (int)std::min<int64_t>((split_elems + 255) / 256, (int64_t)num_sms() * 8);
+  if (emu && a.splits > 1 &&
+      (e = cudaMemsetAsync(a.G, 0, (size_t)split_elems * 8, s)) != cudaSuccess)
+    return e;
   mark_begin(g, s);
   e = launch_pair_any<false>(kind, emu ? PAIR_MODE_EMU : PAIR_MODE_F32OUT, bn, ma, mb, a, grid, s);
   if (e == cudaSuccess && a.splits > 1) {
-    const int64_t total = ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l * BM * bn;
-    const int64_t blocks = (total + 255) / 256;
-    const int cap = num_sms() * 8;
-    k_split_reduce<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(a.part, a.splits, bn, a.single);
+    if (emu)
+      k_split_finish<<<split_grid, 256, 0, s>>>((const int64_t*)a.G, bn, a.sc.xunit, a.single);
+    else
+      k_split_reduce<<<split_grid, 256, 0, s>>>(a.part, a.splits, bn, a.single);
     e = cudaGetLastError();
   }
   mark_end(g, s);

@@ -170,3 +170,24 @@ def test_long_k_tile_sums_stay_accurate():
     want = oracle.entries(p.alpha, A.view(), A.labels, B.view(), B.labels, p.beta, C.view(),
                           C.labels, idx, dot2=True)
     assert rel_frob(got[idx[:, 0], idx[:, 1]], want) <= TOL
+
+
+def test_split_k_few_tiles_with_nonfinite_row():
+    """Two output tiles and K = 16384: the k range is split across CTAs, the
+    splits add into one int64 sum per tile (exact, in any order) and a
+    finishing kernel writes C; a row holding NaN still goes to the native
+    fix-up."""
+    rng = np.random.default_rng(406)
+    m, n, k = 200, 100, 16384
+    A = rng.uniform(-1, 1, (m, k))
+    A[17, 5000] = np.nan
+    Aop = W.Operand(np.asfortranarray(A).reshape(-1, order="F").copy(), (m, k), (1, m), [1, 2])
+    B = W.uniform_operand(rng, (k, n), [2, 3])
+    C = W.uniform_operand(rng, (m, n), [1, 3])
+    p = W.Problem("split_k_emu", -0.5, Aop, B, 2.0, C)
+    Cg, info = run_gpu(p, "f64_emu")
+    assert info["launches"] == 6  # tables, exponents, pack, product, split finish, fix-up
+    got, want = gpu_dense(Cg), run_oracle(p)
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    fin = ~np.isnan(want)
+    assert rel_frob(got[fin], want[fin]) <= TOL
