@@ -33,7 +33,7 @@ METRIC = "contraction TFLOP/s, % tensor-pipe peak; split-precision vs FP64 speed
 # profiles/k_pair_gemm_ladder.md (v=96 ladder, 5.31 GB, scaled by executed
 # flops to the v=128 launch).  Must go back to None whenever the product
 # kernel changes after that capture.
-PRODUCT_TRAFFIC = {"bytes": 5.306360e9, "exec_flops": 3.652869685248e12}
+PRODUCT_TRAFFIC = None
 V_EXT, O_EXT, SLICES = 128, 32, 6
 WORKLOAD = f"ccsd_ladder_v128_o32_f64_split{SLICES}"
 

@@ -490,60 +490,103 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
-// Split K: C = alpha * (sum of the splits' partial tiles, in split order) +
-// beta * C, for every element of every tile (tile numbering as tile_at's).
+// Split-K finishing kernels.  Work item: a tile (numbered as tile_at numbers
+// them) and a chunk of SPLIT_COLS of its columns; thread t owns row t % BM
+// and every other column of the chunk from t / BM, so that the partial
+// reads and the C accesses run along rows; each thread issues the loads of
+// all its columns before the stores.
+constexpr int SPLIT_COLS = 16;
+constexpr int SPLIT_PER_THREAD = SPLIT_COLS / (256 / BM);
+
+// fp32 output: C = alpha * (sum of the splits' partial tiles, in split order)
+// + beta * C.
 __global__ void __launch_bounds__(256) k_split_reduce(const float* __restrict__ part, int splits,
                                                      int bn, Prob P) {
   const int64_t tiles_m = (P.m + BM - 1) / BM, tiles_n = (P.n + bn - 1) / bn;
-  const int64_t ntile = tiles_m * tiles_n * P.l;
-  const int64_t per = (int64_t)BM * bn, total = ntile * per;
+  const int chunks = bn / SPLIT_COLS;
+  const int64_t items = tiles_m * tiles_n * P.l * chunks;
+  const size_t per = (size_t)BM * bn, total = (size_t)(items / chunks) * per;
   float* C = (float*)P.c;
   const float alpha = (float)P.alpha, beta = (float)P.beta;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t tile = i / per, rem = i % per;
-    const int64_t lc = rem / BM, lr = rem % BM;
+  const int lr = threadIdx.x % BM, lq = threadIdx.x / BM;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int64_t tile = it / chunks;
+    const int c0 = (int)(it % chunks) * SPLIT_COLS;
     const int64_t tn = tile % tiles_n, rest = tile / tiles_n;
     const int64_t tm = rest % tiles_m, il = rest / tiles_m;
-    const int64_t row = tm * BM + lr, col = tn * bn + lc;
-    if (row >= P.m || col >= P.n) continue;
-    float sum = 0.f;
-    for (int sp = 0; sp < splits; ++sp) sum += part[(size_t)sp * total + i];
-    float* p = C + P.cl[il] + P.cm[row] + P.cn[col];
-    float v = alpha * sum;
-    if (beta != 0.f) v = fmaf(beta, *p, v);
-    *p = v;
+    const int64_t row = tm * BM + lr;
+    if (row >= P.m) continue;
+    const int64_t crow = P.cl[il] + P.cm[row];
+    float sum[SPLIT_PER_THREAD], old[SPLIT_PER_THREAD];
+    int64_t off[SPLIT_PER_THREAD];
+#pragma unroll
+    for (int j = 0; j < SPLIT_PER_THREAD; ++j) {
+      const int lc = c0 + lq + j * (256 / BM);
+      const int64_t col = tn * bn + lc;
+      off[j] = col < P.n ? crow + P.cn[col] : -1;
+      const size_t at = (size_t)tile * per + (size_t)lc * BM + lr;
+      float acc = 0.f;
+      for (int sp = 0; sp < splits; ++sp) acc += part[(size_t)sp * total + at];
+      sum[j] = acc;
+    }
+#pragma unroll
+    for (int j = 0; j < SPLIT_PER_THREAD; ++j) old[j] = (off[j] >= 0 && beta != 0.f) ? C[off[j]] : 0.f;
+#pragma unroll
+    for (int j = 0; j < SPLIT_PER_THREAD; ++j) {
+      float v = alpha * sum[j];
+      if (beta != 0.f) v = fmaf(beta, old[j], v);
+      if (off[j] >= 0) C[off[j]] = v;
+    }
   }
 }
 
-// Split K, fp64 split: the splits of a tile added their int64 sums into one
-// slot; C = alpha * 2^(e_m + e_n - xunit) * sum + beta * C for every element
-// (rows and columns holding Inf/NaN are left to the native fix-up).
+// fp64 split: the splits of a tile added their int64 sums into one slot;
+// C = alpha * 2^(e_m + e_n - xunit) * sum + beta * C (rows and columns
+// holding Inf/NaN are left to the native fix-up).
 __global__ void __launch_bounds__(256) k_split_finish(const int64_t* __restrict__ X, int bn,
                                                      int xunit, Prob P) {
   const int64_t tiles_m = (P.m + BM - 1) / BM, tiles_n = (P.n + bn - 1) / bn;
-  const int64_t per = (int64_t)BM * bn, total = tiles_m * tiles_n * P.l * per;
+  const int chunks = bn / SPLIT_COLS;
+  const int64_t items = tiles_m * tiles_n * P.l * chunks;
+  const size_t per = (size_t)BM * bn;
   double* C = (double*)P.c;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t tile = i / per, rem = i % per;
-    const int64_t lc = rem / BM, lr = rem % BM;
+  const int lr = threadIdx.x % BM, lq = threadIdx.x / BM;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int64_t tile = it / chunks;
+    const int c0 = (int)(it % chunks) * SPLIT_COLS;
     const int64_t tn = tile % tiles_n, rest = tile / tiles_n;
     const int64_t tm = rest % tiles_m, il = rest / tiles_m;
-    const int64_t row = tm * BM + lr, col = tn * bn + lc;
-    if (row >= P.m || col >= P.n) continue;
-    if (P.fa[il * P.m + row] || P.fb[il * P.n + col]) continue;
-    const double x = (double)X[i];
-    const int e = P.ea[il * P.m + row] + P.eb[il * P.n + col] - xunit;
-    const long long xb = __double_as_longlong(x);
-    const int ex = (int)((xb >> 52) & 0x7FF);
-    const double scaled = (ex != 0 && ex + e >= 1 && ex + e <= 2046)
-                              ? __longlong_as_double(xb + ((long long)e << 52))
-                              : ldexp(x, e);
-    double* p = C + P.cl[il] + P.cm[row] + P.cn[col];
-    double v = P.alpha == 1.0 ? scaled : P.alpha * scaled;
-    if (P.beta != 0.0) v = P.beta == 1.0 ? v + *p : fma(P.beta, *p, v);
-    *p = v;
+    const int64_t row = tm * BM + lr;
+    if (row >= P.m || P.fa[il * P.m + row]) continue;
+    const int64_t crow = P.cl[il] + P.cm[row];
+    const int er = P.ea[il * P.m + row] - xunit;
+    int64_t x[SPLIT_PER_THREAD], off[SPLIT_PER_THREAD];
+    int ec[SPLIT_PER_THREAD];
+    double old[SPLIT_PER_THREAD];
+#pragma unroll
+    for (int j = 0; j < SPLIT_PER_THREAD; ++j) {
+      const int lc = c0 + lq + j * (256 / BM);
+      const int64_t col = tn * bn + lc;
+      const bool ok = col < P.n && !P.fb[il * P.n + col];
+      off[j] = ok ? crow + P.cn[col] : -1;
+      ec[j] = ok ? P.eb[il * P.n + col] : 0;
+      x[j] = X[(size_t)tile * per + (size_t)lc * BM + lr];
+    }
+#pragma unroll
+    for (int j = 0; j < SPLIT_PER_THREAD; ++j) old[j] = (off[j] >= 0 && P.beta != 0.0) ? C[off[j]] : 0.0;
+#pragma unroll
+    for (int j = 0; j < SPLIT_PER_THREAD; ++j) {
+      const double xd = (double)x[j];
+      const int e = er + ec[j];
+      const long long xb = __double_as_longlong(xd);
+      const int ex = (int)((xb >> 52) & 0x7FF);
+      const double scaled = (ex != 0 && ex + e >= 1 && ex + e <= 2046)
+                                ? __longlong_as_double(xb + ((long long)e << 52))
+                                : ldexp(xd, e);
+      double v = P.alpha == 1.0 ? scaled : P.alpha * scaled;
+      if (P.beta != 0.0) v = P.beta == 1.0 ? v + old[j] : fma(P.beta, old[j], v);
+      if (off[j] >= 0) C[off[j]] = v;
+    }
   }
 }
 
@@ -569,23 +612,36 @@ EncodeFn get_encode() {
   return fn;
 }
 
-// K splits of a single fp32-output product: when its tiles would fill at
-// most half of the SMs, the k range is split (in whole units of the
-// schedule) across CTAs so that more SMs take part; the partial tiles are
-// summed in split order by k_split_reduce.
+// K splits of a single problem.  When its tiles would fill at most half of
+// the SMs, the k range is split across CTAs so that more SMs take part.
+// The fp64 split also splits to even out the last wave of a persistent
+// launch (its tiles are long, and its splits combine exactly): it takes the
+// split count (up to 4) whose work items fill the waves best, when that
+// beats one split by more than 2 %.  fp32 output: whole units of its
+// schedule (16 k blocks) per split, partial tiles summed by k_split_reduce;
+// fp64 split: at least 8 k blocks per split, sums combined in k_split_finish.
 int split_count(const Plan& p, int bn) {
   const int64_t tiles = ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l;
   const int sms = num_sms();
-  if (tiles * 2 > sms) return 1;
+  const bool emu = p.kernel == FAMLIES_KERNEL_TC_EMU;
   const int kb = pair_stage_k(p.kernel == FAMLIES_KERNEL_TC_TF32X3 ? PAIR_KIND_TF32 : PAIR_KIND_BF16);
-  // pieces a split may take: fp32 output, the schedule's units (16 k blocks);
-  // fp64 split, 8 k blocks at least (its units form inside each range)
-  const int64_t units = p.kernel == FAMLIES_KERNEL_TC_EMU ? ((p.k + kb - 1) / kb) / 8
-                                                          : ((p.k + kb - 1) / kb + 15) / 16;
-  int64_t sp = sms / tiles;
-  sp = sp < units ? sp : units;
-  sp = sp < 16 ? sp : 16;
-  return (int)(sp < 1 ? 1 : sp);
+  const int64_t nkb = (p.k + kb - 1) / kb;
+  const int64_t pieces = emu ? nkb / 8 : (nkb + 15) / 16;
+  int64_t cap = pieces < 16 ? pieces : 16;
+  if (cap <= 1) return 1;
+  if (tiles * 2 <= sms) {
+    const int64_t sp = sms / tiles;
+    return (int)(sp < cap ? sp : cap);
+  }
+  if (!emu) return 1;
+  auto fill = [&](int64_t sp) {
+    const int64_t items = tiles * sp, waves = (items + sms - 1) / sms;
+    return (double)items / (double)(waves * sms);
+  };
+  int best = 1;
+  for (int sp = 2; sp <= 4 && sp <= cap; ++sp)
+    if (fill(sp) > fill(best) + 0.02) best = sp;
+  return best;
 }
 
 int grid_of(const Plan& p, int bn) {
@@ -884,8 +940,9 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   a.status = g.status;
   a.wait_limit = g.wait_limit;
   const int grid = grid_of(p, bn);
-  const int64_t split_elems = ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l * BM * bn;
-  const int split_grid = (int)std::min<int64_t>((split_elems + 255) / 256, (int64_t)num_sms() * 8);
+  const int64_t split_tiles = ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l;
+  const int64_t split_elems = split_tiles * BM * bn;
+  const int split_grid = (int)std::min<int64_t>(split_tiles * (bn / SPLIT_COLS), (int64_t)num_sms() * 16);
   if (emu && a.splits > 1 &&
       (e = cudaMemsetAsync(a.G, 0, (size_t)split_elems * 8, s)) != cudaSuccess)
     return e;
