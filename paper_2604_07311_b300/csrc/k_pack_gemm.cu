@@ -948,6 +948,7 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     return e;
   mark_begin(g, s);
   e = launch_pair_any<false>(kind, emu ? PAIR_MODE_EMU : PAIR_MODE_F32OUT, bn, ma, mb, a, grid, s);
+  mark_end(g, s);  // the events bracket the product kernel alone
   if (e == cudaSuccess && a.splits > 1) {
     if (emu)
       k_split_finish<<<split_grid, 256, 0, s>>>((const int64_t*)a.G, bn, a.sc.xunit, a.single);
@@ -955,7 +956,6 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
       k_split_reduce<<<split_grid, 256, 0, s>>>(a.part, a.splits, bn, a.single);
     e = cudaGetLastError();
   }
-  mark_end(g, s);
   if (e != cudaSuccess) return e;
   if (emu) e = launch_fixup(g, pa, s);
   return e;
