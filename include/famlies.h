@@ -123,6 +123,11 @@ typedef struct {
  *               the dtype has no kernel for returns FAMLIES_ERR_UNSUPPORTED.
  *   tile_n      tensor-core tile width (64, 128 or 256; 0 = automatic).
  *   wait_limit  iteration cap of every bounded wait (0 = default).
+ *   stall_test  testing only (0 in normal use): nonzero makes the
+ *               tensor-core product kernels first wait, bounded by
+ *               wait_limit, on a barrier phase that nothing completes, so
+ *               the call's kernels stop early and the device status reads
+ *               FAMLIES_ERR_DEVICE_TIMEOUT; C is then left unspecified.
  *   events      optional pair of cudaEvent_t handles created by the caller
  *               (NULL = none): the library records events[0] on the call's
  *               stream immediately before the main product kernel and
@@ -132,7 +137,7 @@ typedef struct {
   int32_t slices;
   int32_t kernel;
   int32_t tile_n;
-  int32_t reserved0;
+  int32_t stall_test;
   int64_t wait_limit;
   void* events[2];
   int64_t reserved[2];

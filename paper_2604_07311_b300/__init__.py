@@ -42,7 +42,7 @@ def _stream_handle(stream):
 
 
 def contract(alpha, A, la, B, lb, beta, C, lc, dtype=None, stream=None, *, slices=0, kernel=0,
-             tile_n=0, wait_limit=0, events=None, return_info=False):
+             tile_n=0, wait_limit=0, events=None, return_info=False, stall_test=0):
     """C := alpha * contract(A, B) + beta * C on the GPU, in place on C.
 
     A, B, C are CUDA torch tensors (any non-negative strides); la, lb, lc are
@@ -54,7 +54,7 @@ def contract(alpha, A, la, B, lb, beta, C, lc, dtype=None, stream=None, *, slice
     code = _dtype_code(dtype, A, C)
     da, db, dc = desc_torch(A, la), desc_torch(B, lb), desc_torch(C, lc)
     info = PlanInfo()
-    opt = options(slices, kernel, tile_n, wait_limit, events)
+    opt = options(slices, kernel, tile_n, wait_limit, events, stall_test)
     check(lib.famlies_contract_ex(float(alpha), da.ref, db.ref, float(beta), dc.ref, code,
                                   _stream_handle(stream), opt, info))
     return (C, info.as_dict()) if return_info else C

@@ -34,7 +34,7 @@ class TensorDesc(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("slices", ctypes.c_int32), ("kernel", ctypes.c_int32), ("tile_n", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("wait_limit", ctypes.c_int64),
+                ("stall_test", ctypes.c_int32), ("wait_limit", ctypes.c_int64),
                 ("events", ctypes.c_void_p * 2), ("reserved", ctypes.c_int64 * 2)]
 
 
@@ -132,10 +132,11 @@ def desc_numpy(x, labels) -> Desc:
     return Desc(x.shape, tuple(s // es for s in x.strides), labels, x.__array_interface__["data"][0])
 
 
-def options(slices=0, kernel=0, tile_n=0, wait_limit=0, events=None) -> Options:
+def options(slices=0, kernel=0, tile_n=0, wait_limit=0, events=None, stall_test=0) -> Options:
     """events: optional (begin, end) torch.cuda.Event pair recorded around the product kernel."""
     o = Options()
     o.slices, o.kernel, o.tile_n, o.wait_limit = int(slices), int(kernel), int(tile_n), int(wait_limit)
+    o.stall_test = int(stall_test)
     if events is not None:
         for i, ev in enumerate(events):
             if getattr(ev, "cuda_event", 0) == 0:

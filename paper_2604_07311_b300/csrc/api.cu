@@ -120,6 +120,7 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
     g.wait_limit = (opt && opt->wait_limit > 0) ? opt->wait_limit : env_wait_limit();
     g.status = device_status_ptr();
     if (!g.status) return FAMLIES_ERR_CUDA;
+    g.stall_test = opt ? opt->stall_test : 0;
     g.ev_begin = opt ? (cudaEvent_t)opt->events[0] : nullptr;
     g.ev_end = opt ? (cudaEvent_t)opt->events[1] : nullptr;
     switch (p.kernel) {

@@ -35,6 +35,7 @@ struct GemmArgs {
   int a_contig, b_contig;  // 1: unit stride along rows/cols, 2: along k
   int64_t wait_limit;      // iteration cap of every bounded wait
   int* status;             // device status word (first error recorded wins)
+  int stall_test;          // testing: product kernels first wait on a barrier nothing completes
   cudaEvent_t ev_begin, ev_end;  // host only: recorded around the product kernel
 };
 

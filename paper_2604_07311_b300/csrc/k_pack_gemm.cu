@@ -70,6 +70,7 @@ struct PairArgs {
   Sched sc;
   double* G;             // fp64 split: per-CTA fp64 tile sums
   int splits;            // fp32 output, single problem: K split across CTAs (1: off)
+  int stall_test;        // testing: the MMA issuer first waits on a barrier nothing completes
   float* part;           // splits > 1: fp32 partial tiles [split][tile][BN][BM]
   int* status;
   int64_t wait_limit;
@@ -77,11 +78,12 @@ struct PairArgs {
 
 template <int KIND, int BN>
 struct PCfg {
-  static constexpr int KB = pair_stage_k(KIND);            // k per stage (128-byte rows)
+  static constexpr int KB = pair_stage_k(KIND);            // k per stage
+  static constexpr int ROWB = pair_row_bytes(KIND);        // bytes of one tile row in a stage
   static constexpr int MMA_K = KIND == PAIR_KIND_BF16 ? 16 : 8;
   static constexpr int KSTEPS = KB / MMA_K;
-  static constexpr int A_BYTES = BM * 128;
-  static constexpr int B_BYTES = BN * 128;
+  static constexpr int A_BYTES = BM * ROWB;
+  static constexpr int B_BYTES = BN * ROWB;
   // Ring stages (as many as ~200 KB holds, at most 8).  The row operand's
   // tiles fill one region and the column operand's another, stage s of each
   // guarded by one barrier pair.  (Separate producers and rings of different
@@ -228,7 +230,7 @@ __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap*
     const CUtensorMap* mb = GROUPED ? T.P->map_b : map_b;
     const int l = (int)T.P->l;
     const int bnp = GROUPED ? T.P->bn : BN;  // this tile's width
-    const uint32_t bytes = (uint32_t)(Cfg::A_BYTES + bnp * 128);
+    const uint32_t bytes = (uint32_t)(Cfg::A_BYTES + bnp * Cfg::ROWB);
     const int row_a = (int)(T.tm * BM), row_b = (int)(T.tn * bnp);
     for (int di = 0; di < sc.ndiag && ok; ++di) {
       const int kcb = sc.kcb[di];
@@ -314,7 +316,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0, acc = 0, accph = 0;
-      bool ok = true;
+      // testing: `done` completes only after this thread's last commit
+      bool ok = !args.stall_test || ptx::mbar_wait(done, 0, lim, abort);
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const TileRef T = tile_at<BN, GROUPED, Cfg::KB, SPLITK>(args, t);
         // the MMA's N is this tile's width (the instruction descriptor's N field)
@@ -332,9 +335,9 @@ __global__ void __launch_bounds__(THREADS, 1)
               for (int kb = kb0; kb < kb1; ++kb) {
                 if (!ptx::mbar_wait(&full[stage], phase, lim, abort)) { ok = false; break; }
                 ptx::tc_fence_after();
-                const uint64_t da = ptx::sdesc_kmajor_sw128(ptx::smem_u32(smem + stage * Cfg::A_BYTES));
+                const uint64_t da = ptx::sdesc_kmajor<Cfg::ROWB>(ptx::smem_u32(smem + stage * Cfg::A_BYTES));
                 const uint64_t db =
-                    ptx::sdesc_kmajor_sw128(ptx::smem_u32(smem + Cfg::B_OFF + stage * Cfg::B_BYTES));
+                    ptx::sdesc_kmajor<Cfg::ROWB>(ptx::smem_u32(smem + Cfg::B_OFF + stage * Cfg::B_BYTES));
 #pragma unroll
                 for (int kk = 0; kk < Cfg::KSTEPS; ++kk) {
                   if (KIND == PAIR_KIND_BF16)
@@ -618,15 +621,19 @@ EncodeFn get_encode() {
 // launch (its tiles are long, and its splits combine exactly): it takes the
 // split count (up to 4) whose work items fill the waves best, when that
 // beats one split by more than 2 %.  fp32 output: whole units of its
-// schedule (16 k blocks) per split, partial tiles summed by k_split_reduce;
-// fp64 split: at least 8 k blocks per split, sums combined in k_split_finish.
+// schedule per split, partial tiles summed by k_split_reduce; fp64 split:
+// at least 512 k per split, sums combined in k_split_finish.
 int split_count(const Plan& p, int bn) {
   const int64_t tiles = ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l;
   const int sms = num_sms();
   const bool emu = p.kernel == FAMLIES_KERNEL_TC_EMU;
-  const int kb = pair_stage_k(p.kernel == FAMLIES_KERNEL_TC_TF32X3 ? PAIR_KIND_TF32 : PAIR_KIND_BF16);
+  const int kind = p.kernel == FAMLIES_KERNEL_TC_TF32X3 ? PAIR_KIND_TF32 : PAIR_KIND_BF16;
+  const int kb = pair_stage_k(kind);
   const int64_t nkb = (p.k + kb - 1) / kb;
-  const int64_t pieces = emu ? nkb / 8 : (nkb + 15) / 16;
+  // pieces a split may take: fp64 split, 512 k at least; fp32 output, whole
+  // units of its schedule
+  const int64_t unit = emu ? 512 / kb : f32out_unit_stages(kind);
+  const int64_t pieces = emu ? nkb / unit : (nkb + unit - 1) / unit;
   int64_t cap = pieces < 16 ? pieces : 16;
   if (cap <= 1) return 1;
   if (tiles * 2 <= sms) {
@@ -745,9 +752,12 @@ bool make_slice_map(CUtensorMap* map, void* base, bool f32, int64_t k, int64_t k
   cuuint64_t strides[2] = {(cuuint64_t)(kp * es), (cuuint64_t)(kp * es * rows)};
   cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, 1u};
   cuuint32_t estr[3] = {1u, 1u, 1u};
+  // the swizzle spans one stage row (see pair_row_bytes)
+  const int rowb = box_k * es;
   return enc(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
              base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             rowb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -781,7 +791,8 @@ static bool make_view_map(CUtensorMap* map, const DirectView& v, int64_t k, int6
   cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, 1u};
   cuuint32_t estr[3] = {1u, 1u, 1u};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(v.base), dims, strides,
-             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             box_k * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -794,13 +805,14 @@ int pair_bn_for(int64_t n, int request) {
 // (0-based slice indices, i + j <= s - 1) has weight 2^(-b (q + 2)); a unit
 // covers kcb 64-wide k blocks so that its exact integer sum stays <= 2^24.
 Sched make_pair_sched(int kernel, int slices, int bits, int64_t k) {
+  const int stage_k = pair_stage_k(PAIR_KIND_BF16);  // the fp64 split's slices are bf16
   Sched sc;
   std::memset(&sc, 0, sizeof(sc));
   if (kernel != FAMLIES_KERNEL_TC_EMU) {
     const bool tf32 = kernel == FAMLIES_KERNEL_TC_TF32X3;
     sc.ndiag = 1;
     sc.slices = tf32 ? 2 : 1;
-    sc.kcb[0] = 16;  // units of 1024 (bf16) or 512 (tf32) k
+    sc.kcb[0] = f32out_unit_stages(tf32 ? PAIR_KIND_TF32 : PAIR_KIND_BF16);
     sc.flush_every[0] = 1;
     if (tf32) {  // lo*hi + hi*lo + hi*hi, hi = slice 0, lo = slice 1
       sc.npairs[0] = 3;
@@ -826,9 +838,9 @@ Sched make_pair_sched(int kernel, int slices, int bits, int64_t k) {
     }
     sc.npairs[di] = q + 1;
     sc.shift[di] = bits * (q + 2);
-    int64_t kcb = (((int64_t)1 << 24) / bound) / 64;
+    int64_t kcb = (((int64_t)1 << 24) / bound) / stage_k;
     sc.kcb[di] = (int)(kcb < 1 ? 1 : kcb);
-    int64_t fe = (((int64_t)1 << 31) - 1) / (bound * sc.kcb[di] * 64);
+    int64_t fe = (((int64_t)1 << 31) - 1) / (bound * sc.kcb[di] * stage_k);
     sc.flush_every[di] = (int)(fe < 1 ? 1 : fe);
   }
   // |tile sum| <= sum over diagonals of k * bound * 2^-shift (in units of 1);
@@ -939,6 +951,7 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   a.part = a.splits > 1 ? (float*)(w + L.part) : nullptr;
   a.status = g.status;
   a.wait_limit = g.wait_limit;
+  a.stall_test = g.stall_test;
   const int grid = grid_of(p, bn);
   const int64_t split_tiles = ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l;
   const int64_t split_elems = split_tiles * BM * bn;

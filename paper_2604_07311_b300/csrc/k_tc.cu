@@ -196,7 +196,8 @@ __global__ void __launch_bounds__(TcCfg<TF32, BN>::THREADS, 1) k_tc(const TcArgs
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0, acc = 0, accph = 0;
-      bool ok = true;
+      // testing: `done` completes only after this thread's last commit
+      bool ok = !g.stall_test || ptx::mbar_wait(done, 0, lim, abort);
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         if (!ptx::mbar_wait(&tempty[acc], accph ^ 1, lim, abort)) { ok = false; break; }
         ptx::tc_fence_after();

@@ -67,6 +67,15 @@ cudaError_t launch_pair_grouped(int kind, int mode, int bn, const Prob* probs,
                                 const TileEntry* tiles, int64_t ntiles, const Sched& sc,
                                 double* G, int grid, int* status, int64_t wait_limit,
                                 cudaStream_t s);
-constexpr int pair_stage_k(int kind) { return kind == PAIR_KIND_BF16 ? 64 : 32; }
+// k per ring stage.  bf16 stages hold rows of kBf16StageK values (64 bytes at
+// 32, read through the 64-byte swizzle; 128 bytes at 64, the 128-byte one);
+// tf32 stages rows of 32 values (128 bytes).  Smaller stages of the same
+// total size let the ring hold more of them.
+constexpr int kBf16StageK = 64;
+constexpr int pair_stage_k(int kind) { return kind == PAIR_KIND_BF16 ? kBf16StageK : 32; }
+constexpr int pair_row_bytes(int kind) { return kind == PAIR_KIND_BF16 ? 2 * kBf16StageK : 128; }
+// Stages per unit of the fp32-output schedule: 1024 k (bf16) or 512 k (tf32)
+// summed in tensor memory before each fp32 register update.
+constexpr int f32out_unit_stages(int kind) { return (kind == PAIR_KIND_BF16 ? 1024 : 512) / pair_stage_k(kind); }
 
 }  // namespace famlies

@@ -148,6 +148,17 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t saddr) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
          ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
+// Same for 64-byte rows with the 64-byte swizzle: 8-row groups 512 bytes
+// apart, layout type 4.
+__device__ __forceinline__ uint64_t sdesc_kmajor_sw64(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+         ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+template <int ROW_BYTES>
+__device__ __forceinline__ uint64_t sdesc_kmajor(uint32_t saddr) {
+  static_assert(ROW_BYTES == 128 || ROW_BYTES == 64, "128- or 64-byte swizzled rows");
+  return ROW_BYTES == 128 ? sdesc_kmajor_sw128(saddr) : sdesc_kmajor_sw64(saddr);
+}
 
 // Instruction descriptor: fp32 accumulator, K-major A and B, M x N tile.
 // fmt: kind::f16 -> 0 f16, 1 bf16; kind::tf32 -> 2.

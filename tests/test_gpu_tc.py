@@ -162,11 +162,13 @@ def test_simt_f32_forced():
 
 @pytest.mark.parametrize("path", PATHS)
 def test_bounded_wait_timeout_reports_status_and_context_survives(path):
-    """A wait that runs out (limit of one poll) ends the kernel with a status
-    code instead of hanging; the next normal call on the same context works."""
+    """A wait that runs out (the test hook makes the MMA issuer wait on a
+    barrier phase nothing completes, bounded by 1000 polls) ends the kernels
+    with a status code instead of hanging; the next normal call on the same
+    context works."""
     p = W.transpose_free(v=24, o=12, pad=7)
     assert fm.device_status() == 0
-    run_gpu(p, "bf16", wait_limit=1, kernel=path)
+    run_gpu(p, "bf16", wait_limit=1000, kernel=path, stall_test=1)
     assert fm.device_status() == fm._lib.ERR_DEVICE_TIMEOUT
     assert fm.device_status() == 0  # read clears it
     C, _ = run_gpu(p, "bf16", kernel=path)
