@@ -69,9 +69,11 @@ struct PairArgs {
   int64_t ntiles;        // grouped: tile count
   Sched sc;
   double* G;             // fp64 split: per-CTA fp64 tile sums
-  int splits;            // fp32 output, single problem: K split across CTAs (1: off)
+  int splits;            // single problem: K splits of each tail tile (1: off)
+  int64_t full;          // splits > 1: the leading tiles that run whole (the rest is the tail)
+  int64_t* xtail;        // fp64 split, splits > 1: int64 sums of the tail tiles [tail][BN][BM]
   int stall_test;        // testing: the MMA issuer first waits on a barrier nothing completes
-  float* part;           // splits > 1: fp32 partial tiles [split][tile][BN][BM]
+  float* part;           // fp32 output, splits > 1: partial tail tiles [split][tail][BN][BM]
   int* status;
   int64_t wait_limit;
 };
@@ -116,41 +118,40 @@ template <int BN, bool GROUPED, bool SPLITK>
 __device__ __forceinline__ int64_t tile_count(const PairArgs& a) {
   if (GROUPED) return a.ntiles;
   const Prob& P = a.single;
-  return ((P.m + BM - 1) / BM) * ((P.n + BN - 1) / BN) * P.l * (SPLITK ? a.splits : 1);
+  const int64_t ntile = ((P.m + BM - 1) / BM) * ((P.n + BN - 1) / BN) * P.l;
+  return SPLITK ? a.full + (ntile - a.full) * a.splits : ntile;
 }
 
 // Item t of the launch.  Single problems walk column tiles fastest, so the
-// CTAs running at the same time share A tiles through L2; with split K the
-// splits are the slowest index (concurrent CTAs read the same k range).  A
-// split covers whole units of the schedule's first k-block count.
+// CTAs running at the same time share A tiles through L2.  With split K the
+// first `full` items are whole tiles (whole rounds of the persistent grid);
+// each tail tile then runs as `splits` items over parts of its k range,
+// splits the slowest index (concurrent CTAs read the same k range).  A split
+// covers whole units of the fp32-output schedule, or any k blocks for the
+// fp64 split (each diagonal forms its units inside the range).
 template <int BN, bool GROUPED, int KB, bool SPLITK>
 __device__ __forceinline__ TileRef tile_at(const PairArgs& a, int64_t t) {
   if (GROUPED) {
     const TileEntry e = a.tiles[t];
     const Prob* P = a.probs + e.p;
-    return TileRef{P, e.tm, e.tn, e.il, 0, 0, 0, (int)((P->k + KB - 1) / KB)};
+    return TileRef{P, e.tm, e.tn, e.il, 0, -1, 0, (int)((P->k + KB - 1) / KB)};
   }
   const Prob& P = a.single;
   const int64_t tiles_m = (P.m + BM - 1) / BM, tiles_n = (P.n + BN - 1) / BN;
   const int nkb = (int)((P.k + KB - 1) / KB);
-  if (!SPLITK) {
-    const int64_t tn = t % tiles_n, rest = t / tiles_n;
-    return TileRef{&a.single, rest % tiles_m, tn, rest / tiles_m, t, 0, 0, nkb};
-  }
-  const int64_t ntile = tiles_m * tiles_n * P.l;
-  const int64_t tile = t % ntile;
-  const int split = (int)(t / ntile);
-  const int64_t tn = tile % tiles_n, rest = tile / tiles_n;
-  int lo = 0, hi = nkb;
-  {
-    // fp32 output: whole units of its schedule; fp64 split: any k block
-    // (each diagonal forms its units inside the range)
+  int64_t tile = t;
+  int split = -1, lo = 0, hi = nkb;
+  if (SPLITK && t >= a.full) {
+    const int64_t tail = tiles_m * tiles_n * P.l - a.full, u = t - a.full;
+    tile = a.full + u % tail;
+    split = (int)(u / tail);
     const int kcb = a.sc.ndiag > 1 ? 1 : a.sc.kcb[0];
     const int64_t units = (nkb + kcb - 1) / kcb;
     lo = (int)(units * split / a.splits) * kcb;
     hi = (int)(units * (split + 1) / a.splits) * kcb;
     hi = hi < nkb ? hi : nkb;
   }
+  const int64_t tn = tile % tiles_n, rest = tile / tiles_n;
   return TileRef{&a.single, rest % tiles_m, tn, rest / tiles_m, tile, split, lo, hi};
 }
 
@@ -408,10 +409,12 @@ __global__ void __launch_bounds__(THREADS, 1)
           if (acc == 0) accph ^= 1;
         }
         if (!ok) break;
-        if (SPLITK) {
-          // split K: this item's partial tile, reduced (with alpha, beta) later
-          float* Pt = args.part + ((size_t)T.split * (size_t)(tile_count<BN, GROUPED, SPLITK>(args) / args.splits) +
-                                   (size_t)T.tile) * BM * BN + (size_t)lc0 * BM + qd * 32 + lane;
+        if (SPLITK && T.split >= 0) {
+          // a split of a tail tile: its partial tile, reduced (with alpha,
+          // beta) by k_split_reduce
+          const int64_t tail = ((P.m + BM - 1) / BM) * ((P.n + BN - 1) / BN) * P.l - args.full;
+          float* Pt = args.part + ((size_t)T.split * (size_t)tail + (size_t)(T.tile - args.full)) * BM * BN +
+                      (size_t)lc0 * BM + qd * 32 + lane;
 #pragma unroll
           for (int j = 0; j < CPT; ++j) Pt[(size_t)j * BM] = S[j];
         } else if (rv) {
@@ -433,10 +436,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         int32_t S[CPT];
 #pragma unroll
         for (int j = 0; j < CPT; ++j) S[j] = 0;
-        // tile sums: per CTA, or (split K) per tile, shared by the tile's
-        // splits through the reductions and finished by k_split_finish
-        const size_t xslot = SPLITK ? (size_t)T.tile : (size_t)blockIdx.x;
-        int64_t* Xt = (int64_t*)args.G + xslot * BM * BN + (size_t)(hf * CPT) * BM + qd * 32 + lane;
+        // tile sums: per CTA for a whole tile; for a split of a tail tile the
+        // tile's slot, shared by its splits through the reductions and
+        // finished by k_split_finish
+        const bool part_item = SPLITK && T.split >= 0;
+        int64_t* Xt = (part_item ? args.xtail + (size_t)(T.tile - args.full) * BM * BN
+                                 : (int64_t*)args.G + (size_t)blockIdx.x * BM * BN) +
+                      (size_t)(hf * CPT) * BM + qd * 32 + lane;
         bool first_flush = true;
         for (int di = 0; di < sc.ndiag && ok; ++di) {
           const int kcb = sc.kcb[di];
@@ -470,13 +476,13 @@ __global__ void __launch_bounds__(THREADS, 1)
               for (int j = 0; j < CPT; ++j) {
                 int64_t v = (int64_t)S[j];
                 v = xs >= 0 ? (int64_t)((uint64_t)v << xs) : ((v + ((int64_t)1 << (-xs - 1))) >> (-xs));
-                if (first_flush && !SPLITK) Xt[(size_t)j * BM] = v;
+                if (first_flush && !part_item) Xt[(size_t)j * BM] = v;
                 else atomicAdd((unsigned long long*)(Xt + (size_t)j * BM), (unsigned long long)v);
                 S[j] = 0;
               }
               first_flush = false;
             }
-            if (SPLITK || !(last_unit && di == sc.ndiag - 1) || !rv || P.fa[il * P.m + row]) continue;
+            if (part_item || !(last_unit && di == sc.ndiag - 1) || !rv || P.fa[il * P.m + row]) continue;
             finish_tile<CPT>(P, Xt, sc.xunit, il, row, crow, col0, lc0, bnp);
           }
         }
@@ -504,16 +510,16 @@ constexpr int SPLIT_PER_THREAD = SPLIT_COLS / (256 / BM);
 // fp32 output: C = alpha * (sum of the splits' partial tiles, in split order)
 // + beta * C.
 __global__ void __launch_bounds__(256) k_split_reduce(const float* __restrict__ part, int splits,
-                                                     int bn, Prob P) {
+                                                     int64_t full, int bn, Prob P) {
   const int64_t tiles_m = (P.m + BM - 1) / BM, tiles_n = (P.n + bn - 1) / bn;
   const int chunks = bn / SPLIT_COLS;
-  const int64_t items = tiles_m * tiles_n * P.l * chunks;
-  const size_t per = (size_t)BM * bn, total = (size_t)(items / chunks) * per;
+  const int64_t tail = tiles_m * tiles_n * P.l - full, items = tail * chunks;
+  const size_t per = (size_t)BM * bn, total = (size_t)tail * per;
   float* C = (float*)P.c;
   const float alpha = (float)P.alpha, beta = (float)P.beta;
   const int lr = threadIdx.x % BM, lq = threadIdx.x / BM;
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
-    const int64_t tile = it / chunks;
+    const int64_t ti = it / chunks, tile = full + ti;  // ti: index among the tail tiles
     const int c0 = (int)(it % chunks) * SPLIT_COLS;
     const int64_t tn = tile % tiles_n, rest = tile / tiles_n;
     const int64_t tm = rest % tiles_m, il = rest / tiles_m;
@@ -527,7 +533,7 @@ __global__ void __launch_bounds__(256) k_split_reduce(const float* __restrict__ 
       const int lc = c0 + lq + j * (256 / BM);
       const int64_t col = tn * bn + lc;
       off[j] = col < P.n ? crow + P.cn[col] : -1;
-      const size_t at = (size_t)tile * per + (size_t)lc * BM + lr;
+      const size_t at = (size_t)ti * per + (size_t)lc * BM + lr;
       float acc = 0.f;
       for (int sp = 0; sp < splits; ++sp) acc += part[(size_t)sp * total + at];
       sum[j] = acc;
@@ -546,16 +552,16 @@ __global__ void __launch_bounds__(256) k_split_reduce(const float* __restrict__ 
 // fp64 split: the splits of a tile added their int64 sums into one slot;
 // C = alpha * 2^(e_m + e_n - xunit) * sum + beta * C (rows and columns
 // holding Inf/NaN are left to the native fix-up).
-__global__ void __launch_bounds__(256) k_split_finish(const int64_t* __restrict__ X, int bn,
-                                                     int xunit, Prob P) {
+__global__ void __launch_bounds__(256) k_split_finish(const int64_t* __restrict__ X, int64_t full,
+                                                     int bn, int xunit, Prob P) {
   const int64_t tiles_m = (P.m + BM - 1) / BM, tiles_n = (P.n + bn - 1) / bn;
   const int chunks = bn / SPLIT_COLS;
-  const int64_t items = tiles_m * tiles_n * P.l * chunks;
+  const int64_t items = (tiles_m * tiles_n * P.l - full) * chunks;
   const size_t per = (size_t)BM * bn;
   double* C = (double*)P.c;
   const int lr = threadIdx.x % BM, lq = threadIdx.x / BM;
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
-    const int64_t tile = it / chunks;
+    const int64_t ti = it / chunks, tile = full + ti;  // ti: index among the tail tiles
     const int c0 = (int)(it % chunks) * SPLIT_COLS;
     const int64_t tn = tile % tiles_n, rest = tile / tiles_n;
     const int64_t tm = rest % tiles_m, il = rest / tiles_m;
@@ -573,7 +579,7 @@ __global__ void __launch_bounds__(256) k_split_finish(const int64_t* __restrict_
       const bool ok = col < P.n && !P.fb[il * P.n + col];
       off[j] = ok ? crow + P.cn[col] : -1;
       ec[j] = ok ? P.eb[il * P.n + col] : 0;
-      x[j] = X[(size_t)tile * per + (size_t)lc * BM + lr];
+      x[j] = X[(size_t)ti * per + (size_t)lc * BM + lr];
     }
 #pragma unroll
     for (int j = 0; j < SPLIT_PER_THREAD; ++j) old[j] = (off[j] >= 0 && P.beta != 0.0) ? C[off[j]] : 0.0;
@@ -615,49 +621,68 @@ EncodeFn get_encode() {
   return fn;
 }
 
-// K splits of a single problem.  When its tiles would fill at most half of
-// the SMs, the k range is split across CTAs so that more SMs take part.
-// The fp64 split also splits to even out the last wave of a persistent
-// launch (its tiles are long, and its splits combine exactly): it takes the
-// split count (up to 4) whose work items fill the waves best, when that
-// beats one split by more than 2 %.  fp32 output: whole units of its
-// schedule per split, partial tiles summed by k_split_reduce; fp64 split:
-// at least 512 k per split, sums combined in k_split_finish.
-int split_count(const Plan& p, int bn) {
+// K splits of a single problem.  A persistent launch over T tiles on the
+// SMs runs whole rounds of tiles and then a last, partly empty one (the
+// tail: T mod SMs tiles; all of them when T < SMs).  The tail tiles may each
+// run as s items over parts of their k range: the tail then takes
+// ceil(tail * s / SMs) / s rounds instead of one (plus a little per item for
+// its pipeline start and flushes).  s minimises that, each step up taken
+// when it saves more than 2 %: up to 16 when all tiles fit in one round,
+// else up to 4 (more splits of long tiles only multiply the partial-sum
+// traffic), and no more than the k range allows (whole units of the
+// fp32-output schedule, at least 512 k for the fp64 split).  Partial tiles
+// meet in k_split_reduce (fp32 output) or in an int64 slot per tile finished
+// by k_split_finish (fp64 split).
+struct SplitPlan {
+  int splits;    // 1: no split
+  int64_t full;  // leading tiles that run whole
+  int64_t tail;  // tiles that run split
+};
+
+SplitPlan split_plan(const Plan& p, int bn) {
   const int64_t tiles = ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l;
-  const int sms = num_sms();
+  const int64_t sms = num_sms();
   const bool emu = p.kernel == FAMLIES_KERNEL_TC_EMU;
   const int kind = p.kernel == FAMLIES_KERNEL_TC_TF32X3 ? PAIR_KIND_TF32 : PAIR_KIND_BF16;
   const int kb = pair_stage_k(kind);
   const int64_t nkb = (p.k + kb - 1) / kb;
-  // pieces a split may take: fp64 split, 512 k at least; fp32 output, whole
-  // units of its schedule
   const int64_t unit = emu ? 512 / kb : f32out_unit_stages(kind);
   const int64_t pieces = emu ? nkb / unit : (nkb + unit - 1) / unit;
-  int64_t cap = pieces < 16 ? pieces : 16;
-  if (cap <= 1) return 1;
-  if (tiles * 2 <= sms) {
-    const int64_t sp = sms / tiles;
-    return (int)(sp < cap ? sp : cap);
-  }
-  if (!emu) return 1;
-  auto fill = [&](int64_t sp) {
-    const int64_t items = tiles * sp, waves = (items + sms - 1) / sms;
-    return (double)items / (double)(waves * sms);
+  const int64_t full = (tiles / sms) * sms, tail = tiles - full;
+  const int64_t most = full == 0 ? 16 : 4;
+  const int64_t cap = pieces < most ? pieces : most;
+  SplitPlan none{1, tiles, 0};
+  if (cap <= 1 || tail == 0) return none;
+  auto rounds = [&](int64_t sp) {
+    return (double)((tail * sp + sms - 1) / sms) * (1.0 / (double)sp + 0.01);
   };
-  int best = 1;
-  for (int sp = 2; sp <= 4 && sp <= cap; ++sp)
-    if (fill(sp) > fill(best) + 0.02) best = sp;
-  return best;
+  int64_t best = 1;
+  for (int64_t sp = 2; sp <= cap; ++sp)
+    if (rounds(sp) < 0.98 * rounds(best)) best = sp;
+  // fp64 split with whole rounds too: splitting every tile instead (so every
+  // tile is finished outside the product kernel, whose epilogue then never
+  // stalls on a tile's end) measures faster when it needs no more rounds
+  if (emu && full > 0 && cap >= 2) {
+    const double whole = (double)(full / sms) + (best > 1 ? rounds(best) : 1.0);
+    for (int64_t sp = 2; sp <= 4 && sp <= cap; ++sp) {
+      const double all = (double)((tiles * sp + sms - 1) / sms) / (double)sp;
+      if (all <= whole + 1e-9) return SplitPlan{(int)sp, 0, tiles};
+    }
+  }
+  if (best == 1) return none;
+  return SplitPlan{(int)best, full, tail};
 }
 
+int split_count(const Plan& p, int bn) { return split_plan(p, bn).splits; }
+
 int grid_of(const Plan& p, int bn) {
-  const int64_t tiles = ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l * split_count(p, bn);
-  return (int)(tiles < num_sms() ? tiles : num_sms());
+  const SplitPlan sp = split_plan(p, bn);
+  const int64_t items = sp.full + sp.tail * sp.splits;
+  return (int)(items < num_sms() ? items : num_sms());
 }
 
 struct Layout {
-  size_t a, b, ea, eb, fa, fb, la, lb, G, part, total;
+  size_t a, b, ea, eb, fa, fb, la, lb, G, xtail, part, total;
 };
 
 Layout layout_of(const Plan& p) {
@@ -679,16 +704,15 @@ Layout layout_of(const Plan& p) {
     L.fb = off; off += up((size_t)p.l * p.n * 4);
     L.la = off; off += up((size_t)(p.l * p.m + 1) * 4);
     L.lb = off; off += up((size_t)(p.l * p.n + 1) * 4);
-    // per-CTA tile sums, or (split K) one per tile
-    const size_t ntile = (size_t)((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l;
-    const size_t slots = split_count(p, bn) > 1 ? ntile : (size_t)grid_of(p, bn);
-    L.G = off; off += up(slots * BM * bn * 8);
+    // per-CTA tile sums; split K adds one slot per tail tile
+    const SplitPlan sp = split_plan(p, bn);
+    L.G = off; off += up((size_t)grid_of(p, bn) * BM * bn * 8);
+    L.xtail = off; off += up((size_t)sp.tail * BM * bn * 8);
   } else {
     const int bn = pair_bn_for(p.n, p.tile_n);
-    const int sp = split_count(p, bn);
-    if (sp > 1) {
-      const size_t tiles = (size_t)((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l;
-      L.part = off; off += up((size_t)sp * tiles * BM * bn * 4);
+    const SplitPlan sp = split_plan(p, bn);
+    if (sp.splits > 1) {
+      L.part = off; off += up((size_t)sp.splits * sp.tail * BM * bn * 4);
     }
   }
   L.total = off;
@@ -947,26 +971,27 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
                   pa.op[0].flag, pa.op[1].flag, p.m, p.n, p.k, p.l, g.alpha, g.beta, bn};
   a.sc = make_pair_sched(p.kernel, p.slices, bits, p.k);
   a.G = emu ? (double*)(w + L.G) : nullptr;
-  a.splits = split_count(p, bn);
-  a.part = a.splits > 1 ? (float*)(w + L.part) : nullptr;
+  const SplitPlan spl = split_plan(p, bn);
+  a.splits = spl.splits;
+  a.full = spl.full;
+  a.xtail = emu && spl.splits > 1 ? (int64_t*)(w + L.xtail) : nullptr;
+  a.part = !emu && spl.splits > 1 ? (float*)(w + L.part) : nullptr;
   a.status = g.status;
   a.wait_limit = g.wait_limit;
   a.stall_test = g.stall_test;
   const int grid = grid_of(p, bn);
-  const int64_t split_tiles = ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l;
-  const int64_t split_elems = split_tiles * BM * bn;
-  const int split_grid = (int)std::min<int64_t>(split_tiles * (bn / SPLIT_COLS), (int64_t)num_sms() * 16);
+  const int split_grid = (int)std::min<int64_t>(spl.tail * (bn / SPLIT_COLS), (int64_t)num_sms() * 16);
   if (emu && a.splits > 1 &&
-      (e = cudaMemsetAsync(a.G, 0, (size_t)split_elems * 8, s)) != cudaSuccess)
+      (e = cudaMemsetAsync(a.xtail, 0, (size_t)spl.tail * BM * bn * 8, s)) != cudaSuccess)
     return e;
   mark_begin(g, s);
   e = launch_pair_any<false>(kind, emu ? PAIR_MODE_EMU : PAIR_MODE_F32OUT, bn, ma, mb, a, grid, s);
   mark_end(g, s);  // the events bracket the product kernel alone
   if (e == cudaSuccess && a.splits > 1) {
     if (emu)
-      k_split_finish<<<split_grid, 256, 0, s>>>((const int64_t*)a.G, bn, a.sc.xunit, a.single);
+      k_split_finish<<<split_grid, 256, 0, s>>>(a.xtail, a.full, bn, a.sc.xunit, a.single);
     else
-      k_split_reduce<<<split_grid, 256, 0, s>>>(a.part, a.splits, bn, a.single);
+      k_split_reduce<<<split_grid, 256, 0, s>>>(a.part, a.splits, a.full, bn, a.single);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return e;
