@@ -191,3 +191,24 @@ def test_split_k_few_tiles_with_nonfinite_row():
     assert np.array_equal(np.isnan(got), np.isnan(want))
     fin = ~np.isnan(want)
     assert rel_frob(got[fin], want[fin]) <= TOL
+
+
+def test_split_every_tile_over_several_rounds():
+    """178 tiles on 148 SMs: rather than a whole round plus a 30-tile tail,
+    every tile splits K in four (712 items, 1.25 rounds of work instead of 2)
+    and meets in its int64 slot; sampled entries against the oracle's
+    compensated dot products."""
+    rng = np.random.default_rng(407)
+    m, n, k = 89 * 128, 512, 2048
+    A = W.uniform_operand(rng, (m, k), [1, 2])
+    B = W.uniform_operand(rng, (k, n), [2, 3])
+    C = W.uniform_operand(rng, (m, n), [1, 3])
+    p = W.Problem("split_tail_emu", 1.0, A, B, -1.0, C)
+    Cg, info = run_gpu(p, "f64_emu", tile_n=256)
+    assert info["launches"] == 6  # tables, exponents, pack, product, split finish, fix-up
+    got = gpu_dense(Cg)
+    rows = np.concatenate([rng.integers(74 * 128, m, 48), rng.integers(0, 74 * 128, 16)])
+    idx = np.stack([rows, rng.integers(0, n, rows.size)], axis=1)
+    want = oracle.entries(p.alpha, A.view(), A.labels, B.view(), B.labels, p.beta, C.view(),
+                          C.labels, idx, dot2=True)
+    assert rel_frob(got[idx[:, 0], idx[:, 1]], want) <= TOL

@@ -206,3 +206,22 @@ def test_split_k_integer_exact():
     Cg, info = run_gpu(p, "bf16", kernel=KERNEL_PACKED)
     assert info["launches"] == 4
     assert np.array_equal(gpu_dense(Cg), run_oracle(p))
+
+
+def test_split_tail_after_whole_rounds_integer_exact():
+    """178 tiles on 148 SMs: one whole round, then the 30-tile tail split
+    along K; integer-valued bf16 inputs make every partial sum exact, so
+    sampled entries (tail tiles and whole ones) match the oracle exactly."""
+    rng = np.random.default_rng(642)
+    m, n, k = 89 * 128, 512, 4096
+    A = W.integer_operand(rng, (m, k), [1, 2], lo=-2, hi=2)
+    B = W.integer_operand(rng, (k, n), [2, 3], lo=-2, hi=2)
+    C = W.zeros_operand((m, n), [1, 3])
+    p = W.Problem("split_tail", 1.0, A, B, 0.0, C)
+    Cg, info = run_gpu(p, "bf16", kernel=KERNEL_PACKED, tile_n=256)
+    assert info["launches"] == 4  # tables + pack + product + split reduction
+    got = gpu_dense(Cg)
+    rows = np.concatenate([rng.integers(74 * 128, m, 48), rng.integers(0, 74 * 128, 16)])
+    idx = np.stack([rows, rng.integers(0, n, rows.size)], axis=1)
+    want = oracle.entries(1.0, A.view(), A.labels, B.view(), B.labels, 0.0, C.view(), C.labels, idx)
+    assert np.array_equal(got[idx[:, 0], idx[:, 1]], want)
