@@ -239,8 +239,23 @@ constexpr int TLD = PK + 1;  // shared tile row length (padded against bank conf
 // reading along the operand's unit-stride index: with unit stride along k
 // the threads of a warp take consecutive k of one row, otherwise
 // consecutive rows at one k.  Entries past the operand's edge are zero.
+// Entries a thread moves per tile (PR = PK = 64 with 256 threads: 16), in
+// the order load_tile visits them; entry i of thread t is row
+// t / PK + 4 i, column t % PK (unit stride along k) or row t % PR, column
+// t / PR + 4 i (otherwise).
+constexpr int PER_THREAD = PR * PK / 256;
+
+__device__ __forceinline__ int stage_slot(int contig, int i) {
+  return contig == 2 ? (threadIdx.x / PK + i * (256 / PK)) * TLD + threadIdx.x % PK
+                     : (threadIdx.x % PR) * TLD + threadIdx.x / PR + i * (256 / PR);
+}
+
+// 4- and 8-byte values go straight to shared memory by asynchronous copies;
+// 2-byte values (no asynchronous copy that small) are loaded into registers
+// (`regs`) and stored by store_regs once the current tile is converted.
 template <int PMODE>
-__device__ __forceinline__ void load_tile(const PackTile& t, typename PackT<PMODE>::T* buf) {
+__device__ __forceinline__ void load_tile(const PackTile& t, typename PackT<PMODE>::T* buf,
+                                          typename PackT<PMODE>::T (&regs)[PER_THREAD]) {
   using T = typename PackT<PMODE>::T;
   constexpr int NT = 256;
   const PackArgs& pa = *t.pa;
@@ -252,9 +267,11 @@ __device__ __forceinline__ void load_tile(const PackTile& t, typename PackT<PMOD
   const int64_t r0 = tr * PR, k0 = tk * PK;
   const int rmax = (int)min((int64_t)PR, o.rows - r0), kmax = (int)min((int64_t)PK, pa.k - k0);
   const T* const base = X + o.loff[il];
+  int slot = 0;  // entries are visited in order: the i-th put is entry i
   auto put = [&](T* dst, const T* src, bool ok) {
     if constexpr (sizeof(T) >= 4) cp_async_elem<sizeof(T)>(dst, ok ? src : X, ok);
-    else *dst = ok ? __ldg(src) : T(0);
+    else regs[slot] = ok ? __ldg(src) : T(0);
+    ++slot;
   };
   if (o.contig == 2) {
     const int kk = threadIdx.x % PK;
@@ -263,9 +280,12 @@ __device__ __forceinline__ void load_tile(const PackTile& t, typename PackT<PMOD
     T* dst = buf + kk;
     if (o.affine & 1) {
       const int64_t step = (NT / PK) * o.rs;
-      int r = threadIdx.x / PK;
-      src += (r0 + r) * o.rs;
-      for (; r < PR; r += NT / PK, src += step) put(dst + r * TLD, src, kok && r < rmax);
+      src += (r0 + threadIdx.x / PK) * o.rs;
+#pragma unroll
+      for (int i = 0; i < PR / (NT / PK); ++i, src += step) {
+        const int r = threadIdx.x / PK + i * (NT / PK);
+        put(dst + r * TLD, src, kok && r < rmax);
+      }
     } else {
       // the table reads first, all in flight together, then the copies
       constexpr int NI = PR / (NT / PK);
@@ -288,9 +308,12 @@ __device__ __forceinline__ void load_tile(const PackTile& t, typename PackT<PMOD
     T* dst = buf + r * TLD;
     if (o.affine & 2) {
       const int64_t step = (NT / PR) * o.ks;
-      int kk = threadIdx.x / PR;
-      src += (k0 + kk) * o.ks;
-      for (; kk < PK; kk += NT / PR, src += step) put(dst + kk, src, rok && kk < kmax);
+      src += (k0 + threadIdx.x / PR) * o.ks;
+#pragma unroll
+      for (int i = 0; i < PK / (NT / PR); ++i, src += step) {
+        const int kk = threadIdx.x / PR + i * (NT / PR);
+        put(dst + kk, src, rok && kk < kmax);
+      }
     } else {
       constexpr int NI = PK / (NT / PR);
       int64_t off[NI];
@@ -306,6 +329,13 @@ __device__ __forceinline__ void load_tile(const PackTile& t, typename PackT<PMOD
       }
     }
   }
+}
+
+template <int PMODE>
+__device__ __forceinline__ void store_regs(const PackTile& t, typename PackT<PMODE>::T* buf,
+                                           const typename PackT<PMODE>::T (&regs)[PER_THREAD]) {
+#pragma unroll
+  for (int i = 0; i < PER_THREAD; ++i) buf[stage_slot(t.o->contig, i)] = regs[i];
 }
 
 // Converts a staged tile and writes it as 16-byte K-major chunks of every
@@ -376,21 +406,30 @@ __device__ __forceinline__ void pack_pipeline(int64_t g0, int64_t gstep, int64_t
   T* const buf0 = (T*)pack_smem;
   auto buf = [&](int j) { return buf0 + (j & 1) * (PR * TLD); };
   if (g0 >= total) return;
+  T regs[PER_THREAD];
   PackTile cur = loc(g0);
-  load_tile<PMODE>(cur, buf(0));
+  load_tile<PMODE>(cur, buf(0), regs);
+  if constexpr (sizeof(T) < 4) store_regs<PMODE>(cur, buf(0), regs);
   cp_async_commit();
   int i = 0;
   for (int64_t g = g0; g < total; g += gstep, ++i) {
     PackTile nxt = cur;
-    if (g + gstep < total) {
+    const bool more = g + gstep < total;
+    if (more) {
       nxt = loc(g + gstep);
-      load_tile<PMODE>(nxt, buf(i + 1));
+      load_tile<PMODE>(nxt, buf(i + 1), regs);
     }
     cp_async_commit();
     cp_async_wait<1>();  // this thread's copies of the current tile have landed
-    __syncthreads();     // ... and everyone else's
+    __syncthreads();     // ... and everyone else's; the tile before is emitted
     emit_tile<PMODE>(cur, buf(i));
-    __syncthreads();     // the buffer is free for the tile after next
+    if constexpr (sizeof(T) < 4) {
+      // the register-held loads of the next tile return while this one is
+      // converted; buf(i + 1) was last read by the emit before the barrier
+      if (more) store_regs<PMODE>(nxt, buf(i + 1), regs);
+    } else {
+      __syncthreads();   // the buffer is free for the tile after next
+    }
     cur = nxt;
   }
 }
