@@ -404,6 +404,36 @@ def run_other(args):
                               "ms_per_step": ms, "tflops": p.flops / ms / 1e9, "product_ms": kms,
                               "product_exec_tflops": pairs * p.flops / kms / 1e9,
                               "bf16_peak_sustained": sustained, "peak_source": src}), flush=True)
+    elif args.workload == "network":
+        # A CCSD-flavoured two-step network in one call: the intermediate
+        # X[c,d,i,j] = sum_{k,l} T[c,d,k,l] Y[k,l,i,j] stays on the device,
+        # then R[a,b,i,j] = sum_{c,d} V[a,b,c,d] X[c,d,i,j] + R (emulated fp64).
+        v, o = 96, 32
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(5)
+        V = torch.randn(v, v, v, v, device="cuda", dtype=torch.float64, generator=gen) / 128
+        T = torch.randn(v, v, o, o, device="cuda", dtype=torch.float64, generator=gen) * 1e-2
+        Y = torch.randn(o, o, o, o, device="cuda", dtype=torch.float64, generator=gen)
+        R = torch.zeros(v, v, o, o, device="cuda", dtype=torch.float64)
+        X = torch.empty(v, v, o, o, device="cuda", dtype=torch.float64)
+        lv, lt, ly, lx, lr = W.L("abcd"), W.L("cdkl"), W.L("klij"), W.L("cdij"), W.L("abij")
+        # the library lays an intermediate out first mode fastest: listing X's
+        # labels as (j, i, d, c) gives it the same layout as the row-major
+        # torch tensor X[c,d,i,j] of the separate calls (d fastest in V too,
+        # so the contracted pair (c, d) fuses into one mode in both operands)
+        net = [(V, lv), (T, lt), (Y, ly), ((o, o, v, v), W.L("jidc")), (R, lr)]
+        steps = [(1, 2, 3, 1.0, 0.0), (0, 3, 4, 1.0, 1.0)]
+        flops = 2 * v * v * o * o * o * o + 2 * v * v * v * v * o * o
+        ms = _cuda_ms(lambda: fm.contract_network(net, steps, dtype="f64_emu"), args.steps, args.warmup)
+
+        def separate():
+            fm.contract(1.0, T, lt, Y, ly, 0.0, X, lx, dtype="f64_emu")
+            fm.contract(1.0, V, lv, X, lx, 1.0, R, lr, dtype="f64_emu")
+        ms_sep = _cuda_ms(separate, args.steps, args.warmup)
+        print(json.dumps({"workload": "network_ladder_v96_o32_two_steps_f64_split6", "flops": flops,
+                          "network_ms": ms, "network_tflops": flops / ms / 1e9,
+                          "separate_calls_ms": ms_sep, "separate_tflops": flops / ms_sep / 1e9}),
+              flush=True)
     elif args.workload == "autograd":
         from paper_2604_07311_b300.autograd import contract_autograd
         d = W.autograd_problem()
@@ -453,7 +483,7 @@ def run_other(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="ladder",
-                    choices=["ladder", "transpose_free", "block_sparse", "autograd"],
+                    choices=["ladder", "transpose_free", "block_sparse", "autograd", "network"],
                     help="ladder is the benchmark line; the others print secondary measurements")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)

@@ -258,6 +258,34 @@ FAMLIES_API int famlies_contract_noalloc(double alpha, const famlies_tensor_t* A
                                          const famlies_tensor_t* C, famlies_dtype_t dtype,
                                          void* stream);
 
+/* Contraction networks: a pre-ordered sequence of tensor contractions run
+ * through the same planner and kernels (Sec. 3, Girder 5, tensor contraction
+ * networks).  `tensors` lists every tensor of the network; step i computes
+ *   tensors[c] := alpha * contract(tensors[a], tensors[b]) + beta * tensors[c]
+ * over the tensors' own labels, like famlies_contract_ex, in the given order
+ * on `stream` with one dtype and one options block (NULL: defaults).
+ * A tensor whose `data` is NULL is an intermediate: the library allocates
+ * it dense (first mode fastest; its `strides` are ignored) from the
+ * stream-ordered pool before the first step and frees it after the last,
+ * all on `stream`; intermediates never reach the caller.  Ownership of every
+ * other tensor stays with the caller.
+ * Errors, found before anything is launched: an index out of range or a
+ * step whose c equals its a or b, an intermediate read before a step writes
+ * it or first written with beta != 0 (FAMLIES_ERR_INVALID_ARG); dtype BF16
+ * with an intermediate (its products are fp32, its operands bf16:
+ * FAMLIES_ERR_UNSUPPORTED); any error a step's planning reports.  An
+ * allocation failure returns FAMLIES_ERR_ALLOC; a launch failure stops the
+ * sequence with FAMLIES_ERR_CUDA (earlier steps have run). */
+typedef struct {
+  int32_t a, b, c;   /* indices into the tensor list */
+  int32_t reserved;  /* 0 */
+  double alpha, beta;
+} famlies_step_t;
+
+FAMLIES_API int famlies_network(const famlies_tensor_t* tensors, int32_t ntensors,
+                                const famlies_step_t* steps, int32_t nsteps, famlies_dtype_t dtype,
+                                void* stream, const famlies_options_t* opt);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,7 +10,7 @@ from __future__ import annotations
 from ._lib import (BF16, DTYPES, F32, F64, F64_EMU, KERNELS, Desc, FamliesError, PlanInfo,
                    desc_numpy, desc_torch, load, options, check, error_string)
 
-__all__ = ["contract", "contract_host", "contract_batched", "plan", "device_status",
+__all__ = ["contract", "contract_host", "contract_batched", "contract_network", "plan", "device_status",
            "FamliesError", "F64", "F64_EMU", "F32", "BF16", "lib_path", "Contract", "contract_autograd"]
 
 
@@ -105,6 +105,33 @@ def contract_batched(alpha, As, las, Bs, lbs, beta, Cs, lcs, dtype=None, stream=
     check(lib.famlies_contract_batched(n, aa, ta, tb, bb, tc, code, _stream_handle(stream),
                                        1 if use_graph else 0))
     return Cs
+
+
+def contract_network(tensors, steps, dtype="f64", stream=None, *, slices=0, kernel=0):
+    """A pre-ordered sequence of contractions through the library, in one call.
+
+    tensors: list of (tensor, labels) for caller tensors (CUDA torch tensors,
+    any strides) or (shape, labels) for intermediates, which the library
+    allocates dense on the device and frees at the end.  steps: list of
+    (a, b, c, alpha, beta): tensors[c] := alpha * contract(tensors[a],
+    tensors[b]) + beta * tensors[c], run in order on `stream`.
+    """
+    import ctypes
+    from ._lib import Step, TensorDesc
+    lib = load()
+    code = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    descs = []
+    for x, labels in tensors:
+        if hasattr(x, "data_ptr"):
+            descs.append(desc_torch(x, labels))
+        else:
+            shape = tuple(int(e) for e in x)
+            descs.append(Desc(shape, (0,) * len(shape), labels, 0))
+    n = len(descs)
+    tt = (TensorDesc * max(n, 1))(*[d.t for d in descs])
+    ss = (Step * max(len(steps), 1))(*[Step(int(a), int(b), int(c), 0, float(al), float(be))
+                                       for a, b, c, al, be in steps])
+    check(lib.famlies_network(tt, n, ss, len(steps), code, _stream_handle(stream), options(slices, kernel)))
 
 
 def contract_noalloc(alpha, A, la, B, lb, beta, C, lc, dtype=None, stream=None):

@@ -38,6 +38,12 @@ class Options(ctypes.Structure):
                 ("events", ctypes.c_void_p * 2), ("reserved", ctypes.c_int64 * 2)]
 
 
+class Step(ctypes.Structure):
+    """famlies_step_t: tensors[c] := alpha * contract(tensors[a], tensors[b]) + beta * tensors[c]."""
+    _fields_ = [("a", ctypes.c_int32), ("b", ctypes.c_int32), ("c", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("alpha", ctypes.c_double), ("beta", ctypes.c_double)]
+
+
 class PlanInfo(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
                 ("batch", ctypes.c_int64), ("m_modes", ctypes.c_int32), ("n_modes", ctypes.c_int32),
@@ -81,11 +87,14 @@ def load(path: str | None = None):
                                              ctypes.POINTER(ctypes.c_double), T, ctypes.c_int, vp,
                                              ctypes.c_int]
     lib.famlies_plan.argtypes = [T, T, T, ctypes.c_int, ctypes.POINTER(Options), ctypes.POINTER(PlanInfo)]
+    lib.famlies_network.argtypes = [T, ctypes.c_int32, ctypes.POINTER(Step), ctypes.c_int32, ctypes.c_int,
+                                    vp, ctypes.POINTER(Options)]
     lib.famlies_error_string.argtypes = [ctypes.c_int]
     lib.famlies_error_string.restype = ctypes.c_char_p
     lib.famlies_device_status.argtypes = [vp]
     for f in ("famlies_contract", "famlies_contract_ex", "famlies_contract_host",
-              "famlies_contract_batched", "famlies_plan", "famlies_device_status", "famlies_version"):
+              "famlies_contract_batched", "famlies_plan", "famlies_device_status", "famlies_version",
+              "famlies_network"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib

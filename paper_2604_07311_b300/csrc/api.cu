@@ -194,6 +194,92 @@ int famlies_contract_ex(double alpha, const famlies_tensor_t* A, const famlies_t
   return run_plan(p, alpha, beta, (cudaStream_t)stream, opt, info);
 }
 
+int famlies_network(const famlies_tensor_t* tensors, int32_t ntensors,
+                    const famlies_step_t* steps, int32_t nsteps, famlies_dtype_t dtype,
+                    void* stream, const famlies_options_t* opt) {
+  if (!tensors || ntensors <= 0 || nsteps < 0 || (nsteps > 0 && !steps))
+    return FAMLIES_ERR_INVALID_ARG;
+  // Which tensors are intermediates, and is each one written (with beta = 0)
+  // before it is read?
+  std::vector<char> inter(ntensors), written(ntensors, 0);
+  bool any_inter = false;
+  for (int i = 0; i < ntensors; ++i) inter[i] = tensors[i].data == nullptr;
+  for (int i = 0; i < nsteps; ++i) {
+    const famlies_step_t& st = steps[i];
+    if (st.a < 0 || st.a >= ntensors || st.b < 0 || st.b >= ntensors || st.c < 0 ||
+        st.c >= ntensors || st.c == st.a || st.c == st.b)
+      return FAMLIES_ERR_INVALID_ARG;
+    if ((inter[st.a] && !written[st.a]) || (inter[st.b] && !written[st.b]))
+      return FAMLIES_ERR_INVALID_ARG;
+    if (inter[st.c] && !written[st.c] && st.beta != 0.0) return FAMLIES_ERR_INVALID_ARG;
+    written[st.c] = 1;
+    any_inter = any_inter || inter[st.a] || inter[st.b] || inter[st.c];
+  }
+  if (any_inter && dtype == FAMLIES_BF16) return FAMLIES_ERR_UNSUPPORTED;
+  const int64_t es = (dtype == FAMLIES_F32) ? 4 : 8;
+
+  // Descriptors with the intermediates' dense strides; device memory for them.
+  std::vector<famlies_tensor_t> t(tensors, tensors + ntensors);
+  std::vector<std::vector<int64_t>> dense(ntensors);
+  std::vector<int64_t> bytes(ntensors, 0);
+  for (int i = 0; i < ntensors; ++i) {
+    if (!inter[i]) continue;
+    if (t[i].ndim < 0 || t[i].ndim > FAMLIES_MAX_NDIM || (t[i].ndim > 0 && !t[i].extents))
+      return FAMLIES_ERR_INVALID_ARG;
+    dense[i].resize(t[i].ndim > 0 ? t[i].ndim : 1);
+    int64_t n = 1;
+    for (int d = 0; d < t[i].ndim; ++d) {
+      if (t[i].extents[d] < 0) return FAMLIES_ERR_INVALID_ARG;
+      dense[i][d] = n;
+      n *= t[i].extents[d];
+    }
+    t[i].strides = dense[i].data();
+    bytes[i] = n * es;
+    t[i].size_bytes = bytes[i];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<void*> owned;
+  auto release = [&] {
+    for (void* q : owned) cudaFreeAsync(q, s);
+    owned.clear();
+  };
+  if (any_inter) {
+    int rc = check_device();
+    if (rc) return rc;
+    for (int i = 0; i < ntensors; ++i) {
+      if (!inter[i] || !written[i]) continue;
+      void* q = nullptr;
+      // a zero-size intermediate still gets a distinct address (alias checks)
+      if (cudaMallocAsync(&q, bytes[i] > 0 ? bytes[i] : 256, s) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return FAMLIES_ERR_ALLOC;
+      }
+      owned.push_back(q);
+      t[i].data = q;
+    }
+  }
+  // Plan every step first, so that a planning error launches nothing.
+  std::vector<Plan> plans(nsteps);
+  for (int i = 0; i < nsteps; ++i) {
+    const famlies_step_t& st = steps[i];
+    int rc = make_plan(st.alpha, &t[st.a], &t[st.b], &t[st.c], dtype, opt, &plans[i]);
+    if (rc) {
+      release();
+      return rc;
+    }
+  }
+  for (int i = 0; i < nsteps; ++i) {
+    int rc = run_plan(plans[i], steps[i].alpha, steps[i].beta, s, opt, nullptr);
+    if (rc) {
+      release();
+      return rc;
+    }
+  }
+  release();
+  return FAMLIES_OK;
+}
+
 int famlies_contract(double alpha, const famlies_tensor_t* A, const famlies_tensor_t* B,
                      double beta, const famlies_tensor_t* C, famlies_dtype_t dtype,
                      void* stream) {

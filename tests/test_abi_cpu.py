@@ -130,3 +130,35 @@ def test_no_device_is_reported_not_faked():
     dc = _lib.Desc((4, 6), (1, 4), [1, 3], 0x40000000)
     rc = lib.famlies_contract(1.0, da.ref, db.ref, 0.0, dc.ref, 0, None)
     assert rc == -10
+
+
+def _net_err(tensors, steps, dtype="f64"):
+    with pytest.raises(fm.FamliesError) as e:
+        fm.contract_network(tensors, steps, dtype=dtype, stream=0)
+    return e.value.code
+
+
+def test_network_validation_before_any_launch():
+    """famlies_network rejects malformed sequences on the host, before it
+    touches a device: indices out of range, a step writing one of its own
+    operands, an intermediate read before it is written or first written
+    with beta != 0, and bf16 intermediates."""
+    INVALID, UNSUPPORTED = -1, -6
+    t = [((4, 5), [1, 2]), ((5, 6), [2, 3]), ((4, 6), [1, 3])]  # all intermediates
+    assert _net_err(t, [(0, 1, 3, 1.0, 0.0)]) == INVALID            # c out of range
+    assert _net_err(t, [(0, 1, 0, 1.0, 0.0)]) == INVALID            # c == a
+    assert _net_err(t, [(0, 1, 2, 1.0, 0.0)]) == INVALID            # A, B never written
+    u = [((4, 5), [1, 2]), ((5, 6), [2, 3]), ((4, 6), [1, 3]), ((6, 7), [3, 4]), ((4, 7), [1, 4])]
+    # 2 := 0 * 1 needs 0 and 1 written first; 4 := 2 * 3 with beta != 0 on a fresh 4
+    assert _net_err(u, [(0, 1, 2, 1.0, 0.0)]) == INVALID
+    assert _net_err(u, [(2, 3, 4, 1.0, 1.0)]) == INVALID
+    # bf16 with an intermediate: caller tensors at fake addresses (the check
+    # comes before anything is dereferenced)
+    import ctypes
+    lib = _lib.load()
+    descs = [_lib.Desc((4, 5), (1, 4), [1, 2], 0x10000, 40), _lib.Desc((5, 6), (1, 5), [2, 3], 0x20000, 60),
+             _lib.Desc((4, 6), (0, 0), [1, 3], 0), _lib.Desc((6, 7), (1, 6), [3, 4], 0x30000, 84),
+             _lib.Desc((4, 7), (1, 4), [1, 4], 0x40000, 56)]
+    tt = (_lib.TensorDesc * 5)(*[d.t for d in descs])
+    ss = (_lib.Step * 2)(_lib.Step(0, 1, 2, 0, 1.0, 0.0), _lib.Step(2, 3, 4, 0, 1.0, 0.0))
+    assert lib.famlies_network(tt, 5, ss, 2, fm.BF16, None, None) == UNSUPPORTED
