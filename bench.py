@@ -434,6 +434,59 @@ def run_other(args):
                           "network_ms": ms, "network_tflops": flops / ms / 1e9,
                           "separate_calls_ms": ms_sep, "separate_tflops": flops / ms_sep / 1e9}),
               flush=True)
+    elif args.workload == "ladder_sym":
+        # The ladder with V read as its packed lower triangle (V symmetric
+        # under (ab) <-> (cd)) against the same contraction on dense V;
+        # device-resident, then end to end from pinned host buffers.
+        v, o = V_EXT, O_EXT
+        n = v * v
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(6)
+        Vd = torch.randn(n, n, device="cuda", dtype=torch.float64, generator=gen) / 128
+        Vd = torch.tril(Vd) + torch.tril(Vd, -1).T
+        iu = torch.triu_indices(n, n, device="cuda")
+        Vp = Vd[iu[0], iu[1]].contiguous()  # row q of the upper triangle = column q of the lower
+        del iu
+        Vd = Vd.reshape(v, v, v, v)  # row-major flattening of a symmetric matrix is column-major
+        T = torch.randn(o, o, v, v, device="cuda", dtype=torch.float64, generator=gen).permute(3, 2, 1, 0) * 1e-2
+        C0 = torch.rand(o, o, v, v, device="cuda", dtype=torch.float64, generator=gen).permute(3, 2, 1, 0)
+        Cs, Cd = C0.clone(), C0.clone()
+        lv, lt, lc = W.L("dcba"), W.L("cdij"), W.L("abij")  # Vd's torch order is (d, c, b, a)
+        ext = (v, v, v, v)
+        flops = 2 * v ** 4 * o * o
+        f_sym = lambda: fm.contract_sym(1.0, Vp, ext, W.L("abcd"), T, lt, 1.0, Cs, lc)
+        f_den = lambda: fm.contract(1.0, Vd, lv, T, lt, 1.0, Cd, lc, dtype="f64_emu")
+        ms_sym = _cuda_ms(f_sym, args.steps, args.warmup)
+        ms_den = _cuda_ms(f_den, args.steps, args.warmup)
+        Cs.copy_(C0)
+        Cd.copy_(C0)
+        f_sym()
+        f_den()
+        torch.cuda.synchronize()
+        diff = float((Cs - Cd).abs().max())
+        # end to end: V, T and C in from pinned host memory, C back, every step
+        hV, hVp = Vd.cpu().pin_memory(), Vp.cpu().pin_memory()
+        hT, hC = T.cpu().pin_memory(), C0.cpu().pin_memory()
+        out = torch.empty_like(hC).pin_memory()
+
+        def e2e(packed):
+            Vdev = (Vp if packed else Vd)
+            Vdev.copy_(hVp if packed else hV, non_blocking=True)
+            T.copy_(hT, non_blocking=True)
+            Cx = Cs if packed else Cd
+            Cx.copy_(hC, non_blocking=True)
+            (f_sym if packed else f_den)()
+            out.copy_(Cx, non_blocking=True)
+        e2e_sym = _cuda_ms(lambda: e2e(True), args.steps, args.warmup)
+        e2e_den = _cuda_ms(lambda: e2e(False), args.steps, args.warmup)
+        print(json.dumps({"workload": f"ladder_v{v}_o{o}_f64_split6_packed_symmetric_V", "flops": flops,
+                          "sym_ms": ms_sym, "sym_tflops": flops / ms_sym / 1e9,
+                          "dense_ms": ms_den, "dense_tflops": flops / ms_den / 1e9,
+                          "V_bytes_packed": Vp.numel() * 8, "V_bytes_dense": Vd.numel() * 8,
+                          "max_abs_diff_sym_vs_dense": diff,
+                          "e2e_sym_ms": e2e_sym, "e2e_sym_tflops": flops / e2e_sym / 1e9,
+                          "e2e_dense_ms": e2e_den, "e2e_dense_tflops": flops / e2e_den / 1e9}),
+              flush=True)
     elif args.workload == "autograd":
         from paper_2604_07311_b300.autograd import contract_autograd
         d = W.autograd_problem()
@@ -483,7 +536,7 @@ def run_other(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="ladder",
-                    choices=["ladder", "transpose_free", "block_sparse", "autograd", "network"],
+                    choices=["ladder", "transpose_free", "block_sparse", "autograd", "network", "ladder_sym"],
                     help="ladder is the benchmark line; the others print secondary measurements")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)

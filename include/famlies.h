@@ -258,6 +258,35 @@ FAMLIES_API int famlies_contract_noalloc(double alpha, const famlies_tensor_t* A
                                          const famlies_tensor_t* C, famlies_dtype_t dtype,
                                          void* stream);
 
+/* Contraction with a symmetric dense operand (Sec. 3, "tensor contraction
+ * with general and symmetric dense tensors").  A is symmetric under the
+ * exchange of its first and second halves of modes,
+ *   A[x_1..x_h, y_1..y_h] = A[y_1..y_h, x_1..x_h],
+ * both halves with the same extents.  With p and q the fused indices of the
+ * two halves (first mode fastest, 0 <= p, q < n = product of a half's
+ * extents), only the elements with p >= q are stored, column by column:
+ * element (p, q) at data[q * n - q * (q - 1) / 2 + (p - q)], n (n + 1) / 2
+ * elements in all (LAPACK's lower packed storage of the n x n matrix).
+ * Same operation and conventions as famlies_contract_ex with A expanded;
+ * A is read once (half the bytes of its dense form).
+ * Supported: dtype F64_EMU, with one half of A's modes contracted and the
+ * other free (each half fusing into one index) and no batch label; other
+ * cases return FAMLIES_ERR_UNSUPPORTED.  A's size_bytes (0 = unchecked)
+ * is checked against the packed size; the aliasing check uses the packed
+ * range.  Options as for famlies_contract_ex (the kernel choice is fixed). */
+typedef struct {
+  int32_t ndim;            /* even, 2..FAMLIES_MAX_NDIM */
+  const int64_t* extents;  /* ndim; extents[i] == extents[i + ndim/2] */
+  const int32_t* labels;   /* ndim distinct labels */
+  const void* data;        /* device pointer, packed lower triangle */
+  int64_t size_bytes;
+} famlies_symtensor_t;
+
+FAMLIES_API int famlies_contract_sym(double alpha, const famlies_symtensor_t* A,
+                                     const famlies_tensor_t* B, double beta,
+                                     const famlies_tensor_t* C, famlies_dtype_t dtype, void* stream,
+                                     const famlies_options_t* opt, famlies_plan_info_t* info);
+
 /* Contraction networks: a pre-ordered sequence of tensor contractions run
  * through the same planner and kernels (Sec. 3, Girder 5, tensor contraction
  * networks).  `tensors` lists every tensor of the network; step i computes

@@ -10,7 +10,7 @@ from __future__ import annotations
 from ._lib import (BF16, DTYPES, F32, F64, F64_EMU, KERNELS, Desc, FamliesError, PlanInfo,
                    desc_numpy, desc_torch, load, options, check, error_string)
 
-__all__ = ["contract", "contract_host", "contract_batched", "contract_network", "plan", "device_status",
+__all__ = ["contract", "contract_host", "contract_batched", "contract_network", "contract_sym", "plan", "device_status",
            "FamliesError", "F64", "F64_EMU", "F32", "BF16", "lib_path", "Contract", "contract_autograd"]
 
 
@@ -132,6 +132,36 @@ def contract_network(tensors, steps, dtype="f64", stream=None, *, slices=0, kern
     ss = (Step * max(len(steps), 1))(*[Step(int(a), int(b), int(c), 0, float(al), float(be))
                                        for a, b, c, al, be in steps])
     check(lib.famlies_network(tt, n, ss, len(steps), code, _stream_handle(stream), options(slices, kernel)))
+
+
+def contract_sym(alpha, Ap, extents, la, B, lb, beta, C, lc, dtype="f64_emu", stream=None, *, slices=0,
+                 wait_limit=0, events=None, return_info=False):
+    """C := alpha * contract(A, B) + beta * C with A symmetric, in place on C.
+
+    A[x, y] = A[y, x] for the first and second halves x, y of its modes
+    (`extents` lists all of them, both halves alike).  Ap is a 1-D CUDA
+    tensor holding the lower triangle of A as an n x n matrix (n = product
+    of a half's extents; fused indices first mode fastest), column by column:
+    n (n + 1) / 2 elements.  B and C as for `contract`.
+    """
+    import ctypes
+    from ._lib import SymTensorDesc
+    lib = load()
+    code = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    nd = len(extents)
+    if len(la) != nd:
+        raise ValueError("one label per mode of A")
+    e = (ctypes.c_int64 * max(nd, 1))(*[int(x) for x in extents])
+    lab = (ctypes.c_int32 * max(nd, 1))(*[int(x) for x in la])
+    if Ap.dim() != 1 or Ap.stride(0) != 1:
+        raise ValueError("Ap must be a contiguous 1-D tensor")
+    sa = SymTensorDesc(nd, e, lab, ctypes.c_void_p(Ap.data_ptr()), Ap.numel() * Ap.element_size())
+    db, dc = desc_torch(B, lb), desc_torch(C, lc)
+    info = PlanInfo()
+    opt = options(slices, 0, 0, wait_limit, events)
+    check(lib.famlies_contract_sym(float(alpha), ctypes.byref(sa), db.ref, float(beta), dc.ref, code,
+                                   _stream_handle(stream), opt, info))
+    return (C, info.as_dict()) if return_info else C
 
 
 def contract_noalloc(alpha, A, la, B, lb, beta, C, lc, dtype=None, stream=None):

@@ -32,6 +32,13 @@ class TensorDesc(ctypes.Structure):
                 ("data", ctypes.c_void_p), ("size_bytes", ctypes.c_int64)]
 
 
+class SymTensorDesc(ctypes.Structure):
+    """famlies_symtensor_t: a symmetric operand stored as a packed lower triangle."""
+    _fields_ = [("ndim", ctypes.c_int32), ("extents", ctypes.POINTER(ctypes.c_int64)),
+                ("labels", ctypes.POINTER(ctypes.c_int32)), ("data", ctypes.c_void_p),
+                ("size_bytes", ctypes.c_int64)]
+
+
 class Options(ctypes.Structure):
     _fields_ = [("slices", ctypes.c_int32), ("kernel", ctypes.c_int32), ("tile_n", ctypes.c_int32),
                 ("stall_test", ctypes.c_int32), ("wait_limit", ctypes.c_int64),
@@ -89,12 +96,14 @@ def load(path: str | None = None):
     lib.famlies_plan.argtypes = [T, T, T, ctypes.c_int, ctypes.POINTER(Options), ctypes.POINTER(PlanInfo)]
     lib.famlies_network.argtypes = [T, ctypes.c_int32, ctypes.POINTER(Step), ctypes.c_int32, ctypes.c_int,
                                     vp, ctypes.POINTER(Options)]
+    lib.famlies_contract_sym.argtypes = [d, ctypes.POINTER(SymTensorDesc), T, d, T, ctypes.c_int, vp,
+                                         ctypes.POINTER(Options), ctypes.POINTER(PlanInfo)]
     lib.famlies_error_string.argtypes = [ctypes.c_int]
     lib.famlies_error_string.restype = ctypes.c_char_p
     lib.famlies_device_status.argtypes = [vp]
     for f in ("famlies_contract", "famlies_contract_ex", "famlies_contract_host",
               "famlies_contract_batched", "famlies_plan", "famlies_device_status", "famlies_version",
-              "famlies_network"):
+              "famlies_network", "famlies_contract_sym"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib

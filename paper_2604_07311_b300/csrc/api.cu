@@ -104,7 +104,7 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
     err = launch_scale(p, t, beta, s);
     ++launches;
   } else {
-    GemmArgs g;
+    GemmArgs g = {};
     g.a = p.a;
     g.b = p.b;
     g.c = p.c;
@@ -121,6 +121,8 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
     g.status = device_status_ptr();
     if (!g.status) return FAMLIES_ERR_CUDA;
     g.stall_test = opt ? opt->stall_test : 0;
+    g.sym_n = p.sym_n;
+    g.sym_side = p.sym_side;
     g.ev_begin = opt ? (cudaEvent_t)opt->events[0] : nullptr;
     g.ev_end = opt ? (cudaEvent_t)opt->events[1] : nullptr;
     switch (p.kernel) {
@@ -192,6 +194,64 @@ int famlies_contract_ex(double alpha, const famlies_tensor_t* A, const famlies_t
   int rc = make_plan(alpha, A, B, C, dtype, opt, &p);
   if (rc) return rc;
   return run_plan(p, alpha, beta, (cudaStream_t)stream, opt, info);
+}
+
+int famlies_contract_sym(double alpha, const famlies_symtensor_t* A, const famlies_tensor_t* B,
+                         double beta, const famlies_tensor_t* C, famlies_dtype_t dtype,
+                         void* stream, const famlies_options_t* opt, famlies_plan_info_t* info) {
+  if (!A || !B || !C || A->ndim < 2 || A->ndim > FAMLIES_MAX_NDIM || A->ndim % 2 ||
+      !A->extents || !A->labels)
+    return FAMLIES_ERR_INVALID_ARG;
+  if (dtype != FAMLIES_F64_EMU) return FAMLIES_ERR_UNSUPPORTED;
+  const int h = A->ndim / 2;
+  int64_t n = 1;
+  for (int i = 0; i < h; ++i) {
+    if (A->extents[i] < 0 || A->extents[i] != A->extents[i + h]) return FAMLIES_ERR_INVALID_ARG;
+    n *= A->extents[i];
+  }
+  const int64_t packed = n * (n + 1) / 2;
+  if (A->size_bytes > 0 && packed * 8 > A->size_bytes) return FAMLIES_ERR_OUT_OF_BOUNDS;
+  // Plan A as its dense expansion (first mode fastest): the halves' fused
+  // indices p and q then have strides 1 and n.  A stand-in address keeps the
+  // planner's aliasing check (which would see n^2 elements) off the packed
+  // data; the packed range is checked here instead.
+  int64_t st[FAMLIES_MAX_NDIM];
+  int64_t acc = 1;
+  for (int i = 0; i < A->ndim; ++i) {
+    st[i] = acc;
+    acc *= A->extents[i];
+  }
+  famlies_tensor_t dense = {A->ndim, A->extents, st, A->labels, (void*)(uintptr_t)256, 0};
+  famlies_options_t o = {};
+  if (opt) o = *opt;
+  o.kernel = 2;  // the packed tensor-core path
+  Plan p;
+  int rc = make_plan(alpha, &dense, B, C, dtype, &o, &p);
+  if (rc) return rc;
+  if (p.kernel == FAMLIES_KERNEL_NONE || p.kernel == FAMLIES_KERNEL_SCALE)
+    return run_plan(p, alpha, beta, (cudaStream_t)stream, &o, info);  // A is not read
+  if (p.kernel != FAMLIES_KERNEL_TC_EMU) return FAMLIES_ERR_UNSUPPORTED;
+  if (!A->data) return FAMLIES_ERR_INVALID_ARG;
+  {
+    const int64_t sc = p.span_c * p.es_c;
+    const char* c0 = (const char*)C->data;
+    const char* a0 = (const char*)A->data;
+    if (c0 < a0 + packed * 8 && a0 < c0 + sc) return FAMLIES_ERR_ALIAS;
+  }
+  // A's side and classes: one mode each (after fusion) for its rows and k,
+  // of extent n, with strides 1 and n in the dense expansion.
+  const int side = p.swapped ? 1 : 0;
+  const ClassModes& R = side == 0 ? p.M : p.N;
+  if (R.n != 1 || p.K.n != 1 || p.L.n != 0 || R.m[0].ext != n || p.K.m[0].ext != n)
+    return FAMLIES_ERR_UNSUPPORTED;
+  const int64_t sr = side == 0 ? R.m[0].sa : R.m[0].sb;
+  const int64_t sk = side == 0 ? p.K.m[0].sa : p.K.m[0].sb;
+  if (!((sr == 1 && sk == n) || (sr == n && sk == 1))) return FAMLIES_ERR_UNSUPPORTED;
+  if (side == 0) p.a = A->data;
+  else p.b = A->data;
+  p.sym_n = n;
+  p.sym_side = side;
+  return run_plan(p, alpha, beta, (cudaStream_t)stream, &o, info);
 }
 
 int famlies_network(const famlies_tensor_t* tensors, int32_t ntensors,

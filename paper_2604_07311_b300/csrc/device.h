@@ -36,6 +36,8 @@ struct GemmArgs {
   int64_t wait_limit;      // iteration cap of every bounded wait
   int* status;             // device status word (first error recorded wins)
   int stall_test;          // testing: product kernels first wait on a barrier nothing completes
+  int64_t sym_n;           // > 0: operand sym_side is a packed symmetric matrix (see Plan)
+  int sym_side;
   cudaEvent_t ev_begin, ev_end;  // host only: recorded around the product kernel
 };
 

@@ -31,6 +31,17 @@ __device__ __forceinline__ void mark_row(const PackOp& o, int64_t idx) {
   }
 }
 
+// Element (p, q) of a symmetric n x n matrix stored as its lower triangle,
+// column by column: column q holds rows q..n-1 and starts at q n - q (q-1)/2.
+__host__ __device__ __forceinline__ int64_t sym_at(int64_t p, int64_t q, int64_t n) {
+  if (p < q) {
+    const int64_t t = p;
+    p = q;
+    q = t;
+  }
+  return q * n - q * (q - 1) / 2 + (p - q);
+}
+
 // Offsets of row r and contracted index k of an operand: affine when the
 // class fused to one mode, otherwise read from the offset tables.
 __device__ __forceinline__ int64_t row_off(const PackOp& o, int64_t r) {
@@ -339,8 +350,9 @@ __device__ __forceinline__ void store_regs(const PackTile& t, typename PackT<PMO
 }
 
 // Converts a staged tile and writes it as 16-byte K-major chunks of every
-// slice.
-template <int PMODE>
+// slice.  TR: the staged tile holds the transpose (buf[kk][r]), as the
+// symmetric pack uses one staged block for both of its mirror images.
+template <int PMODE, bool TR = false>
 __device__ __forceinline__ void emit_tile(const PackTile& t, const typename PackT<PMODE>::T* buf) {
   const PackArgs& pa = *t.pa;
   const PackOp& o = *t.o;
@@ -353,7 +365,12 @@ __device__ __forceinline__ void emit_tile(const PackTile& t, const typename Pack
     const int64_t gr = tr * PR + r, gk0 = tk * PK + c * 8;
     if (gr >= o.rows || gk0 >= pa.k) continue;
     const size_t rowbase = ((size_t)il * o.rows + gr) * pa.kp + gk0;
-    const auto* v = buf + r * TLD + c * 8;
+    typename PackT<PMODE>::T vt[8];
+    if constexpr (TR) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) vt[j] = buf[(c * 8 + j) * TLD + r];
+    }
+    const auto* v = TR ? vt : buf + r * TLD + c * 8;
     if constexpr (PMODE == PACK_BF16) {
       uint32_t w[4];
 #pragma unroll
@@ -387,6 +404,119 @@ __device__ __forceinline__ void emit_tile(const PackTile& t, const typename Pack
         default: split8<7>(v, ex, bad, out, slice_stride); break;
       }
     }
+  }
+}
+
+// ---------------------------------------------------------------- symmetric
+// The operand is the lower triangle of a symmetric n x n matrix stored
+// column by column (famlies_contract_sym).  Both kernels walk its PR x PK
+// blocks (P, Q) with P >= Q, numbered row by row of the block triangle, and
+// read each stored element once, along the stored columns.
+
+// Block (P, Q) of lower-triangle block number t: t = P (P + 1) / 2 + Q.
+__device__ __forceinline__ void tri_block(int64_t t, int64_t& P, int64_t& Q) {
+  int64_t p = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((p + 1) * (p + 2) / 2 <= t) ++p;
+  while (p * (p + 1) / 2 > t) --p;
+  P = p;
+  Q = t - p * (p + 1) / 2;
+}
+
+// Row exponent bounds: a stored element (p, q) bounds row p and, being also
+// element (q, p), row q.
+__device__ __forceinline__ void rowexp_sym_body(const PackOp& o) {
+  const double* __restrict__ X = (const double*)o.x;
+  const int64_t n = o.sym_n, nb = (n + PR - 1) / PR, nblk = nb * (nb + 1) / 2;
+  __shared__ int rmx[4][PR], rbad[4][PR];
+  __shared__ int cmx[2][4][PK / 4], cbad[2][4][PK / 4];
+  const int tid = threadIdx.x, r = tid % PR, qi = tid / PR, lane = tid & 31, wh = (tid >> 5) & 1;
+  for (int64_t t = blockIdx.x; t < nblk; t += gridDim.x) {
+    int64_t P, Q;
+    tri_block(t, P, Q);
+    const int64_t p = P * PR + r;
+    int mxr = -1100, badr = 0;
+#pragma unroll
+    for (int i = 0; i < PK / 4; ++i) {
+      const int64_t q = Q * PK + qi + 4 * i;
+      int mxc = -1100, badc = 0;
+      if (p < n && q < n && p >= q) {  // consecutive p of one stored column
+        exp_update(__ldg(X + sym_at(p, q, n)), mxc, badc);
+        mxr = max(mxr, mxc);
+        badr |= badc;
+      }
+      mxc = __reduce_max_sync(0xffffffffu, mxc);
+      badc = __reduce_or_sync(0xffffffffu, badc);
+      if (lane == 0) {
+        cmx[wh][qi][i] = mxc;
+        cbad[wh][qi][i] = badc;
+      }
+    }
+    rmx[qi][r] = mxr;
+    rbad[qi][r] = badr;
+    __syncthreads();
+    if (tid < PR) {  // rows P * PR + tid
+      const int64_t pp = P * PR + tid;
+      const int m = max(max(rmx[0][tid], rmx[1][tid]), max(rmx[2][tid], rmx[3][tid]));
+      const int b = rbad[0][tid] | rbad[1][tid] | rbad[2][tid] | rbad[3][tid];
+      if (pp < n && m > -1100) atomicMax(&o.e[pp], m);
+      if (pp < n && b) mark_row(o, pp);
+    } else if (tid < PR + PK) {  // rows Q * PK + j (the mirror images)
+      const int j = tid - PR, jq = j % 4, ji = j / 4;
+      const int64_t qq = Q * PK + jq + 4 * ji;
+      const int m = max(cmx[0][jq][ji], cmx[1][jq][ji]);
+      const int b = cbad[0][jq][ji] | cbad[1][jq][ji];
+      if (qq < n && m > -1100) atomicMax(&o.e[qq], m);
+      if (qq < n && b) mark_row(o, qq);
+    }
+    __syncthreads();
+  }
+}
+
+// Stages block (P, Q): buf[r][kk] = element (P PR + r, Q PK + kk), read along
+// the stored columns (diagonal blocks also read their mirrored half).
+__device__ __forceinline__ void load_sym_block(const PackOp& o, int64_t P, int64_t Q, double* buf) {
+  const double* __restrict__ X = (const double*)o.x;
+  const int64_t n = o.sym_n;
+  const int r = threadIdx.x % PR;
+  const int64_t p = P * PR + r;
+#pragma unroll
+  for (int i = 0; i < PER_THREAD; ++i) {
+    const int kk = threadIdx.x / PR + i * (256 / PR);
+    const int64_t q = Q * PK + kk;
+    const bool ok = p < n && q < n;
+    cp_async_elem<8>(buf + r * TLD + kk, ok ? X + sym_at(p, q, n) : X, ok);
+  }
+}
+
+// Slices of the symmetric operand: block (P, Q) gives rows P x k Q and, off
+// the diagonal, its transpose, rows Q x k P; double-buffered like
+// pack_pipeline.
+__device__ __forceinline__ void pack_sym_body(const PackArgs& pa, const PackOp& o) {
+  extern __shared__ __align__(16) unsigned char pack_smem[];
+  double* const buf0 = (double*)pack_smem;
+  auto buf = [&](int j) { return buf0 + (j & 1) * (PR * TLD); };
+  const int64_t n = o.sym_n, nb = (n + PR - 1) / PR, nblk = nb * (nb + 1) / 2;
+  if ((int64_t)blockIdx.x >= nblk) return;
+  int64_t P, Q;
+  tri_block(blockIdx.x, P, Q);
+  load_sym_block(o, P, Q, buf(0));
+  cp_async_commit();
+  int i = 0;
+  for (int64_t t = blockIdx.x; t < nblk; t += gridDim.x, ++i) {
+    int64_t Pn = P, Qn = Q;
+    if (t + gridDim.x < nblk) {
+      tri_block(t + gridDim.x, Pn, Qn);
+      load_sym_block(o, Pn, Qn, buf(i + 1));
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    // tile numbers as emit_tile decodes them: row block + nb * k block
+    emit_tile<PACK_F64>(PackTile{&pa, &o, P + nb * Q}, buf(i));
+    if (P != Q) emit_tile<PACK_F64, true>(PackTile{&pa, &o, Q + nb * P}, buf(i));
+    __syncthreads();
+    P = Pn;
+    Q = Qn;
   }
 }
 
@@ -461,7 +591,18 @@ __device__ __forceinline__ void fixup_body(const GemmArgs& g, const int32_t* __r
     }
     const int64_t ab = g.t.al[il] + g.t.am[m], bb = g.t.bl[il] + g.t.bn[n];
     double acc = 0.0;
-    for (int64_t k = 0; k < g.k; ++k) acc = fma(A[ab + g.t.ak[k]], B[bb + g.t.bk[k]], acc);
+    if (g.sym_n > 0) {
+      // the tables hold offsets p + n q of the dense symmetric matrix
+      const int64_t sn = g.sym_n;
+      for (int64_t k = 0; k < g.k; ++k) {
+        int64_t oa = ab + g.t.ak[k], ob = bb + g.t.bk[k];
+        if (g.sym_side == 0) oa = sym_at(oa % sn, oa / sn, sn);
+        else ob = sym_at(ob % sn, ob / sn, sn);
+        acc = fma(A[oa], B[ob], acc);
+      }
+    } else {
+      for (int64_t k = 0; k < g.k; ++k) acc = fma(A[ab + g.t.ak[k]], B[bb + g.t.bk[k]], acc);
+    }
     double* p = C + g.t.cl[il] + g.t.cm[m] + g.t.cn[n];
     double v = g.alpha * acc;
     if (g.beta != 0.0) v = fma(g.beta, *p, v);
@@ -484,6 +625,14 @@ __global__ void __launch_bounds__(256, 3) k_pack(const __grid_constant__ PackArg
   const PackOp* o = &pa.op[blockIdx.z];
   pack_pipeline<PMODE>(blockIdx.x, gridDim.x, n_pack_tiles(o->rows, pa.k, pa.l),
                        [&](int64_t g) { return PackTile{&pa, o, g}; });
+}
+
+__global__ void __launch_bounds__(256) k_rowexp_sym(const __grid_constant__ PackArgs pa, int side) {
+  rowexp_sym_body(pa.op[side]);
+}
+
+__global__ void __launch_bounds__(256, 3) k_pack_sym(const __grid_constant__ PackArgs pa, int side) {
+  pack_sym_body(pa, pa.op[side]);
 }
 
 __global__ void __launch_bounds__(256) k_fixup(GemmArgs g, const int32_t* list_a,
@@ -610,6 +759,7 @@ static cudaError_t configure_pack_kernels() {
   configure(k_pack_grouped<PACK_BF16>, pack_smem_bytes<PACK_BF16>());
   configure(k_pack_grouped<PACK_TF32>, pack_smem_bytes<PACK_TF32>());
   configure(k_pack_grouped<PACK_F64>, pack_smem_bytes<PACK_F64>());
+  configure(k_pack_sym, pack_smem_bytes<PACK_F64>());
   e = cudaGetLastError();
   if (e == cudaSuccess && dev < kMaxDev) done[dev] = true;
   return e;
@@ -629,6 +779,26 @@ cudaError_t launch_pack(int pmode, const PackArgs& pa, cudaStream_t s) {
     k_pack<PACK_TF32><<<grid, 256, pack_smem_bytes<PACK_TF32>(), s>>>(pa);
   else
     k_pack<PACK_F64><<<grid, 256, pack_smem_bytes<PACK_F64>(), s>>>(pa);
+  return cudaGetLastError();
+}
+
+static int64_t sym_blocks(const PackOp& o) {
+  const int64_t nb = (o.sym_n + PR - 1) / PR;
+  return nb * (nb + 1) / 2;
+}
+
+cudaError_t launch_rowexp_sym(const PackArgs& pa, int side, cudaStream_t s) {
+  const int64_t nblk = sym_blocks(pa.op[side]);
+  if (nblk <= 0) return cudaSuccess;
+  k_rowexp_sym<<<grid_for(nblk), 256, 0, s>>>(pa, side);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_sym(const PackArgs& pa, int side, cudaStream_t s) {
+  if (cudaError_t e = configure_pack_kernels(); e != cudaSuccess) return e;
+  const int64_t nblk = sym_blocks(pa.op[side]);
+  if (nblk <= 0) return cudaSuccess;
+  k_pack_sym<<<grid_for(nblk), 256, pack_smem_bytes<PACK_F64>(), s>>>(pa, side);
   return cudaGetLastError();
 }
 

@@ -906,7 +906,8 @@ int64_t packed_workspace_bytes(const Plan& p) { return (int64_t)layout_of(p).tot
 
 int packed_launches(const Plan& p) {
   if (p.kernel == FAMLIES_KERNEL_TC_EMU)  // exponents + pack + product (+ split finish) + fix-up
-    return 4 + (split_count(p, pair_bn_for(p.n, p.tile_n)) > 1 ? 1 : 0);
+    return 4 + (split_count(p, pair_bn_for(p.n, p.tile_n)) > 1 ? 1 : 0) +
+           (p.sym_n > 0 ? 2 : 0);  // (+ the symmetric operand's exponents and pack)
   DirectView v;
   const bool tf32 = p.kernel == FAMLIES_KERNEL_TC_TF32X3;
   const bool da = !tf32 && direct_view(p.M, p.K, p.L, 0, p.a, &v);
@@ -931,6 +932,8 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   pa.op[1] = PackOp{g.b, g.t.bn, g.t.bk, g.t.bl, p.n, p.b_contig, w + L.b, nullptr, nullptr, nullptr};
   set_affine(pa.op[0], p.M, p.K, 0);
   set_affine(pa.op[1], p.N, p.K, 1);
+  const bool sym = p.sym_n > 0;
+  if (sym) pa.op[p.sym_side].sym_n = p.sym_n;
   cudaError_t e;
   if (emu) {
     pa.op[0].e = (int32_t*)(w + L.ea);
@@ -942,7 +945,10 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     // exponents start at a large negative value, flags and list counts at 0
     if ((e = cudaMemsetAsync(w + L.ea, 0x80, L.fa - L.ea, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w + L.fa, 0, L.G - L.fa, s)) != cudaSuccess) return e;
-    if ((e = launch_rowexp(pa, s)) != cudaSuccess) return e;
+    PackArgs pg = pa;  // the generic kernels skip a symmetric operand
+    if (sym) pg.op[p.sym_side].rows = 0;
+    if ((e = launch_rowexp(pg, s)) != cudaSuccess) return e;
+    if (sym && (e = launch_rowexp_sym(pa, p.sym_side, s)) != cudaSuccess) return e;
   }
   const int bn = pair_bn_for(p.n, p.tile_n);
   const int S = pa.slices;
@@ -957,9 +963,13 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   const bool db = !emu && !tf32 && direct_view(p.N, p.K, p.L, 1, p.b, &vb);
   if (da) pa.op[0].rows = 0;  // nothing to pack
   if (db) pa.op[1].rows = 0;
-  if ((!da || !db) &&
-      (e = launch_pack(emu ? PACK_F64 : (tf32 ? PACK_TF32 : PACK_BF16), pa, s)) != cudaSuccess)
-    return e;
+  if (!da || !db) {
+    PackArgs pg = pa;
+    if (sym) pg.op[p.sym_side].rows = 0;
+    if ((e = launch_pack(emu ? PACK_F64 : (tf32 ? PACK_TF32 : PACK_BF16), pg, s)) != cudaSuccess)
+      return e;
+    if (sym && (e = launch_pack_sym(pa, p.sym_side, s)) != cudaSuccess) return e;
+  }
   const bool ok_a = da ? make_view_map(&ma, va, p.k, p.m, p.l, kbk, BM)
                        : make_slice_map(&ma, w + L.a, tf32, p.k, kp, p.m, (int64_t)S * p.l, kbk, BM);
   const bool ok_b = db ? make_view_map(&mb, vb, p.k, p.n, p.l, kbk, bn)

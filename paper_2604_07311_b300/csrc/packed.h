@@ -34,6 +34,10 @@ struct PackOp {
   // (the tables are then not read).
   int affine;
   int64_t rs, ks;
+  // > 0: the operand is the lower triangle of a symmetric sym_n x sym_n
+  // matrix, column by column; rows and k index the two sides (packed by
+  // k_rowexp_sym / k_pack_sym, not by the generic kernels).
+  int64_t sym_n;
 };
 
 // Sets the affine fields of a pack operand from its row and k classes
@@ -50,6 +54,11 @@ struct PackArgs {
 cudaError_t launch_rowexp(const PackArgs& pa, cudaStream_t s);
 // Writes the slices of both operands.
 cudaError_t launch_pack(int pmode, const PackArgs& pa, cudaStream_t s);
+// Symmetric packed operand pa.op[side] (fp64 split): row exponents and flags
+// (every stored element bounds its row and, by symmetry, its column) and its
+// slices, both from one read of the lower triangle.
+cudaError_t launch_rowexp_sym(const PackArgs& pa, int side, cudaStream_t s);
+cudaError_t launch_pack_sym(const PackArgs& pa, int side, cudaStream_t s);
 // fp64 split: recomputes in native fp64 the outputs of flagged rows/columns.
 cudaError_t launch_fixup(const GemmArgs& g, const PackArgs& pa, cudaStream_t s);
 

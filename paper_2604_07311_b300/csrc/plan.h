@@ -51,6 +51,12 @@ struct Plan {
   int kernel = FAMLIES_KERNEL_NONE;
   int slices = 6;
   int tile_n = 0;  // tensor-core tile width request (0 = automatic)
+  // Symmetric packed operand (famlies_contract_sym): n > 0 when the row
+  // (side 0) or column (side 1) operand is stored as the lower triangle of
+  // a symmetric n x n matrix; its classes are then one mode each (rows and
+  // k of extent n) and its tables hold the offsets of the dense layout.
+  int64_t sym_n = 0;
+  int sym_side = -1;
 };
 
 // Validates and plans; returns FAMLIES_OK or a FAMLIES_ERR_* code.  Never

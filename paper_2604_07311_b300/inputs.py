@@ -96,6 +96,13 @@ def _operand(values: np.ndarray, extents, labels, lead_pad: int = 0, rng=None) -
     return op
 
 
+def packed_lower(M: np.ndarray) -> np.ndarray:
+    """Lower triangle of a square matrix, column by column (LAPACK's lower
+    packed storage): M[p, q], p >= q, lands at q * n - q * (q - 1) / 2 + p - q."""
+    n = M.shape[0]
+    return np.concatenate([M[q:, q] for q in range(n)]) if n else np.zeros(0)
+
+
 def uniform_operand(rng, extents, labels, lo=-1.0, hi=1.0, lead_pad=0) -> Operand:
     vals = rng.uniform(lo, hi, size=tuple(extents))
     return _operand(vals, extents, labels, lead_pad, rng)

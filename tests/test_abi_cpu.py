@@ -162,3 +162,38 @@ def test_network_validation_before_any_launch():
     tt = (_lib.TensorDesc * 5)(*[d.t for d in descs])
     ss = (_lib.Step * 2)(_lib.Step(0, 1, 2, 0, 1.0, 0.0), _lib.Step(2, 3, 4, 0, 1.0, 0.0))
     assert lib.famlies_network(tt, 5, ss, 2, fm.BF16, None, None) == UNSUPPORTED
+
+
+def _sym_rc(ext, la, b, c, dtype=None, size_bytes=0):
+    """famlies_contract_sym on descriptors at fake addresses (host checks only)."""
+    import ctypes
+    lib = _lib.load()
+    nd = len(ext)
+    e = (ctypes.c_int64 * nd)(*ext)
+    lab = (ctypes.c_int32 * nd)(*la)
+    a = _lib.SymTensorDesc(nd, e, lab, ctypes.c_void_p(0x10000000), size_bytes)
+    info = _lib.PlanInfo()
+    return lib.famlies_contract_sym(1.0, ctypes.byref(a), b.ref, 0.0, c.ref,
+                                    fm.F64_EMU if dtype is None else dtype, None, None, ctypes.byref(info))
+
+
+def test_symmetric_operand_validation():
+    """famlies_contract_sym checks the symmetric operand on the host: an even
+    number of modes with equal halves, the packed size, the dtype, and one
+    fused index per half (one contracted, one free)."""
+    INVALID, OOB, UNSUPPORTED = -1, -5, -6
+    v, o = 4, 3
+    B = _lib.Desc((v, v, o), (1, v, v * v), [3, 4, 5], 0x20000000)
+    C = _lib.Desc((v, v, o), (1, v, v * v), [1, 2, 5], 0x40000000)
+    assert _sym_rc((v, v, v), [1, 2, 3], B, C) == INVALID                     # odd number of modes
+    assert _sym_rc((v, v, v, v + 1), [1, 2, 3, 4], B, C) == INVALID           # halves differ
+    assert _sym_rc((v, v, v, v), [1, 2, 3, 4], B, C, dtype=fm.F64) == UNSUPPORTED
+    n = v * v
+    assert _sym_rc((v, v, v, v), [1, 2, 3, 4], B, C, size_bytes=n * (n + 1) // 2 * 8 - 8) == OOB
+    # K = (c, d) stored d-fastest in B: the contracted half does not fuse
+    Bt = _lib.Desc((v, v, o), (v, 1, v * v), [3, 4, 5], 0x20000000)
+    assert _sym_rc((v, v, v, v), [1, 2, 3, 4], Bt, C) == UNSUPPORTED
+    # one mode of each half contracted, the others free
+    B2 = _lib.Desc((v, v, o), (1, v, v * v), [2, 4, 5], 0x20000000)
+    C2 = _lib.Desc((v, v, o), (1, v, v * v), [1, 3, 5], 0x40000000)
+    assert _sym_rc((v, v, v, v), [1, 2, 3, 4], B2, C2) == UNSUPPORTED
