@@ -16,6 +16,12 @@ Parity status per function (what pins it, see tests/test_oracle.py):
                rank-1, Kronecker), invariants, special cases.
   entries   -- pinned: agrees with contract; Dot2 mode checked against exact
                rational arithmetic (fractions.Fraction).
+  gemmt_tridiag -- pinned: exact integer brute force over the dense T
+               (Python ints), closed forms (A = identity gives T's lower
+               triangle, A = a permutation gives the permuted T, k = 1 gives
+               a scaled outer product), the exact zero diagonal of A T A^T
+               for skew-symmetric T, the untouched upper triangle, and the
+               alpha = 0 / beta = 0 conventions.
 """
 from __future__ import annotations
 
@@ -133,3 +139,36 @@ def entries(alpha, A, la, B, lb, beta, C, lc, index, dot2: bool = False) -> np.n
     if rc:
         raise OracleError(rc)
     return out
+
+
+def gemmt_tridiag(alpha, A, sub, diag, sup, beta, C) -> np.ndarray:
+    """Lower triangle of C := beta * C + alpha * A T A^T, in place on C (n x n).
+
+    The sandwiched product of the paper's skew-symmetric factorisations
+    (Sec. 3, "Beyond LAPACK functionality"), evaluated in the two steps the
+    paper names for it: B = T A^T with T tridiagonal (T[p+1,p] = sub[p],
+    T[p,p] = diag[p], T[p,p+1] = sup[p]; diag None: zero diagonal; sup
+    None: sup = -sub, T skew-symmetric), then the GEMMT update C := beta C
+    + alpha A B of the entries i >= j only.  T is a band: only its three
+    diagonals multiply.  alpha == 0: A is not read; beta == 0: C is not read
+    (BLAS conventions).  A is n x k; all float64.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    n, k = A.shape
+    low = np.tril(np.ones((n, n), dtype=bool))
+    if alpha == 0.0 or k == 0 or n == 0:
+        C[low] = 0.0 if beta == 0.0 else beta * C[low]
+        return C
+    sub = np.zeros(0) if sub is None else np.asarray(sub, dtype=np.float64)
+    sup = -sub if sup is None else np.asarray(sup, dtype=np.float64)
+    B = np.zeros((k, n))
+    for p in range(k):  # row p of T A^T: the band of T's row p against A's columns
+        if p > 0:
+            B[p] += sub[p - 1] * A[:, p - 1]
+        if diag is not None:
+            B[p] += diag[p] * A[:, p]
+        if p + 1 < k:
+            B[p] += sup[p] * A[:, p + 1]
+    full = A @ B
+    C[low] = alpha * full[low] if beta == 0.0 else alpha * full[low] + beta * C[low]
+    return C

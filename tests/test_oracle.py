@@ -337,3 +337,113 @@ def test_workload_generators_shapes():
     assert np.array_equal(V, V.transpose(2, 3, 0, 1))  # (ab)<->(cd) symmetry
     blocks = W.block_sparse(nblocks=5)
     assert all(set(b.meta["ext"]) <= set(range(8, 97, 8)) for b in blocks)
+
+
+# ---------------------------------------------------------------------------
+# Sandwiched product C := beta C + alpha A T A^T, lower triangle (gemmt_tridiag)
+# ---------------------------------------------------------------------------
+
+def _dense_tridiag(k, sub, diag, sup):
+    T = [[0] * k for _ in range(k)]
+    for p in range(k):
+        if diag is not None:
+            T[p][p] = diag[p]
+        if p + 1 < k:
+            T[p + 1][p] = sub[p]
+            T[p][p + 1] = -sub[p] if sup is None else sup[p]
+    return T
+
+
+@pytest.mark.parametrize("n,k,skew", [(5, 4, True), (6, 7, False), (3, 1, False), (4, 2, True)])
+def test_gemmt_bruteforce_exact_integer(n, k, skew):
+    """Every (p, q) of the dense T summed in Python integers (off-band zeros
+    included): the oracle's banded two-step evaluation is exact on small
+    integers."""
+    rng = np.random.default_rng(900 + n * 10 + k)
+    A = rng.integers(-3, 4, size=(n, k))
+    sub = rng.integers(-3, 4, size=max(k - 1, 0))
+    diag = None if skew else rng.integers(-3, 4, size=k)
+    sup = None if skew else rng.integers(-3, 4, size=max(k - 1, 0))
+    C0 = rng.integers(-5, 6, size=(n, n)).astype(np.float64)
+    alpha, beta = -1, 2
+    T = _dense_tridiag(k, [int(x) for x in sub], None if diag is None else [int(x) for x in diag],
+                       None if sup is None else [int(x) for x in sup])
+    want = C0.copy()
+    for i in range(n):
+        for j in range(i + 1):
+            s = sum(int(A[i, p]) * T[p][q] * int(A[j, q]) for p in range(k) for q in range(k))
+            want[i, j] = alpha * s + beta * C0[i, j]
+    got = oracle.gemmt_tridiag(alpha, A.astype(np.float64), sub, diag, sup, beta, C0.copy())
+    assert np.array_equal(got, want)
+
+
+def test_gemmt_identity_gives_lower_triangle_of_T():
+    """A = I: A T A^T = T, so C's lower triangle becomes T's: the diagonal
+    and the subdiagonal, never the superdiagonal (a swapped sub/sup or a
+    transposed product fails here)."""
+    k = 6
+    sub = np.arange(1.0, k)
+    diag = np.arange(10.0, 10.0 + k)
+    sup = -np.arange(100.0, 100.0 + k - 1)
+    C = np.full((k, k), 7.0)
+    oracle.gemmt_tridiag(1.0, np.eye(k), sub, diag, sup, 0.0, C)
+    for i in range(k):
+        for j in range(k):
+            if i < j:
+                assert C[i, j] == 7.0  # upper triangle untouched
+            elif i == j:
+                assert C[i, j] == diag[i]
+            elif i == j + 1:
+                assert C[i, j] == sub[j]
+            else:
+                assert C[i, j] == 0.0
+
+
+def test_gemmt_permutation_permutes_T():
+    """A = the permutation matrix of pi: (A T A^T)[i, j] = T[pi(i), pi(j)]."""
+    k = 7
+    rng = np.random.default_rng(910)
+    pi = rng.permutation(k)
+    P = np.zeros((k, k))
+    P[np.arange(k), pi] = 1.0
+    sub, diag, sup = rng.standard_normal(k - 1), rng.standard_normal(k), rng.standard_normal(k - 1)
+    T = np.array(_dense_tridiag(k, list(sub), list(diag), list(sup)), dtype=np.float64)
+    C = np.zeros((k, k))
+    oracle.gemmt_tridiag(1.0, P, sub, diag, sup, 0.0, C)
+    for i in range(k):
+        for j in range(i + 1):
+            assert C[i, j] == T[pi[i], pi[j]]
+
+
+def test_gemmt_k1_outer_product_and_skew_zero_diagonal():
+    """k = 1: C = beta C + alpha d a a^T (lower).  Skew-symmetric T with
+    integer A: A T A^T is skew-symmetric, so its diagonal is exactly 0."""
+    a = np.array([[1.0], [-2.0], [3.0]])
+    C = np.ones((3, 3))
+    oracle.gemmt_tridiag(2.0, a, None, np.array([5.0]), None, 1.0, C)
+    want = np.tril(1.0 + 10.0 * (a @ a.T)) + np.triu(np.ones((3, 3)), 1)
+    assert np.array_equal(C, want)
+    rng = np.random.default_rng(920)
+    A = rng.integers(-9, 10, size=(8, 11)).astype(np.float64)
+    sub = rng.integers(-9, 10, size=10).astype(np.float64)
+    C = np.zeros((8, 8))
+    oracle.gemmt_tridiag(1.0, A, sub, None, None, 0.0, C)
+    assert np.all(np.diag(C) == 0.0)
+    assert np.any(np.tril(C, -1) != 0.0)
+
+
+def test_gemmt_alpha_beta_conventions():
+    """alpha == 0 reads no A (NaN in A ignored), beta == 0 reads no C (NaN in
+    C overwritten); the strictly upper triangle is never touched."""
+    A = np.full((4, 3), np.nan)
+    C = np.arange(16.0).reshape(4, 4)
+    C0 = C.copy()
+    oracle.gemmt_tridiag(0.0, A, np.ones(2), None, None, 0.5, C)
+    assert np.array_equal(np.tril(C), 0.5 * np.tril(C0))
+    assert np.array_equal(np.triu(C, 1), np.triu(C0, 1))
+    A = np.ones((4, 3))
+    C = np.full((4, 4), np.nan)
+    oracle.gemmt_tridiag(1.0, A, np.ones(2), None, np.ones(2), 0.0, C)
+    iu = np.triu_indices(4, 1)
+    assert not np.isnan(np.tril(C)).any()
+    assert np.isnan(C[iu]).all()
