@@ -487,6 +487,39 @@ def run_other(args):
                           "e2e_sym_ms": e2e_sym, "e2e_sym_tflops": flops / e2e_sym / 1e9,
                           "e2e_dense_ms": e2e_den, "e2e_dense_tflops": flops / e2e_den / 1e9}),
               flush=True)
+    elif args.workload == "gemmt":
+        # The sandwiched update C := C - A T A^T of a skew-symmetric
+        # factorisation (T tridiagonal skew-symmetric, lower triangle of C):
+        # a panel-width k and a square case, against the same update done
+        # the unfused way (T A^T formed by torch, then the full square
+        # product through the library).
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(7)
+        for n, k in ((16384, 256), (8192, 8192)):
+            flops = n * (n + 1) * k  # 2k per entry of the lower triangle
+            row = {"workload": f"gemmt_skew_tridiag_n{n}_k{k}", "flops": flops}
+            for dt, tdt in (("f64_emu", torch.float64), ("f64", torch.float64), ("f32", torch.float32)):
+                A = torch.randn(k, n, device="cuda", dtype=tdt, generator=gen).t()  # column-major
+                sub = torch.randn(k - 1, device="cuda", dtype=tdt, generator=gen)
+                C = torch.randn(n, n, device="cuda", dtype=tdt, generator=gen).t()
+                f = lambda **kw: fm.gemmt_tridiag(-1.0, A, sub, None, None, 1.0, C, dtype=dt, **kw)
+                steps = args.steps if dt != "f64" else max(1, min(args.steps, 3))
+                ms = _cuda_ms(f, steps, min(args.warmup, 3) if dt == "f64" else args.warmup)
+                row[f"{dt}_ms"] = ms
+                row[f"{dt}_tflops"] = flops / ms / 1e9
+                if dt == "f64_emu":
+                    row["f64_emu_product_ms"] = _product_ms(f, 3)
+                    # unfused: B = T A^T materialised, then C := C - A B on all of C
+                    B = torch.zeros(k, n, device="cuda", dtype=tdt)
+
+                    def unfused():
+                        B.zero_()
+                        B[1:] += sub[:, None] * A.t()[:-1]
+                        B[:-1] -= sub[:, None] * A.t()[1:]
+                        fm.contract(-1.0, A, [1, 3], B, [3, 2], 1.0, C, [1, 2], dtype="f64_emu")
+                    ms_u = _cuda_ms(unfused, args.steps, args.warmup)
+                    row["unfused_full_square_f64_emu_ms"] = ms_u
+            print(json.dumps(row), flush=True)
     elif args.workload == "autograd":
         from paper_2604_07311_b300.autograd import contract_autograd
         d = W.autograd_problem()
@@ -536,7 +569,8 @@ def run_other(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="ladder",
-                    choices=["ladder", "transpose_free", "block_sparse", "autograd", "network", "ladder_sym"],
+                    choices=["ladder", "transpose_free", "block_sparse", "autograd", "network", "ladder_sym",
+                             "gemmt"],
                     help="ladder is the benchmark line; the others print secondary measurements")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)

@@ -287,6 +287,30 @@ FAMLIES_API int famlies_contract_sym(double alpha, const famlies_symtensor_t* A,
                                      const famlies_tensor_t* C, famlies_dtype_t dtype, void* stream,
                                      const famlies_options_t* opt, famlies_plan_info_t* info);
 
+/* Sandwiched product with a tridiagonal middle factor (Sec. 3, "Beyond
+ * LAPACK functionality": the update C := C - A T A^T of skew-symmetric
+ * factorisations, a GEMMT that updates one triangle of C, with T A^T formed
+ * while the operand is packed instead of in a workspace):
+ *   C[i,j] := beta * C[i,j] + alpha * sum_{p,q} A[i,p] T[p,q] A[j,q]
+ * for i >= j only; the strictly upper triangle of C is neither read nor
+ * written.  A is n x k, element (i,p) at A[i*rs_a + p*cs_a]; C is n x n,
+ * element (i,j) at C[i*rs_c + j*cs_c] (strides in elements, >= 0).
+ * T is k x k tridiagonal, given by device vectors:
+ *   T[p+1,p] = t_sub[p] (k-1 entries), T[p,p] = t_diag[p] (k entries),
+ *   T[p,p+1] = t_sup[p] (k-1 entries);
+ * t_diag == NULL means a zero diagonal, t_sup == NULL means t_sup = -t_sub
+ * (T skew-symmetric).  Only the three diagonals are multiplied (a banded
+ * T: no 0 * Inf from entries off the band).  dtype: FAMLIES_F64 (native
+ * CUDA cores), FAMLIES_F64_EMU or FAMLIES_F32 (tensor cores); A, C and the
+ * vectors hold the dtype's elements (fp64 or fp32); BF16 returns
+ * FAMLIES_ERR_UNSUPPORTED.  Error codes, options (kernel choice fixed by the
+ * dtype) and info as for famlies_contract_ex; C must not overlap A. */
+FAMLIES_API int famlies_gemmt_tridiag(int64_t n, int64_t k, double alpha, const void* A, int64_t rs_a,
+                                      int64_t cs_a, const void* t_sub, const void* t_diag,
+                                      const void* t_sup, double beta, void* C, int64_t rs_c,
+                                      int64_t cs_c, famlies_dtype_t dtype, void* stream,
+                                      const famlies_options_t* opt, famlies_plan_info_t* info);
+
 /* Contraction networks: a pre-ordered sequence of tensor contractions run
  * through the same planner and kernels (Sec. 3, Girder 5, tensor contraction
  * networks).  `tensors` lists every tensor of the network; step i computes

@@ -10,7 +10,7 @@ from __future__ import annotations
 from ._lib import (BF16, DTYPES, F32, F64, F64_EMU, KERNELS, Desc, FamliesError, PlanInfo,
                    desc_numpy, desc_torch, load, options, check, error_string)
 
-__all__ = ["contract", "contract_host", "contract_batched", "contract_network", "contract_sym", "plan", "device_status",
+__all__ = ["contract", "contract_host", "contract_batched", "contract_network", "contract_sym", "gemmt_tridiag", "plan", "device_status",
            "FamliesError", "F64", "F64_EMU", "F32", "BF16", "lib_path", "Contract", "contract_autograd"]
 
 
@@ -161,6 +161,37 @@ def contract_sym(alpha, Ap, extents, la, B, lb, beta, C, lc, dtype="f64_emu", st
     opt = options(slices, 0, 0, wait_limit, events)
     check(lib.famlies_contract_sym(float(alpha), ctypes.byref(sa), db.ref, float(beta), dc.ref, code,
                                    _stream_handle(stream), opt, info))
+    return (C, info.as_dict()) if return_info else C
+
+
+def gemmt_tridiag(alpha, A, t_sub, t_diag, t_sup, beta, C, dtype=None, stream=None, *, slices=0,
+                  wait_limit=0, events=None, return_info=False):
+    """C := beta * C + alpha * A T A^T on the lower triangle of C (i >= j).
+
+    A: (n, k) CUDA tensor, C: (n, n), any non-negative strides.  T is k x k
+    tridiagonal: t_sub (k-1), t_diag (k) and t_sup (k-1) are contiguous 1-D
+    CUDA tensors of A's dtype, or None (t_diag None: zero diagonal; t_sup
+    None: t_sup = -t_sub, T skew-symmetric).  dtype 'f64', 'f64_emu' or
+    'f32' (None: from A).  The strictly upper triangle of C is untouched.
+    """
+    lib = load()
+    code = _dtype_code(dtype, A, C)
+    if A.dim() != 2 or C.dim() != 2 or C.shape[0] != C.shape[1] or C.shape[0] != A.shape[0]:
+        raise ValueError("A must be (n, k) and C (n, n)")
+
+    def vec(v, length):
+        if v is None:
+            return None
+        if v.dim() != 1 or v.numel() < length or (v.numel() > 1 and v.stride(0) != 1):
+            raise ValueError("band vectors must be contiguous 1-D tensors of the right length")
+        return v.data_ptr()
+    n, k = A.shape
+    info = PlanInfo()
+    opt = options(slices, 0, 0, wait_limit, events)
+    check(lib.famlies_gemmt_tridiag(int(n), int(k), float(alpha), A.data_ptr(), A.stride(0), A.stride(1),
+                                    vec(t_sub, k - 1), vec(t_diag, k), vec(t_sup, k - 1), float(beta),
+                                    C.data_ptr(), C.stride(0), C.stride(1), code, _stream_handle(stream),
+                                    opt, info))
     return (C, info.as_dict()) if return_info else C
 
 

@@ -98,12 +98,15 @@ def load(path: str | None = None):
                                     vp, ctypes.POINTER(Options)]
     lib.famlies_contract_sym.argtypes = [d, ctypes.POINTER(SymTensorDesc), T, d, T, ctypes.c_int, vp,
                                          ctypes.POINTER(Options), ctypes.POINTER(PlanInfo)]
+    i64 = ctypes.c_int64
+    lib.famlies_gemmt_tridiag.argtypes = [i64, i64, d, vp, i64, i64, vp, vp, vp, d, vp, i64, i64, ctypes.c_int,
+                                          vp, ctypes.POINTER(Options), ctypes.POINTER(PlanInfo)]
     lib.famlies_error_string.argtypes = [ctypes.c_int]
     lib.famlies_error_string.restype = ctypes.c_char_p
     lib.famlies_device_status.argtypes = [vp]
     for f in ("famlies_contract", "famlies_contract_ex", "famlies_contract_host",
               "famlies_contract_batched", "famlies_plan", "famlies_device_status", "famlies_version",
-              "famlies_network", "famlies_contract_sym"):
+              "famlies_network", "famlies_contract_sym", "famlies_gemmt_tridiag"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib

@@ -123,6 +123,9 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
     g.stall_test = opt ? opt->stall_test : 0;
     g.sym_n = p.sym_n;
     g.sym_side = p.sym_side;
+    g.band = p.band;
+    g.band_op = p.band_side + 1;
+    g.tri = p.tri;
     g.ev_begin = opt ? (cudaEvent_t)opt->events[0] : nullptr;
     g.ev_end = opt ? (cudaEvent_t)opt->events[1] : nullptr;
     switch (p.kernel) {
@@ -251,6 +254,44 @@ int famlies_contract_sym(double alpha, const famlies_symtensor_t* A, const famli
   else p.b = A->data;
   p.sym_n = n;
   p.sym_side = side;
+  return run_plan(p, alpha, beta, (cudaStream_t)stream, &o, info);
+}
+
+int famlies_gemmt_tridiag(int64_t n, int64_t k, double alpha, const void* A, int64_t rs_a,
+                          int64_t cs_a, const void* t_sub, const void* t_diag, const void* t_sup,
+                          double beta, void* C, int64_t rs_c, int64_t cs_c, famlies_dtype_t dtype,
+                          void* stream, const famlies_options_t* opt, famlies_plan_info_t* info) {
+  if (n < 0 || k < 0 || rs_a < 0 || cs_a < 0 || rs_c < 0 || cs_c < 0) return FAMLIES_ERR_INVALID_ARG;
+  if (dtype != FAMLIES_F64 && dtype != FAMLIES_F64_EMU && dtype != FAMLIES_F32)
+    return FAMLIES_ERR_UNSUPPORTED;
+  if (k > 1 && !t_sub) return FAMLIES_ERR_INVALID_ARG;
+  // The operation as a contraction C[i,j] = A[i,p] B[p,j] whose column
+  // operand B is A^T with the band applied along p: both operands read A.
+  const int64_t ea[2] = {n, k}, sa[2] = {rs_a, cs_a};
+  const int64_t eb[2] = {k, n}, sb[2] = {cs_a, rs_a};
+  const int64_t ec[2] = {n, n}, scs[2] = {rs_c, cs_c};
+  const int32_t la[2] = {1, 3}, lb[2] = {3, 2}, lc[2] = {1, 2};
+  famlies_tensor_t ta = {2, ea, sa, la, const_cast<void*>(A), 0};
+  famlies_tensor_t tb = {2, eb, sb, lb, const_cast<void*>(A), 0};
+  famlies_tensor_t tc = {2, ec, scs, lc, C, 0};
+  famlies_options_t o = {};
+  if (opt) o = *opt;
+  o.kernel = dtype == FAMLIES_F64 ? 1 : 2;  // CUDA cores / packed tensor cores
+  Plan p;
+  int rc = make_plan(alpha, &ta, &tb, &tc, dtype, &o, &p);
+  if (rc) return rc;
+  // kernel indices: rows are C's i unless the planner put C's unit stride
+  // (then j) on the rows
+  p.tri = p.swapped ? 2 : 1;
+  if (p.kernel != FAMLIES_KERNEL_NONE && p.kernel != FAMLIES_KERNEL_SCALE) {
+    if (p.kernel != FAMLIES_KERNEL_SIMT_F64 && p.kernel != FAMLIES_KERNEL_TC_EMU &&
+        p.kernel != FAMLIES_KERNEL_TC_TF32X3)
+      return FAMLIES_ERR_UNSUPPORTED;
+    p.band_side = p.swapped ? 0 : 1;
+    p.band.sub = t_sub;
+    p.band.diag = t_diag;
+    p.band.sup = t_sup;
+  }
   return run_plan(p, alpha, beta, (cudaStream_t)stream, &o, info);
 }
 

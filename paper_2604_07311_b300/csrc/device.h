@@ -38,6 +38,9 @@ struct GemmArgs {
   int stall_test;          // testing: product kernels first wait on a barrier nothing completes
   int64_t sym_n;           // > 0: operand sym_side is a packed symmetric matrix (see Plan)
   int sym_side;
+  Band band;               // tridiagonal factor (see Plan) of operand band_op - 1 (0: none)
+  int band_op;
+  int tri;                 // 0: all of C; 1: only row >= col; 2: only row <= col
   cudaEvent_t ev_begin, ev_end;  // host only: recorded around the product kernel
 };
 
@@ -82,6 +85,32 @@ int64_t packed_workspace_bytes(const Plan& p);
 cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream_t s);
 // Kernel launches launch_packed makes for plan p.
 int packed_launches(const Plan& p);
+
+// Whether C's element (row r, column c) of the kernel's indices is updated
+// under triangle mode tri (see Plan::tri).
+__host__ __device__ __forceinline__ bool tri_keep(int tri, int64_t r, int64_t c) {
+  return tri == 0 || (tri == 1 ? r >= c : r <= c);
+}
+
+// Element p of a banded operand row (see Band): x is the source, base the
+// row's offset, its k offsets koff[q] (koff null: q * ks).  One fixed order
+// of operations, so that every kernel computing it gets the same value.
+template <class T>
+__device__ __forceinline__ T band_at(const T* __restrict__ x, int64_t base, const int64_t* koff,
+                                     int64_t ks, int64_t p, int64_t k, const Band& b) {
+  const T* s = (const T*)b.sub;
+  const T* d = (const T*)b.diag;
+  const T* u = (const T*)b.sup;
+  auto at = [&](int64_t q) { return x[base + (koff ? koff[q] : q * ks)]; };
+  auto fm = [](T a, T b, T c) {
+    if constexpr (sizeof(T) == 4) return fmaf(a, b, c);
+    else return fma(a, b, c);
+  };
+  T v = d ? d[p] * at(p) : T(0);
+  if (p > 0) v = fm(s[p - 1], at(p - 1), v);
+  if (p + 1 < k) v = fm(u ? u[p] : -s[p], at(p + 1), v);
+  return v;
+}
 
 // Number of int64 entries the offset tables of a plan need.
 inline int64_t table_entries(const Plan& p) {

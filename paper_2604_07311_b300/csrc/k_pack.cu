@@ -564,6 +564,69 @@ __device__ __forceinline__ void pack_pipeline(int64_t g0, int64_t gstep, int64_t
   }
 }
 
+// ------------------------------------------------------------ banded operand
+// Row exponents of a banded operand (fp64 split).  Item: 64 rows x KCH k;
+// thread (r, g) takes row r and k = k0 + g, k0 + g + 4, ..., so that a
+// warp's loads run along rows (the unit-stride index of a column-major
+// source) and the three neighbours each value reads come from L1.
+__device__ __forceinline__ void rowexp_band_body(const PackArgs& pa, const PackOp& o) {
+  const double* __restrict__ X = (const double*)o.x;
+  const int64_t tiles_r = (o.rows + PR - 1) / PR, tiles_k = (pa.k + KCH - 1) / KCH;
+  const int64_t items = tiles_r * tiles_k;
+  __shared__ int smx[4][PR], sbad[4][PR];
+  const int r = threadIdx.x % PR, g = threadIdx.x / PR;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int64_t tr = it % tiles_r, tk = it / tiles_r;
+    const int64_t row = tr * PR + r;
+    const int64_t k0 = tk * KCH, k1 = min(pa.k, k0 + KCH);
+    int mx = -1100, bad = 0;
+    if (row < o.rows)
+      for (int64_t p = k0 + g; p < k1; p += 4)
+        exp_update(band_at<double>(X, row * o.rs, nullptr, o.ks, p, pa.k, o.band), mx, bad);
+    smx[g][r] = mx;
+    sbad[g][r] = bad;
+    __syncthreads();
+    if (threadIdx.x < PR) {
+      const int t = threadIdx.x;
+      const int64_t rr = tr * PR + t;
+      const int m = max(max(smx[0][t], smx[1][t]), max(smx[2][t], smx[3][t]));
+      const int bd = sbad[0][t] | sbad[1][t] | sbad[2][t] | sbad[3][t];
+      if (rr < o.rows && m > -1100) atomicMax(&o.e[rr], m);
+      if (rr < o.rows && bd) mark_row(o, rr);
+    }
+    __syncthreads();
+  }
+}
+
+// Slices of a banded operand: each 64 x 64 tile's band values are computed
+// into shared memory (row r, k = kk; the same arithmetic as the exponent
+// pass) and emitted like any staged tile.
+template <int PMODE>
+__device__ __forceinline__ void pack_band_body(const PackArgs& pa, const PackOp& o) {
+  using T = typename PackT<PMODE>::T;
+  extern __shared__ __align__(16) unsigned char pack_smem[];
+  T* const buf = (T*)pack_smem;
+  const T* __restrict__ X = (const T*)o.x;
+  const int64_t tiles_r = (o.rows + PR - 1) / PR, tiles_k = (pa.k + PK - 1) / PK;
+  const int64_t items = tiles_r * tiles_k;
+  const int r = threadIdx.x % PR;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int64_t tr = it % tiles_r, tk = it / tiles_r;
+    const int64_t row = tr * PR + r;
+#pragma unroll 4
+    for (int i = 0; i < PER_THREAD; ++i) {
+      const int kk = threadIdx.x / PR + i * (256 / PR);
+      const int64_t p = tk * PK + kk;
+      buf[r * TLD + kk] =
+          (row < o.rows && p < pa.k) ? band_at<T>(X, row * o.rs, nullptr, o.ks, p, pa.k, o.band) : T(0);
+    }
+    __syncthreads();
+    // tile number as emit_tile decodes it: row tile + tiles_r * k tile
+    emit_tile<PMODE>(PackTile{&pa, &o, it}, buf);
+    __syncthreads();
+  }
+}
+
 __device__ __forceinline__ void fixup_body(const GemmArgs& g, const int32_t* __restrict__ list_a,
                                            const int32_t* __restrict__ list_b,
                                            const int32_t* __restrict__ flag_a) {
@@ -589,9 +652,16 @@ __device__ __forceinline__ void fixup_body(const GemmArgs& g, const int32_t* __r
       m = j % g.m;
       if (flag_a[il * g.m + m]) continue;  // done by the row pass
     }
+    if (!tri_keep(g.tri, m, n)) continue;  // outside the updated triangle
     const int64_t ab = g.t.al[il] + g.t.am[m], bb = g.t.bl[il] + g.t.bn[n];
     double acc = 0.0;
-    if (g.sym_n > 0) {
+    if (g.band_op) {
+      for (int64_t k = 0; k < g.k; ++k) {
+        const double va = g.band_op == 1 ? band_at<double>(A, ab, g.t.ak, 0, k, g.k, g.band) : A[ab + g.t.ak[k]];
+        const double vb = g.band_op == 2 ? band_at<double>(B, bb, g.t.bk, 0, k, g.k, g.band) : B[bb + g.t.bk[k]];
+        acc = fma(va, vb, acc);
+      }
+    } else if (g.sym_n > 0) {
       // the tables hold offsets p + n q of the dense symmetric matrix
       const int64_t sn = g.sym_n;
       for (int64_t k = 0; k < g.k; ++k) {
@@ -629,6 +699,15 @@ __global__ void __launch_bounds__(256, 3) k_pack(const __grid_constant__ PackArg
 
 __global__ void __launch_bounds__(256) k_rowexp_sym(const __grid_constant__ PackArgs pa, int side) {
   rowexp_sym_body(pa.op[side]);
+}
+
+__global__ void __launch_bounds__(256) k_rowexp_band(const __grid_constant__ PackArgs pa, int side) {
+  rowexp_band_body(pa, pa.op[side]);
+}
+
+template <int PMODE>
+__global__ void __launch_bounds__(256) k_pack_band(const __grid_constant__ PackArgs pa, int side) {
+  pack_band_body<PMODE>(pa, pa.op[side]);
 }
 
 __global__ void __launch_bounds__(256, 3) k_pack_sym(const __grid_constant__ PackArgs pa, int side) {
@@ -799,6 +878,25 @@ cudaError_t launch_pack_sym(const PackArgs& pa, int side, cudaStream_t s) {
   const int64_t nblk = sym_blocks(pa.op[side]);
   if (nblk <= 0) return cudaSuccess;
   k_pack_sym<<<grid_for(nblk), 256, pack_smem_bytes<PACK_F64>(), s>>>(pa, side);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rowexp_band(const PackArgs& pa, int side, cudaStream_t s) {
+  const PackOp& o = pa.op[side];
+  const int64_t items = ((o.rows + PR - 1) / PR) * ((pa.k + KCH - 1) / KCH);
+  if (items <= 0) return cudaSuccess;
+  k_rowexp_band<<<grid_for(items), 256, 0, s>>>(pa, side);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_band(int pmode, const PackArgs& pa, int side, cudaStream_t s) {
+  const PackOp& o = pa.op[side];
+  const int64_t items = ((o.rows + PR - 1) / PR) * ((pa.k + PK - 1) / PK);
+  if (items <= 0) return cudaSuccess;
+  if (pmode == PACK_TF32)
+    k_pack_band<PACK_TF32><<<grid_for(items), 256, PR * TLD * sizeof(float), s>>>(pa, side);
+  else
+    k_pack_band<PACK_F64><<<grid_for(items), 256, PR * TLD * sizeof(double), s>>>(pa, side);
   return cudaGetLastError();
 }
 

@@ -114,11 +114,32 @@ struct TileRef {
   int kb_lo, kb_hi;
 };
 
+// Output tiles of a single problem: the whole grid of bn-wide tiles, or
+// those of its triangle list; and the coordinates of tile number `tile`
+// (column tiles fastest, then row tiles, then the batch).
+__host__ __device__ __forceinline__ int64_t prob_tiles(const Prob& P, int bn) {
+  return P.tri_list ? P.tri_tiles : ((P.m + BM - 1) / BM) * ((P.n + bn - 1) / bn) * P.l;
+}
+__device__ __forceinline__ void tile_coords(const Prob& P, int bn, int64_t tile, int64_t& tm, int64_t& tn,
+                                            int64_t& il) {
+  if (P.tri_list) {
+    const int2 e = P.tri_list[tile];
+    tm = e.x;
+    tn = e.y;
+    il = 0;
+    return;
+  }
+  const int64_t tiles_m = (P.m + BM - 1) / BM, tiles_n = (P.n + bn - 1) / bn;
+  tn = tile % tiles_n;
+  const int64_t rest = tile / tiles_n;
+  tm = rest % tiles_m;
+  il = rest / tiles_m;
+}
+
 template <int BN, bool GROUPED, bool SPLITK>
 __device__ __forceinline__ int64_t tile_count(const PairArgs& a) {
   if (GROUPED) return a.ntiles;
-  const Prob& P = a.single;
-  const int64_t ntile = ((P.m + BM - 1) / BM) * ((P.n + BN - 1) / BN) * P.l;
+  const int64_t ntile = prob_tiles(a.single, BN);
   return SPLITK ? a.full + (ntile - a.full) * a.splits : ntile;
 }
 
@@ -137,12 +158,11 @@ __device__ __forceinline__ TileRef tile_at(const PairArgs& a, int64_t t) {
     return TileRef{P, e.tm, e.tn, e.il, 0, -1, 0, (int)((P->k + KB - 1) / KB)};
   }
   const Prob& P = a.single;
-  const int64_t tiles_m = (P.m + BM - 1) / BM, tiles_n = (P.n + BN - 1) / BN;
   const int nkb = (int)((P.k + KB - 1) / KB);
   int64_t tile = t;
   int split = -1, lo = 0, hi = nkb;
   if (SPLITK && t >= a.full) {
-    const int64_t tail = tiles_m * tiles_n * P.l - a.full, u = t - a.full;
+    const int64_t tail = prob_tiles(P, BN) - a.full, u = t - a.full;
     tile = a.full + u % tail;
     split = (int)(u / tail);
     const int kcb = a.sc.ndiag > 1 ? 1 : a.sc.kcb[0];
@@ -151,8 +171,9 @@ __device__ __forceinline__ TileRef tile_at(const PairArgs& a, int64_t t) {
     hi = (int)(units * (split + 1) / a.splits) * kcb;
     hi = hi < nkb ? hi : nkb;
   }
-  const int64_t tn = tile % tiles_n, rest = tile / tiles_n;
-  return TileRef{&a.single, rest % tiles_m, tn, rest / tiles_m, tile, split, lo, hi};
+  int64_t tm, tn, il;
+  tile_coords(P, BN, tile, tm, tn, il);
+  return TileRef{&a.single, tm, tn, il, tile, split, lo, hi};
 }
 
 // The end of an fp64-split tile: C = alpha * 2^(e_m + e_n - xunit) * X + beta
@@ -179,7 +200,7 @@ __device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, int x
 #pragma unroll
     for (int j = 0; j < FG; ++j) {
       const int64_t col = col0 + j0 + j;
-      use[j] = lc0 + j0 + j < bnp && col < P.n;
+      use[j] = lc0 + j0 + j < bnp && col < P.n && tri_keep(P.tri, row, col);
       ecol[j] = use[j] ? ebl[col] : 0;
       coff[j] = use[j] ? P.cn[col] : 0;
       use[j] = use[j] && !fbl[col];
@@ -412,7 +433,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (SPLITK && T.split >= 0) {
           // a split of a tail tile: its partial tile, reduced (with alpha,
           // beta) by k_split_reduce
-          const int64_t tail = ((P.m + BM - 1) / BM) * ((P.n + BN - 1) / BN) * P.l - args.full;
+          const int64_t tail = prob_tiles(P, BN) - args.full;
           float* Pt = args.part + ((size_t)T.split * (size_t)tail + (size_t)(T.tile - args.full)) * BM * BN +
                       (size_t)lc0 * BM + qd * 32 + lane;
 #pragma unroll
@@ -423,7 +444,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int j = 0; j < CPT; ++j) {
             const int64_t col = col0 + j;
-            if (lc0 + j < bnp && col < P.n) {
+            if (lc0 + j < bnp && col < P.n && tri_keep(P.tri, row, col)) {
               float* p = C + crow + P.cn[col];
               float v = alpha * S[j];
               if (beta != 0.f) v = fmaf(beta, *p, v);
@@ -511,9 +532,8 @@ constexpr int SPLIT_PER_THREAD = SPLIT_COLS / (256 / BM);
 // + beta * C.
 __global__ void __launch_bounds__(256) k_split_reduce(const float* __restrict__ part, int splits,
                                                      int64_t full, int bn, Prob P) {
-  const int64_t tiles_m = (P.m + BM - 1) / BM, tiles_n = (P.n + bn - 1) / bn;
   const int chunks = bn / SPLIT_COLS;
-  const int64_t tail = tiles_m * tiles_n * P.l - full, items = tail * chunks;
+  const int64_t tail = prob_tiles(P, bn) - full, items = tail * chunks;
   const size_t per = (size_t)BM * bn, total = (size_t)tail * per;
   float* C = (float*)P.c;
   const float alpha = (float)P.alpha, beta = (float)P.beta;
@@ -521,8 +541,8 @@ __global__ void __launch_bounds__(256) k_split_reduce(const float* __restrict__ 
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
     const int64_t ti = it / chunks, tile = full + ti;  // ti: index among the tail tiles
     const int c0 = (int)(it % chunks) * SPLIT_COLS;
-    const int64_t tn = tile % tiles_n, rest = tile / tiles_n;
-    const int64_t tm = rest % tiles_m, il = rest / tiles_m;
+    int64_t tm, tn, il;
+    tile_coords(P, bn, tile, tm, tn, il);
     const int64_t row = tm * BM + lr;
     if (row >= P.m) continue;
     const int64_t crow = P.cl[il] + P.cm[row];
@@ -532,7 +552,7 @@ __global__ void __launch_bounds__(256) k_split_reduce(const float* __restrict__ 
     for (int j = 0; j < SPLIT_PER_THREAD; ++j) {
       const int lc = c0 + lq + j * (256 / BM);
       const int64_t col = tn * bn + lc;
-      off[j] = col < P.n ? crow + P.cn[col] : -1;
+      off[j] = col < P.n && tri_keep(P.tri, row, col) ? crow + P.cn[col] : -1;
       const size_t at = (size_t)ti * per + (size_t)lc * BM + lr;
       float acc = 0.f;
       for (int sp = 0; sp < splits; ++sp) acc += part[(size_t)sp * total + at];
@@ -554,17 +574,16 @@ __global__ void __launch_bounds__(256) k_split_reduce(const float* __restrict__ 
 // holding Inf/NaN are left to the native fix-up).
 __global__ void __launch_bounds__(256) k_split_finish(const int64_t* __restrict__ X, int64_t full,
                                                      int bn, int xunit, Prob P) {
-  const int64_t tiles_m = (P.m + BM - 1) / BM, tiles_n = (P.n + bn - 1) / bn;
   const int chunks = bn / SPLIT_COLS;
-  const int64_t items = (tiles_m * tiles_n * P.l - full) * chunks;
+  const int64_t items = (prob_tiles(P, bn) - full) * chunks;
   const size_t per = (size_t)BM * bn;
   double* C = (double*)P.c;
   const int lr = threadIdx.x % BM, lq = threadIdx.x / BM;
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
     const int64_t ti = it / chunks, tile = full + ti;  // ti: index among the tail tiles
     const int c0 = (int)(it % chunks) * SPLIT_COLS;
-    const int64_t tn = tile % tiles_n, rest = tile / tiles_n;
-    const int64_t tm = rest % tiles_m, il = rest / tiles_m;
+    int64_t tm, tn, il;
+    tile_coords(P, bn, tile, tm, tn, il);
     const int64_t row = tm * BM + lr;
     if (row >= P.m || P.fa[il * P.m + row]) continue;
     const int64_t crow = P.cl[il] + P.cm[row];
@@ -576,7 +595,7 @@ __global__ void __launch_bounds__(256) k_split_finish(const int64_t* __restrict_
     for (int j = 0; j < SPLIT_PER_THREAD; ++j) {
       const int lc = c0 + lq + j * (256 / BM);
       const int64_t col = tn * bn + lc;
-      const bool ok = col < P.n && !P.fb[il * P.n + col];
+      const bool ok = col < P.n && !P.fb[il * P.n + col] && tri_keep(P.tri, row, col);
       off[j] = ok ? crow + P.cn[col] : -1;
       ec[j] = ok ? P.eb[il * P.n + col] : 0;
       x[j] = X[(size_t)ti * per + (size_t)lc * BM + lr];
@@ -597,6 +616,53 @@ __global__ void __launch_bounds__(256) k_split_finish(const int64_t* __restrict_
       if (off[j] >= 0) C[off[j]] = v;
     }
   }
+}
+
+// The tiles of a triangle of C (tri 1: row >= col, 2: row <= col): row tile
+// tm meets it in the column tiles [lo, hi).
+__host__ __device__ __forceinline__ void tri_run(int tri, int64_t tm, int bn, int64_t tiles_n, int64_t& lo,
+                                                 int64_t& hi) {
+  if (tri == 1) {
+    lo = 0;
+    hi = (tm * BM + BM - 1) / bn + 1;
+    hi = hi < tiles_n ? hi : tiles_n;
+  } else {
+    lo = tm * BM / bn;
+    lo = lo < tiles_n ? lo : tiles_n;
+    hi = tiles_n;
+  }
+}
+
+// Writes the triangle's tile list, row tile by row tile (column tiles
+// fastest, so the CTAs running together share row tiles through L2):
+// thread tm writes its row tile's run after the earlier runs.
+__global__ void __launch_bounds__(256) k_tri_tiles(int tri, int64_t tiles_m, int64_t tiles_n, int bn,
+                                                  int2* __restrict__ out) {
+  for (int64_t tm = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tm < tiles_m;
+       tm += (int64_t)gridDim.x * blockDim.x) {
+    int64_t off = 0, lo, hi;
+    for (int64_t t = 0; t < tm; ++t) {
+      tri_run(tri, t, bn, tiles_n, lo, hi);
+      off += hi - lo;
+    }
+    tri_run(tri, tm, bn, tiles_n, lo, hi);
+    for (int64_t tn = lo; tn < hi; ++tn) out[off++] = make_int2((int)tm, (int)tn);
+  }
+}
+
+int64_t tri_tile_count(const Plan& p, int bn) {
+  const int64_t tiles_m = (p.m + BM - 1) / BM, tiles_n = (p.n + bn - 1) / bn;
+  int64_t n = 0, lo, hi;
+  for (int64_t tm = 0; tm < tiles_m; ++tm) {
+    tri_run(p.tri, tm, bn, tiles_n, lo, hi);
+    n += hi - lo;
+  }
+  return n;
+}
+
+// Output tiles the product of plan p runs (host side of prob_tiles).
+int64_t plan_tiles(const Plan& p, int bn) {
+  return p.tri ? tri_tile_count(p, bn) : ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l;
 }
 
 // ----------------------------------------------------------------- launch
@@ -640,7 +706,7 @@ struct SplitPlan {
 };
 
 SplitPlan split_plan(const Plan& p, int bn) {
-  const int64_t tiles = ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) * p.l;
+  const int64_t tiles = plan_tiles(p, bn);
   const int64_t sms = num_sms();
   const bool emu = p.kernel == FAMLIES_KERNEL_TC_EMU;
   const int kind = p.kernel == FAMLIES_KERNEL_TC_TF32X3 ? PAIR_KIND_TF32 : PAIR_KIND_BF16;
@@ -682,7 +748,7 @@ int grid_of(const Plan& p, int bn) {
 }
 
 struct Layout {
-  size_t a, b, ea, eb, fa, fb, la, lb, G, xtail, part, total;
+  size_t a, b, ea, eb, fa, fb, la, lb, G, xtail, part, tri, total;
 };
 
 Layout layout_of(const Plan& p) {
@@ -714,6 +780,10 @@ Layout layout_of(const Plan& p) {
     if (sp.splits > 1) {
       L.part = off; off += up((size_t)sp.splits * sp.tail * BM * bn * 4);
     }
+  }
+  if (p.tri) {
+    L.tri = off;
+    off += up((size_t)tri_tile_count(p, pair_bn_for(p.n, p.tile_n)) * sizeof(int2));
   }
   L.total = off;
   return L;
@@ -905,14 +975,16 @@ cudaError_t launch_pair_grouped(int kind, int mode, int bn, const Prob* probs,
 int64_t packed_workspace_bytes(const Plan& p) { return (int64_t)layout_of(p).total; }
 
 int packed_launches(const Plan& p) {
+  const int tri = p.tri ? 1 : 0;  // the triangle's tile list
   if (p.kernel == FAMLIES_KERNEL_TC_EMU)  // exponents + pack + product (+ split finish) + fix-up
-    return 4 + (split_count(p, pair_bn_for(p.n, p.tile_n)) > 1 ? 1 : 0) +
-           (p.sym_n > 0 ? 2 : 0);  // (+ the symmetric operand's exponents and pack)
+    return 4 + (split_count(p, pair_bn_for(p.n, p.tile_n)) > 1 ? 1 : 0) + tri +
+           (p.sym_n > 0 || p.band_side >= 0 ? 2 : 0);  // (+ the symmetric or banded operand's own)
   DirectView v;
   const bool tf32 = p.kernel == FAMLIES_KERNEL_TC_TF32X3;
   const bool da = !tf32 && direct_view(p.M, p.K, p.L, 0, p.a, &v);
   const bool db = !tf32 && direct_view(p.N, p.K, p.L, 1, p.b, &v);
-  return ((da && db) ? 0 : 1) + 1 + (split_count(p, pair_bn_for(p.n, p.tile_n)) > 1 ? 1 : 0);
+  return ((da && db) ? 0 : 1) + 1 + (split_count(p, pair_bn_for(p.n, p.tile_n)) > 1 ? 1 : 0) + tri +
+         (p.band_side >= 0 ? 1 : 0);
 }
 
 cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream_t s) {
@@ -934,6 +1006,14 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   set_affine(pa.op[1], p.N, p.K, 1);
   const bool sym = p.sym_n > 0;
   if (sym) pa.op[p.sym_side].sym_n = p.sym_n;
+  const bool band = p.band_side >= 0;
+  if (band) {
+    PackOp& o = pa.op[p.band_side];
+    if (o.affine != 3 || p.l != 1) return cudaErrorNotSupported;
+    o.banded = 1;
+    o.band = p.band;
+  }
+  const int own = sym ? p.sym_side : (band ? p.band_side : -1);  // packed by its own kernels
   cudaError_t e;
   if (emu) {
     pa.op[0].e = (int32_t*)(w + L.ea);
@@ -945,10 +1025,11 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     // exponents start at a large negative value, flags and list counts at 0
     if ((e = cudaMemsetAsync(w + L.ea, 0x80, L.fa - L.ea, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w + L.fa, 0, L.G - L.fa, s)) != cudaSuccess) return e;
-    PackArgs pg = pa;  // the generic kernels skip a symmetric operand
-    if (sym) pg.op[p.sym_side].rows = 0;
+    PackArgs pg = pa;  // the generic kernels skip a symmetric or banded operand
+    if (own >= 0) pg.op[own].rows = 0;
     if ((e = launch_rowexp(pg, s)) != cudaSuccess) return e;
     if (sym && (e = launch_rowexp_sym(pa, p.sym_side, s)) != cudaSuccess) return e;
+    if (band && (e = launch_rowexp_band(pa, p.band_side, s)) != cudaSuccess) return e;
   }
   const int bn = pair_bn_for(p.n, p.tile_n);
   const int S = pa.slices;
@@ -959,16 +1040,18 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   // rows and batches) are read by TMA straight from the caller's tensor;
   // only the others are packed.
   DirectView va, vb;
-  const bool da = !emu && !tf32 && direct_view(p.M, p.K, p.L, 0, p.a, &va);
-  const bool db = !emu && !tf32 && direct_view(p.N, p.K, p.L, 1, p.b, &vb);
+  const bool da = !emu && !tf32 && !band && direct_view(p.M, p.K, p.L, 0, p.a, &va);
+  const bool db = !emu && !tf32 && !band && direct_view(p.N, p.K, p.L, 1, p.b, &vb);
   if (da) pa.op[0].rows = 0;  // nothing to pack
   if (db) pa.op[1].rows = 0;
   if (!da || !db) {
     PackArgs pg = pa;
-    if (sym) pg.op[p.sym_side].rows = 0;
+    if (own >= 0) pg.op[own].rows = 0;
     if ((e = launch_pack(emu ? PACK_F64 : (tf32 ? PACK_TF32 : PACK_BF16), pg, s)) != cudaSuccess)
       return e;
     if (sym && (e = launch_pack_sym(pa, p.sym_side, s)) != cudaSuccess) return e;
+    if (band && (e = launch_pack_band(emu ? PACK_F64 : PACK_TF32, pa, p.band_side, s)) != cudaSuccess)
+      return e;
   }
   const bool ok_a = da ? make_view_map(&ma, va, p.k, p.m, p.l, kbk, BM)
                        : make_slice_map(&ma, w + L.a, tf32, p.k, kp, p.m, (int64_t)S * p.l, kbk, BM);
@@ -979,6 +1062,17 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   std::memset(&a, 0, sizeof(a));
   a.single = Prob{nullptr, nullptr, g.c, g.t.cm, g.t.cn, g.t.cl, pa.op[0].e, pa.op[1].e,
                   pa.op[0].flag, pa.op[1].flag, p.m, p.n, p.k, p.l, g.alpha, g.beta, bn};
+  if (p.tri) {
+    if (p.l != 1) return cudaErrorNotSupported;
+    const int64_t tiles_m = (p.m + BM - 1) / BM, tiles_n = (p.n + bn - 1) / bn;
+    int2* list = (int2*)(w + L.tri);
+    k_tri_tiles<<<(int)std::min<int64_t>((tiles_m + 255) / 256, 1024), 256, 0, s>>>(p.tri, tiles_m, tiles_n,
+                                                                                   bn, list);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    a.single.tri = p.tri;
+    a.single.tri_list = list;
+    a.single.tri_tiles = tri_tile_count(p, bn);
+  }
   a.sc = make_pair_sched(p.kernel, p.slices, bits, p.k);
   a.G = emu ? (double*)(w + L.G) : nullptr;
   const SplitPlan spl = split_plan(p, bn);

@@ -140,12 +140,13 @@ cudaError_t launch_tables_grouped(const TableJob* jobs, int64_t njobs, int64_t m
 
 // ---------------------------------------------------------------- C := beta*C
 template <typename T>
-__global__ void k_scale(T* __restrict__ c, Tables t, int64_t m, int64_t n, int64_t l, T beta) {
+__global__ void k_scale(T* __restrict__ c, Tables t, int64_t m, int64_t n, int64_t l, T beta, int tri) {
   const int64_t total = m * n * l;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     int64_t im = i % m, r = i / m;
     int64_t in = r % n, il = r / n;
+    if (!tri_keep(tri, im, in)) continue;  // outside the updated triangle
     T* p = c + t.cm[im] + t.cn[in] + t.cl[il];
     *p = beta == T(0) ? T(0) : beta * *p;  // beta == 0: C is not read
   }
@@ -157,9 +158,9 @@ cudaError_t launch_scale(const Plan& p, const Tables& t, double beta, cudaStream
   int grid = (int)(blocks > 4 * 148 * 8 ? 4 * 148 * 8 : blocks);
   if (grid < 1) grid = 1;
   if (p.es_c == 8)
-    k_scale<double><<<grid, 256, 0, s>>>((double*)p.c, t, p.m, p.n, p.l, beta);
+    k_scale<double><<<grid, 256, 0, s>>>((double*)p.c, t, p.m, p.n, p.l, beta, p.tri);
   else
-    k_scale<float><<<grid, 256, 0, s>>>((float*)p.c, t, p.m, p.n, p.l, (float)beta);
+    k_scale<float><<<grid, 256, 0, s>>>((float*)p.c, t, p.m, p.n, p.l, (float)beta, p.tri);
   return cudaGetLastError();
 }
 
@@ -185,6 +186,8 @@ __global__ void __launch_bounds__(256) k_simt(GemmArgs g) {
     const int64_t tm = tile % tiles_m, rest = tile / tiles_m;
     const int64_t tn = rest % tiles_n, il = rest / tiles_n;
     const int64_t m0 = tm * BM, n0 = tn * BN;
+    // a tile wholly outside the updated triangle has nothing to do
+    if (g.tri == 1 ? m0 + BM - 1 < n0 : (g.tri == 2 && m0 > n0 + BN - 1)) continue;
     const int64_t al = g.t.al[il], bl = g.t.bl[il], cl = g.t.cl[il];
     T acc[TM][TN];
 #pragma unroll
@@ -197,13 +200,19 @@ __global__ void __launch_bounds__(256) k_simt(GemmArgs g) {
         int mm, kk;
         if (g.a_contig == 2) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
         const int64_t gm = m0 + mm, gk = k0 + kk;
-        As[kk][mm] = (gm < g.m && gk < g.k) ? A[al + g.t.am[gm] + g.t.ak[gk]] : T(0);
+        As[kk][mm] = (gm < g.m && gk < g.k)
+                         ? (g.band_op == 1 ? band_at<T>(A, al + g.t.am[gm], g.t.ak, 0, gk, g.k, g.band)
+                                           : A[al + g.t.am[gm] + g.t.ak[gk]])
+                         : T(0);
       }
       for (int e = tid; e < BN * BK; e += 256) {
         int nn, kk;
         if (g.b_contig == 2) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
         const int64_t gn = n0 + nn, gk = k0 + kk;
-        Bs[kk][nn] = (gn < g.n && gk < g.k) ? B[bl + g.t.bn[gn] + g.t.bk[gk]] : T(0);
+        Bs[kk][nn] = (gn < g.n && gk < g.k)
+                         ? (g.band_op == 2 ? band_at<T>(B, bl + g.t.bn[gn], g.t.bk, 0, gk, g.k, g.band)
+                                           : B[bl + g.t.bn[gn] + g.t.bk[gk]])
+                         : T(0);
       }
       __syncthreads();
 #pragma unroll 4
@@ -228,7 +237,7 @@ __global__ void __launch_bounds__(256) k_simt(GemmArgs g) {
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
         const int64_t gn = n0 + tx + j * (BN / TN);
-        if (gn >= g.n) continue;
+        if (gn >= g.n || !tri_keep(g.tri, gm, gn)) continue;
         T* p = C + crow + g.t.cn[gn];
         T v = alpha * acc[i][j];
         if (beta != T(0)) v = fma(beta, *p, v);

@@ -49,6 +49,12 @@ struct Prob {
   int64_t m, n, k, l;
   double alpha, beta;
   int bn;  // grouped launches: this problem's tile width (64, 128 or 256, <= the launch's)
+  // Single problems restricted to a triangle of C (tri 1: row >= col, 2:
+  // row <= col; no batch): the tiles that meet it, listed row tile by row
+  // tile (tri_list[i] = {tm, tn}), tri_tiles of them.
+  int tri;
+  const int2* tri_list;
+  int64_t tri_tiles;
 };
 
 // One entry of a grouped launch's tile list: problem, row tile, column tile, batch.

@@ -35,6 +35,19 @@ struct ClassModes {
   }
 };
 
+// A tridiagonal factor applied along k to one operand (the sandwiched
+// product C := beta C + alpha A T A^T, famlies_gemmt_tridiag): element
+// (r, p) of the operand the kernels see is
+//   sub[p-1] x(r, p-1) + diag[p] x(r, p) + sup[p] x(r, p+1)
+// of its strided source x, terms outside 0..k-1 left out (a band: entries
+// of T off its three diagonals are not multiplied).  diag == null: no
+// diagonal term; sup == null: sup[p] = -sub[p] (T skew-symmetric).
+struct Band {
+  const void* sub = nullptr;
+  const void* diag = nullptr;
+  const void* sup = nullptr;
+};
+
 struct Plan {
   famlies_dtype_t dtype;
   ClassModes M, N, K, L;   // after role swap: M belongs to the row operand
@@ -57,6 +70,12 @@ struct Plan {
   // k of extent n) and its tables hold the offsets of the dense layout.
   int64_t sym_n = 0;
   int sym_side = -1;
+  // Sandwiched product: operand band_side (0 row, 1 column) carries the
+  // tridiagonal factor band; tri != 0 restricts the update to a triangle of
+  // C in the kernel's indices (1: row >= col, 2: row <= col; no batch).
+  Band band;
+  int band_side = -1;
+  int tri = 0;
 };
 
 // Validates and plans; returns FAMLIES_OK or a FAMLIES_ERR_* code.  Never

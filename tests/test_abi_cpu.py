@@ -197,3 +197,20 @@ def test_symmetric_operand_validation():
     B2 = _lib.Desc((v, v, o), (1, v, v * v), [2, 4, 5], 0x20000000)
     C2 = _lib.Desc((v, v, o), (1, v, v * v), [1, 3, 5], 0x40000000)
     assert _sym_rc((v, v, v, v), [1, 2, 3, 4], B2, C2) == UNSUPPORTED
+
+
+def test_gemmt_validation():
+    """famlies_gemmt_tridiag rejects bad arguments on the host: negative
+    sizes or strides, bf16, a missing subdiagonal, and C overlapping A
+    (checked by the planner before any device work)."""
+    lib = _lib.load()
+    opt = _lib.options()
+    info = _lib.PlanInfo()
+    call = lambda n, k, A, rsa, csa, sub, C, rsc, csc, dt=fm.F64_EMU: lib.famlies_gemmt_tridiag(
+        n, k, -1.0, A, rsa, csa, sub, None, None, 1.0, C, rsc, csc, dt, None, opt, info)
+    A, C, sub = 0x10000000, 0x20000000, 0x30000000
+    assert call(-1, 4, A, 1, 8, sub, C, 1, 8) == -1
+    assert call(8, 4, A, -1, 8, sub, C, 1, 8) == -1
+    assert call(8, 4, A, 1, 8, sub, C, 1, 8, fm.BF16) == -6
+    assert call(8, 4, A, 1, 8, None, C, 1, 8) == -1          # k > 1 needs the subdiagonal
+    assert call(8, 4, A, 1, 8, sub, A + 64, 1, 8) == -4     # C overlaps A
