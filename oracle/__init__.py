@@ -22,6 +22,10 @@ Parity status per function (what pins it, see tests/test_oracle.py):
                a scaled outer product), the exact zero diagonal of A T A^T
                for skew-symmetric T, the untouched upper triangle, and the
                alpha = 0 / beta = 0 conventions.
+  mttkrp    -- pinned: exact integer brute force over every index tuple
+               (Python ints), the rank-one closed form (X an outer product
+               of vectors gives products of dot products), the two-way case
+               (X U or X^T U), R = 1 with all-ones factors (a mode sum).
 """
 from __future__ import annotations
 
@@ -172,3 +176,30 @@ def gemmt_tridiag(alpha, A, sub, diag, sup, beta, C) -> np.ndarray:
     full = A @ B
     C[low] = alpha * full[low] if beta == 0.0 else alpha * full[low] + beta * C[low]
     return C
+
+
+def mttkrp(alpha, X, mode, U, beta, M) -> np.ndarray:
+    """M := beta * M + alpha * X_(mode) KR, in place on M (I_mode x R).
+
+    The matricised-tensor-times-Khatri-Rao-product of CP-ALS (Sec. 3,
+    Girder 5): KR[(i_m)_{m != mode}, r] = prod over m != mode, in increasing
+    m, of U[m][i_m, r], and M[i, r] = sum over the other modes of
+    X[..., i, ...] KR[..., r].  The Khatri-Rao product is formed explicitly
+    (broadcast products), then contracted with X by numpy.tensordot.
+    alpha == 0: X and the factors are not read; beta == 0: M is not read.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    N = X.ndim
+    R = M.shape[1]
+    if alpha == 0.0 or X.size == 0:
+        M[...] = 0.0 if beta == 0.0 else beta * M
+        return M
+    others = [m for m in range(N) if m != mode]
+    KR = None
+    for j, m in enumerate(others):  # KR[i_0, ..., i_j, r], factors multiplied left to right
+        f = np.asarray(U[m], dtype=np.float64)
+        f = f.reshape((1,) * j + (f.shape[0], R))
+        KR = f if KR is None else KR[..., None, :] * f
+    prod = np.tensordot(X, KR, axes=(others, list(range(len(others)))))
+    M[...] = alpha * prod if beta == 0.0 else alpha * prod + beta * M
+    return M

@@ -447,3 +447,69 @@ def test_gemmt_alpha_beta_conventions():
     iu = np.triu_indices(4, 1)
     assert not np.isnan(np.tril(C)).any()
     assert np.isnan(C[iu]).all()
+
+
+# ---------------------------------------------------------------------------
+# Matricised tensor times Khatri-Rao product (mttkrp)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape,mode", [((3, 4, 5), 0), ((3, 4, 5), 1), ((3, 4, 5), 2), ((2, 3, 2, 3), 2)])
+def test_mttkrp_bruteforce_exact_integer(shape, mode):
+    """Every index tuple of X summed in Python integers."""
+    rng = np.random.default_rng(1100 + sum(shape) + mode)
+    R = 3
+    X = rng.integers(-3, 4, size=shape)
+    U = [rng.integers(-3, 4, size=(e, R)) for e in shape]
+    M0 = rng.integers(-5, 6, size=(shape[mode], R)).astype(np.float64)
+    want = M0.copy()
+    for i in range(shape[mode]):
+        for r in range(R):
+            s = 0
+            for idx in itertools.product(*[range(e) for e in shape]):
+                if idx[mode] != i:
+                    continue
+                t = int(X[idx])
+                for m, im in enumerate(idx):
+                    if m != mode:
+                        t *= int(U[m][im, r])
+                s += t
+            want[i, r] = 2 * s - 1 * M0[i, r]
+    got = oracle.mttkrp(2.0, X.astype(np.float64), mode, [u.astype(np.float64) for u in U], -1.0, M0.copy())
+    assert np.array_equal(got, want)
+
+
+def test_mttkrp_rank_one_closed_form():
+    """X = a o b o c (outer product): M[i, r] = a[i] (b . U1[:, r]) (c . U2[:, r])
+    for mode 0, and the analogous products for modes 1 and 2."""
+    rng = np.random.default_rng(1110)
+    a, b, c = rng.standard_normal(6), rng.standard_normal(5), rng.standard_normal(4)
+    X = np.einsum("i,j,k->ijk", a, b, c)
+    U = [rng.standard_normal((6, 3)), rng.standard_normal((5, 3)), rng.standard_normal((4, 3))]
+    vecs = [a, b, c]
+    for mode in range(3):
+        M = np.zeros((X.shape[mode], 3))
+        oracle.mttkrp(1.0, X, mode, U, 0.0, M)
+        want = vecs[mode][:, None] * np.prod([vecs[m] @ U[m] for m in range(3) if m != mode], axis=0)[None, :]
+        assert np.allclose(M, want, rtol=1e-13, atol=1e-13)
+
+
+def test_mttkrp_two_way_is_a_matrix_product():
+    """N = 2: mode 0 gives X U1, mode 1 gives X^T U0 (a transposed operand
+    would fail on the non-square X)."""
+    rng = np.random.default_rng(1120)
+    X = rng.integers(-4, 5, size=(5, 7)).astype(np.float64)
+    U0, U1 = rng.integers(-4, 5, size=(5, 2)).astype(np.float64), rng.integers(-4, 5, size=(7, 2)).astype(np.float64)
+    M = np.zeros((5, 2))
+    assert np.array_equal(oracle.mttkrp(1.0, X, 0, [None, U1], 0.0, M), X @ U1)
+    M = np.zeros((7, 2))
+    assert np.array_equal(oracle.mttkrp(1.0, X, 1, [U0, None], 0.0, M), X.T @ U0)
+
+
+def test_mttkrp_all_ones_factors_sum_the_other_modes():
+    """R = 1 and all-ones factors: M[i, 0] is the sum of X over the other modes."""
+    rng = np.random.default_rng(1130)
+    X = rng.integers(-9, 10, size=(4, 3, 5, 2)).astype(np.float64)
+    U = [np.ones((e, 1)) for e in X.shape]
+    M = np.zeros((5, 1))
+    oracle.mttkrp(1.0, X, 2, U, 0.0, M)
+    assert np.array_equal(M[:, 0], X.sum(axis=(0, 1, 3)))
