@@ -520,6 +520,28 @@ def run_other(args):
                     ms_u = _cuda_ms(unfused, args.steps, args.warmup)
                     row["unfused_full_square_f64_emu_ms"] = ms_u
             print(json.dumps(row), flush=True)
+    elif args.workload == "mttkrp":
+        # CP-ALS's inner contraction on a 3-way tensor: M = X_(n) (U_b kr U_c)
+        # for each mode n, the Khatri-Rao operand generated while packed.
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(8)
+        I, R = 512, 64
+        flops = 2 * I ** 3 * R
+        for dt, tdt in (("f64_emu", torch.float64), ("f64", torch.float64), ("f32", torch.float32)):
+            X = torch.randn(I, I, I, device="cuda", dtype=tdt, generator=gen).permute(2, 1, 0)  # column-major
+            U = [torch.randn(R, I, device="cuda", dtype=tdt, generator=gen).t() for _ in range(3)]
+            row = {"workload": f"mttkrp_3way_{I}_R{R}", "dtype": dt, "flops": flops,
+                   "x_bytes": X.numel() * X.element_size()}
+            for mode in range(3):
+                M = torch.zeros(R, I, device="cuda", dtype=tdt).t()
+                f = lambda **kw: fm.mttkrp(1.0, X, mode, U, 0.0, M, dtype=dt, **kw)
+                steps = args.steps if dt != "f64" else max(1, min(args.steps, 3))
+                ms = _cuda_ms(f, steps, min(args.warmup, 2) if dt == "f64" else args.warmup)
+                row[f"mode{mode}_ms"] = ms
+                row[f"mode{mode}_tflops"] = flops / ms / 1e9
+                row[f"mode{mode}_x_gbs"] = row["x_bytes"] / ms / 1e6
+            del X
+            print(json.dumps(row), flush=True)
     elif args.workload == "autograd":
         from paper_2604_07311_b300.autograd import contract_autograd
         d = W.autograd_problem()
@@ -570,7 +592,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="ladder",
                     choices=["ladder", "transpose_free", "block_sparse", "autograd", "network", "ladder_sym",
-                             "gemmt"],
+                             "gemmt", "mttkrp"],
                     help="ladder is the benchmark line; the others print secondary measurements")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)

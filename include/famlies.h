@@ -311,6 +311,33 @@ FAMLIES_API int famlies_gemmt_tridiag(int64_t n, int64_t k, double alpha, const 
                                       int64_t cs_c, famlies_dtype_t dtype, void* stream,
                                       const famlies_options_t* opt, famlies_plan_info_t* info);
 
+/* A matrix operand: element (i, j) at data[i * rs + j * cs] (strides in
+ * elements, >= 0), rows x cols. */
+typedef struct {
+  const void* data;
+  int64_t rows, cols;
+  int64_t rs, cs;
+} famlies_matrix_t;
+
+/* Matricised tensor times Khatri-Rao product, the inner contraction of
+ * CP-ALS (Sec. 3, Girder 5: CP-ALS among the tensor factorisations):
+ *   M[i, r] := beta * M[i, r]
+ *            + alpha * sum over the other modes of X[.., i (mode `mode`), ..]
+ *                      * prod_{m != mode} U[m][i_m, r]
+ * X is an N-way tensor (2 <= N <= FAMLIES_MAX_NDIM; its labels are
+ * ignored), U an array of N factor matrices (U[m] is X->extents[m] x R;
+ * U[mode] is ignored), M is X->extents[mode] x R, R = M->cols.  The
+ * Khatri-Rao product of the factors is never stored: its elements are
+ * formed (products in increasing m) as the operand is packed.  dtype:
+ * FAMLIES_F64 (native), FAMLIES_F64_EMU, FAMLIES_F32; all operands hold the
+ * dtype's elements; BF16 returns FAMLIES_ERR_UNSUPPORTED.  M must not
+ * overlap X or a factor (FAMLIES_ERR_ALIAS).  Error codes, options (kernel
+ * choice fixed by the dtype) and info as for famlies_contract_ex. */
+FAMLIES_API int famlies_mttkrp(double alpha, const famlies_tensor_t* X, int32_t mode,
+                               const famlies_matrix_t* U, double beta, const famlies_matrix_t* M,
+                               famlies_dtype_t dtype, void* stream, const famlies_options_t* opt,
+                               famlies_plan_info_t* info);
+
 /* Contraction networks: a pre-ordered sequence of tensor contractions run
  * through the same planner and kernels (Sec. 3, Girder 5, tensor contraction
  * networks).  `tensors` lists every tensor of the network; step i computes

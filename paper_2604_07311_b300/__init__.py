@@ -10,7 +10,7 @@ from __future__ import annotations
 from ._lib import (BF16, DTYPES, F32, F64, F64_EMU, KERNELS, Desc, FamliesError, PlanInfo,
                    desc_numpy, desc_torch, load, options, check, error_string)
 
-__all__ = ["contract", "contract_host", "contract_batched", "contract_network", "contract_sym", "gemmt_tridiag", "plan", "device_status",
+__all__ = ["contract", "contract_host", "contract_batched", "contract_network", "contract_sym", "gemmt_tridiag", "mttkrp", "plan", "device_status",
            "FamliesError", "F64", "F64_EMU", "F32", "BF16", "lib_path", "Contract", "contract_autograd"]
 
 
@@ -193,6 +193,36 @@ def gemmt_tridiag(alpha, A, t_sub, t_diag, t_sup, beta, C, dtype=None, stream=No
                                     C.data_ptr(), C.stride(0), C.stride(1), code, _stream_handle(stream),
                                     opt, info))
     return (C, info.as_dict()) if return_info else C
+
+
+def mttkrp(alpha, X, mode, factors, beta, M, dtype=None, stream=None, *, slices=0, wait_limit=0,
+           events=None, return_info=False):
+    """M := beta * M + alpha * X_(mode) (Khatri-Rao product of the other factors).
+
+    X: N-way CUDA tensor (any non-negative strides); factors: N entries, the
+    (I_m, R) CUDA matrices for m != mode (factors[mode] is ignored, may be
+    None); M: (I_mode, R).  dtype 'f64', 'f64_emu' or 'f32' (None: from X).
+    """
+    import ctypes
+    from ._lib import MatrixDesc
+    lib = load()
+    code = _dtype_code(dtype, X, M)
+    if M.dim() != 2 or len(factors) != X.dim():
+        raise ValueError("M must be (I_mode, R) and factors one per mode of X")
+    mats = []
+    for m, u in enumerate(factors):
+        if m == mode or u is None:
+            mats.append(MatrixDesc(None, 0, 0, 0, 0))
+        else:
+            mats.append(MatrixDesc(u.data_ptr(), u.shape[0], u.shape[1], u.stride(0), u.stride(1)))
+    arr = (MatrixDesc * len(mats))(*mats)
+    md = MatrixDesc(M.data_ptr(), M.shape[0], M.shape[1], M.stride(0), M.stride(1))
+    dx = desc_torch(X, list(range(1, X.dim() + 1)))
+    info = PlanInfo()
+    opt = options(slices, 0, 0, wait_limit, events)
+    check(lib.famlies_mttkrp(float(alpha), dx.ref, int(mode), arr, float(beta), ctypes.byref(md), code,
+                             _stream_handle(stream), opt, info))
+    return (M, info.as_dict()) if return_info else M
 
 
 def contract_noalloc(alpha, A, la, B, lb, beta, C, lc, dtype=None, stream=None):

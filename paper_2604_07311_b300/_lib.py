@@ -39,6 +39,12 @@ class SymTensorDesc(ctypes.Structure):
                 ("size_bytes", ctypes.c_int64)]
 
 
+class MatrixDesc(ctypes.Structure):
+    """famlies_matrix_t: element (i, j) at data[i * rs + j * cs]."""
+    _fields_ = [("data", ctypes.c_void_p), ("rows", ctypes.c_int64), ("cols", ctypes.c_int64),
+                ("rs", ctypes.c_int64), ("cs", ctypes.c_int64)]
+
+
 class Options(ctypes.Structure):
     _fields_ = [("slices", ctypes.c_int32), ("kernel", ctypes.c_int32), ("tile_n", ctypes.c_int32),
                 ("stall_test", ctypes.c_int32), ("wait_limit", ctypes.c_int64),
@@ -101,12 +107,15 @@ def load(path: str | None = None):
     i64 = ctypes.c_int64
     lib.famlies_gemmt_tridiag.argtypes = [i64, i64, d, vp, i64, i64, vp, vp, vp, d, vp, i64, i64, ctypes.c_int,
                                           vp, ctypes.POINTER(Options), ctypes.POINTER(PlanInfo)]
+    lib.famlies_mttkrp.argtypes = [d, T, ctypes.c_int32, ctypes.POINTER(MatrixDesc), d,
+                                   ctypes.POINTER(MatrixDesc), ctypes.c_int, vp, ctypes.POINTER(Options),
+                                   ctypes.POINTER(PlanInfo)]
     lib.famlies_error_string.argtypes = [ctypes.c_int]
     lib.famlies_error_string.restype = ctypes.c_char_p
     lib.famlies_device_status.argtypes = [vp]
     for f in ("famlies_contract", "famlies_contract_ex", "famlies_contract_host",
               "famlies_contract_batched", "famlies_plan", "famlies_device_status", "famlies_version",
-              "famlies_network", "famlies_contract_sym", "famlies_gemmt_tridiag"):
+              "famlies_network", "famlies_contract_sym", "famlies_gemmt_tridiag", "famlies_mttkrp"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib

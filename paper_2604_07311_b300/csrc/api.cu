@@ -126,6 +126,8 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
     g.band = p.band;
     g.band_op = p.band_side + 1;
     g.tri = p.tri;
+    g.krp = p.krp;
+    g.krp_op = p.krp_side + 1;
     g.ev_begin = opt ? (cudaEvent_t)opt->events[0] : nullptr;
     g.ev_end = opt ? (cudaEvent_t)opt->events[1] : nullptr;
     switch (p.kernel) {
@@ -291,6 +293,78 @@ int famlies_gemmt_tridiag(int64_t n, int64_t k, double alpha, const void* A, int
     p.band.sub = t_sub;
     p.band.diag = t_diag;
     p.band.sup = t_sup;
+  }
+  return run_plan(p, alpha, beta, (cudaStream_t)stream, &o, info);
+}
+
+int famlies_mttkrp(double alpha, const famlies_tensor_t* X, int32_t mode, const famlies_matrix_t* U,
+                   double beta, const famlies_matrix_t* M, famlies_dtype_t dtype, void* stream,
+                   const famlies_options_t* opt, famlies_plan_info_t* info) {
+  if (!X || !U || !M || X->ndim < 2 || X->ndim > FAMLIES_MAX_NDIM || mode < 0 || mode >= X->ndim ||
+      !X->extents || !X->strides)
+    return FAMLIES_ERR_INVALID_ARG;
+  if (dtype != FAMLIES_F64 && dtype != FAMLIES_F64_EMU && dtype != FAMLIES_F32)
+    return FAMLIES_ERR_UNSUPPORTED;
+  const int N = X->ndim;
+  const int64_t R = M->cols;
+  const int es = dtype == FAMLIES_F32 ? 4 : 8;
+  if (R < 0 || M->rows != X->extents[mode] || M->rs < 0 || M->cs < 0) return FAMLIES_ERR_EXTENT_MISMATCH;
+  auto span = [](const famlies_matrix_t& a) {
+    return (a.rows == 0 || a.cols == 0) ? (int64_t)0 : (a.rows - 1) * a.rs + (a.cols - 1) * a.cs + 1;
+  };
+  auto overlap = [&](const famlies_matrix_t& a) {
+    const char* a0 = (const char*)a.data;
+    const char* m0 = (const char*)M->data;
+    return span(a) > 0 && span(*M) > 0 && a0 < m0 + span(*M) * es && m0 < a0 + span(a) * es;
+  };
+  // The contraction M[i, r] = X[.., i, ..] KR[(i_m), r] whose column operand,
+  // the Khatri-Rao product KR, has a dense layout (the other modes in order,
+  // first fastest, then r) that the kernels decode instead of reading.
+  int32_t lx[FAMLIES_MAX_NDIM], lb[FAMLIES_MAX_NDIM];
+  int64_t eb[FAMLIES_MAX_NDIM], sb[FAMLIES_MAX_NDIM];
+  const int32_t RL = 99;  // r's label (X's modes are 1..N)
+  Krp q;
+  int64_t acc = 1;
+  for (int m = 0; m < N; ++m) {
+    lx[m] = m + 1;
+    if (m == mode) continue;
+    const famlies_matrix_t& u = U[m];
+    if (u.rows != X->extents[m] || u.cols != R || u.rs < 0 || u.cs < 0) return FAMLIES_ERR_EXTENT_MISMATCH;
+    if (overlap(u)) return FAMLIES_ERR_ALIAS;
+    eb[q.nf] = X->extents[m];
+    sb[q.nf] = acc;
+    lb[q.nf] = m + 1;
+    q.u[q.nf] = u.data;
+    q.rs[q.nf] = u.rs;
+    q.cs[q.nf] = u.cs;
+    q.ext[q.nf] = X->extents[m] > 0 ? X->extents[m] : 1;
+    q.st[q.nf] = acc;
+    ++q.nf;
+    acc *= X->extents[m] > 0 ? X->extents[m] : 1;
+  }
+  eb[q.nf] = R;
+  sb[q.nf] = acc;
+  lb[q.nf] = RL;
+  famlies_tensor_t tx = {N, X->extents, X->strides, lx, X->data, X->size_bytes};
+  // a stand-in address: the Khatri-Rao operand is generated, never read
+  famlies_tensor_t tb = {q.nf + 1, eb, sb, lb, (void*)(uintptr_t)256, 0};
+  const int64_t ec[2] = {M->rows, R}, scs[2] = {M->rs, M->cs};
+  const int32_t lc[2] = {mode + 1, RL};
+  famlies_tensor_t tm = {2, ec, scs, lc, const_cast<void*>(M->data), 0};
+  famlies_options_t o = {};
+  if (opt) o = *opt;
+  o.kernel = dtype == FAMLIES_F64 ? 1 : 2;  // CUDA cores / packed tensor cores
+  Plan p;
+  int rc = make_plan(alpha, &tx, &tb, &tm, dtype, &o, &p);
+  if (rc) return rc;
+  if (p.kernel != FAMLIES_KERNEL_NONE && p.kernel != FAMLIES_KERNEL_SCALE) {
+    if (p.kernel != FAMLIES_KERNEL_SIMT_F64 && p.kernel != FAMLIES_KERNEL_TC_EMU &&
+        p.kernel != FAMLIES_KERNEL_TC_TF32X3)
+      return FAMLIES_ERR_UNSUPPORTED;
+    for (int f = 0; f < q.nf; ++f)
+      if (!q.u[f]) return FAMLIES_ERR_INVALID_ARG;
+    p.krp = q;
+    p.krp_side = p.swapped ? 0 : 1;
   }
   return run_plan(p, alpha, beta, (cudaStream_t)stream, &o, info);
 }

@@ -41,6 +41,8 @@ struct GemmArgs {
   Band band;               // tridiagonal factor (see Plan) of operand band_op - 1 (0: none)
   int band_op;
   int tri;                 // 0: all of C; 1: only row >= col; 2: only row <= col
+  Krp krp;                 // Khatri-Rao operand (see Plan) is operand krp_op - 1 (0: none)
+  int krp_op;
   cudaEvent_t ev_begin, ev_end;  // host only: recorded around the product kernel
 };
 
@@ -109,6 +111,18 @@ __device__ __forceinline__ T band_at(const T* __restrict__ x, int64_t base, cons
   T v = d ? d[p] * at(p) : T(0);
   if (p > 0) v = fm(s[p - 1], at(p - 1), v);
   if (p + 1 < k) v = fm(u ? u[p] : -s[p], at(p + 1), v);
+  return v;
+}
+
+// Element (r, k) of a Khatri-Rao operand (see Krp) whose k offset is off.
+template <class T>
+__device__ __forceinline__ T krp_at(const Krp& q, int64_t r, int64_t off) {
+  T v = T(1);
+  for (int f = 0; f < q.nf; ++f) {
+    const int64_t i = (off / q.st[f]) % q.ext[f];
+    const T u = ((const T*)q.u[f])[i * q.rs[f] + r * q.cs[f]];
+    v = f == 0 ? u : v * u;
+  }
   return v;
 }
 

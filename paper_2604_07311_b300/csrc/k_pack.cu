@@ -564,25 +564,75 @@ __device__ __forceinline__ void pack_pipeline(int64_t g0, int64_t gstep, int64_t
   }
 }
 
-// ------------------------------------------------------------ banded operand
-// Row exponents of a banded operand (fp64 split).  Item: 64 rows x KCH k;
-// thread (r, g) takes row r and k = k0 + g, k0 + g + 4, ..., so that a
-// warp's loads run along rows (the unit-stride index of a column-major
-// source) and the three neighbours each value reads come from L1.
-__device__ __forceinline__ void rowexp_band_body(const PackArgs& pa, const PackOp& o) {
-  const double* __restrict__ X = (const double*)o.x;
-  const int64_t tiles_r = (o.rows + PR - 1) / PR, tiles_k = (pa.k + KCH - 1) / KCH;
-  const int64_t items = tiles_r * tiles_k;
+// ---------------------------------------------------------- generated operands
+// Values of a generated operand's 64 x 64 tile (row tile tr, k tile tk)
+// into buf[r * TLD + kk], zero past its edges; thread t computes row t % PR.
+// Band: sub/diag/sup against the affine source (the same arithmetic as
+// band_at everywhere).  Khatri-Rao: the factor digits of the tile's k
+// offsets are decoded once per tile into dig (shared, [factor][kk]), then
+// each value is the product of its factors' entries, in factor order.
+template <class T>
+__device__ __forceinline__ void gen_tile(const PackArgs& pa, const PackOp& o, int64_t tr, int64_t tk, T* buf,
+                                         int32_t* dig) {
+  const int r = threadIdx.x % PR;
+  const int64_t row = tr * PR + r;
+  if (o.gen == 1) {
+    const T* __restrict__ X = (const T*)o.x;
+#pragma unroll 4
+    for (int i = 0; i < PER_THREAD; ++i) {
+      const int kk = threadIdx.x / PR + i * (256 / PR);
+      const int64_t p = tk * PK + kk;
+      buf[r * TLD + kk] =
+          (row < o.rows && p < pa.k) ? band_at<T>(X, row * o.rs, nullptr, o.ks, p, pa.k, o.band) : T(0);
+    }
+    return;
+  }
+  // Khatri-Rao: lanes run along k, so that a warp reads consecutive rows of
+  // the first factor (its fastest digit) and one row of the others
+  const Krp& q = o.krp;
+  for (int i = threadIdx.x; i < q.nf * PK; i += 256) {
+    const int f = i / PK, kk = i % PK;
+    const int64_t k = tk * PK + kk;
+    const int64_t off = k < pa.k ? ((o.affine & 2) ? k * o.ks : o.koff[k]) : 0;
+    dig[i] = (int32_t)((off / q.st[f]) % q.ext[f]);
+  }
+  __syncthreads();
+  const int kk = threadIdx.x % PK;
+  const int64_t k = tk * PK + kk;
+#pragma unroll 4
+  for (int i = 0; i < PER_THREAD; ++i) {
+    const int rr = threadIdx.x / PK + i * (256 / PK);
+    const int64_t rw = tr * PR + rr;
+    T v = T(0);
+    if (rw < o.rows && k < pa.k)
+      for (int f = 0; f < q.nf; ++f) {
+        const T u = ((const T*)q.u[f])[(int64_t)dig[f * PK + kk] * q.rs[f] + rw * q.cs[f]];
+        v = f == 0 ? u : v * u;
+      }
+    buf[rr * TLD + kk] = v;
+  }
+}
+
+// Row exponents and non-finite flags of a generated operand (fp64 split):
+// per tile, thread (r, g) scans row r's k = 16 g .. 16 g + 15 of the staged
+// values.
+__device__ __forceinline__ void rowexp_gen_body(const PackArgs& pa, const PackOp& o) {
+  __shared__ double buf[PR * TLD];
+  __shared__ int32_t dig[kMaxModes * PK];
   __shared__ int smx[4][PR], sbad[4][PR];
+  const int64_t tiles_r = (o.rows + PR - 1) / PR, tiles_k = (pa.k + PK - 1) / PK;
+  const int64_t items = tiles_r * tiles_k;
   const int r = threadIdx.x % PR, g = threadIdx.x / PR;
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
     const int64_t tr = it % tiles_r, tk = it / tiles_r;
-    const int64_t row = tr * PR + r;
-    const int64_t k0 = tk * KCH, k1 = min(pa.k, k0 + KCH);
+    gen_tile<double>(pa, o, tr, tk, buf, dig);
+    __syncthreads();
     int mx = -1100, bad = 0;
-    if (row < o.rows)
-      for (int64_t p = k0 + g; p < k1; p += 4)
-        exp_update(band_at<double>(X, row * o.rs, nullptr, o.ks, p, pa.k, o.band), mx, bad);
+    const int64_t krem = pa.k - tk * PK;
+    const int kmax = krem < PK ? (int)krem : PK;
+#pragma unroll 4
+    for (int j = 0; j < PK / 4; ++j)
+      if (g * (PK / 4) + j < kmax) exp_update(buf[r * TLD + g * (PK / 4) + j], mx, bad);
     smx[g][r] = mx;
     sbad[g][r] = bad;
     __syncthreads();
@@ -598,28 +648,18 @@ __device__ __forceinline__ void rowexp_band_body(const PackArgs& pa, const PackO
   }
 }
 
-// Slices of a banded operand: each 64 x 64 tile's band values are computed
-// into shared memory (row r, k = kk; the same arithmetic as the exponent
-// pass) and emitted like any staged tile.
+// Slices of a generated operand: each tile's values are staged in shared
+// memory and emitted like any staged tile.
 template <int PMODE>
-__device__ __forceinline__ void pack_band_body(const PackArgs& pa, const PackOp& o) {
+__device__ __forceinline__ void pack_gen_body(const PackArgs& pa, const PackOp& o) {
   using T = typename PackT<PMODE>::T;
   extern __shared__ __align__(16) unsigned char pack_smem[];
+  __shared__ int32_t dig[kMaxModes * PK];
   T* const buf = (T*)pack_smem;
-  const T* __restrict__ X = (const T*)o.x;
   const int64_t tiles_r = (o.rows + PR - 1) / PR, tiles_k = (pa.k + PK - 1) / PK;
   const int64_t items = tiles_r * tiles_k;
-  const int r = threadIdx.x % PR;
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
-    const int64_t tr = it % tiles_r, tk = it / tiles_r;
-    const int64_t row = tr * PR + r;
-#pragma unroll 4
-    for (int i = 0; i < PER_THREAD; ++i) {
-      const int kk = threadIdx.x / PR + i * (256 / PR);
-      const int64_t p = tk * PK + kk;
-      buf[r * TLD + kk] =
-          (row < o.rows && p < pa.k) ? band_at<T>(X, row * o.rs, nullptr, o.ks, p, pa.k, o.band) : T(0);
-    }
+    gen_tile<T>(pa, o, it % tiles_r, it / tiles_r, buf, dig);
     __syncthreads();
     // tile number as emit_tile decodes it: row tile + tiles_r * k tile
     emit_tile<PMODE>(PackTile{&pa, &o, it}, buf);
@@ -655,7 +695,13 @@ __device__ __forceinline__ void fixup_body(const GemmArgs& g, const int32_t* __r
     if (!tri_keep(g.tri, m, n)) continue;  // outside the updated triangle
     const int64_t ab = g.t.al[il] + g.t.am[m], bb = g.t.bl[il] + g.t.bn[n];
     double acc = 0.0;
-    if (g.band_op) {
+    if (g.krp_op) {
+      for (int64_t k = 0; k < g.k; ++k) {
+        const double va = g.krp_op == 1 ? krp_at<double>(g.krp, m, g.t.ak[k]) : A[ab + g.t.ak[k]];
+        const double vb = g.krp_op == 2 ? krp_at<double>(g.krp, n, g.t.bk[k]) : B[bb + g.t.bk[k]];
+        acc = fma(va, vb, acc);
+      }
+    } else if (g.band_op) {
       for (int64_t k = 0; k < g.k; ++k) {
         const double va = g.band_op == 1 ? band_at<double>(A, ab, g.t.ak, 0, k, g.k, g.band) : A[ab + g.t.ak[k]];
         const double vb = g.band_op == 2 ? band_at<double>(B, bb, g.t.bk, 0, k, g.k, g.band) : B[bb + g.t.bk[k]];
@@ -701,13 +747,13 @@ __global__ void __launch_bounds__(256) k_rowexp_sym(const __grid_constant__ Pack
   rowexp_sym_body(pa.op[side]);
 }
 
-__global__ void __launch_bounds__(256) k_rowexp_band(const __grid_constant__ PackArgs pa, int side) {
-  rowexp_band_body(pa, pa.op[side]);
+__global__ void __launch_bounds__(256) k_rowexp_gen(const __grid_constant__ PackArgs pa, int side) {
+  rowexp_gen_body(pa, pa.op[side]);
 }
 
 template <int PMODE>
-__global__ void __launch_bounds__(256) k_pack_band(const __grid_constant__ PackArgs pa, int side) {
-  pack_band_body<PMODE>(pa, pa.op[side]);
+__global__ void __launch_bounds__(256) k_pack_gen(const __grid_constant__ PackArgs pa, int side) {
+  pack_gen_body<PMODE>(pa, pa.op[side]);
 }
 
 __global__ void __launch_bounds__(256, 3) k_pack_sym(const __grid_constant__ PackArgs pa, int side) {
@@ -881,22 +927,22 @@ cudaError_t launch_pack_sym(const PackArgs& pa, int side, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_rowexp_band(const PackArgs& pa, int side, cudaStream_t s) {
+cudaError_t launch_rowexp_gen(const PackArgs& pa, int side, cudaStream_t s) {
   const PackOp& o = pa.op[side];
-  const int64_t items = ((o.rows + PR - 1) / PR) * ((pa.k + KCH - 1) / KCH);
+  const int64_t items = ((o.rows + PR - 1) / PR) * ((pa.k + PK - 1) / PK);
   if (items <= 0) return cudaSuccess;
-  k_rowexp_band<<<grid_for(items), 256, 0, s>>>(pa, side);
+  k_rowexp_gen<<<grid_for(items), 256, 0, s>>>(pa, side);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_band(int pmode, const PackArgs& pa, int side, cudaStream_t s) {
+cudaError_t launch_pack_gen(int pmode, const PackArgs& pa, int side, cudaStream_t s) {
   const PackOp& o = pa.op[side];
   const int64_t items = ((o.rows + PR - 1) / PR) * ((pa.k + PK - 1) / PK);
   if (items <= 0) return cudaSuccess;
   if (pmode == PACK_TF32)
-    k_pack_band<PACK_TF32><<<grid_for(items), 256, PR * TLD * sizeof(float), s>>>(pa, side);
+    k_pack_gen<PACK_TF32><<<grid_for(items), 256, PR * TLD * sizeof(float), s>>>(pa, side);
   else
-    k_pack_band<PACK_F64><<<grid_for(items), 256, PR * TLD * sizeof(double), s>>>(pa, side);
+    k_pack_gen<PACK_F64><<<grid_for(items), 256, PR * TLD * sizeof(double), s>>>(pa, side);
   return cudaGetLastError();
 }
 

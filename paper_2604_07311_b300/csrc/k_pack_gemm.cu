@@ -227,6 +227,42 @@ __device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, int x
   }
 }
 
+// The end of an fp64-split tile whose int64 sums X stayed in this thread's
+// registers (64-wide tiles): the same update as finish_tile, unrolled.
+template <int CPT>
+__device__ __forceinline__ void finish_regs(const Prob& P, const int64_t (&X)[CPT], int xunit, int64_t il,
+                                            int64_t row, int64_t crow, int64_t col0, int lc0, int bnp) {
+  double* C = (double*)P.c;
+  const double alpha = P.alpha, beta = P.beta;
+  const int er = P.ea[il * P.m + row] - xunit;
+  const int32_t* ebl = P.eb + il * P.n;
+  const int32_t* fbl = P.fb + il * P.n;
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) {
+    const int64_t col = col0 + j;
+    if (!(lc0 + j < bnp && col < P.n && tri_keep(P.tri, row, col)) || fbl[col]) continue;
+    double* pc = C + crow + P.cn[col];
+    const int e = er + ebl[col];
+    const double x = (double)X[j];
+    const long long xb = __double_as_longlong(x);
+    const int ex = (int)((xb >> 52) & 0x7FF);
+    const double scaled = (ex != 0 && ex + e >= 1 && ex + e <= 2046)
+                              ? __longlong_as_double(xb + ((long long)e << 52))
+                              : ldexp(x, e);
+    double v = alpha == 1.0 ? scaled : alpha * scaled;
+    if (beta != 0.0) v = beta == 1.0 ? v + *pc : fma(beta, *pc, v);
+    *pc = v;
+  }
+}
+
+// k blocks per chunk of an item: the item's k range runs chunk by chunk,
+// every diagonal over the chunk before the next chunk (the slices of a
+// chunk stay in L2 across the diagonals); 0 in the schedule: one chunk.
+__device__ __forceinline__ int chunk_of(const Sched& sc, const TileRef& T) {
+  const int n = T.kb_hi - T.kb_lo;
+  return sc.chunk > 0 ? sc.chunk : (n > 1 ? n : 1);
+}
+
 // The TMA producer: walks the CTA's unit sequence (tiles, diagonals, units,
 // pairs, k blocks, exactly as the MMA issuer consumes it) and fills stage s
 // of both operand regions per k block.  On a timeout it sets the abort flag;
@@ -254,10 +290,13 @@ __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap*
     const int bnp = GROUPED ? T.P->bn : BN;  // this tile's width
     const uint32_t bytes = (uint32_t)(Cfg::A_BYTES + bnp * Cfg::ROWB);
     const int row_a = (int)(T.tm * BM), row_b = (int)(T.tn * bnp);
+    const int ch = chunk_of(sc, T);
+    for (int c0 = T.kb_lo; c0 < T.kb_hi && ok; c0 += ch) {
+    const int c1 = c0 + ch < T.kb_hi ? c0 + ch : T.kb_hi;
     for (int di = 0; di < sc.ndiag && ok; ++di) {
       const int kcb = sc.kcb[di];
-      for (int kb0 = T.kb_lo; kb0 < T.kb_hi && ok; kb0 += kcb) {
-        const int kb1 = kb0 + kcb < T.kb_hi ? kb0 + kcb : T.kb_hi;
+      for (int kb0 = c0; kb0 < c1 && ok; kb0 += kcb) {
+        const int kb1 = kb0 + kcb < c1 ? kb0 + kcb : c1;
         for (int p = 0; p < sc.npairs[di] && ok; ++p) {
           // slices are stored [slice][batch][rows][k]
           const int za = sc.pa[di][p] * l + (int)T.il;
@@ -272,6 +311,7 @@ __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap*
           }
         }
       }
+    }
     }
   }
   if (!ok && !*abort) record_timeout(abort, args.status);
@@ -345,10 +385,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         // the MMA's N is this tile's width (the instruction descriptor's N field)
         const uint32_t idesc =
             GROUPED ? ptx::idesc_make(BM, T.P->bn, KIND == PAIR_KIND_BF16 ? 1u : 2u) : Cfg::IDESC;
+        const int ch = chunk_of(sc, T);
+        for (int c0 = T.kb_lo; c0 < T.kb_hi && ok; c0 += ch) {
+        const int c1 = c0 + ch < T.kb_hi ? c0 + ch : T.kb_hi;
         for (int di = 0; di < sc.ndiag && ok; ++di) {
           const int kcb = sc.kcb[di];
-          for (int kb0 = T.kb_lo; kb0 < T.kb_hi && ok; kb0 += kcb) {
-            const int kb1 = kb0 + kcb < T.kb_hi ? kb0 + kcb : T.kb_hi;
+          for (int kb0 = c0; kb0 < c1 && ok; kb0 += kcb) {
+            const int kb1 = kb0 + kcb < c1 ? kb0 + kcb : c1;
             if (!ptx::mbar_wait(&tempty[acc], accph ^ 1, lim, abort)) { ok = false; break; }
             ptx::tc_fence_after();
             const uint32_t dt = tmem_base + acc * BN;
@@ -377,6 +420,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             acc ^= 1;
             if (acc == 0) accph ^= 1;
           }
+        }
         }
       }
       if (!ok && !*abort) record_timeout(abort, args.status);
@@ -453,8 +497,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
       } else {
-        // fp64 split: int32 running sums per diagonal, fp64 tile sums in G.
+        // fp64 split: int32 running sums per diagonal, int64 tile sums in G
+        // (64-wide tiles: in registers, XR).
+        constexpr bool XREG = BN == 64;
         int32_t S[CPT];
+        int64_t XR[XREG ? CPT : 1];
 #pragma unroll
         for (int j = 0; j < CPT; ++j) S[j] = 0;
         // tile sums: per CTA for a whole tile; for a split of a tail tile the
@@ -465,9 +512,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                                  : (int64_t*)args.G + (size_t)blockIdx.x * BM * BN) +
                       (size_t)(hf * CPT) * BM + qd * 32 + lane;
         bool first_flush = true;
+        const int ch = chunk_of(sc, T);
+        for (int c0 = T.kb_lo; c0 < T.kb_hi && ok; c0 += ch) {
+        const int c1 = c0 + ch < T.kb_hi ? c0 + ch : T.kb_hi;
         for (int di = 0; di < sc.ndiag && ok; ++di) {
           const int kcb = sc.kcb[di];
-          const int nunits = (nkb + kcb - 1) / kcb;
+          const int nunits = (c1 - c0 + kcb - 1) / kcb;
           for (int u = 0; u < nunits; ++u) {
             if (!ptx::mbar_wait(&tfull[acc], accph, lim, abort)) { ok = false; break; }
             ptx::tc_fence_after();
@@ -488,24 +538,35 @@ __global__ void __launch_bounds__(THREADS, 1)
             acc ^= 1;
             if (acc == 0) accph ^= 1;
             if (!flush) continue;
-            // X += S * 2^xshift in int64 (exact, order-free): the first
-            // flush of a tile stores, later ones are fire-and-forget
-            // reductions performed at L2, so no flush waits on memory.
+            // X += S * 2^xshift in int64 (exact, order-free): in registers
+            // for 64-wide tiles; otherwise the first flush of a tile
+            // stores, later ones are fire-and-forget reductions performed
+            // at L2, so no flush waits on memory.
             {
               const int xs = sc.xshift[di];
 #pragma unroll
               for (int j = 0; j < CPT; ++j) {
                 int64_t v = (int64_t)S[j];
                 v = xs >= 0 ? (int64_t)((uint64_t)v << xs) : ((v + ((int64_t)1 << (-xs - 1))) >> (-xs));
-                if (first_flush && !part_item) Xt[(size_t)j * BM] = v;
+                if (XREG) XR[XREG ? j : 0] = first_flush ? v : XR[XREG ? j : 0] + v;
+                else if (first_flush && !part_item) Xt[(size_t)j * BM] = v;
                 else atomicAdd((unsigned long long*)(Xt + (size_t)j * BM), (unsigned long long)v);
                 S[j] = 0;
               }
               first_flush = false;
             }
-            if (part_item || !(last_unit && di == sc.ndiag - 1) || !rv || P.fa[il * P.m + row]) continue;
-            finish_tile<CPT>(P, Xt, sc.xunit, il, row, crow, col0, lc0, bnp);
+            if (!(last_unit && di == sc.ndiag - 1 && c1 == T.kb_hi)) continue;  // not the item's end
+            if (XREG && part_item) {  // a split's register sums join its tile's slot
+#pragma unroll
+              for (int j = 0; j < CPT; ++j)
+                atomicAdd((unsigned long long*)(Xt + (size_t)j * BM), (unsigned long long)XR[XREG ? j : 0]);
+              continue;
+            }
+            if (part_item || !rv || P.fa[il * P.m + row]) continue;
+            if constexpr (XREG) finish_regs<CPT>(P, XR, sc.xunit, il, row, crow, col0, lc0, bnp);
+            else finish_tile<CPT>(P, Xt, sc.xunit, il, row, crow, col0, lc0, bnp);
           }
+        }
         }
       }
     }
@@ -693,8 +754,9 @@ EncodeFn get_encode() {
 // run as s items over parts of their k range: the tail then takes
 // ceil(tail * s / SMs) / s rounds instead of one (plus a little per item for
 // its pipeline start and flushes).  s minimises that, each step up taken
-// when it saves more than 2 %: up to 16 when all tiles fit in one round,
-// else up to 4 (more splits of long tiles only multiply the partial-sum
+// when it saves more than 2 %: when all tiles fit in one round up to
+// max(16, SMs / tiles) (a few tall tiles with a long K fill the SMs), else
+// up to 4 (more splits of long tiles only multiply the partial-sum
 // traffic), and no more than the k range allows (whole units of the
 // fp32-output schedule, at least 512 k for the fp64 split).  Partial tiles
 // meet in k_split_reduce (fp32 output) or in an int64 slot per tile finished
@@ -715,7 +777,8 @@ SplitPlan split_plan(const Plan& p, int bn) {
   const int64_t unit = emu ? 512 / kb : f32out_unit_stages(kind);
   const int64_t pieces = emu ? nkb / unit : (nkb + unit - 1) / unit;
   const int64_t full = (tiles / sms) * sms, tail = tiles - full;
-  const int64_t most = full == 0 ? 16 : 4;
+  // all tiles in one round: enough splits to fill the SMs (at least 16)
+  const int64_t most = full == 0 ? std::max<int64_t>(16, (sms + tail - 1) / tail) : 4;
   const int64_t cap = pieces < most ? pieces : most;
   SplitPlan none{1, tiles, 0};
   if (cap <= 1 || tail == 0) return none;
@@ -978,13 +1041,13 @@ int packed_launches(const Plan& p) {
   const int tri = p.tri ? 1 : 0;  // the triangle's tile list
   if (p.kernel == FAMLIES_KERNEL_TC_EMU)  // exponents + pack + product (+ split finish) + fix-up
     return 4 + (split_count(p, pair_bn_for(p.n, p.tile_n)) > 1 ? 1 : 0) + tri +
-           (p.sym_n > 0 || p.band_side >= 0 ? 2 : 0);  // (+ the symmetric or banded operand's own)
+           (p.sym_n > 0 || p.band_side >= 0 || p.krp_side >= 0 ? 2 : 0);  // (+ a symmetric or generated operand's own)
   DirectView v;
   const bool tf32 = p.kernel == FAMLIES_KERNEL_TC_TF32X3;
   const bool da = !tf32 && direct_view(p.M, p.K, p.L, 0, p.a, &v);
   const bool db = !tf32 && direct_view(p.N, p.K, p.L, 1, p.b, &v);
   return ((da && db) ? 0 : 1) + 1 + (split_count(p, pair_bn_for(p.n, p.tile_n)) > 1 ? 1 : 0) + tri +
-         (p.band_side >= 0 ? 1 : 0);
+         (p.band_side >= 0 || p.krp_side >= 0 ? 1 : 0);
 }
 
 cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream_t s) {
@@ -1006,14 +1069,17 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   set_affine(pa.op[1], p.N, p.K, 1);
   const bool sym = p.sym_n > 0;
   if (sym) pa.op[p.sym_side].sym_n = p.sym_n;
-  const bool band = p.band_side >= 0;
-  if (band) {
-    PackOp& o = pa.op[p.band_side];
-    if (o.affine != 3 || p.l != 1) return cudaErrorNotSupported;
-    o.banded = 1;
+  // a generated operand: banded (its source affine) or Khatri-Rao, no batch
+  const int gside = p.band_side >= 0 ? p.band_side : p.krp_side;
+  const bool gen = gside >= 0;
+  if (gen) {
+    PackOp& o = pa.op[gside];
+    if (p.l != 1 || (p.band_side >= 0 && o.affine != 3)) return cudaErrorNotSupported;
+    o.gen = p.band_side >= 0 ? 1 : 2;
     o.band = p.band;
+    o.krp = p.krp;
   }
-  const int own = sym ? p.sym_side : (band ? p.band_side : -1);  // packed by its own kernels
+  const int own = sym ? p.sym_side : gside;  // packed by its own kernels (-1: none)
   cudaError_t e;
   if (emu) {
     pa.op[0].e = (int32_t*)(w + L.ea);
@@ -1025,11 +1091,11 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     // exponents start at a large negative value, flags and list counts at 0
     if ((e = cudaMemsetAsync(w + L.ea, 0x80, L.fa - L.ea, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w + L.fa, 0, L.G - L.fa, s)) != cudaSuccess) return e;
-    PackArgs pg = pa;  // the generic kernels skip a symmetric or banded operand
+    PackArgs pg = pa;  // the generic kernels skip a symmetric or generated operand
     if (own >= 0) pg.op[own].rows = 0;
     if ((e = launch_rowexp(pg, s)) != cudaSuccess) return e;
     if (sym && (e = launch_rowexp_sym(pa, p.sym_side, s)) != cudaSuccess) return e;
-    if (band && (e = launch_rowexp_band(pa, p.band_side, s)) != cudaSuccess) return e;
+    if (gen && (e = launch_rowexp_gen(pa, gside, s)) != cudaSuccess) return e;
   }
   const int bn = pair_bn_for(p.n, p.tile_n);
   const int S = pa.slices;
@@ -1040,8 +1106,8 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   // rows and batches) are read by TMA straight from the caller's tensor;
   // only the others are packed.
   DirectView va, vb;
-  const bool da = !emu && !tf32 && !band && direct_view(p.M, p.K, p.L, 0, p.a, &va);
-  const bool db = !emu && !tf32 && !band && direct_view(p.N, p.K, p.L, 1, p.b, &vb);
+  const bool da = !emu && !tf32 && !gen && direct_view(p.M, p.K, p.L, 0, p.a, &va);
+  const bool db = !emu && !tf32 && !gen && direct_view(p.N, p.K, p.L, 1, p.b, &vb);
   if (da) pa.op[0].rows = 0;  // nothing to pack
   if (db) pa.op[1].rows = 0;
   if (!da || !db) {
@@ -1050,7 +1116,7 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     if ((e = launch_pack(emu ? PACK_F64 : (tf32 ? PACK_TF32 : PACK_BF16), pg, s)) != cudaSuccess)
       return e;
     if (sym && (e = launch_pack_sym(pa, p.sym_side, s)) != cudaSuccess) return e;
-    if (band && (e = launch_pack_band(emu ? PACK_F64 : PACK_TF32, pa, p.band_side, s)) != cudaSuccess)
+    if (gen && (e = launch_pack_gen(emu ? PACK_F64 : PACK_TF32, pa, gside, s)) != cudaSuccess)
       return e;
   }
   const bool ok_a = da ? make_view_map(&ma, va, p.k, p.m, p.l, kbk, BM)
@@ -1074,6 +1140,9 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     a.single.tri_tiles = tri_tile_count(p, bn);
   }
   a.sc = make_pair_sched(p.kernel, p.slices, bits, p.k);
+  // fp64 split on 64-wide tiles: chunks of 256 k (the slices an item reads
+  // for one chunk, over all the CTAs, stay well inside L2)
+  if (emu && bn == 64) a.sc.chunk = 4;
   a.G = emu ? (double*)(w + L.G) : nullptr;
   const SplitPlan spl = split_plan(p, bn);
   a.splits = spl.splits;

@@ -201,8 +201,9 @@ __global__ void __launch_bounds__(256) k_simt(GemmArgs g) {
         if (g.a_contig == 2) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
         const int64_t gm = m0 + mm, gk = k0 + kk;
         As[kk][mm] = (gm < g.m && gk < g.k)
-                         ? (g.band_op == 1 ? band_at<T>(A, al + g.t.am[gm], g.t.ak, 0, gk, g.k, g.band)
-                                           : A[al + g.t.am[gm] + g.t.ak[gk]])
+                         ? (g.band_op == 1   ? band_at<T>(A, al + g.t.am[gm], g.t.ak, 0, gk, g.k, g.band)
+                            : g.krp_op == 1 ? krp_at<T>(g.krp, gm, g.t.ak[gk])
+                                            : A[al + g.t.am[gm] + g.t.ak[gk]])
                          : T(0);
       }
       for (int e = tid; e < BN * BK; e += 256) {
@@ -210,8 +211,9 @@ __global__ void __launch_bounds__(256) k_simt(GemmArgs g) {
         if (g.b_contig == 2) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
         const int64_t gn = n0 + nn, gk = k0 + kk;
         Bs[kk][nn] = (gn < g.n && gk < g.k)
-                         ? (g.band_op == 2 ? band_at<T>(B, bl + g.t.bn[gn], g.t.bk, 0, gk, g.k, g.band)
-                                           : B[bl + g.t.bn[gn] + g.t.bk[gk]])
+                         ? (g.band_op == 2   ? band_at<T>(B, bl + g.t.bn[gn], g.t.bk, 0, gk, g.k, g.band)
+                            : g.krp_op == 2 ? krp_at<T>(g.krp, gn, g.t.bk[gk])
+                                            : B[bl + g.t.bn[gn] + g.t.bk[gk]])
                          : T(0);
       }
       __syncthreads();

@@ -38,10 +38,12 @@ struct PackOp {
   // matrix, column by column; rows and k index the two sides (packed by
   // k_rowexp_sym / k_pack_sym, not by the generic kernels).
   int64_t sym_n;
-  // banded != 0: the operand carries a tridiagonal factor along k (see
-  // Band; packed by k_rowexp_band / k_pack_band from its affine source).
-  int banded;
+  // gen != 0: the operand is generated as it is packed (k_rowexp_gen /
+  // k_pack_gen): 1 = its affine source with a tridiagonal factor along k
+  // (band), 2 = a Khatri-Rao product of factor matrices (krp).
+  int gen;
   Band band;
+  Krp krp;
 };
 
 // Sets the affine fields of a pack operand from its row and k classes
@@ -63,11 +65,11 @@ cudaError_t launch_pack(int pmode, const PackArgs& pa, cudaStream_t s);
 // slices, both from one read of the lower triangle.
 cudaError_t launch_rowexp_sym(const PackArgs& pa, int side, cudaStream_t s);
 cudaError_t launch_pack_sym(const PackArgs& pa, int side, cudaStream_t s);
-// Banded operand pa.op[side] (see Band): row exponents and flags (fp64
-// split) and its slices (PACK_F64 or PACK_TF32), the band values computed
-// from the affine source as the tiles are staged.
-cudaError_t launch_rowexp_band(const PackArgs& pa, int side, cudaStream_t s);
-cudaError_t launch_pack_band(int pmode, const PackArgs& pa, int side, cudaStream_t s);
+// Generated operand pa.op[side] (banded or Khatri-Rao, see PackOp::gen):
+// row exponents and flags (fp64 split) and its slices (PACK_F64 or
+// PACK_TF32), the values computed as each tile is staged.
+cudaError_t launch_rowexp_gen(const PackArgs& pa, int side, cudaStream_t s);
+cudaError_t launch_pack_gen(int pmode, const PackArgs& pa, int side, cudaStream_t s);
 // fp64 split: recomputes in native fp64 the outputs of flagged rows/columns.
 cudaError_t launch_fixup(const GemmArgs& g, const PackArgs& pa, cudaStream_t s);
 

@@ -32,6 +32,9 @@ struct Sched {
   // negative).  xunit is as fine as K allows without int64 overflow.
   int xunit;
   int xshift[kPairMaxDiag];
+  // k blocks per chunk (fp64 split, 64-wide tiles, whose sums stay in
+  // registers so that chunk boundaries cost no memory traffic); 0: one chunk
+  int chunk;
 };
 
 // What the product needs to know about one problem.

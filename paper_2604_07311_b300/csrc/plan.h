@@ -48,6 +48,17 @@ struct Band {
   const void* sup = nullptr;
 };
 
+// A Khatri-Rao operand (famlies_mttkrp): element (r, k) is the product,
+// factor by factor in order, of U_f[i_f, r] (element (i, r) of factor f at
+// u[f] + i * rs[f] + r * cs[f]), where i_f = (o / st[f]) % ext[f] are the
+// digits of k's offset o in the operand's dense layout.
+struct Krp {
+  int nf = 0;
+  const void* u[kMaxModes] = {};
+  int64_t rs[kMaxModes] = {}, cs[kMaxModes] = {};
+  int64_t ext[kMaxModes] = {}, st[kMaxModes] = {};
+};
+
 struct Plan {
   famlies_dtype_t dtype;
   ClassModes M, N, K, L;   // after role swap: M belongs to the row operand
@@ -76,6 +87,10 @@ struct Plan {
   Band band;
   int band_side = -1;
   int tri = 0;
+  // Matricised tensor times Khatri-Rao product: operand krp_side is the
+  // Khatri-Rao product krp, generated while it is packed.
+  Krp krp;
+  int krp_side = -1;
 };
 
 // Validates and plans; returns FAMLIES_OK or a FAMLIES_ERR_* code.  Never

@@ -214,3 +214,23 @@ def test_gemmt_validation():
     assert call(8, 4, A, 1, 8, sub, C, 1, 8, fm.BF16) == -6
     assert call(8, 4, A, 1, 8, None, C, 1, 8) == -1          # k > 1 needs the subdiagonal
     assert call(8, 4, A, 1, 8, sub, A + 64, 1, 8) == -4     # C overlaps A
+
+
+def test_mttkrp_validation():
+    """famlies_mttkrp checks shapes, dtype and aliasing on the host."""
+    import ctypes
+    lib = _lib.load()
+    X = _lib.Desc((4, 5, 6), (1, 4, 20), [0, 0, 0], 0x10000000)
+    M = lambda rows, ptr=0x20000000: _lib.MatrixDesc(ptr, rows, 3, 1, rows)
+    U = lambda e, ptr: _lib.MatrixDesc(ptr, e, 3, 1, e)
+    us = (_lib.MatrixDesc * 3)(U(4, 0x30000000), U(5, 0x40000000), U(6, 0x50000000))
+    info = _lib.PlanInfo()
+    call = lambda mode, m, dt=fm.F64_EMU, u=us: lib.famlies_mttkrp(1.0, X.ref, mode, u, 0.0, ctypes.byref(m),
+                                                                   dt, None, None, ctypes.byref(info))
+    assert call(3, M(4)) == -1                        # mode out of range
+    assert call(0, M(5)) == -3                        # M's rows are not X's extent
+    assert call(0, M(4), fm.BF16) == -6
+    bad = (_lib.MatrixDesc * 3)(U(4, 0x30000000), U(7, 0x40000000), U(6, 0x50000000))
+    assert call(0, M(4), u=bad) == -3                 # a factor of the wrong height
+    assert call(0, M(4, 0x40000000 + 16)) == -4       # M overlaps a factor
+    assert call(0, M(4, 0x10000000 + 64)) == -4       # M overlaps X
