@@ -178,6 +178,18 @@ def gemmt_tridiag(alpha, A, sub, diag, sup, beta, C) -> np.ndarray:
     return C
 
 
+def khatri_rao(U, mode, N) -> np.ndarray:
+    """KR[i_a, i_b, ..., r] = U[a][i_a, r] * U[b][i_b, r] * ... over the modes
+    a < b < ... other than `mode` (of N), multiplied left to right: the
+    Khatri-Rao product of the factors as an (N-1)+1-way array."""
+    KR = None
+    for j, m in enumerate(m for m in range(N) if m != mode):
+        f = np.asarray(U[m], dtype=np.float64)
+        f = f.reshape((1,) * j + f.shape)
+        KR = f if KR is None else KR[..., None, :] * f
+    return KR
+
+
 def mttkrp(alpha, X, mode, U, beta, M) -> np.ndarray:
     """M := beta * M + alpha * X_(mode) KR, in place on M (I_mode x R).
 
@@ -195,11 +207,7 @@ def mttkrp(alpha, X, mode, U, beta, M) -> np.ndarray:
         M[...] = 0.0 if beta == 0.0 else beta * M
         return M
     others = [m for m in range(N) if m != mode]
-    KR = None
-    for j, m in enumerate(others):  # KR[i_0, ..., i_j, r], factors multiplied left to right
-        f = np.asarray(U[m], dtype=np.float64)
-        f = f.reshape((1,) * j + (f.shape[0], R))
-        KR = f if KR is None else KR[..., None, :] * f
+    KR = khatri_rao(U, mode, N)
     prod = np.tensordot(X, KR, axes=(others, list(range(len(others)))))
     M[...] = alpha * prod if beta == 0.0 else alpha * prod + beta * M
     return M
