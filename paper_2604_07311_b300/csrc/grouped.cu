@@ -86,7 +86,7 @@ GroupSetup layout_group(const std::vector<const Plan*>& ps, int bn_max) {
     G.pack_total += pack_tiles(p.m, p.k, p.l) + pack_tiles(p.n, p.k, p.l);
     G.c_bytes += up256((size_t)p.span_c * p.es_c);
   }
-  if (emu) G.ws_g = up256((size_t)num_sms() * kPairBM * bn_max * 8);
+  if (emu) G.ws_g = up256((size_t)2 * num_sms() * kPairBM * bn_max * 8);  // two sums per element
   G.ws_total = G.ws_main + G.ws_exp + G.ws_flag + G.ws_g;
   return G;
 }

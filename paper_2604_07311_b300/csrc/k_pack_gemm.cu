@@ -181,21 +181,25 @@ __device__ __forceinline__ TileRef tile_at(const PairArgs& a, int64_t t) {
 // groups of columns whose table entries, X and C are loaded together.  X is
 // read from L2 (the reductions that built it ran there).  Not inlined: it
 // runs once per tile and keeps its registers out of the drain loop's budget.
-template <int CPT>
-__device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, int xunit, int64_t il,
+template <int CPT, bool FINE>
+__device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, const Sched& sc, int64_t il,
                                          int64_t row, int64_t crow, int64_t col0, int lc0, int bnp) {
+  // the fine sums follow the coarse ones in the tile's slot (tiles 2 CPT wide)
+  const int64_t* Lt = Xt + (size_t)BM * (2 * CPT);
+  const int xunit = sc.xunit, xlo = sc.xlo;
   double* C = (double*)P.c;
   const double alpha = P.alpha, beta = P.beta;
   const int er = P.ea[il * P.m + row] - xunit;
   const int32_t* ebl = P.eb + il * P.n;
   const int32_t* fbl = P.fb + il * P.n;
+  const double lsc = ldexp(1.0, xunit - xlo);
   constexpr int FG = 8;
 #pragma unroll 1
   for (int j0 = 0; j0 < CPT; j0 += FG) {
     bool use[FG];
     int ecol[FG];
     int64_t coff[FG];
-    int64_t g[FG];
+    int64_t g[FG], gl[FG];
     double cold[FG];
 #pragma unroll
     for (int j = 0; j < FG; ++j) {
@@ -205,6 +209,7 @@ __device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, int x
       coff[j] = use[j] ? P.cn[col] : 0;
       use[j] = use[j] && !fbl[col];
       g[j] = __ldcg(Xt + (size_t)(j0 + j) * BM);
+      gl[j] = FINE ? __ldcg(Lt + (size_t)(j0 + j) * BM) : 0;
     }
 #pragma unroll
     for (int j = 0; j < FG; ++j) cold[j] = (use[j] && beta != 0.0) ? C[crow + coff[j]] : 0.0;
@@ -214,7 +219,8 @@ __device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, int x
       // 2^e built from its bits when it is a normal number
       // x * 2^e by adding e to x's exponent field (integer arithmetic: the
       // fp64 pipe is narrow) when the result stays a normal number
-      const double x = (double)g[j];
+      // the two sums in units of 2^-xunit (lsc: an exact power of two)
+      const double x = FINE ? (double)g[j] + (double)gl[j] * lsc : (double)g[j];
       const long long xb = __double_as_longlong(x);
       const int ex = (int)((xb >> 52) & 0x7FF);
       const double scaled = (ex != 0 && ex + e >= 1 && ex + e <= 2046)
@@ -225,42 +231,6 @@ __device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, int x
       if (use[j]) C[crow + coff[j]] = v;
     }
   }
-}
-
-// The end of an fp64-split tile whose int64 sums X stayed in this thread's
-// registers (64-wide tiles): the same update as finish_tile, unrolled.
-template <int CPT>
-__device__ __forceinline__ void finish_regs(const Prob& P, const int64_t (&X)[CPT], int xunit, int64_t il,
-                                            int64_t row, int64_t crow, int64_t col0, int lc0, int bnp) {
-  double* C = (double*)P.c;
-  const double alpha = P.alpha, beta = P.beta;
-  const int er = P.ea[il * P.m + row] - xunit;
-  const int32_t* ebl = P.eb + il * P.n;
-  const int32_t* fbl = P.fb + il * P.n;
-#pragma unroll
-  for (int j = 0; j < CPT; ++j) {
-    const int64_t col = col0 + j;
-    if (!(lc0 + j < bnp && col < P.n && tri_keep(P.tri, row, col)) || fbl[col]) continue;
-    double* pc = C + crow + P.cn[col];
-    const int e = er + ebl[col];
-    const double x = (double)X[j];
-    const long long xb = __double_as_longlong(x);
-    const int ex = (int)((xb >> 52) & 0x7FF);
-    const double scaled = (ex != 0 && ex + e >= 1 && ex + e <= 2046)
-                              ? __longlong_as_double(xb + ((long long)e << 52))
-                              : ldexp(x, e);
-    double v = alpha == 1.0 ? scaled : alpha * scaled;
-    if (beta != 0.0) v = beta == 1.0 ? v + *pc : fma(beta, *pc, v);
-    *pc = v;
-  }
-}
-
-// k blocks per chunk of an item: the item's k range runs chunk by chunk,
-// every diagonal over the chunk before the next chunk (the slices of a
-// chunk stay in L2 across the diagonals); 0 in the schedule: one chunk.
-__device__ __forceinline__ int chunk_of(const Sched& sc, const TileRef& T) {
-  const int n = T.kb_hi - T.kb_lo;
-  return sc.chunk > 0 ? sc.chunk : (n > 1 ? n : 1);
 }
 
 // The TMA producer: walks the CTA's unit sequence (tiles, diagonals, units,
@@ -290,13 +260,10 @@ __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap*
     const int bnp = GROUPED ? T.P->bn : BN;  // this tile's width
     const uint32_t bytes = (uint32_t)(Cfg::A_BYTES + bnp * Cfg::ROWB);
     const int row_a = (int)(T.tm * BM), row_b = (int)(T.tn * bnp);
-    const int ch = chunk_of(sc, T);
-    for (int c0 = T.kb_lo; c0 < T.kb_hi && ok; c0 += ch) {
-    const int c1 = c0 + ch < T.kb_hi ? c0 + ch : T.kb_hi;
     for (int di = 0; di < sc.ndiag && ok; ++di) {
       const int kcb = sc.kcb[di];
-      for (int kb0 = c0; kb0 < c1 && ok; kb0 += kcb) {
-        const int kb1 = kb0 + kcb < c1 ? kb0 + kcb : c1;
+      for (int kb0 = T.kb_lo; kb0 < T.kb_hi && ok; kb0 += kcb) {
+        const int kb1 = kb0 + kcb < T.kb_hi ? kb0 + kcb : T.kb_hi;
         for (int p = 0; p < sc.npairs[di] && ok; ++p) {
           // slices are stored [slice][batch][rows][k]
           const int za = sc.pa[di][p] * l + (int)T.il;
@@ -311,7 +278,6 @@ __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap*
           }
         }
       }
-    }
     }
   }
   if (!ok && !*abort) record_timeout(abort, args.status);
@@ -385,13 +351,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         // the MMA's N is this tile's width (the instruction descriptor's N field)
         const uint32_t idesc =
             GROUPED ? ptx::idesc_make(BM, T.P->bn, KIND == PAIR_KIND_BF16 ? 1u : 2u) : Cfg::IDESC;
-        const int ch = chunk_of(sc, T);
-        for (int c0 = T.kb_lo; c0 < T.kb_hi && ok; c0 += ch) {
-        const int c1 = c0 + ch < T.kb_hi ? c0 + ch : T.kb_hi;
         for (int di = 0; di < sc.ndiag && ok; ++di) {
           const int kcb = sc.kcb[di];
-          for (int kb0 = c0; kb0 < c1 && ok; kb0 += kcb) {
-            const int kb1 = kb0 + kcb < c1 ? kb0 + kcb : c1;
+          for (int kb0 = T.kb_lo; kb0 < T.kb_hi && ok; kb0 += kcb) {
+            const int kb1 = kb0 + kcb < T.kb_hi ? kb0 + kcb : T.kb_hi;
             if (!ptx::mbar_wait(&tempty[acc], accph ^ 1, lim, abort)) { ok = false; break; }
             ptx::tc_fence_after();
             const uint32_t dt = tmem_base + acc * BN;
@@ -420,7 +383,6 @@ __global__ void __launch_bounds__(THREADS, 1)
             acc ^= 1;
             if (acc == 0) accph ^= 1;
           }
-        }
         }
       }
       if (!ok && !*abort) record_timeout(abort, args.status);
@@ -497,27 +459,30 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
       } else {
-        // fp64 split: int32 running sums per diagonal, int64 tile sums in G
-        // (64-wide tiles: in registers, XR).
-        constexpr bool XREG = BN == 64;
+        // fp64 split: int32 running sums per diagonal, two int64 tile sums:
+        // Xt in units of 2^-xunit (the diagonals whose weight is at least
+        // that) and Lt in units of 2^-xlo (the finer ones), so that every
+        // flush is an exact shift however long K is and however many
+        // splits share a tile.
         int32_t S[CPT];
-        int64_t XR[XREG ? CPT : 1];
 #pragma unroll
         for (int j = 0; j < CPT; ++j) S[j] = 0;
-        // tile sums: per CTA for a whole tile; for a split of a tail tile the
-        // tile's slot, shared by its splits through the reductions and
-        // finished by k_split_finish
+        // tile sums: a slot per CTA for a whole tile; for a split of a tail
+        // tile the tile's slot, shared by its splits through the reductions
+        // and finished by k_split_finish.  A slot holds the coarse sums, then
+        // the fine ones (BM x BN each); the fine diagonals are di < nlow (the
+        // walk runs from the least significant diagonal up).
         const bool part_item = SPLITK && T.split >= 0;
-        int64_t* Xt = (part_item ? args.xtail + (size_t)(T.tile - args.full) * BM * BN
-                                 : (int64_t*)args.G + (size_t)blockIdx.x * BM * BN) +
+        constexpr bool FINE = MODE == PAIR_MODE_EMU_FINE;
+        constexpr size_t slot = (size_t)BM * BN * (FINE ? 2 : 1);
+        int64_t* Xt = (part_item ? args.xtail + (size_t)(T.tile - args.full) * slot
+                                 : (int64_t*)args.G + (size_t)blockIdx.x * slot) +
                       (size_t)(hf * CPT) * BM + qd * 32 + lane;
         bool first_flush = true;
-        const int ch = chunk_of(sc, T);
-        for (int c0 = T.kb_lo; c0 < T.kb_hi && ok; c0 += ch) {
-        const int c1 = c0 + ch < T.kb_hi ? c0 + ch : T.kb_hi;
         for (int di = 0; di < sc.ndiag && ok; ++di) {
           const int kcb = sc.kcb[di];
-          const int nunits = (c1 - c0 + kcb - 1) / kcb;
+          const int nunits = (nkb + kcb - 1) / kcb;
+          if (FINE && di == sc.nlow) first_flush = true;  // the first diagonal of the coarse sums
           for (int u = 0; u < nunits; ++u) {
             if (!ptx::mbar_wait(&tfull[acc], accph, lim, abort)) { ok = false; break; }
             ptx::tc_fence_after();
@@ -538,35 +503,26 @@ __global__ void __launch_bounds__(THREADS, 1)
             acc ^= 1;
             if (acc == 0) accph ^= 1;
             if (!flush) continue;
-            // X += S * 2^xshift in int64 (exact, order-free): in registers
-            // for 64-wide tiles; otherwise the first flush of a tile
-            // stores, later ones are fire-and-forget reductions performed
-            // at L2, so no flush waits on memory.
+            // sum += S * 2^xshift in int64 (exact, order-free): the first
+            // flush into a tile's sum stores, later ones are fire-and-forget
+            // reductions performed at L2, so no flush waits on memory.
             {
               const int xs = sc.xshift[di];
+              int64_t* D = (FINE && di < sc.nlow) ? Xt + (size_t)BM * BN : Xt;
+              const bool first = first_flush && !part_item;
 #pragma unroll
               for (int j = 0; j < CPT; ++j) {
                 int64_t v = (int64_t)S[j];
                 v = xs >= 0 ? (int64_t)((uint64_t)v << xs) : ((v + ((int64_t)1 << (-xs - 1))) >> (-xs));
-                if (XREG) XR[XREG ? j : 0] = first_flush ? v : XR[XREG ? j : 0] + v;
-                else if (first_flush && !part_item) Xt[(size_t)j * BM] = v;
-                else atomicAdd((unsigned long long*)(Xt + (size_t)j * BM), (unsigned long long)v);
+                if (first) D[(size_t)j * BM] = v;
+                else atomicAdd((unsigned long long*)(D + (size_t)j * BM), (unsigned long long)v);
                 S[j] = 0;
               }
               first_flush = false;
             }
-            if (!(last_unit && di == sc.ndiag - 1 && c1 == T.kb_hi)) continue;  // not the item's end
-            if (XREG && part_item) {  // a split's register sums join its tile's slot
-#pragma unroll
-              for (int j = 0; j < CPT; ++j)
-                atomicAdd((unsigned long long*)(Xt + (size_t)j * BM), (unsigned long long)XR[XREG ? j : 0]);
-              continue;
-            }
-            if (part_item || !rv || P.fa[il * P.m + row]) continue;
-            if constexpr (XREG) finish_regs<CPT>(P, XR, sc.xunit, il, row, crow, col0, lc0, bnp);
-            else finish_tile<CPT>(P, Xt, sc.xunit, il, row, crow, col0, lc0, bnp);
+            if (part_item || !(last_unit && di == sc.ndiag - 1) || !rv || P.fa[il * P.m + row]) continue;
+            finish_tile<CPT, FINE>(P, Xt, sc, il, row, crow, col0, lc0, bnp);
           }
-        }
         }
       }
     }
@@ -634,10 +590,11 @@ __global__ void __launch_bounds__(256) k_split_reduce(const float* __restrict__ 
 // C = alpha * 2^(e_m + e_n - xunit) * sum + beta * C (rows and columns
 // holding Inf/NaN are left to the native fix-up).
 __global__ void __launch_bounds__(256) k_split_finish(const int64_t* __restrict__ X, int64_t full,
-                                                     int bn, int xunit, Prob P) {
+                                                     int bn, int xunit, int xlo, int nlow, Prob P) {
   const int chunks = bn / SPLIT_COLS;
   const int64_t items = (prob_tiles(P, bn) - full) * chunks;
-  const size_t per = (size_t)BM * bn;
+  const size_t per = (size_t)BM * bn, slot = per * (nlow ? 2 : 1);
+  const double lsc = ldexp(1.0, xunit - xlo);
   double* C = (double*)P.c;
   const int lr = threadIdx.x % BM, lq = threadIdx.x / BM;
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
@@ -649,7 +606,7 @@ __global__ void __launch_bounds__(256) k_split_finish(const int64_t* __restrict_
     if (row >= P.m || P.fa[il * P.m + row]) continue;
     const int64_t crow = P.cl[il] + P.cm[row];
     const int er = P.ea[il * P.m + row] - xunit;
-    int64_t x[SPLIT_PER_THREAD], off[SPLIT_PER_THREAD];
+    int64_t x[SPLIT_PER_THREAD], xl[SPLIT_PER_THREAD], off[SPLIT_PER_THREAD];
     int ec[SPLIT_PER_THREAD];
     double old[SPLIT_PER_THREAD];
 #pragma unroll
@@ -659,13 +616,16 @@ __global__ void __launch_bounds__(256) k_split_finish(const int64_t* __restrict_
       const bool ok = col < P.n && !P.fb[il * P.n + col] && tri_keep(P.tri, row, col);
       off[j] = ok ? crow + P.cn[col] : -1;
       ec[j] = ok ? P.eb[il * P.n + col] : 0;
-      x[j] = X[(size_t)ti * per + (size_t)lc * BM + lr];
+      // a tile's slot: coarse sums, then fine sums (see the product's epilogue)
+      const size_t at = (size_t)ti * slot + (size_t)lc * BM + lr;
+      x[j] = X[at];
+      xl[j] = nlow ? X[at + per] : 0;
     }
 #pragma unroll
     for (int j = 0; j < SPLIT_PER_THREAD; ++j) old[j] = (off[j] >= 0 && P.beta != 0.0) ? C[off[j]] : 0.0;
 #pragma unroll
     for (int j = 0; j < SPLIT_PER_THREAD; ++j) {
-      const double xd = (double)x[j];
+      const double xd = (double)x[j] + (double)xl[j] * lsc;
       const int e = er + ec[j];
       const long long xb = __double_as_longlong(xd);
       const int ex = (int)((xb >> 52) & 0x7FF);
@@ -835,8 +795,9 @@ Layout layout_of(const Plan& p) {
     L.lb = off; off += up((size_t)(p.l * p.n + 1) * 4);
     // per-CTA tile sums; split K adds one slot per tail tile
     const SplitPlan sp = split_plan(p, bn);
-    L.G = off; off += up((size_t)grid_of(p, bn) * BM * bn * 8);
-    L.xtail = off; off += up((size_t)sp.tail * BM * bn * 8);
+    // two int64 sums per element (coarse and fine diagonals)
+    L.G = off; off += up((size_t)2 * grid_of(p, bn) * BM * bn * 8);
+    L.xtail = off; off += up((size_t)2 * sp.tail * BM * bn * 8);
   } else {
     const int bn = pair_bn_for(p.n, p.tile_n);
     const SplitPlan sp = split_plan(p, bn);
@@ -893,6 +854,8 @@ template <bool GROUPED>
 cudaError_t launch_pair_any(int kind, int mode, int bn, const CUtensorMap& ma,
                             const CUtensorMap& mb, const PairArgs& a, int grid, cudaStream_t s) {
   if (mode == PAIR_MODE_EMU) return launch_pair_bn<PAIR_KIND_BF16, PAIR_MODE_EMU, GROUPED>(bn, ma, mb, a, grid, s);
+  if (mode == PAIR_MODE_EMU_FINE)
+    return launch_pair_bn<PAIR_KIND_BF16, PAIR_MODE_EMU_FINE, GROUPED>(bn, ma, mb, a, grid, s);
   if (kind == PAIR_KIND_TF32)
     return launch_pair_bn<PAIR_KIND_TF32, PAIR_MODE_F32OUT, GROUPED>(bn, ma, mb, a, grid, s);
   return launch_pair_bn<PAIR_KIND_BF16, PAIR_MODE_F32OUT, GROUPED>(bn, ma, mb, a, grid, s);
@@ -961,7 +924,7 @@ int pair_bn_for(int64_t n, int request) {
 // Unit schedule.  fp64 split with s slices of b bits: diagonal q = i + j
 // (0-based slice indices, i + j <= s - 1) has weight 2^(-b (q + 2)); a unit
 // covers kcb 64-wide k blocks so that its exact integer sum stays <= 2^24.
-Sched make_pair_sched(int kernel, int slices, int bits, int64_t k) {
+Sched make_pair_sched(int kernel, int slices, int bits, int64_t k, int64_t parts) {
   const int stage_k = pair_stage_k(PAIR_KIND_BF16);  // the fp64 split's slices are bf16
   Sched sc;
   std::memset(&sc, 0, sizeof(sc));
@@ -1013,7 +976,38 @@ Sched make_pair_sched(int kernel, int slices, int bits, int64_t k) {
   int xunit = (int)std::floor(62.0 - std::log2(T)) - 1;
   if (xunit > sc.shift[0]) xunit = sc.shift[0];  // di = 0 is the least significant diagonal
   sc.xunit = xunit;
-  for (int di = 0; di < s; ++di) sc.xshift[di] = xunit - sc.shift[di];
+  // Diagonals finer than 2^-xunit are rounded to it at each flush (at most
+  // half a unit) if they go into the coarse sum.  The digits themselves
+  // carry each scaled element to 2^-(bits*slices), so over k terms the
+  // split's own error grows like sqrt(k) 2^-(bits*slices) and the flushes'
+  // like sqrt(nflush) 2^-xunit (random walks).  When the latter would pass
+  // a quarter of the former, i.e. nflush 4^(bits*slices - xunit) > k / 16
+  // (long K, many splits sharing a tile), the fine diagonals get a second,
+  // exact sum in units of 2^-xlo (their own finest weight, unless K makes
+  // even their sum too large).
+  const int64_t kk = k < 1 ? 1 : k, np = parts < 1 ? 1 : parts;
+  const int64_t kpart = (kk + np - 1) / np, nkb_part = (kpart + stage_k - 1) / stage_k;
+  double TL = 0.0, nflush = 0.0;
+  int nfine = 0;
+  for (int di = 0; di < s; ++di) {
+    if (sc.shift[di] <= xunit) continue;
+    ++nfine;
+    const int q = s - 1 - di;
+    int64_t bound = 0;
+    for (int i = 0; i <= q; ++i) bound += maxd(i) * maxd(q - i);
+    TL += std::ldexp((double)kk * (double)bound, -sc.shift[di]);
+    const int64_t units = (nkb_part + sc.kcb[di] - 1) / sc.kcb[di];
+    nflush += (double)np * (double)((units + sc.flush_every[di] - 1) / sc.flush_every[di]);
+  }
+  const bool fine = nfine > 0 && nflush * std::ldexp(1.0, 2 * (bits * s - xunit)) > (double)kk / 16.0;
+  sc.xlo = sc.shift[0];
+  if (fine && TL > 0.0) {
+    const int cap = (int)std::floor(62.0 - std::log2(TL)) - 1;
+    if (sc.xlo > cap) sc.xlo = cap;
+  }
+  sc.nlow = fine ? nfine : 0;  // shifts fall as di rises, so the fine diagonals are di < nlow
+  for (int di = 0; di < s; ++di)
+    sc.xshift[di] = (di < sc.nlow ? sc.xlo : xunit) - sc.shift[di];
   return sc;
 }
 
@@ -1032,6 +1026,7 @@ cudaError_t launch_pair_grouped(int kind, int mode, int bn, const Prob* probs,
   a.wait_limit = wait_limit;
   CUtensorMap unused;
   std::memset(&unused, 0, sizeof(unused));
+  if (mode == PAIR_MODE_EMU && sc.nlow) mode = PAIR_MODE_EMU_FINE;
   return launch_pair_any<true>(kind, mode, bn, unused, unused, a, grid, s);
 }
 
@@ -1139,12 +1134,9 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     a.single.tri_list = list;
     a.single.tri_tiles = tri_tile_count(p, bn);
   }
-  a.sc = make_pair_sched(p.kernel, p.slices, bits, p.k);
-  // fp64 split on 64-wide tiles: chunks of 256 k (the slices an item reads
-  // for one chunk, over all the CTAs, stay well inside L2)
-  if (emu && bn == 64) a.sc.chunk = 4;
-  a.G = emu ? (double*)(w + L.G) : nullptr;
   const SplitPlan spl = split_plan(p, bn);
+  a.sc = make_pair_sched(p.kernel, p.slices, bits, p.k, spl.splits);
+  a.G = emu ? (double*)(w + L.G) : nullptr;
   a.splits = spl.splits;
   a.full = spl.full;
   a.xtail = emu && spl.splits > 1 ? (int64_t*)(w + L.xtail) : nullptr;
@@ -1155,14 +1147,16 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   const int grid = grid_of(p, bn);
   const int split_grid = (int)std::min<int64_t>(spl.tail * (bn / SPLIT_COLS), (int64_t)num_sms() * 16);
   if (emu && a.splits > 1 &&
-      (e = cudaMemsetAsync(a.xtail, 0, (size_t)spl.tail * BM * bn * 8, s)) != cudaSuccess)
+      (e = cudaMemsetAsync(a.xtail, 0, (size_t)(a.sc.nlow ? 2 : 1) * spl.tail * BM * bn * 8, s)) != cudaSuccess)
     return e;
   mark_begin(g, s);
-  e = launch_pair_any<false>(kind, emu ? PAIR_MODE_EMU : PAIR_MODE_F32OUT, bn, ma, mb, a, grid, s);
+  const int mode = emu ? (a.sc.nlow ? PAIR_MODE_EMU_FINE : PAIR_MODE_EMU) : PAIR_MODE_F32OUT;
+  e = launch_pair_any<false>(kind, mode, bn, ma, mb, a, grid, s);
   mark_end(g, s);  // the events bracket the product kernel alone
   if (e == cudaSuccess && a.splits > 1) {
     if (emu)
-      k_split_finish<<<split_grid, 256, 0, s>>>(a.xtail, a.full, bn, a.sc.xunit, a.single);
+      k_split_finish<<<split_grid, 256, 0, s>>>(a.xtail, a.full, bn, a.sc.xunit, a.sc.xlo, a.sc.nlow,
+                                                a.single);
     else
       k_split_reduce<<<split_grid, 256, 0, s>>>(a.part, a.splits, a.full, bn, a.single);
     e = cudaGetLastError();

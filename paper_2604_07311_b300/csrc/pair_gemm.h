@@ -16,7 +16,9 @@ constexpr int kPairBM = 128;      // rows of an output tile
 constexpr int kPairMaxDiag = 10;
 
 enum { PAIR_KIND_BF16 = 0, PAIR_KIND_TF32 = 1 };
-enum { PAIR_MODE_F32OUT = 0, PAIR_MODE_EMU = 1 };
+// fp32 output; fp64 split with one int64 sum per output; fp64 split with a
+// second, exact sum for the fine diagonals (Sched::nlow > 0)
+enum { PAIR_MODE_F32OUT = 0, PAIR_MODE_EMU = 1, PAIR_MODE_EMU_FINE = 2 };
 
 // The unit schedule of one output tile (identical for every tile of a launch).
 struct Sched {
@@ -27,14 +29,14 @@ struct Sched {
   int flush_every[kPairMaxDiag];  // units between flushes of the int32 sums
   int npairs[kPairMaxDiag];
   int8_t pa[kPairMaxDiag][8], pb[kPairMaxDiag][8];  // slice of A and B in each pair
-  // fp64 split: the tile sums are int64 in units of 2^-xunit; a diagonal's
-  // int32 sums enter them shifted by xshift (a right shift, rounded, when
-  // negative).  xunit is as fine as K allows without int64 overflow.
-  int xunit;
+  // fp64 split: int64 sums per output in units of 2^-xunit (as fine as K
+  // allows without overflow) and, when nlow > 0, a second one in units of
+  // 2^-xlo for the nlow diagonals finer than 2^-xunit (di < nlow: the walk
+  // starts from the least significant).  A diagonal's int32 sums enter its
+  // sum shifted by xshift: left (exact), or right with rounding for a fine
+  // diagonal folded into the coarse sum (nlow = 0).
+  int xunit, xlo, nlow;
   int xshift[kPairMaxDiag];
-  // k blocks per chunk (fp64 split, 64-wide tiles, whose sums stay in
-  // registers so that chunk boundaries cost no memory traffic); 0: one chunk
-  int chunk;
 };
 
 // What the product needs to know about one problem.
@@ -65,8 +67,9 @@ struct TileEntry {
   int32_t p, tm, tn, il;
 };
 
-// k: the largest contracted extent the schedule serves (bounds the tile sums).
-Sched make_pair_sched(int kernel, int slices, int bits, int64_t k);
+// k: the largest contracted extent the schedule serves (bounds the tile sums);
+// parts: the work items that share one tile's sums (its K splits).
+Sched make_pair_sched(int kernel, int slices, int bits, int64_t k, int64_t parts = 1);
 int pair_bn_for(int64_t n, int request);
 // 3-D map over slices [z][rows][kp] (k innermost), box {box_k, box_rows, 1}.
 bool make_slice_map(CUtensorMap* map, void* base, bool f32, int64_t k, int64_t kp, int64_t rows,

@@ -138,3 +138,29 @@ def test_hooi_projection_as_a_network(dtype):
     want = np.zeros((I, Q, S))
     oracle.contract(1.0, T, W.L("iqk"), U2.view(), W.L("ks"), 0.0, want, W.L("iqs"))
     assert rel_frob(Yd.to(torch.float64).cpu().numpy(), want) <= TOL[dtype]
+
+
+def test_mttkrp_full_size_every_mode_sampled_dot2():
+    """The benchmark's shape, X 512^3 fp64 with R = 64 (K = 262144),
+    emulated fp64, every mode, on 512 sampled entries of M evaluated by the
+    oracle with the compensated dot product over the oracle's Khatri-Rao
+    product (a plain fp64 sum of 262144 random-sign terms is itself off by
+    ~1e-12 relative)."""
+    rng = np.random.default_rng(1260)
+    I, R = 512, 64
+    X = rng.standard_normal((I, I, I))
+    U = [rng.standard_normal((I, R)) for _ in range(3)]
+    Xd = torch.from_numpy(X).cuda()
+    Ud = [torch.from_numpy(u).cuda().t().contiguous().t() for u in U]
+    L = [1, 2, 3]
+    for mode in range(3):
+        Md = torch.zeros(R, I, dtype=torch.float64, device="cuda").t()
+        fm.mttkrp(1.0, Xd, mode, Ud, 0.0, Md, dtype="f64_emu")
+        torch.cuda.synchronize()
+        KR = oracle.khatri_rao(U, mode, 3)
+        others = [m + 1 for m in range(3) if m != mode]
+        idx = np.stack([rng.integers(0, I, size=512), rng.integers(0, R, size=512)], axis=1)
+        want = oracle.entries(1.0, X, L, KR, others + [9], 0.0, np.zeros((I, R)), [mode + 1, 9], idx,
+                              dot2=True)
+        got = Md.cpu().numpy()[idx[:, 0], idx[:, 1]]
+        assert rel_frob(got, want) <= 1e-13

@@ -135,3 +135,25 @@ def test_scale_only_and_empty(dtype):
     fm.gemmt_tridiag(1.0, E, sd, dd, ud, 1.0, torch.empty((0, 0), dtype=torch.float64, device="cuda"),
                      dtype=dtype)
     torch.cuda.synchronize()
+
+
+def test_full_size_panel_update():
+    """The benchmark's panel update, n = 16384, k = 256, emulated fp64 in the
+    launch configuration the benchmark times, against the oracle on the
+    whole lower triangle."""
+    rng = np.random.default_rng(1010)
+    n, k = 16384, 256
+    A = rng.standard_normal((n, k))
+    sub = rng.standard_normal(k - 1)
+    Ad = torch.from_numpy(A).cuda().t().contiguous().t()
+    sd = torch.from_numpy(sub).cuda()
+    C = rng.standard_normal((n, n))
+    Cd = torch.from_numpy(C).cuda().t().contiguous().t()
+    fm.gemmt_tridiag(-1.0, Ad, sd, None, None, 1.0, Cd, dtype="f64_emu")
+    torch.cuda.synchronize()
+    got = Cd.cpu().numpy()
+    del Cd
+    want = oracle.gemmt_tridiag(-1.0, A, sub, None, None, 1.0, C.copy())
+    low = np.tril(np.ones((n, n), dtype=bool))
+    assert np.array_equal(got[~low], C[~low])
+    assert rel_frob(got[low], want[low]) <= 1e-13

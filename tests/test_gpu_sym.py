@@ -133,3 +133,29 @@ def test_nan_in_the_triangle_reaches_both_mirrored_rows():
     assert np.isnan(want).any()
     fin = ~np.isnan(want)
     assert rel_frob(got[fin], want[fin]) <= TOL
+
+
+def test_full_size_ladder_packed_matches_dense_bit_for_bit():
+    """v = 128, o = 32 (the benchmark's ladder): V read from its packed
+    triangle gives the same slices, exponents and tile order as dense V, so
+    the result is bit-identical to the dense path's (which the full-size
+    sampled test checks against the oracle), and sampled entries match the
+    oracle."""
+    p = W.ladder(v=128, o=32)
+    n = 128 * 128
+    M = p.A.buf.reshape(n, n)  # symmetric: either flattening
+    Ap = torch.from_numpy(W.packed_lower(M)).cuda()
+    T = to_device(p.B, torch.float64)
+    Cs = to_device(p.C, torch.float64)
+    Cd = to_device(p.C, torch.float64)
+    Vd = to_device(p.A, torch.float64)
+    fm.contract_sym(p.alpha, Ap, p.A.extents, p.A.labels, T, p.B.labels, p.beta, Cs, p.C.labels)
+    fm.contract(p.alpha, Vd, p.A.labels, T, p.B.labels, p.beta, Cd, p.C.labels, dtype="f64_emu")
+    torch.cuda.synchronize()
+    assert torch.equal(Cs, Cd)
+    rng = np.random.default_rng(860)
+    idx = np.stack([rng.integers(0, e, size=256) for e in p.C.extents], axis=1)
+    want = oracle.entries(p.alpha, p.A.view(), p.A.labels, p.B.view(), p.B.labels, p.beta, p.C.view(),
+                          p.C.labels, idx, dot2=True)
+    got = Cs.cpu().numpy()[tuple(idx.T)]
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
