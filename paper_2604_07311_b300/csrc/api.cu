@@ -461,6 +461,148 @@ int famlies_contract(double alpha, const famlies_tensor_t* A, const famlies_tens
   return famlies_contract_ex(alpha, A, B, beta, C, dtype, stream, nullptr, nullptr);
 }
 
+namespace {
+
+// The copy stream of a device (for host calls whose copies overlap compute).
+cudaStream_t copy_stream() {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    streams[dev] = nullptr;
+  }
+  return streams[dev];
+}
+
+int find_label(const famlies_tensor_t* t, int32_t label) {
+  for (int i = 0; i < t->ndim; ++i)
+    if (t->labels[i] == label) return i;
+  return -1;
+}
+
+// Host-buffer contraction whose larger input X sits in pinned memory and is
+// large: X is copied in chunks along its outermost mode on a copy stream,
+// and each chunk's contraction runs on the call's stream as soon as its
+// bytes have landed, so the transfers and the kernels overlap.  A chunk of
+// a contracted label adds into C (beta for the first chunk, then 1); a
+// chunk of a free or batch label writes its own part of C.  Returns 1 when
+// the path does not apply (the caller then copies whole operands).
+int contract_host_chunked(double alpha, const famlies_tensor_t* A, const famlies_tensor_t* B, double beta,
+                          const famlies_tensor_t* C, famlies_dtype_t dtype, cudaStream_t s,
+                          const famlies_options_t* opt, const Plan& p) {
+  constexpr int kChunks = 8;
+  constexpr int64_t kMinChunkBytes = (int64_t)64 << 20;
+  if (p.kernel == FAMLIES_KERNEL_SCALE) return 1;
+  const int64_t span_a = p.swapped ? p.span_b : p.span_a, span_b = p.swapped ? p.span_a : p.span_b;
+  const int es_a = p.swapped ? p.es_b : p.es_a, es_b = p.swapped ? p.es_a : p.es_b;
+  const bool x_is_a = span_a * es_a >= span_b * es_b;
+  const famlies_tensor_t* X = x_is_a ? A : B;
+  const famlies_tensor_t* Y = x_is_a ? B : A;
+  const int64_t span_x = x_is_a ? span_a : span_b, span_y = x_is_a ? span_b : span_a;
+  const int es_x = x_is_a ? es_a : es_b, es_y = x_is_a ? es_b : es_a;
+  if (span_x * es_x < kChunks * kMinChunkBytes) return 1;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, X->data) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (at.type != cudaMemoryTypeHost) return 1;  // pageable: copies would not overlap
+  // the outermost mode: chunks along it must be disjoint ranges of memory
+  int m = 0;
+  for (int i = 1; i < X->ndim; ++i)
+    if (X->strides[i] > X->strides[m]) m = i;
+  const int64_t ext = X->extents[m], st = X->strides[m];
+  int64_t rest = 1;
+  for (int i = 0; i < X->ndim; ++i)
+    if (i != m) rest += (X->extents[i] - 1) * X->strides[i];
+  if (ext < 2 || st < rest) return 1;
+  cudaStream_t sc = copy_stream();
+  if (!sc) return 1;
+  const int nch = (int)(ext < kChunks ? ext : kChunks);
+  const int iy = find_label(Y, X->labels[m]), ic = find_label(C, X->labels[m]);
+
+  const int64_t bytes_x = span_x * es_x, bytes_y = span_y * es_y, bytes_c = p.span_c * p.es_c;
+  auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
+  void* dev = nullptr;
+  if (cudaMallocAsync(&dev, up(bytes_x) + up(bytes_y) + up(bytes_c) + 256, s) != cudaSuccess) {
+    cudaGetLastError();
+    return FAMLIES_ERR_ALLOC;
+  }
+  char* dx = (char*)dev;
+  char* dy = dx + up(bytes_x);
+  char* dc = dy + up(bytes_y);
+  int64_t entries_c = 1;
+  for (int i = 0; i < C->ndim; ++i) entries_c *= C->extents[i];
+  const bool copy_c_in = beta != 0.0 || entries_c != p.span_c;
+  std::vector<cudaEvent_t> ev(nch + 1, nullptr);
+  for (auto& e : ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  cudaError_t e = cudaSuccess;
+  int rc = FAMLIES_OK;
+  // All host-to-device copies go in order on the copy stream (one copy
+  // engine serves them in that order): the smaller input and C first, which
+  // every chunk needs, then X's chunks; chunk i's contraction waits for its
+  // copy only.  The copy stream starts once the workspace exists.
+  e = cudaEventRecord(ev[nch], s);
+  if (!e) e = cudaStreamWaitEvent(sc, ev[nch], 0);
+  if (!e && bytes_y) e = cudaMemcpyAsync(dy, Y->data, bytes_y, cudaMemcpyHostToDevice, sc);
+  if (!e && copy_c_in) e = cudaMemcpyAsync(dc, C->data, bytes_c, cudaMemcpyHostToDevice, sc);
+  for (int i = 0; i < nch && !e; ++i) {
+    const int64_t e0 = ext * i / nch, e1 = ext * (i + 1) / nch;
+    const int64_t off = e0 * st * es_x, nb = ((e1 - e0 - 1) * st + rest) * es_x;
+    e = cudaMemcpyAsync(dx + off, (const char*)X->data + off, nb, cudaMemcpyHostToDevice, sc);
+    if (!e) e = cudaEventRecord(ev[i], sc);
+  }
+  int64_t ex_x[FAMLIES_MAX_NDIM], ex_y[FAMLIES_MAX_NDIM], ex_c[FAMLIES_MAX_NDIM];
+  for (int i = 0; i < nch && !e && !rc; ++i) {
+    const int64_t e0 = ext * i / nch, e1 = ext * (i + 1) / nch;
+    famlies_tensor_t xi = *X, yi = *Y, ci = *C;
+    std::memcpy(ex_x, X->extents, sizeof(int64_t) * X->ndim);
+    std::memcpy(ex_y, Y->extents, sizeof(int64_t) * Y->ndim);
+    std::memcpy(ex_c, C->extents, sizeof(int64_t) * C->ndim);
+    ex_x[m] = e1 - e0;
+    xi.extents = ex_x;
+    xi.data = dx + e0 * st * es_x;
+    yi.data = dy;
+    if (iy >= 0) {
+      ex_y[iy] = e1 - e0;
+      yi.data = dy + e0 * Y->strides[iy] * es_y;
+    }
+    yi.extents = ex_y;
+    ci.data = dc;
+    if (ic >= 0) {
+      ex_c[ic] = e1 - e0;
+      ci.data = dc + e0 * C->strides[ic] * p.es_c;
+    }
+    ci.extents = ex_c;
+    xi.size_bytes = yi.size_bytes = ci.size_bytes = 0;
+    const double bi = (ic >= 0 || i == 0) ? beta : 1.0;  // a contracted label accumulates
+    e = cudaStreamWaitEvent(s, ev[i], 0);
+    if (e) break;
+    Plan pc;
+    rc = make_plan(alpha, x_is_a ? &xi : &yi, x_is_a ? &yi : &xi, &ci, dtype, opt, &pc);
+    if (!rc) rc = run_plan(pc, alpha, bi, s, opt, nullptr);
+  }
+  if (!e && !rc) e = cudaMemcpyAsync(C->data, dc, bytes_c, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(dev, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  cudaError_t e3 = cudaStreamSynchronize(sc);
+  for (auto& v : ev) cudaEventDestroy(v);
+  if (rc) return rc;
+  if (e != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+    cudaGetLastError();
+    return FAMLIES_ERR_CUDA;
+  }
+  return FAMLIES_OK;
+}
+
+}  // namespace
+
 int famlies_contract_host(double alpha, const famlies_tensor_t* A, const famlies_tensor_t* B,
                           double beta, const famlies_tensor_t* C, famlies_dtype_t dtype,
                           void* stream, const famlies_options_t* opt) {
@@ -470,6 +612,7 @@ int famlies_contract_host(double alpha, const famlies_tensor_t* A, const famlies
   if (p.kernel == FAMLIES_KERNEL_NONE) return FAMLIES_OK;
   if ((rc = check_device())) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = contract_host_chunked(alpha, A, B, beta, C, dtype, s, opt, p)) != 1) return rc;
   // Spans in the caller's operand order (the plan may have swapped roles).
   const int64_t span_a = p.swapped ? p.span_b : p.span_a;
   const int64_t span_b = p.swapped ? p.span_a : p.span_b;
