@@ -33,7 +33,7 @@ METRIC = "contraction TFLOP/s, % tensor-pipe peak; split-precision vs FP64 speed
 # profiles/k_pair_gemm_ladder.md (v=112 ladder, 11.58 GB, the same split-K
 # kernel; scaled by executed flops to the v=128 launch).  Must go back to None
 # whenever the product kernel changes after that capture.
-PRODUCT_TRAFFIC = {"bytes": 11.575240e9, "exec_flops": 6.767392063488e12}
+PRODUCT_TRAFFIC = {"bytes": 11.566092e9, "exec_flops": 6.767392063488e12}
 V_EXT, O_EXT, SLICES = 128, 32, 6
 WORKLOAD = f"ccsd_ladder_v128_o32_f64_split{SLICES}"
 
