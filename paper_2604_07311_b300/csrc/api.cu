@@ -237,6 +237,11 @@ int famlies_contract_sym(double alpha, const famlies_symtensor_t* A, const famli
     return run_plan(p, alpha, beta, (cudaStream_t)stream, &o, info);  // A is not read
   if (p.kernel != FAMLIES_KERNEL_TC_EMU) return FAMLIES_ERR_UNSUPPORTED;
   if (!A->data) return FAMLIES_ERR_INVALID_ARG;
+  if (n == 1) {  // a 1 x 1 triangle is its own dense matrix
+    dense.data = const_cast<void*>(A->data);
+    dense.size_bytes = A->size_bytes;
+    return famlies_contract_ex(alpha, &dense, B, beta, C, dtype, stream, &o, info);
+  }
   {
     const int64_t sc = p.span_c * p.es_c;
     const char* c0 = (const char*)C->data;

@@ -164,3 +164,29 @@ def test_mttkrp_full_size_every_mode_sampled_dot2():
                               dot2=True)
         got = Md.cpu().numpy()[idx[:, 0], idx[:, 1]]
         assert rel_frob(got, want) <= 1e-13
+
+
+def test_mttkrp_degenerate_shapes():
+    """R = 0 (nothing to write), an empty contracted mode (M := beta M), and
+    an extent-1 mode (dropped from the Khatri-Rao digits)."""
+    X = torch.rand(5, 0, 4, dtype=torch.float64, device="cuda")
+    U = [torch.rand(5, 3, dtype=torch.float64, device="cuda"), torch.rand(0, 3, dtype=torch.float64, device="cuda"),
+         torch.rand(4, 3, dtype=torch.float64, device="cuda")]
+    M = torch.rand(5, 3, dtype=torch.float64, device="cuda")
+    M0 = M.clone()
+    fm.mttkrp(1.0, X, 0, U, 0.5, M, dtype="f64_emu")
+    torch.cuda.synchronize()
+    assert torch.equal(M, 0.5 * M0)
+    E = torch.empty(5, 0, dtype=torch.float64, device="cuda")
+    X2 = torch.rand(5, 4, 6, dtype=torch.float64, device="cuda")
+    fm.mttkrp(1.0, X2, 0, [None, torch.empty(4, 0, dtype=torch.float64, device="cuda"),
+                           torch.empty(6, 0, dtype=torch.float64, device="cuda")], 0.0, E, dtype="f64_emu")
+    rng = np.random.default_rng(1270)
+    Xh = rng.uniform(-1, 1, size=(30, 1, 20))
+    Uh = [rng.uniform(-1, 1, size=(e, 7)) for e in (30, 1, 20)]
+    Md = torch.zeros(7, 30, dtype=torch.float64, device="cuda").t()
+    fm.mttkrp(1.0, torch.from_numpy(Xh).cuda(), 0, [None] + [torch.from_numpy(u).cuda() for u in Uh[1:]], 0.0,
+              Md, dtype="f64_emu")
+    torch.cuda.synchronize()
+    want = oracle.mttkrp(1.0, Xh, 0, Uh, 0.0, np.zeros((30, 7)))
+    assert rel_frob(Md.cpu().numpy(), want) <= 1e-13

@@ -83,3 +83,20 @@ def test_planning_error_launches_nothing():
     assert e.value.code == -3  # FAMLIES_ERR_EXTENT_MISMATCH
     torch.cuda.synchronize()
     assert torch.equal(C, before)
+
+
+def test_empty_network_and_single_step():
+    """No steps: nothing runs; one step equals the plain contraction."""
+    rng = np.random.default_rng(703)
+    A = W.uniform_operand(rng, (20, 30), [1, 2])
+    B = W.uniform_operand(rng, (30, 25), [2, 3])
+    C = W.uniform_operand(rng, (20, 25), [1, 3])
+    Ad, Bd, Cd = (to_device(x, torch.float64) for x in (A, B, C))
+    before = Cd.clone()
+    fm.contract_network([(Ad, [1, 2]), (Bd, [2, 3]), (Cd, [1, 3])], [], dtype="f64_emu")
+    torch.cuda.synchronize()
+    assert torch.equal(Cd, before)
+    fm.contract_network([(Ad, [1, 2]), (Bd, [2, 3]), (Cd, [1, 3])], [(0, 1, 2, 2.0, -1.0)], dtype="f64_emu")
+    torch.cuda.synchronize()
+    want = _oracle_step(2.0, A.view(), [1, 2], B.view(), [2, 3], -1.0, C.view(), [1, 3])
+    assert rel_frob(gpu_dense(Cd), want) <= 1e-13

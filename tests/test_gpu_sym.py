@@ -159,3 +159,19 @@ def test_full_size_ladder_packed_matches_dense_bit_for_bit():
                           p.C.labels, idx, dot2=True)
     got = Cs.cpu().numpy()[tuple(idx.T)]
     assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+def test_degenerate_symmetric_operands():
+    """n = 1 (a 1 x 1 triangle) and an empty free extent of B (nothing to
+    write)."""
+    rng = np.random.default_rng(870)
+    M, Vd = _sym_dense(rng, (1,))
+    B = W.uniform_operand(rng, (1, 9), [2, 3])
+    C = W.uniform_operand(rng, (1, 9), [1, 3])
+    got, _ = _run(2.0, M, (1, 1), [1, 2], B, [2, 3], 0.5, C, [1, 3])
+    assert rel_frob(got, _want(2.0, Vd, [1, 2], B, [2, 3], 0.5, C, [1, 3])) <= TOL
+    Ap = torch.from_numpy(W.packed_lower(M)).cuda()
+    Bd = torch.empty(1, 0, dtype=torch.float64, device="cuda")
+    Cd = torch.empty(1, 0, dtype=torch.float64, device="cuda")
+    fm.contract_sym(1.0, Ap, (1, 1), [1, 2], Bd, [2, 3], 0.0, Cd, [1, 3])
+    torch.cuda.synchronize()
