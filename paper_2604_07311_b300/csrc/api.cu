@@ -85,6 +85,8 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
     extra = packed_workspace_bytes(p);
   else if (p.kernel == FAMLIES_KERNEL_TC_BF16_GATHER || p.kernel == FAMLIES_KERNEL_TC_TF32X3_GATHER)
     extra = tc_workspace_bytes(p);
+  else if (p.kernel == FAMLIES_KERNEL_SIMT_F64 || p.kernel == FAMLIES_KERNEL_SIMT_F32)
+    extra = simt_workspace_bytes(p);
   extra = (extra + 255) / 256 * 256;
   tab_bytes = (tab_bytes + 255) / 256 * 256;
   Workspace ws;
@@ -133,8 +135,8 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
     switch (p.kernel) {
       case FAMLIES_KERNEL_SIMT_F64:
       case FAMLIES_KERNEL_SIMT_F32:
-        err = launch_simt(p, g, s);
-        ++launches;
+        err = launch_simt(p, g, extra ? ws.ptr : nullptr, s);
+        launches += extra ? 2 : 1;  // (+ the split reduction)
         break;
       case FAMLIES_KERNEL_TC_BF16_GATHER:
       case FAMLIES_KERNEL_TC_TF32X3_GATHER:

@@ -43,6 +43,7 @@ struct GemmArgs {
   int tri;                 // 0: all of C; 1: only row >= col; 2: only row <= col
   Krp krp;                 // Khatri-Rao operand (see Plan) is operand krp_op - 1 (0: none)
   int krp_op;
+  void* part;              // CUDA-core split K: partial results [split][l][n][m] (null: none)
   cudaEvent_t ev_begin, ev_end;  // host only: recorded around the product kernel
 };
 
@@ -79,7 +80,10 @@ int read_clear_status(int* value);
 // ---- launchers (each returns a cudaError_t from the launch)
 cudaError_t launch_tables(const Plan& p, int64_t* ws, Tables* t, cudaStream_t s);
 cudaError_t launch_scale(const Plan& p, const Tables& t, double beta, cudaStream_t s);
-cudaError_t launch_simt(const Plan& p, const GemmArgs& g, cudaStream_t s);
+// ws: workspace of simt_workspace_bytes(p) bytes, or null (no K split).
+cudaError_t launch_simt(const Plan& p, const GemmArgs& g, void* ws, cudaStream_t s);
+// Bytes of the partial tiles a CUDA-core launch splits K into (0: no split).
+int64_t simt_workspace_bytes(const Plan& p);
 cudaError_t launch_tc(const Plan& p, const GemmArgs& g, int tile_n, void* ws, cudaStream_t s);
 int64_t tc_workspace_bytes(const Plan& p);
 // Packed paths (bf16, tf32 split, fp64 split): workspace size and launch.

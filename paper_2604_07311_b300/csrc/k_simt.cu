@@ -181,6 +181,9 @@ __global__ void __launch_bounds__(256) k_simt(GemmArgs g) {
   const int64_t tiles_m = (g.m + BM - 1) / BM, tiles_n = (g.n + BN - 1) / BN;
   const int64_t ntiles = tiles_m * tiles_n * g.l;
   const T alpha = (T)g.alpha, beta = (T)g.beta;
+  // split K (blockIdx.y of gridDim.y): this block's k range; its partial
+  // results go to g.part for k_simt_reduce
+  const int64_t kbeg = g.k * blockIdx.y / gridDim.y, kend = g.k * (blockIdx.y + 1) / gridDim.y;
 
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t tm = tile % tiles_m, rest = tile / tiles_m;
@@ -195,12 +198,12 @@ __global__ void __launch_bounds__(256) k_simt(GemmArgs g) {
 #pragma unroll
       for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
 
-    for (int64_t k0 = 0; k0 < g.k; k0 += BK) {
+    for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
       for (int e = tid; e < BM * BK; e += 256) {
         int mm, kk;
         if (g.a_contig == 2) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
         const int64_t gm = m0 + mm, gk = k0 + kk;
-        As[kk][mm] = (gm < g.m && gk < g.k)
+        As[kk][mm] = (gm < g.m && gk < kend)
                          ? (g.band_op == 1   ? band_at<T>(A, al + g.t.am[gm], g.t.ak, 0, gk, g.k, g.band)
                             : g.krp_op == 1 ? krp_at<T>(g.krp, gm, g.t.ak[gk])
                                             : A[al + g.t.am[gm] + g.t.ak[gk]])
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(256) k_simt(GemmArgs g) {
         int nn, kk;
         if (g.b_contig == 2) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
         const int64_t gn = n0 + nn, gk = k0 + kk;
-        Bs[kk][nn] = (gn < g.n && gk < g.k)
+        Bs[kk][nn] = (gn < g.n && gk < kend)
                          ? (g.band_op == 2   ? band_at<T>(B, bl + g.t.bn[gn], g.t.bk, 0, gk, g.k, g.band)
                             : g.krp_op == 2 ? krp_at<T>(g.krp, gn, g.t.bk[gk])
                                             : B[bl + g.t.bn[gn] + g.t.bk[gk]])
@@ -240,6 +243,10 @@ __global__ void __launch_bounds__(256) k_simt(GemmArgs g) {
       for (int j = 0; j < TN; ++j) {
         const int64_t gn = n0 + tx + j * (BN / TN);
         if (gn >= g.n || !tri_keep(g.tri, gm, gn)) continue;
+        if (g.part) {  // a split's partial result, summed by k_simt_reduce
+          ((T*)g.part)[(((size_t)blockIdx.y * g.l + il) * g.n + gn) * g.m + gm] = acc[i][j];
+          continue;
+        }
         T* p = C + crow + g.t.cn[gn];
         T v = alpha * acc[i][j];
         if (beta != T(0)) v = fma(beta, *p, v);
@@ -249,22 +256,85 @@ __global__ void __launch_bounds__(256) k_simt(GemmArgs g) {
   }
 }
 
-cudaError_t launch_simt(const Plan& p, const GemmArgs& g, cudaStream_t s) {
+// Split-K reduction of the CUDA-core kernel: C = alpha * (sum of the
+// splits' partial results, in split order) + beta * C, inside the triangle.
+template <typename T>
+__global__ void __launch_bounds__(256) k_simt_reduce(GemmArgs g, int splits) {
+  const int64_t total = g.m * g.n * g.l;
+  const T* P = (const T*)g.part;
+  T* C = (T*)g.c;
+  const T alpha = (T)g.alpha, beta = (T)g.beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t im = i % g.m, r = i / g.m;
+    const int64_t in = r % g.n, il = r / g.n;
+    if (!tri_keep(g.tri, im, in)) continue;
+    T acc = T(0);
+    for (int sp = 0; sp < splits; ++sp) acc += P[(size_t)sp * total + i];
+    T* p = C + g.t.cl[il] + g.t.cm[im] + g.t.cn[in];
+    T v = alpha * acc;
+    if (beta != T(0)) v = fma(beta, *p, v);
+    *p = v;
+  }
+}
+
+namespace {
+
+// Tile shape and grid of the CUDA-core kernel, and its K splits: a launch
+// with fewer tiles than SMs splits K (at least 256 per split) so that every
+// SM gets work.
+struct SimtShape {
+  int bm, bn, blocks_per_sm;
+  int64_t tiles;
+  int splits;
+};
+
+SimtShape simt_shape(const Plan& p) {
+  SimtShape sh;
+  sh.bm = sh.bn = p.es_a == 8 ? 64 : 128;
+  sh.blocks_per_sm = p.es_a == 8 ? 8 : 4;
+  sh.tiles = ((p.m + sh.bm - 1) / sh.bm) * ((p.n + sh.bn - 1) / sh.bn) * p.l;
+  const int64_t sms = num_sms();
+  int64_t sp = 1;
+  if (sh.tiles < sms) {
+    sp = (2 * sms + sh.tiles - 1) / sh.tiles;
+    const int64_t kmax = p.k / 256;
+    if (sp > kmax) sp = kmax;
+    if (sp > 64) sp = 64;
+    if (sp < 1) sp = 1;
+  }
+  sh.splits = (int)sp;
+  return sh;
+}
+
+}  // namespace
+
+int64_t simt_workspace_bytes(const Plan& p) {
+  const SimtShape sh = simt_shape(p);
+  return sh.splits > 1 ? (int64_t)sh.splits * p.m * p.n * p.l * p.es_c : 0;
+}
+
+cudaError_t launch_simt(const Plan& p, const GemmArgs& g0, void* ws, cudaStream_t s) {
   const int sms = num_sms();
-  if (p.es_a == 8) {
-    constexpr int BM = 64, BN = 64;
-    int64_t tiles = ((p.m + BM - 1) / BM) * ((p.n + BN - 1) / BN) * p.l;
-    int grid = (int)(tiles < (int64_t)sms * 8 ? tiles : (int64_t)sms * 8);
-    mark_begin(g, s);
-    k_simt<double, BM, BN, 16, 4, 4><<<grid, 256, 0, s>>>(g);
-    mark_end(g, s);
-  } else {
-    constexpr int BM = 128, BN = 128;
-    int64_t tiles = ((p.m + BM - 1) / BM) * ((p.n + BN - 1) / BN) * p.l;
-    int grid = (int)(tiles < (int64_t)sms * 4 ? tiles : (int64_t)sms * 4);
-    mark_begin(g, s);
-    k_simt<float, BM, BN, 16, 8, 8><<<grid, 256, 0, s>>>(g);
-    mark_end(g, s);
+  const SimtShape sh = simt_shape(p);
+  GemmArgs g = g0;
+  const int splits = ws ? sh.splits : 1;
+  g.part = splits > 1 ? ws : nullptr;
+  const int64_t cap = (int64_t)sms * sh.blocks_per_sm;
+  const dim3 grid((unsigned)(sh.tiles < cap ? sh.tiles : cap), (unsigned)splits);
+  mark_begin(g, s);
+  if (p.es_a == 8)
+    k_simt<double, 64, 64, 16, 4, 4><<<grid, 256, 0, s>>>(g);
+  else
+    k_simt<float, 128, 128, 16, 8, 8><<<grid, 256, 0, s>>>(g);
+  mark_end(g, s);
+  if (splits > 1) {
+    const int64_t total = p.m * p.n * p.l, blocks = (total + 255) / 256;
+    const int rg = (int)(blocks < (int64_t)sms * 8 ? blocks : (int64_t)sms * 8);
+    if (p.es_a == 8)
+      k_simt_reduce<double><<<rg, 256, 0, s>>>(g, splits);
+    else
+      k_simt_reduce<float><<<rg, 256, 0, s>>>(g, splits);
   }
   return cudaGetLastError();
 }

@@ -120,7 +120,7 @@ extern "C" FAMLIES_API int famlies_contract_noalloc(double alpha, const famlies_
     g.b_contig = p.b_contig;
     g.wait_limit = (int64_t)1 << 26;
     g.status = status;
-    err = launch_simt(p, g, s);
+    err = launch_simt(p, g, nullptr, s);
   }
   if (err != cudaSuccess) {
     cudaGetLastError();

@@ -110,3 +110,20 @@ def test_host_buffers_entry_point():
 
 def test_device_status_clean():
     assert fm.device_status() == 0
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-13), ("f32", 1e-5)])
+def test_cuda_core_few_tiles_split_k(dtype, tol):
+    """100 x 50 outputs (2 tiles) with K = 30000: the CUDA-core kernel splits
+    K across the SMs and sums the partial tiles in split order."""
+    rng = np.random.default_rng(1400)
+    A = W.uniform_operand(rng, (100, 30000), [1, 2])
+    B = W.uniform_operand(rng, (30000, 50), [2, 3])
+    C = W.uniform_operand(rng, (100, 50), [1, 3])
+    p = W.Problem("few_tiles", 0.5, A, B, -2.0, C)
+    dt = {"f64": torch.float64, "f32": torch.float32}[dtype]
+    got, info = run_gpu(p, dtype, kernel=1)
+    assert info["kernel_name"] == ("simt_f64" if dtype == "f64" else "simt_f32")
+    assert info["launches"] == 3  # tables, split product, reduction
+    want = run_oracle(p, dt, dt)
+    assert rel_frob(gpu_dense(got), want) <= tol

@@ -79,7 +79,7 @@ def test_row_major_a_and_many_tiles():
     _check(host, devs, -1.0, 1.0, "f64_emu")
 
 
-@pytest.mark.parametrize("dtype", ["f64_emu", "f32"])
+@pytest.mark.parametrize("dtype", ["f64_emu", "f32", "f64"])
 def test_few_tiles_long_k_splits_k(dtype):
     """n = 200 (two tiles of the triangle), k = 20000: the product splits K
     across the SMs and the finishing kernel writes the triangle."""
@@ -87,7 +87,7 @@ def test_few_tiles_long_k_splits_k(dtype):
     host, devs = _case(rng, 200, 20000, dt=DT[dtype])
     info = _check(host, devs, -1.0, 1.0, dtype)
     # tables, tile list, packs (+ exponents), product, split finish (+ fix-up)
-    assert info["launches"] == (9 if dtype == "f64_emu" else 6)
+    assert info["launches"] == {"f64_emu": 9, "f32": 6, "f64": 3}[dtype]
 
 
 def test_nan_in_a_reaches_its_row_and_column():
