@@ -424,7 +424,7 @@ __device__ __forceinline__ void tri_block(int64_t t, int64_t& P, int64_t& Q) {
 
 // Row exponent bounds: a stored element (p, q) bounds row p and, being also
 // element (q, p), row q.
-__device__ __forceinline__ void rowexp_sym_body(const PackOp& o) {
+__device__ __forceinline__ void rowexp_sym_body(const PackOp& o, int32_t* __restrict__ scr) {
   const double* __restrict__ X = (const double*)o.x;
   const int64_t n = o.sym_n, nb = (n + PR - 1) / PR, nblk = nb * (nb + 1) / 2;
   __shared__ int rmx[4][PR], rbad[4][PR];
@@ -454,18 +454,21 @@ __device__ __forceinline__ void rowexp_sym_body(const PackOp& o) {
     rmx[qi][r] = mxr;
     rbad[qi][r] = badr;
     __syncthreads();
-    if (tid < PR) {  // rows P * PR + tid
+    // the tile's maxima go to its scratch entry (k_rowexp_sym_reduce takes
+    // each row's maximum over its tiles): rows P * PR + r at [0, PR), the
+    // mirror images, rows Q * PK + j, at [PR, PR + PK)
+    if (tid < PR) {
       const int64_t pp = P * PR + tid;
       const int m = max(max(rmx[0][tid], rmx[1][tid]), max(rmx[2][tid], rmx[3][tid]));
       const int b = rbad[0][tid] | rbad[1][tid] | rbad[2][tid] | rbad[3][tid];
-      if (pp < n && m > -1100) atomicMax(&o.e[pp], m);
+      scr[t * (PR + PK) + tid] = m;
       if (pp < n && b) mark_row(o, pp);
-    } else if (tid < PR + PK) {  // rows Q * PK + j (the mirror images)
+    } else if (tid < PR + PK) {
       const int j = tid - PR, jq = j % 4, ji = j / 4;
       const int64_t qq = Q * PK + jq + 4 * ji;
       const int m = max(cmx[0][jq][ji], cmx[1][jq][ji]);
       const int b = cbad[0][jq][ji] | cbad[1][jq][ji];
-      if (qq < n && m > -1100) atomicMax(&o.e[qq], m);
+      scr[t * (PR + PK) + PR + jq + 4 * ji] = m;
       if (qq < n && b) mark_row(o, qq);
     }
     __syncthreads();
@@ -743,8 +746,32 @@ __global__ void __launch_bounds__(256, 3) k_pack(const __grid_constant__ PackArg
                        [&](int64_t g) { return PackTile{&pa, o, g}; });
 }
 
-__global__ void __launch_bounds__(256) k_rowexp_sym(const __grid_constant__ PackArgs pa, int side) {
-  rowexp_sym_body(pa.op[side]);
+__global__ void __launch_bounds__(256) k_rowexp_sym(const __grid_constant__ PackArgs pa, int side,
+                                                   int32_t* scr) {
+  rowexp_sym_body(pa.op[side], scr);
+}
+
+// Row p's exponent bound: the maximum over the tiles of the triangle that
+// hold row p, as a row (tiles (P, Q), Q <= P) or as a mirror image (tiles
+// (Q, P), Q >= P), P = p / PR.  Block P takes rows P * PR + r, its four
+// thread groups every fourth tile, combined in shared memory; one writer
+// per row.
+__global__ void __launch_bounds__(256) k_rowexp_sym_reduce(const __grid_constant__ PackArgs pa, int side,
+                                                          const int32_t* __restrict__ scr) {
+  const PackOp& o = pa.op[side];
+  const int64_t n = o.sym_n, nb = (n + PR - 1) / PR, P = blockIdx.x;
+  const int r = threadIdx.x % PR, g = threadIdx.x / PR;
+  __shared__ int part[4][PR];
+  int m = -1100;
+  for (int64_t Q = g; Q <= P; Q += 4) m = max(m, scr[(P * (P + 1) / 2 + Q) * (PR + PK) + r]);
+  for (int64_t Q = P + g; Q < nb; Q += 4) m = max(m, scr[(Q * (Q + 1) / 2 + P) * (PR + PK) + PR + r]);
+  part[g][r] = m;
+  __syncthreads();
+  if (threadIdx.x < PR) {
+    const int64_t p = P * PR + r;
+    const int mm = max(max(part[0][r], part[1][r]), max(part[2][r], part[3][r]));
+    if (p < n && mm > -1100) o.e[p] = mm;
+  }
 }
 
 __global__ void __launch_bounds__(256) k_rowexp_gen(const __grid_constant__ PackArgs pa, int side) {
@@ -912,10 +939,17 @@ static int64_t sym_blocks(const PackOp& o) {
   return nb * (nb + 1) / 2;
 }
 
-cudaError_t launch_rowexp_sym(const PackArgs& pa, int side, cudaStream_t s) {
+int64_t sym_scratch_bytes(int64_t n) {
+  const int64_t nb = (n + PR - 1) / PR;
+  return nb * (nb + 1) / 2 * (PR + PK) * (int64_t)sizeof(int32_t);
+}
+
+cudaError_t launch_rowexp_sym(const PackArgs& pa, int side, int32_t* scr, cudaStream_t s) {
   const int64_t nblk = sym_blocks(pa.op[side]);
   if (nblk <= 0) return cudaSuccess;
-  k_rowexp_sym<<<grid_for(nblk), 256, 0, s>>>(pa, side);
+  k_rowexp_sym<<<grid_for(nblk), 256, 0, s>>>(pa, side, scr);
+  const int64_t nb = (pa.op[side].sym_n + PR - 1) / PR;
+  k_rowexp_sym_reduce<<<(unsigned)nb, 256, 0, s>>>(pa, side, scr);
   return cudaGetLastError();
 }
 

@@ -771,7 +771,7 @@ int grid_of(const Plan& p, int bn) {
 }
 
 struct Layout {
-  size_t a, b, ea, eb, fa, fb, la, lb, G, xtail, part, tri, total;
+  size_t a, b, ea, eb, fa, fb, la, lb, G, xtail, part, tri, sym, total;
 };
 
 Layout layout_of(const Plan& p) {
@@ -804,6 +804,10 @@ Layout layout_of(const Plan& p) {
     if (sp.splits > 1) {
       L.part = off; off += up((size_t)sp.splits * sp.tail * BM * bn * 4);
     }
+  }
+  if (p.sym_n > 0) {  // per-tile maxima of the symmetric operand's exponent pass
+    L.sym = off;
+    off += up((size_t)sym_scratch_bytes(p.sym_n));
   }
   if (p.tri) {
     L.tri = off;
@@ -1036,7 +1040,8 @@ int packed_launches(const Plan& p) {
   const int tri = p.tri ? 1 : 0;  // the triangle's tile list
   if (p.kernel == FAMLIES_KERNEL_TC_EMU)  // exponents + pack + product (+ split finish) + fix-up
     return 4 + (split_count(p, pair_bn_for(p.n, p.tile_n)) > 1 ? 1 : 0) + tri +
-           (p.sym_n > 0 || p.band_side >= 0 || p.krp_side >= 0 ? 2 : 0);  // (+ a symmetric or generated operand's own)
+           (p.band_side >= 0 || p.krp_side >= 0 ? 2 : 0) +  // (+ a generated operand's own)
+           (p.sym_n > 0 ? 3 : 0);  // (+ a symmetric operand's exponents, their reduction, pack)
   DirectView v;
   const bool tf32 = p.kernel == FAMLIES_KERNEL_TC_TF32X3;
   const bool da = !tf32 && direct_view(p.M, p.K, p.L, 0, p.a, &v);
@@ -1089,7 +1094,7 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     PackArgs pg = pa;  // the generic kernels skip a symmetric or generated operand
     if (own >= 0) pg.op[own].rows = 0;
     if ((e = launch_rowexp(pg, s)) != cudaSuccess) return e;
-    if (sym && (e = launch_rowexp_sym(pa, p.sym_side, s)) != cudaSuccess) return e;
+    if (sym && (e = launch_rowexp_sym(pa, p.sym_side, (int32_t*)(w + L.sym), s)) != cudaSuccess) return e;
     if (gen && (e = launch_rowexp_gen(pa, gside, s)) != cudaSuccess) return e;
   }
   const int bn = pair_bn_for(p.n, p.tile_n);

@@ -63,7 +63,9 @@ cudaError_t launch_pack(int pmode, const PackArgs& pa, cudaStream_t s);
 // Symmetric packed operand pa.op[side] (fp64 split): row exponents and flags
 // (every stored element bounds its row and, by symmetry, its column) and its
 // slices, both from one read of the lower triangle.
-cudaError_t launch_rowexp_sym(const PackArgs& pa, int side, cudaStream_t s);
+// scr: sym_scratch_bytes(sym_n) of workspace for the per-tile maxima.
+cudaError_t launch_rowexp_sym(const PackArgs& pa, int side, int32_t* scr, cudaStream_t s);
+int64_t sym_scratch_bytes(int64_t n);
 cudaError_t launch_pack_sym(const PackArgs& pa, int side, cudaStream_t s);
 // Generated operand pa.op[side] (banded or Khatri-Rao, see PackOp::gen):
 // row exponents and flags (fp64 split) and its slices (PACK_F64 or
