@@ -8,6 +8,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "device.h"
 #include "plan.h"
@@ -64,6 +65,28 @@ int64_t env_wait_limit() {
   return v;
 }
 
+// FAMLIES_LOG=1: one line per planned call on stderr (kernel, sizes, role swap).
+bool env_log() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("FAMLIES_LOG");
+    v = (e && e[0] && e[0] != '0') ? 1 : 0;
+  }
+  return v == 1;
+}
+
+// A profiler range around one library call (host side: enqueue order).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+
+const char* kernel_name(int k) {
+  static const char* names[] = {"none", "scale", "simt_f64", "simt_f32", "tc_bf16", "tc_tf32x3",
+                                "tc_emu", "tc_bf16_gather", "tc_tf32x3_gather"};
+  return (k >= 0 && k <= 8) ? names[k] : "?";
+}
+
 struct Workspace {
   void* ptr = nullptr;
   cudaStream_t s = nullptr;
@@ -75,7 +98,14 @@ struct Workspace {
 int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
              const famlies_options_t* opt, famlies_plan_info_t* info) {
   fill_info(p, info);
+  if (env_log())
+    std::fprintf(stderr,
+                 "famlies: %s m=%lld n=%lld k=%lld batch=%lld modes=%d/%d/%d/%d swapped=%d slices=%d%s%s%s\n",
+                 kernel_name(p.kernel), (long long)p.m, (long long)p.n, (long long)p.k, (long long)p.l, p.M.n,
+                 p.N.n, p.K.n, p.L.n, (int)p.swapped, p.slices, p.sym_n ? " symmetric" : "",
+                 p.band_side >= 0 ? " banded" : "", p.krp_side >= 0 ? " khatri-rao" : "");
   if (p.kernel == FAMLIES_KERNEL_NONE) return FAMLIES_OK;
+  Range range(kernel_name(p.kernel));
   int rc = check_device();
   if (rc) return rc;
   int64_t tab_bytes = table_entries(p) * (int64_t)sizeof(int64_t);

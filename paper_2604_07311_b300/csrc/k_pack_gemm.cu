@@ -48,6 +48,7 @@
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "device.h"
 #include "packed.h"
@@ -1093,7 +1094,10 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     if ((e = cudaMemsetAsync(w + L.fa, 0, L.G - L.fa, s)) != cudaSuccess) return e;
     PackArgs pg = pa;  // the generic kernels skip a symmetric or generated operand
     if (own >= 0) pg.op[own].rows = 0;
-    if ((e = launch_rowexp(pg, s)) != cudaSuccess) return e;
+    nvtxRangePushA("exponents");
+    e = launch_rowexp(pg, s);
+    nvtxRangePop();
+    if (e != cudaSuccess) return e;
     if (sym && (e = launch_rowexp_sym(pa, p.sym_side, (int32_t*)(w + L.sym), s)) != cudaSuccess) return e;
     if (gen && (e = launch_rowexp_gen(pa, gside, s)) != cudaSuccess) return e;
   }
@@ -1111,6 +1115,10 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   if (da) pa.op[0].rows = 0;  // nothing to pack
   if (db) pa.op[1].rows = 0;
   if (!da || !db) {
+    struct Range {  // closes on every exit of the block
+      Range() { nvtxRangePushA("pack"); }
+      ~Range() { nvtxRangePop(); }
+    } range;
     PackArgs pg = pa;
     if (own >= 0) pg.op[own].rows = 0;
     if ((e = launch_pack(emu ? PACK_F64 : (tf32 ? PACK_TF32 : PACK_BF16), pg, s)) != cudaSuccess)
@@ -1155,8 +1163,10 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
       (e = cudaMemsetAsync(a.xtail, 0, (size_t)(a.sc.nlow ? 2 : 1) * spl.tail * BM * bn * 8, s)) != cudaSuccess)
     return e;
   mark_begin(g, s);
+  nvtxRangePushA("product");
   const int mode = emu ? (a.sc.nlow ? PAIR_MODE_EMU_FINE : PAIR_MODE_EMU) : PAIR_MODE_F32OUT;
   e = launch_pair_any<false>(kind, mode, bn, ma, mb, a, grid, s);
+  nvtxRangePop();
   mark_end(g, s);  // the events bracket the product kernel alone
   if (e == cudaSuccess && a.splits > 1) {
     if (emu)
@@ -1167,7 +1177,11 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return e;
-  if (emu) e = launch_fixup(g, pa, s);
+  if (emu) {
+    nvtxRangePushA("fixup");
+    e = launch_fixup(g, pa, s);
+    nvtxRangePop();
+  }
   return e;
 }
 

@@ -234,3 +234,4 @@ def test_mttkrp_validation():
     assert call(0, M(4), u=bad) == -3                 # a factor of the wrong height
     assert call(0, M(4, 0x40000000 + 16)) == -4       # M overlaps a factor
     assert call(0, M(4, 0x10000000 + 64)) == -4       # M overlaps X
+
