@@ -548,7 +548,7 @@ constexpr int SPLIT_PER_THREAD = SPLIT_COLS / (256 / BM);
 
 // fp32 output: C = alpha * (sum of the splits' partial tiles, in split order)
 // + beta * C.
-__global__ void __launch_bounds__(256) k_split_reduce(const float* __restrict__ part, int splits,
+__global__ void __launch_bounds__(256, 4) k_split_reduce(const float* __restrict__ part, int splits,
                                                      int64_t full, int bn, Prob P) {
   const int chunks = bn / SPLIT_COLS;
   const int64_t tail = prob_tiles(P, bn) - full, items = tail * chunks;
@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(256) k_split_reduce(const float* __restrict__ 
 // fp64 split: the splits of a tile added their int64 sums into one slot;
 // C = alpha * 2^(e_m + e_n - xunit) * sum + beta * C (rows and columns
 // holding Inf/NaN are left to the native fix-up).
-__global__ void __launch_bounds__(256) k_split_finish(const int64_t* __restrict__ X, int64_t full,
+__global__ void __launch_bounds__(256, 3) k_split_finish(const int64_t* __restrict__ X, int64_t full,
                                                      int bn, int xunit, int xlo, int nlow, Prob P) {
   const int chunks = bn / SPLIT_COLS;
   const int64_t items = (prob_tiles(P, bn) - full) * chunks;
