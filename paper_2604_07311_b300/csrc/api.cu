@@ -246,6 +246,7 @@ int famlies_contract_sym(double alpha, const famlies_symtensor_t* A, const famli
     if (A->extents[i] < 0 || A->extents[i] != A->extents[i + h]) return FAMLIES_ERR_INVALID_ARG;
     n *= A->extents[i];
   }
+  if (n > ((int64_t)1 << 30)) return FAMLIES_ERR_UNSUPPORTED;  // packed bytes must fit int64
   const int64_t packed = n * (n + 1) / 2;
   if (A->size_bytes > 0 && packed * 8 > A->size_bytes) return FAMLIES_ERR_OUT_OF_BOUNDS;
   // Plan A as its dense expansion (first mode fastest): the halves' fused
@@ -377,8 +378,11 @@ int famlies_mttkrp(double alpha, const famlies_tensor_t* X, int32_t mode, const 
     q.ext[q.nf] = X->extents[m] > 0 ? X->extents[m] : 1;
     q.st[q.nf] = acc;
     ++q.nf;
-    acc *= X->extents[m] > 0 ? X->extents[m] : 1;
+    const int64_t e = X->extents[m] > 0 ? X->extents[m] : 1;
+    if (acc > ((int64_t)1 << 62) / e) return FAMLIES_ERR_UNSUPPORTED;  // the Khatri-Rao layout's offsets
+    acc *= e;
   }
+  if (R > 0 && acc > ((int64_t)1 << 62) / R) return FAMLIES_ERR_UNSUPPORTED;
   eb[q.nf] = R;
   sb[q.nf] = acc;
   lb[q.nf] = RL;

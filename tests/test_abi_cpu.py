@@ -235,3 +235,21 @@ def test_mttkrp_validation():
     assert call(0, M(4, 0x40000000 + 16)) == -4       # M overlaps a factor
     assert call(0, M(4, 0x10000000 + 64)) == -4       # M overlaps X
 
+
+
+def test_oversized_generated_operands_are_rejected():
+    """A packed symmetric operand whose size overflows and a Khatri-Rao layout
+    whose offsets overflow are refused on the host (UNSUPPORTED)."""
+    big = 1 << 31
+    B = _lib.Desc((big, 3), (1, big), [2, 3], 0x20000000)
+    C = _lib.Desc((big, 3), (1, big), [1, 3], 0x40000000)
+    assert _sym_rc((big, big), [1, 2], B, C) == -6
+    import ctypes
+    lib = _lib.load()
+    e = 1 << 21
+    X = _lib.Desc((4, e, e, e), (1, 4, 4 * e, 4 * e * e), [0, 0, 0, 0], 0x10000000)
+    us = (_lib.MatrixDesc * 4)(*[_lib.MatrixDesc(0x30000000, n, 3, 1, n) for n in (4, e, e, e)])
+    M = _lib.MatrixDesc(0x50000000, 4, 3, 1, 4)
+    info = _lib.PlanInfo()
+    assert lib.famlies_mttkrp(1.0, X.ref, 0, us, 0.0, ctypes.byref(M), fm.F64_EMU, None, None,
+                              ctypes.byref(info)) == -6
