@@ -168,7 +168,10 @@ cudaError_t launch_scale(const Plan& p, const Tables& t, double beta, cudaStream
 // 256 threads; thread (tx, ty) owns rows ty + i*(BM/TM) and columns
 // tx + j*(BN/TN) of the tile (interleaved so shared-memory reads of a warp
 // hit distinct banks).
-template <typename T, int BM, int BN, int BK, int TM, int TN>
+// GEN: the launch has a generated operand (band, Khatri-Rao) or a triangle
+// of C; plain contractions run the GEN = false instantiation, which has
+// neither the extra loads nor the checks.
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool GEN>
 __global__ void __launch_bounds__(256) k_simt(GemmArgs g) {
   static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
   __shared__ T As[BK][BM + 1];
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(256) k_simt(GemmArgs g) {
     const int64_t tn = rest % tiles_n, il = rest / tiles_n;
     const int64_t m0 = tm * BM, n0 = tn * BN;
     // a tile wholly outside the updated triangle has nothing to do
-    if (g.tri == 1 ? m0 + BM - 1 < n0 : (g.tri == 2 && m0 > n0 + BN - 1)) continue;
+    if (GEN && (g.tri == 1 ? m0 + BM - 1 < n0 : (g.tri == 2 && m0 > n0 + BN - 1))) continue;
     const int64_t al = g.t.al[il], bl = g.t.bl[il], cl = g.t.cl[il];
     T acc[TM][TN];
 #pragma unroll
@@ -204,9 +207,9 @@ __global__ void __launch_bounds__(256) k_simt(GemmArgs g) {
         if (g.a_contig == 2) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
         const int64_t gm = m0 + mm, gk = k0 + kk;
         As[kk][mm] = (gm < g.m && gk < kend)
-                         ? (g.band_op == 1   ? band_at<T>(A, al + g.t.am[gm], g.t.ak, 0, gk, g.k, g.band)
-                            : g.krp_op == 1 ? krp_at<T>(g.krp, gm, g.t.ak[gk])
-                                            : A[al + g.t.am[gm] + g.t.ak[gk]])
+                         ? ((GEN && g.band_op == 1)  ? band_at<T>(A, al + g.t.am[gm], g.t.ak, 0, gk, g.k, g.band)
+                            : (GEN && g.krp_op == 1) ? krp_at<T>(g.krp, gm, g.t.ak[gk])
+                                                     : A[al + g.t.am[gm] + g.t.ak[gk]])
                          : T(0);
       }
       for (int e = tid; e < BN * BK; e += 256) {
@@ -214,9 +217,9 @@ __global__ void __launch_bounds__(256) k_simt(GemmArgs g) {
         if (g.b_contig == 2) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
         const int64_t gn = n0 + nn, gk = k0 + kk;
         Bs[kk][nn] = (gn < g.n && gk < kend)
-                         ? (g.band_op == 2   ? band_at<T>(B, bl + g.t.bn[gn], g.t.bk, 0, gk, g.k, g.band)
-                            : g.krp_op == 2 ? krp_at<T>(g.krp, gn, g.t.bk[gk])
-                                            : B[bl + g.t.bn[gn] + g.t.bk[gk]])
+                         ? ((GEN && g.band_op == 2)  ? band_at<T>(B, bl + g.t.bn[gn], g.t.bk, 0, gk, g.k, g.band)
+                            : (GEN && g.krp_op == 2) ? krp_at<T>(g.krp, gn, g.t.bk[gk])
+                                                     : B[bl + g.t.bn[gn] + g.t.bk[gk]])
                          : T(0);
       }
       __syncthreads();
@@ -242,7 +245,7 @@ __global__ void __launch_bounds__(256) k_simt(GemmArgs g) {
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
         const int64_t gn = n0 + tx + j * (BN / TN);
-        if (gn >= g.n || !tri_keep(g.tri, gm, gn)) continue;
+        if (gn >= g.n || (GEN && !tri_keep(g.tri, gm, gn))) continue;
         if (g.part) {  // a split's partial result, summed by k_simt_reduce
           ((T*)g.part)[(((size_t)blockIdx.y * g.l + il) * g.n + gn) * g.m + gm] = acc[i][j];
           continue;
@@ -322,11 +325,15 @@ cudaError_t launch_simt(const Plan& p, const GemmArgs& g0, void* ws, cudaStream_
   g.part = splits > 1 ? ws : nullptr;
   const int64_t cap = (int64_t)sms * sh.blocks_per_sm;
   const dim3 grid((unsigned)(sh.tiles < cap ? sh.tiles : cap), (unsigned)splits);
+  const bool gen = g.band_op || g.krp_op || g.tri;
   mark_begin(g, s);
-  if (p.es_a == 8)
-    k_simt<double, 64, 64, 16, 4, 4><<<grid, 256, 0, s>>>(g);
-  else
-    k_simt<float, 128, 128, 16, 8, 8><<<grid, 256, 0, s>>>(g);
+  if (p.es_a == 8) {
+    if (gen) k_simt<double, 64, 64, 16, 4, 4, true><<<grid, 256, 0, s>>>(g);
+    else k_simt<double, 64, 64, 16, 4, 4, false><<<grid, 256, 0, s>>>(g);
+  } else {
+    if (gen) k_simt<float, 128, 128, 16, 8, 8, true><<<grid, 256, 0, s>>>(g);
+    else k_simt<float, 128, 128, 16, 8, 8, false><<<grid, 256, 0, s>>>(g);
+  }
   mark_end(g, s);
   if (splits > 1) {
     const int64_t total = p.m * p.n * p.l, blocks = (total + 255) / 256;
