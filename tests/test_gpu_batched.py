@@ -136,3 +136,29 @@ def test_graph_cache_rekeys_on_new_pointers():
         C.copy_(C3)
     batched_call(blocks, As, Bs, Cs, "f64_emu", True)  # the first set again: replay
     check(blocks, Cs, "f64_emu")
+
+
+def test_long_k_block_uses_exact_fine_sums_in_the_grouped_launch():
+    """A block with K = 2^18 next to a small one in one grouped launch: the
+    schedule keeps a second, exact int64 sum for the fine diagonals (per-CTA
+    slots twice as wide); sampled entries of the long block match the
+    oracle's compensated sums, the small block matches the oracle."""
+    import oracle
+    rng = np.random.default_rng(1800)
+    K = 1 << 18
+    A1 = W.uniform_operand(rng, (64, K), [1, 2])
+    B1 = W.uniform_operand(rng, (K, 48), [2, 3])
+    C1 = W.zeros_operand((64, 48), [1, 3])
+    A2 = W.uniform_operand(rng, (100, 70), [1, 2])
+    B2 = W.uniform_operand(rng, (70, 90), [2, 3])
+    C2 = W.uniform_operand(rng, (100, 90), [1, 3])
+    dev = [to_device(x, torch.float64) for x in (A1, B1, C1, A2, B2, C2)]
+    fm.contract_batched(1.0, [dev[0], dev[3]], [[1, 2], [1, 2]], [dev[1], dev[4]], [[2, 3], [2, 3]], 0.5,
+                        [dev[2], dev[5]], [[1, 3], [1, 3]], dtype="f64_emu")
+    torch.cuda.synchronize()
+    idx = np.stack([rng.integers(0, 64, size=256), rng.integers(0, 48, size=256)], axis=1)
+    want = oracle.entries(1.0, A1.view(), [1, 2], B1.view(), [2, 3], 0.5, C1.view(), [1, 3], idx, dot2=True)
+    got = gpu_dense(dev[2])[idx[:, 0], idx[:, 1]]
+    assert rel_frob(got, want) <= 1e-13
+    p2 = W.Problem("small", 1.0, A2, B2, 0.5, C2)
+    assert rel_frob(gpu_dense(dev[5]), run_oracle(p2)) <= 1e-13
