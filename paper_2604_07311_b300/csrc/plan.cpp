@@ -12,6 +12,7 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 namespace famlies {
@@ -264,10 +265,17 @@ int make_plan(double alpha, const famlies_tensor_t* A, const famlies_tensor_t* B
       p.kernel = FAMLIES_KERNEL_TC_EMU;
       break;
   }
-  p.tile_n = opt ? opt->tile_n : 0;
+  // Options left at 0 take FAMLIES_FORCE_TILE / FAMLIES_SLICES from the
+  // environment when set, else the built-in choices.
+  auto env_int = [](const char* name) {
+    const char* e = std::getenv(name);
+    return e ? std::atoi(e) : 0;
+  };
+  p.tile_n = opt && opt->tile_n ? opt->tile_n : env_int("FAMLIES_FORCE_TILE");
   if (p.tile_n != 0 && p.tile_n != 64 && p.tile_n != 128 && p.tile_n != 256)
     return FAMLIES_ERR_INVALID_ARG;
-  int s = opt && opt->slices ? opt->slices : 6;
+  int s = opt && opt->slices ? opt->slices : env_int("FAMLIES_SLICES");
+  if (s == 0) s = 6;
   if (s < 2 || s > 7) return FAMLIES_ERR_INVALID_ARG;
   p.slices = s;
   *out = p;

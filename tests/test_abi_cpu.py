@@ -4,6 +4,7 @@ validation errors) behaves as specified.  No device is touched."""
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -253,3 +254,21 @@ def test_oversized_generated_operands_are_rejected():
     info = _lib.PlanInfo()
     assert lib.famlies_mttkrp(1.0, X.ref, 0, us, 0.0, ctypes.byref(M), fm.F64_EMU, None, None,
                               ctypes.byref(info)) == -6
+
+
+def test_environment_defaults_for_slices_and_tile_width():
+    """FAMLIES_SLICES and FAMLIES_FORCE_TILE fill options left at 0; an
+    invalid tile width from the environment is refused like one passed in."""
+    code = ("import paper_2604_07311_b300 as fm\n"
+            "i = fm.plan((64, 32), (1, 64), [1, 2], (32, 48), (1, 32), [2, 3], (64, 48), (1, 64), [1, 3], "
+            "dtype='f64_emu')\n"
+            "print(i['slices'])\n"
+            "i = fm.plan((64, 32), (1, 64), [1, 2], (32, 48), (1, 32), [2, 3], (64, 48), (1, 64), [1, 3], "
+            "dtype='f64_emu', slices=4)\n"
+            "print(i['slices'])\n")
+    env = dict(os.environ, FAMLIES_SLICES="5")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=120)
+    assert r.stdout.split() == ["5", "4"], r.stderr
+    env = dict(os.environ, FAMLIES_FORCE_TILE="96")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=120)
+    assert "famlies error -1" in r.stderr
