@@ -79,7 +79,7 @@ struct PairArgs {
   int64_t wait_limit;
 };
 
-template <int KIND, int BN>
+template <int KIND, int BN, int MODE = PAIR_MODE_F32OUT>
 struct PCfg {
   static constexpr int KB = pair_stage_k(KIND);            // k per stage
   static constexpr int ROWB = pair_row_bytes(KIND);        // bytes of one tile row in a stage
@@ -91,13 +91,22 @@ struct PCfg {
   // tiles fill one region and the column operand's another, stage s of each
   // guarded by one barrier pair.  (Separate producers and rings of different
   // depth per operand measured slower on both the fp64 split and bf16.)
-  static constexpr int STAGES =
-      (200 * 1024) / (A_BYTES + B_BYTES) > 8 ? 8 : (200 * 1024) / (A_BYTES + B_BYTES);
+  // PAIR_MODE_EMU_SMEM: the tile's int64 sums (BM x BN) in shared memory
+  // after the ring, which then gets what is left of the 227 KB.
+  static constexpr int X_BYTES = MODE == PAIR_MODE_EMU_SMEM ? BM * BN * 8 : 0;
+  static constexpr int RING = MODE == PAIR_MODE_EMU_SMEM ? 227 * 1024 - X_BYTES - 1536 : 200 * 1024;
+  static constexpr int STAGES = RING / (A_BYTES + B_BYTES) > 8 ? 8 : RING / (A_BYTES + B_BYTES);
   static constexpr int B_OFF = STAGES * A_BYTES;
-  static constexpr int BAR_OFF = B_OFF + STAGES * B_BYTES;
-  static constexpr uint32_t TMEM_COLS = 2 * BN;
+  static constexpr int X_OFF = B_OFF + STAGES * B_BYTES;
+  static constexpr int BAR_OFF = X_OFF + X_BYTES;
+  // Accumulator buffers in tensor memory: two of 256 columns, or four of
+  // 128 (64) columns, so that short units of narrower tiles are drained
+  // while the next ones accumulate.
+  static constexpr int NACC = BN == 256 ? 2 : 4;
+  static constexpr uint32_t TMEM_COLS = NACC * BN;
   static constexpr uint32_t IDESC = ptx::idesc_make(BM, BN, KIND == PAIR_KIND_BF16 ? 1u : 2u);
   static constexpr int SMEM_BYTES = BAR_OFF + 1024 + 512;
+  static_assert(STAGES >= 2 && SMEM_BYTES <= 227 * 1024, "shared memory budget");
 };
 
 __device__ __forceinline__ void record_timeout(volatile int* abort, int* status) {
@@ -182,7 +191,7 @@ __device__ __forceinline__ TileRef tile_at(const PairArgs& a, int64_t t) {
 // groups of columns whose table entries, X and C are loaded together.  X is
 // read from L2 (the reductions that built it ran there).  Not inlined: it
 // runs once per tile and keeps its registers out of the drain loop's budget.
-template <int CPT, bool FINE>
+template <int CPT, bool FINE, bool SMEMX = false>
 __device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, const Sched& sc, int64_t il,
                                          int64_t row, int64_t crow, int64_t col0, int lc0, int bnp) {
   // the fine sums follow the coarse ones in the tile's slot (tiles 2 CPT wide)
@@ -209,7 +218,7 @@ __device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, const
       ecol[j] = use[j] ? ebl[col] : 0;
       coff[j] = use[j] ? P.cn[col] : 0;
       use[j] = use[j] && !fbl[col];
-      g[j] = __ldcg(Xt + (size_t)(j0 + j) * BM);
+      g[j] = SMEMX ? Xt[(size_t)(j0 + j) * BM] : __ldcg(Xt + (size_t)(j0 + j) * BM);  // shared: generic load
       gl[j] = FINE ? __ldcg(Lt + (size_t)(j0 + j) * BM) : 0;
     }
 #pragma unroll
@@ -296,14 +305,14 @@ template <int KIND, int MODE, int BN, bool GROUPED, bool SPLITK>
 __global__ void __launch_bounds__(THREADS, 1)
     k_pair_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                 const __grid_constant__ PairArgs args) {
-  using Cfg = PCfg<KIND, BN>;
+  using Cfg = PCfg<KIND, BN, MODE>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + Cfg::BAR_OFF);
   uint64_t* empty = full + Cfg::STAGES;
   uint64_t* tfull = empty + Cfg::STAGES;
-  uint64_t* tempty = tfull + 2;
-  uint64_t* done = tempty + 2;
+  uint64_t* tempty = tfull + Cfg::NACC;
+  uint64_t* done = tempty + Cfg::NACC;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort = (volatile int*)(tmem_slot + 1);
 
@@ -317,7 +326,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       ptx::mbar_init(&full[s], 1);
       ptx::mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < Cfg::NACC; ++b) {
       ptx::mbar_init(&tfull[b], 1);
       ptx::mbar_init(&tempty[b], EPI_WARPS);
     }
@@ -381,8 +390,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             if (!ok) break;
             ptx::mma_commit(&tfull[acc]);
-            acc ^= 1;
-            if (acc == 0) accph ^= 1;
+            if (++acc == Cfg::NACC) { acc = 0; accph ^= 1; }
           }
         }
       }
@@ -433,8 +441,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           ptx::tc_fence_before();
           __syncwarp();
           if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
-          acc ^= 1;
-          if (acc == 0) accph ^= 1;
+          if (++acc == Cfg::NACC) { acc = 0; accph ^= 1; }
         }
         if (!ok) break;
         if (SPLITK && T.split >= 0) {
@@ -475,9 +482,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         // walk runs from the least significant diagonal up).
         const bool part_item = SPLITK && T.split >= 0;
         constexpr bool FINE = MODE == PAIR_MODE_EMU_FINE;
+        constexpr bool SMEMX = MODE == PAIR_MODE_EMU_SMEM;  // whole tiles' sums in shared memory
         constexpr size_t slot = (size_t)BM * BN * (FINE ? 2 : 1);
         int64_t* Xt = (part_item ? args.xtail + (size_t)(T.tile - args.full) * slot
-                                 : (int64_t*)args.G + (size_t)blockIdx.x * slot) +
+                                 : (SMEMX ? (int64_t*)(smem + Cfg::X_OFF)
+                                          : (int64_t*)args.G + (size_t)blockIdx.x * slot)) +
                       (size_t)(hf * CPT) * BM + qd * 32 + lane;
         bool first_flush = true;
         for (int di = 0; di < sc.ndiag && ok; ++di) {
@@ -501,8 +510,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             ptx::tc_fence_before();
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
-            acc ^= 1;
-            if (acc == 0) accph ^= 1;
+            if (++acc == Cfg::NACC) { acc = 0; accph ^= 1; }
             if (!flush) continue;
             // sum += S * 2^xshift in int64 (exact, order-free): the first
             // flush into a tile's sum stores, later ones are fire-and-forget
@@ -516,13 +524,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                 int64_t v = (int64_t)S[j];
                 v = xs >= 0 ? (int64_t)((uint64_t)v << xs) : ((v + ((int64_t)1 << (-xs - 1))) >> (-xs));
                 if (first) D[(size_t)j * BM] = v;
+                else if (SMEMX && !part_item) D[(size_t)j * BM] += v;  // this thread's own entries
                 else atomicAdd((unsigned long long*)(D + (size_t)j * BM), (unsigned long long)v);
                 S[j] = 0;
               }
               first_flush = false;
             }
             if (part_item || !(last_unit && di == sc.ndiag - 1) || !rv || P.fa[il * P.m + row]) continue;
-            finish_tile<CPT, FINE>(P, Xt, sc, il, row, crow, col0, lc0, bnp);
+            finish_tile<CPT, FINE, SMEMX>(P, Xt, sc, il, row, crow, col0, lc0, bnp);
           }
         }
       }
@@ -821,7 +830,7 @@ Layout layout_of(const Plan& p) {
 template <int KIND, int MODE, int BN, bool GROUPED, bool SPLITK>
 cudaError_t launch_pair_k(const CUtensorMap& ma, const CUtensorMap& mb, const PairArgs& a, int grid,
                           cudaStream_t s) {
-  using Cfg = PCfg<KIND, BN>;
+  using Cfg = PCfg<KIND, BN, MODE>;
   constexpr int kMaxDev = 64;
   static bool attr[kMaxDev] = {};  // per device: function attributes are per context
   int dev = 0;
@@ -861,6 +870,13 @@ cudaError_t launch_pair_any(int kind, int mode, int bn, const CUtensorMap& ma,
   if (mode == PAIR_MODE_EMU) return launch_pair_bn<PAIR_KIND_BF16, PAIR_MODE_EMU, GROUPED>(bn, ma, mb, a, grid, s);
   if (mode == PAIR_MODE_EMU_FINE)
     return launch_pair_bn<PAIR_KIND_BF16, PAIR_MODE_EMU_FINE, GROUPED>(bn, ma, mb, a, grid, s);
+  if (mode == PAIR_MODE_EMU_SMEM) {  // 64- or 128-wide tiles only (a 256-wide tile's sums need 256 KB)
+    if constexpr (!GROUPED) {
+      if (bn == 64) return launch_pair<PAIR_KIND_BF16, PAIR_MODE_EMU_SMEM, 64, false>(ma, mb, a, grid, s);
+      if (bn == 128) return launch_pair<PAIR_KIND_BF16, PAIR_MODE_EMU_SMEM, 128, false>(ma, mb, a, grid, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   if (kind == PAIR_KIND_TF32)
     return launch_pair_bn<PAIR_KIND_TF32, PAIR_MODE_F32OUT, GROUPED>(bn, ma, mb, a, grid, s);
   return launch_pair_bn<PAIR_KIND_BF16, PAIR_MODE_F32OUT, GROUPED>(bn, ma, mb, a, grid, s);
@@ -1164,7 +1180,12 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     return e;
   mark_begin(g, s);
   nvtxRangePushA("product");
-  const int mode = emu ? (a.sc.nlow ? PAIR_MODE_EMU_FINE : PAIR_MODE_EMU) : PAIR_MODE_F32OUT;
+  // fp64 split: a second exact sum when the schedule needs it; for short K
+  // (where the flushes weigh) the tile sums in shared memory when a tile's
+  // fit (<= 128 wide; its ring is then 3 stages deep); else at L2
+  const bool smem_sums = bn <= 128 && p.k <= 512;
+  const int mode = !emu ? PAIR_MODE_F32OUT
+                        : (a.sc.nlow ? PAIR_MODE_EMU_FINE : (smem_sums ? PAIR_MODE_EMU_SMEM : PAIR_MODE_EMU));
   e = launch_pair_any<false>(kind, mode, bn, ma, mb, a, grid, s);
   nvtxRangePop();
   mark_end(g, s);  // the events bracket the product kernel alone
