@@ -70,7 +70,9 @@ struct PairArgs {
   int64_t ntiles;        // grouped: tile count
   Sched sc;
   double* G;             // fp64 split: per-CTA fp64 tile sums
-  int splits;            // single problem: K splits of each tail tile (1: off)
+  int splits;            // single problem: K splits of each tail tile
+  int tailed;            // single problem: tail items write tile slots finished by k_split_finish /
+                         // k_split_reduce (K splits, or the deferred finish of short-K tiles)
   int64_t full;          // splits > 1: the leading tiles that run whole (the rest is the tail)
   int64_t* xtail;        // fp64 split, splits > 1: int64 sums of the tail tiles [tail][BN][BM]
   int stall_test;        // testing: the MMA issuer first waits on a barrier nothing completes
@@ -91,14 +93,10 @@ struct PCfg {
   // tiles fill one region and the column operand's another, stage s of each
   // guarded by one barrier pair.  (Separate producers and rings of different
   // depth per operand measured slower on both the fp64 split and bf16.)
-  // PAIR_MODE_EMU_SMEM: the tile's int64 sums (BM x BN) in shared memory
-  // after the ring, which then gets what is left of the 227 KB.
-  static constexpr int X_BYTES = MODE == PAIR_MODE_EMU_SMEM ? BM * BN * 8 : 0;
-  static constexpr int RING = MODE == PAIR_MODE_EMU_SMEM ? 227 * 1024 - X_BYTES - 1536 : 200 * 1024;
-  static constexpr int STAGES = RING / (A_BYTES + B_BYTES) > 8 ? 8 : RING / (A_BYTES + B_BYTES);
+  static constexpr int STAGES =
+      (200 * 1024) / (A_BYTES + B_BYTES) > 8 ? 8 : (200 * 1024) / (A_BYTES + B_BYTES);
   static constexpr int B_OFF = STAGES * A_BYTES;
-  static constexpr int X_OFF = B_OFF + STAGES * B_BYTES;
-  static constexpr int BAR_OFF = X_OFF + X_BYTES;
+  static constexpr int BAR_OFF = B_OFF + STAGES * B_BYTES;
   // Accumulator buffers in tensor memory: two of 256 columns, or four of
   // 128 (64) columns, so that short units of narrower tiles are drained
   // while the next ones accumulate.
@@ -191,7 +189,7 @@ __device__ __forceinline__ TileRef tile_at(const PairArgs& a, int64_t t) {
 // groups of columns whose table entries, X and C are loaded together.  X is
 // read from L2 (the reductions that built it ran there).  Not inlined: it
 // runs once per tile and keeps its registers out of the drain loop's budget.
-template <int CPT, bool FINE, bool SMEMX = false>
+template <int CPT, bool FINE>
 __device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, const Sched& sc, int64_t il,
                                          int64_t row, int64_t crow, int64_t col0, int lc0, int bnp) {
   // the fine sums follow the coarse ones in the tile's slot (tiles 2 CPT wide)
@@ -218,7 +216,7 @@ __device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, const
       ecol[j] = use[j] ? ebl[col] : 0;
       coff[j] = use[j] ? P.cn[col] : 0;
       use[j] = use[j] && !fbl[col];
-      g[j] = SMEMX ? Xt[(size_t)(j0 + j) * BM] : __ldcg(Xt + (size_t)(j0 + j) * BM);  // shared: generic load
+      g[j] = __ldcg(Xt + (size_t)(j0 + j) * BM);
       gl[j] = FINE ? __ldcg(Lt + (size_t)(j0 + j) * BM) : 0;
     }
 #pragma unroll
@@ -482,11 +480,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         // walk runs from the least significant diagonal up).
         const bool part_item = SPLITK && T.split >= 0;
         constexpr bool FINE = MODE == PAIR_MODE_EMU_FINE;
-        constexpr bool SMEMX = MODE == PAIR_MODE_EMU_SMEM;  // whole tiles' sums in shared memory
         constexpr size_t slot = (size_t)BM * BN * (FINE ? 2 : 1);
         int64_t* Xt = (part_item ? args.xtail + (size_t)(T.tile - args.full) * slot
-                                 : (SMEMX ? (int64_t*)(smem + Cfg::X_OFF)
-                                          : (int64_t*)args.G + (size_t)blockIdx.x * slot)) +
+                                 : (int64_t*)args.G + (size_t)blockIdx.x * slot) +
                       (size_t)(hf * CPT) * BM + qd * 32 + lane;
         bool first_flush = true;
         for (int di = 0; di < sc.ndiag && ok; ++di) {
@@ -524,14 +520,13 @@ __global__ void __launch_bounds__(THREADS, 1)
                 int64_t v = (int64_t)S[j];
                 v = xs >= 0 ? (int64_t)((uint64_t)v << xs) : ((v + ((int64_t)1 << (-xs - 1))) >> (-xs));
                 if (first) D[(size_t)j * BM] = v;
-                else if (SMEMX && !part_item) D[(size_t)j * BM] += v;  // this thread's own entries
                 else atomicAdd((unsigned long long*)(D + (size_t)j * BM), (unsigned long long)v);
                 S[j] = 0;
               }
               first_flush = false;
             }
             if (part_item || !(last_unit && di == sc.ndiag - 1) || !rv || P.fa[il * P.m + row]) continue;
-            finish_tile<CPT, FINE, SMEMX>(P, Xt, sc, il, row, crow, col0, lc0, bnp);
+            finish_tile<CPT, FINE>(P, Xt, sc, il, row, crow, col0, lc0, bnp);
           }
         }
       }
@@ -747,6 +742,10 @@ SplitPlan split_plan(const Plan& p, int bn) {
   const int64_t unit = emu ? 512 / kb : f32out_unit_stages(kind);
   const int64_t pieces = emu ? nkb / unit : (nkb + unit - 1) / unit;
   const int64_t full = (tiles / sms) * sms, tail = tiles - full;
+  // fp64 split with short K: every tile's sums go to its slot and a separate
+  // kernel finishes them (a tile's finish otherwise stalls the product's
+  // epilogue for about half its time)
+  if (emu && p.k <= 512) return SplitPlan{1, 0, tiles};
   // all tiles in one round: enough splits to fill the SMs (at least 16)
   const int64_t most = full == 0 ? std::max<int64_t>(16, (sms + tail - 1) / tail) : 4;
   const int64_t cap = pieces < most ? pieces : most;
@@ -811,7 +810,7 @@ Layout layout_of(const Plan& p) {
   } else {
     const int bn = pair_bn_for(p.n, p.tile_n);
     const SplitPlan sp = split_plan(p, bn);
-    if (sp.splits > 1) {
+    if (sp.tail > 0) {
       L.part = off; off += up((size_t)sp.splits * sp.tail * BM * bn * 4);
     }
   }
@@ -851,7 +850,7 @@ cudaError_t launch_pair(const CUtensorMap& ma, const CUtensorMap& mb, const Pair
   // split K only for single problems (a separate instantiation, so that the
   // common kernel carries none of its bookkeeping)
   if constexpr (!GROUPED) {
-    if (a.splits > 1) return launch_pair_k<KIND, MODE, BN, GROUPED, true>(ma, mb, a, grid, s);
+    if (a.tailed) return launch_pair_k<KIND, MODE, BN, GROUPED, true>(ma, mb, a, grid, s);
   }
   return launch_pair_k<KIND, MODE, BN, GROUPED, false>(ma, mb, a, grid, s);
 }
@@ -870,13 +869,6 @@ cudaError_t launch_pair_any(int kind, int mode, int bn, const CUtensorMap& ma,
   if (mode == PAIR_MODE_EMU) return launch_pair_bn<PAIR_KIND_BF16, PAIR_MODE_EMU, GROUPED>(bn, ma, mb, a, grid, s);
   if (mode == PAIR_MODE_EMU_FINE)
     return launch_pair_bn<PAIR_KIND_BF16, PAIR_MODE_EMU_FINE, GROUPED>(bn, ma, mb, a, grid, s);
-  if (mode == PAIR_MODE_EMU_SMEM) {  // 64- or 128-wide tiles only (a 256-wide tile's sums need 256 KB)
-    if constexpr (!GROUPED) {
-      if (bn == 64) return launch_pair<PAIR_KIND_BF16, PAIR_MODE_EMU_SMEM, 64, false>(ma, mb, a, grid, s);
-      if (bn == 128) return launch_pair<PAIR_KIND_BF16, PAIR_MODE_EMU_SMEM, 128, false>(ma, mb, a, grid, s);
-    }
-    return cudaErrorInvalidValue;
-  }
   if (kind == PAIR_KIND_TF32)
     return launch_pair_bn<PAIR_KIND_TF32, PAIR_MODE_F32OUT, GROUPED>(bn, ma, mb, a, grid, s);
   return launch_pair_bn<PAIR_KIND_BF16, PAIR_MODE_F32OUT, GROUPED>(bn, ma, mb, a, grid, s);
@@ -1056,14 +1048,14 @@ int64_t packed_workspace_bytes(const Plan& p) { return (int64_t)layout_of(p).tot
 int packed_launches(const Plan& p) {
   const int tri = p.tri ? 1 : 0;  // the triangle's tile list
   if (p.kernel == FAMLIES_KERNEL_TC_EMU)  // exponents + pack + product (+ split finish) + fix-up
-    return 4 + (split_count(p, pair_bn_for(p.n, p.tile_n)) > 1 ? 1 : 0) + tri +
+    return 4 + (split_plan(p, pair_bn_for(p.n, p.tile_n)).tail > 0 ? 1 : 0) + tri +
            (p.band_side >= 0 || p.krp_side >= 0 ? 2 : 0) +  // (+ a generated operand's own)
            (p.sym_n > 0 ? 3 : 0);  // (+ a symmetric operand's exponents, their reduction, pack)
   DirectView v;
   const bool tf32 = p.kernel == FAMLIES_KERNEL_TC_TF32X3;
   const bool da = !tf32 && direct_view(p.M, p.K, p.L, 0, p.a, &v);
   const bool db = !tf32 && direct_view(p.N, p.K, p.L, 1, p.b, &v);
-  return ((da && db) ? 0 : 1) + 1 + (split_count(p, pair_bn_for(p.n, p.tile_n)) > 1 ? 1 : 0) + tri +
+  return ((da && db) ? 0 : 1) + 1 + (split_plan(p, pair_bn_for(p.n, p.tile_n)).tail > 0 ? 1 : 0) + tri +
          (p.band_side >= 0 || p.krp_side >= 0 ? 1 : 0);
 }
 
@@ -1167,29 +1159,25 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   a.sc = make_pair_sched(p.kernel, p.slices, bits, p.k, spl.splits);
   a.G = emu ? (double*)(w + L.G) : nullptr;
   a.splits = spl.splits;
+  a.tailed = spl.tail > 0 ? 1 : 0;
   a.full = spl.full;
-  a.xtail = emu && spl.splits > 1 ? (int64_t*)(w + L.xtail) : nullptr;
-  a.part = !emu && spl.splits > 1 ? (float*)(w + L.part) : nullptr;
+  a.xtail = emu && a.tailed ? (int64_t*)(w + L.xtail) : nullptr;
+  a.part = !emu && a.tailed ? (float*)(w + L.part) : nullptr;
   a.status = g.status;
   a.wait_limit = g.wait_limit;
   a.stall_test = g.stall_test;
   const int grid = grid_of(p, bn);
   const int split_grid = (int)std::min<int64_t>(spl.tail * (bn / SPLIT_COLS), (int64_t)num_sms() * 16);
-  if (emu && a.splits > 1 &&
+  if (emu && a.tailed &&
       (e = cudaMemsetAsync(a.xtail, 0, (size_t)(a.sc.nlow ? 2 : 1) * spl.tail * BM * bn * 8, s)) != cudaSuccess)
     return e;
   mark_begin(g, s);
   nvtxRangePushA("product");
-  // fp64 split: a second exact sum when the schedule needs it; for short K
-  // (where the flushes weigh) the tile sums in shared memory when a tile's
-  // fit (<= 128 wide; its ring is then 3 stages deep); else at L2
-  const bool smem_sums = bn <= 128 && p.k <= 512;
-  const int mode = !emu ? PAIR_MODE_F32OUT
-                        : (a.sc.nlow ? PAIR_MODE_EMU_FINE : (smem_sums ? PAIR_MODE_EMU_SMEM : PAIR_MODE_EMU));
+  const int mode = emu ? (a.sc.nlow ? PAIR_MODE_EMU_FINE : PAIR_MODE_EMU) : PAIR_MODE_F32OUT;
   e = launch_pair_any<false>(kind, mode, bn, ma, mb, a, grid, s);
   nvtxRangePop();
   mark_end(g, s);  // the events bracket the product kernel alone
-  if (e == cudaSuccess && a.splits > 1) {
+  if (e == cudaSuccess && a.tailed) {
     if (emu)
       k_split_finish<<<split_grid, 256, 0, s>>>(a.xtail, a.full, bn, a.sc.xunit, a.sc.xlo, a.sc.nlow,
                                                 a.single);

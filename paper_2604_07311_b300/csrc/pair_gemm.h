@@ -18,9 +18,7 @@ constexpr int kPairMaxDiag = 10;
 enum { PAIR_KIND_BF16 = 0, PAIR_KIND_TF32 = 1 };
 // fp32 output; fp64 split with one int64 sum per output; fp64 split with a
 // second, exact sum for the fine diagonals (Sched::nlow > 0)
-// fp64 split with one int64 sum per output kept in shared memory for the
-// CTA's current tile (128-wide tiles at most; split items use global slots)
-enum { PAIR_MODE_F32OUT = 0, PAIR_MODE_EMU = 1, PAIR_MODE_EMU_FINE = 2, PAIR_MODE_EMU_SMEM = 3 };
+enum { PAIR_MODE_F32OUT = 0, PAIR_MODE_EMU = 1, PAIR_MODE_EMU_FINE = 2 };
 
 // The unit schedule of one output tile (identical for every tile of a launch).
 struct Sched {

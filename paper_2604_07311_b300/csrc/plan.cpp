@@ -274,10 +274,6 @@ int make_plan(double alpha, const famlies_tensor_t* A, const famlies_tensor_t* B
   p.tile_n = opt && opt->tile_n ? opt->tile_n : env_int("FAMLIES_FORCE_TILE");
   if (p.tile_n != 0 && p.tile_n != 64 && p.tile_n != 128 && p.tile_n != 256)
     return FAMLIES_ERR_INVALID_ARG;
-  // fp64 split with K <= 256: 128-wide tiles (their sums then stay in shared
-  // memory) measured faster than 256-wide ones (8192^2 x 256: 1.60 vs 1.79
-  // ms); from K = 512 on the wider tiles win.
-  if (p.kernel == FAMLIES_KERNEL_TC_EMU && p.tile_n == 0 && p.k <= 256) p.tile_n = 128;
   int s = opt && opt->slices ? opt->slices : env_int("FAMLIES_SLICES");
   if (s == 0) s = 6;
   if (s < 2 || s > 7) return FAMLIES_ERR_INVALID_ARG;
