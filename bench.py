@@ -2,7 +2,7 @@
 
 Workload (one "step"): the particle-particle ladder contraction
     C[a,b,i,j] += sum_{c,d} V[a,b,c,d] T[c,d,i,j]      (v = 128, o = 32)
-in fp64 storage, computed by the split-precision path (7 bf16 integer
+in fp64 storage, computed by the split-precision path (6 bf16 integer
 slices per operand on the tensor cores, exact fp32 accumulation, fp64
 recombination and beta update): exponent pass + pack + product + fix-up,
 inputs resident in HBM.  The labels fuse to a 16384 x 1024 x 16384
@@ -29,11 +29,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "contraction TFLOP/s, % tensor-pipe peak; split-precision vs FP64 speedup"
-# DRAM bytes per product-kernel launch from the ncu capture summarised in
-# profiles/k_pair_gemm_ladder.md (v=112 ladder, 11.58 GB, the same split-K
-# kernel; scaled by executed flops to the v=128 launch).  Must go back to None
-# whenever the product kernel changes after that capture.
-PRODUCT_TRAFFIC = {"bytes": 11.566092e9, "exec_flops": 6.767392063488e12}
+# DRAM bytes per product-kernel launch from an ncu capture of a smaller ladder
+# with the same kernel, scaled by executed flops to the benchmark launch; None
+# whenever the product kernel has changed since the capture.
+PRODUCT_TRAFFIC = None
 V_EXT, O_EXT, SLICES = 128, 32, 6
 WORKLOAD = f"ccsd_ladder_v128_o32_f64_split{SLICES}"
 

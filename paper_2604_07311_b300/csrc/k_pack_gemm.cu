@@ -732,6 +732,9 @@ struct SplitPlan {
   int64_t tail;  // tiles that run split
 };
 
+// Most workspace the deferred finish of short-K fp64-split tiles may take.
+constexpr int64_t kDeferredFinishBytes = (int64_t)2 << 30;
+
 SplitPlan split_plan(const Plan& p, int bn) {
   const int64_t tiles = plan_tiles(p, bn);
   const int64_t sms = num_sms();
@@ -744,8 +747,14 @@ SplitPlan split_plan(const Plan& p, int bn) {
   const int64_t full = (tiles / sms) * sms, tail = tiles - full;
   // fp64 split with short K: every tile's sums go to its slot and a separate
   // kernel finishes them (a tile's finish otherwise stalls the product's
-  // epilogue for about half its time)
-  if (emu && p.k <= 512) return SplitPlan{1, 0, tiles};
+  // epilogue for about half its time).  The slots take 8 bytes per output
+  // element (16 with the fine sums); above kDeferredFinishBytes of them the
+  // tiles finish inside the product instead.
+  if (emu && p.k <= 512) {
+    const Sched sc = make_pair_sched(p.kernel, p.slices, kSplitBits, p.k, 1);
+    const int64_t slot_bytes = (int64_t)BM * bn * 8 * (sc.nlow ? 2 : 1);
+    if (tiles * slot_bytes <= kDeferredFinishBytes) return SplitPlan{1, 0, tiles};
+  }
   // all tiles in one round: enough splits to fill the SMs (at least 16)
   const int64_t most = full == 0 ? std::max<int64_t>(16, (sms + tail - 1) / tail) : 4;
   const int64_t cap = pieces < most ? pieces : most;
@@ -802,11 +811,13 @@ Layout layout_of(const Plan& p) {
     L.fb = off; off += up((size_t)p.l * p.n * 4);
     L.la = off; off += up((size_t)(p.l * p.m + 1) * 4);
     L.lb = off; off += up((size_t)(p.l * p.n + 1) * 4);
-    // per-CTA tile sums; split K adds one slot per tail tile
+    // per-CTA tile sums for the tiles that run whole; split K (and the
+    // deferred finish) adds one slot per tail tile; one int64 sum per
+    // element, two when the fine diagonals keep their own
     const SplitPlan sp = split_plan(p, bn);
-    // two int64 sums per element (coarse and fine diagonals)
-    L.G = off; off += up((size_t)2 * grid_of(p, bn) * BM * bn * 8);
-    L.xtail = off; off += up((size_t)2 * sp.tail * BM * bn * 8);
+    const size_t sums = make_pair_sched(p.kernel, p.slices, kSplitBits, p.k, sp.splits).nlow ? 2 : 1;
+    L.G = off; off += sp.full > 0 ? up(sums * grid_of(p, bn) * BM * bn * 8) : 0;
+    L.xtail = off; off += up(sums * sp.tail * BM * bn * 8);
   } else {
     const int bn = pair_bn_for(p.n, p.tile_n);
     const SplitPlan sp = split_plan(p, bn);

@@ -1,7 +1,8 @@
 """The no-allocation entry point (famlies_contract_noalloc) against the regular
-one.  It serves callers that may not allocate device memory themselves or
-through the library (a pre-reserved device pool, a real-time loop); its
-offset tables live in a fixed scratch array inside the library.
+one and against the oracle.  It serves callers that may not allocate device
+memory themselves or through the library (a pre-reserved device pool, a
+real-time loop); its offset tables live in a fixed scratch array inside the
+library.
 
 This file is collected last on purpose: if it fails, a run that stops at the
 first failure has already run every other test.  It passes both alone in a
@@ -12,6 +13,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2604_07311_b300 as fm
 from paper_2604_07311_b300 import _lib
 from paper_2604_07311_b300 import inputs as W
@@ -36,6 +38,19 @@ def noalloc_abi(alpha, A, la, B, lb, beta, C, lc, dtype: str) -> int:
              torch.cuda.current_stream().cuda_stream)
 
 
+def oracle_dense(p: W.Problem, dtype: str) -> np.ndarray:
+    """The oracle's result on the inputs as the device holds them."""
+    Ar = W.Operand(torch.from_numpy(p.A.buf).to(TORCH_DT[dtype]).double().numpy(), p.A.extents,
+                   p.A.strides, p.A.labels)
+    Br = W.Operand(torch.from_numpy(p.B.buf).to(TORCH_DT[dtype]).double().numpy(), p.B.extents,
+                   p.B.strides, p.B.labels)
+    Cr = W.Operand(torch.from_numpy(p.C.buf).to(OUT_DT[dtype]).double().numpy(), p.C.extents,
+                   p.C.strides, p.C.labels)
+    want = np.array(Cr.view(), copy=True)
+    oracle.contract(p.alpha, Ar.view(), p.A.labels, Br.view(), p.B.labels, p.beta, want, p.C.labels)
+    return want
+
+
 def both_paths(p: W.Problem, dtype: str):
     A = to_device(p.A, TORCH_DT[dtype])
     B = to_device(p.B, TORCH_DT[dtype])
@@ -55,9 +70,11 @@ def test_noalloc_matches_regular_entry_point_on_consecutive_calls():
              (W.ladder(v=16, o=8), "f64"),
              (random_label_problem(rng, max_ext=6, integer=False), "f64")]
     for p, dtype in cases:
+        exact = oracle_dense(p, dtype)
         for _ in range(2):  # two calls in a row share (and rewrite) the scratch array
             got, want = both_paths(p, dtype)
             assert rel_frob(got, want) <= TOL[dtype], (p.name, dtype)
+            assert rel_frob(got, exact) <= TOL[dtype], (p.name, dtype)
     assert fm.device_status() == 0
 
 
