@@ -391,7 +391,8 @@ def run_other(args):
 
     if args.workload == "transpose_free":
         p = W.transpose_free(v=96, o=48, pad=7)
-        for dt, kind, pairs in (("bf16", 2, 1), ("bf16", 3, 1), ("f32", 2, 3), ("f32", 3, 3), ("f32", 1, 1)):
+        for dt, kind, pairs in (("bf16", 4, 1), ("bf16", 5, 1), ("bf16", 2, 1), ("bf16", 3, 1), ("f32", 2, 3),
+                                ("f32", 3, 3), ("f32", 1, 1)):
             tin = torch.bfloat16 if dt == "bf16" else torch.float32
             A, B, C = put(p.A, tin), put(p.B, tin), put(p.C, torch.float32)
             f = lambda **kw: fm.contract(1.0, A, p.A.labels, B, p.B.labels, 0.0, C, p.C.labels,
@@ -399,7 +400,8 @@ def run_other(args):
             ms = _cuda_ms(f, args.steps, args.warmup)
             kms = _product_ms(f)
             print(json.dumps({"workload": "transpose_free_v96_o48_pad7", "dtype": dt,
-                              "path": {1: "cuda_cores", 2: "packed_tma", 3: "direct_gather"}[kind],
+                              "path": {1: "cuda_cores", 2: "packed_tma", 3: "element_gather",
+                                       4: "direct", 5: "direct_all_gathered"}[kind],
                               "ms_per_step": ms, "tflops": p.flops / ms / 1e9, "product_ms": kms,
                               "product_exec_tflops": pairs * p.flops / kms / 1e9,
                               "bf16_peak_sustained": sustained, "peak_source": src}), flush=True)

@@ -119,9 +119,19 @@ typedef struct {
  *   kernel      0 = automatic; 1 = the SIMT (CUDA-core) kernel (F64, F32);
  *               2 = the packed TMA tensor-core kernel (F32, BF16, F64_EMU);
  *               3 = the tensor-core kernel that gathers operand tiles
- *               straight from the strided tensors (F32, BF16).  A choice
- *               the dtype has no kernel for returns FAMLIES_ERR_UNSUPPORTED.
- *   tile_n      tensor-core tile width (64, 128 or 256; 0 = automatic).
+ *               element by element straight from the strided tensors (F32,
+ *               BF16); 4 = the direct bf16 kernel (BF16): tiles staged
+ *               straight from the caller's tensors, by TMA where the
+ *               strides allow it and by gather warps otherwise, no pack;
+ *               5 = the same with both operands gathered (diagnostics).
+ *               Automatic BF16 takes 4 whenever the call fits it (each
+ *               label class at most two modes after fusion, at most one
+ *               batch mode, each operand unit-stride along a free or a
+ *               contracted mode, k <= 16384) and 2 otherwise.  A choice
+ *               the dtype or the call has no kernel for returns
+ *               FAMLIES_ERR_UNSUPPORTED.
+ *   tile_n      tensor-core tile width (64, 128 or 256, or 192 for the
+ *               direct bf16 kernel; 0 = automatic).
  *   wait_limit  iteration cap of every bounded wait (0 = default).
  *   stall_test  testing only (0 in normal use): nonzero makes the
  *               tensor-core product kernels first wait, bounded by
@@ -172,6 +182,8 @@ typedef struct {
 #define FAMLIES_KERNEL_TC_EMU 6    /* fp64 slice split + tcgen05 slice products + fp64 recombination */
 #define FAMLIES_KERNEL_TC_BF16_GATHER 7   /* tcgen05 bf16, tiles gathered straight from strided A, B */
 #define FAMLIES_KERNEL_TC_TF32X3_GATHER 8 /* tcgen05 three-term tf32, tiles gathered straight */
+#define FAMLIES_KERNEL_TC_BF16_DIRECT 9   /* tcgen05 bf16, tiles staged straight from the strided
+                                             tensors by multi-mode TMA boxes or gather warps */
 
 /* C := alpha*contract(A,B) + beta*C on `stream`.  Asynchronous: returns
  * after enqueueing.  Host-side validation errors return before any launch. */

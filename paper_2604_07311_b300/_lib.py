@@ -16,9 +16,10 @@ LIB_PATH = os.path.join(HERE, "libfamlies.so")
 F64, F64_EMU, F32, BF16 = 0, 1, 2, 3
 DTYPES = {"f64": F64, "f64_emu": F64_EMU, "f32": F32, "bf16": BF16}
 KERNELS = {0: "none", 1: "scale", 2: "simt_f64", 3: "simt_f32", 4: "tc_bf16", 5: "tc_tf32x3",
-           6: "tc_emu", 7: "tc_bf16_gather", 8: "tc_tf32x3_gather"}
-# option values for `kernel=`: automatic, CUDA-core, packed tensor-core, gathered tensor-core
-KERNEL_AUTO, KERNEL_SIMT, KERNEL_PACKED, KERNEL_GATHER = 0, 1, 2, 3
+           6: "tc_emu", 7: "tc_bf16_gather", 8: "tc_tf32x3_gather", 9: "tc_bf16_direct"}
+# option values for `kernel=`: automatic, CUDA-core, packed tensor-core, element-gathered
+# tensor-core, direct bf16 (TMA boxes / gather warps), direct bf16 with both operands gathered
+KERNEL_AUTO, KERNEL_SIMT, KERNEL_PACKED, KERNEL_GATHER, KERNEL_DIRECT, KERNEL_DIRECT_GATHER = 0, 1, 2, 3, 4, 5
 ERR_DEVICE_TIMEOUT = -9
 
 EXPORTS = ["famlies_contract", "famlies_contract_ex", "famlies_contract_host",

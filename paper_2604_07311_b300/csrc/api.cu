@@ -83,8 +83,8 @@ struct Range {
 
 const char* kernel_name(int k) {
   static const char* names[] = {"none", "scale", "simt_f64", "simt_f32", "tc_bf16", "tc_tf32x3",
-                                "tc_emu", "tc_bf16_gather", "tc_tf32x3_gather"};
-  return (k >= 0 && k <= 8) ? names[k] : "?";
+                                "tc_emu", "tc_bf16_gather", "tc_tf32x3_gather", "tc_bf16_direct"};
+  return (k >= 0 && k <= 9) ? names[k] : "?";
 }
 
 struct Workspace {
@@ -108,6 +108,43 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
   Range range(kernel_name(p.kernel));
   int rc = check_device();
   if (rc) return rc;
+  if (p.kernel == FAMLIES_KERNEL_TC_BF16_DIRECT) {
+    // no offset tables: tiles come straight from the operands (workspace
+    // only for an operand that must be re-padded for its tensor map)
+    const int64_t wsb = box_workspace_bytes(p);
+    if (wsb < 0) return FAMLIES_ERR_UNSUPPORTED;
+    Workspace ws;
+    ws.s = s;
+    if (wsb > 0 && cudaMallocAsync(&ws.ptr, wsb, s) != cudaSuccess) {
+      cudaGetLastError();
+      ws.ptr = nullptr;
+      return FAMLIES_ERR_ALLOC;
+    }
+    GemmArgs g = {};
+    g.a = p.a;
+    g.b = p.b;
+    g.c = p.c;
+    g.m = p.m;
+    g.n = p.n;
+    g.k = p.k;
+    g.l = p.l;
+    g.alpha = alpha;
+    g.beta = beta;
+    g.wait_limit = (opt && opt->wait_limit > 0) ? opt->wait_limit : env_wait_limit();
+    g.status = device_status_ptr();
+    if (!g.status) return FAMLIES_ERR_CUDA;
+    g.stall_test = opt ? opt->stall_test : 0;
+    g.ev_begin = opt ? (cudaEvent_t)opt->events[0] : nullptr;
+    g.ev_end = opt ? (cudaEvent_t)opt->events[1] : nullptr;
+    int nl = 0;
+    cudaError_t err = launch_box(p, g, ws.ptr, s, &nl);
+    if (info) info->launches = nl;
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      return err == cudaErrorNotSupported ? FAMLIES_ERR_UNSUPPORTED : FAMLIES_ERR_CUDA;
+    }
+    return FAMLIES_OK;
+  }
   int64_t tab_bytes = table_entries(p) * (int64_t)sizeof(int64_t);
   int64_t extra = 0;
   if (p.kernel == FAMLIES_KERNEL_TC_EMU || p.kernel == FAMLIES_KERNEL_TC_BF16 ||
@@ -710,6 +747,8 @@ int famlies_contract_batched(int64_t count, const double* alpha, const famlies_t
   for (int64_t i = 0; i < count; ++i) {
     int rc = make_plan(alpha[i], &A[i], &B[i], &C[i], dtype, nullptr, &plans[i]);
     if (rc) return rc;
+    // bf16 problems stay on the packed kernel, which the grouped launch runs
+    if (plans[i].kernel == FAMLIES_KERNEL_TC_BF16_DIRECT) plans[i].kernel = FAMLIES_KERNEL_TC_BF16;
   }
   if (count == 0) return FAMLIES_OK;
   int rc = check_device();

@@ -85,6 +85,13 @@ cudaError_t launch_simt(const Plan& p, const GemmArgs& g, void* ws, cudaStream_t
 // Bytes of the partial tiles a CUDA-core launch splits K into (0: no split).
 int64_t simt_workspace_bytes(const Plan& p);
 cudaError_t launch_tc(const Plan& p, const GemmArgs& g, int tile_n, void* ws, cudaStream_t s);
+// Direct bf16 kernel (csrc/k_box.cu; box_applicable in plan.h), no offset
+// tables: its workspace (a re-padded copy of each operand whose strides no
+// tensor map can address; 0 bytes when both can be read as they stand, or
+// when Plan::force_gather stages them by gather warps), and its launch (the
+// re-pad copies, then the product; *launches counts them).
+int64_t box_workspace_bytes(const Plan& p);
+cudaError_t launch_box(const Plan& p, const GemmArgs& g, void* ws, cudaStream_t s, int* launches);
 int64_t tc_workspace_bytes(const Plan& p);
 // Packed paths (bf16, tf32 split, fp64 split): workspace size and launch.
 int64_t packed_workspace_bytes(const Plan& p);

@@ -244,7 +244,8 @@ int make_plan(double alpha, const famlies_tensor_t* A, const famlies_tensor_t* B
 
   // ---- kernel choice
   const int force = opt ? opt->kernel : 0;
-  if (force < 0 || force > 3) return FAMLIES_ERR_INVALID_ARG;
+  if (force < 0 || force > 5) return FAMLIES_ERR_INVALID_ARG;
+  if (force >= 4 && dtype != FAMLIES_BF16 && !p.c_empty && !p.scale_only) return FAMLIES_ERR_UNSUPPORTED;
   if (p.c_empty) p.kernel = FAMLIES_KERNEL_NONE;
   else if (p.scale_only) p.kernel = FAMLIES_KERNEL_SCALE;
   else switch (dtype) {
@@ -272,8 +273,18 @@ int make_plan(double alpha, const famlies_tensor_t* A, const famlies_tensor_t* B
     return e ? std::atoi(e) : 0;
   };
   p.tile_n = opt && opt->tile_n ? opt->tile_n : env_int("FAMLIES_FORCE_TILE");
-  if (p.tile_n != 0 && p.tile_n != 64 && p.tile_n != 128 && p.tile_n != 256)
+  if (p.tile_n != 0 && p.tile_n != 64 && p.tile_n != 128 && p.tile_n != 192 && p.tile_n != 256)
     return FAMLIES_ERR_INVALID_ARG;
+  // bf16: the direct kernel (tiles staged from the caller's strides) when
+  // the call fits it, unless another kernel was asked for
+  if (p.kernel == FAMLIES_KERNEL_TC_BF16 && (force == 0 || force >= 4)) {
+    p.kernel = FAMLIES_KERNEL_TC_BF16_DIRECT;
+    if (!box_applicable(p)) {
+      if (force >= 4) return FAMLIES_ERR_UNSUPPORTED;
+      p.kernel = FAMLIES_KERNEL_TC_BF16;
+    }
+  }
+  p.force_gather = force == 5 ? 3 : 0;
   int s = opt && opt->slices ? opt->slices : env_int("FAMLIES_SLICES");
   if (s == 0) s = 6;
   if (s < 2 || s > 7) return FAMLIES_ERR_INVALID_ARG;

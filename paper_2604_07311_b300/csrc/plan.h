@@ -75,6 +75,7 @@ struct Plan {
   int kernel = FAMLIES_KERNEL_NONE;
   int slices = 6;
   int tile_n = 0;  // tensor-core tile width request (0 = automatic)
+  int force_gather = 0;  // direct bf16 kernel: operands staged by gather warps (bit 0 row, bit 1 column)
   // Symmetric packed operand (famlies_contract_sym): n > 0 when the row
   // (side 0) or column (side 1) operand is stored as the lower triangle of
   // a symmetric n x n matrix; its classes are then one mode each (rows and
@@ -101,5 +102,12 @@ int make_plan(double alpha, const famlies_tensor_t* A, const famlies_tensor_t* B
               Plan* out);
 
 void fill_info(const Plan& p, famlies_plan_info_t* info);
+
+// The direct bf16 kernel (csrc/k_box.cu) accumulates the whole contracted
+// range in tensor memory: at most this many k.
+constexpr int64_t kBoxMaxK = 16384;
+// Whether plan p (kernel TC_BF16 or TC_BF16_DIRECT) fits the direct bf16
+// kernel.  Host only: no device work.
+bool box_applicable(const Plan& p);
 
 }  // namespace famlies

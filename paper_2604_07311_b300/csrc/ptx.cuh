@@ -74,6 +74,17 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// 5-D tiled load (coordinates innermost first).
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int32_t c0, int32_t c1, int32_t c2, int32_t c3,
+                                            int32_t c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
+
 // ------------------------------------------------------------------ tcgen05
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -160,11 +171,41 @@ __device__ __forceinline__ uint64_t sdesc_kmajor(uint32_t saddr) {
   return ROW_BYTES == 128 ? sdesc_kmajor_sw128(saddr) : sdesc_kmajor_sw64(saddr);
 }
 
+// General shared-memory matrix descriptor: start address, leading and
+// stride byte offsets, and the swizzle span in bytes of one row of the
+// layout (128, 64 or 32; layout types 2, 4 and 6).  K-major operands: rows
+// are M (or N) indices, the stride offset steps over 8-row groups and the
+// leading offset is unused.  MN-major operands: rows are k indices holding
+// a run of consecutive M (or N) elements, the stride offset steps over
+// 8-row groups along k and the leading offset from one run of M (N)
+// elements to the next.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo, int swz_bytes) {
+  const uint64_t type = swz_bytes == 128 ? 2 : (swz_bytes == 64 ? 4 : 6);
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) | (type << 61);
+}
+
 // Instruction descriptor: fp32 accumulator, K-major A and B, M x N tile.
 // fmt: kind::f16 -> 0 f16, 1 bf16; kind::tf32 -> 2.
 __host__ __device__ constexpr uint32_t idesc_make(int M, int N, uint32_t fmt) {
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
+}
+
+// Same with the operands' majorness: a_mn / b_mn = 1 when A / B is stored
+// MN-major in shared memory (the descriptor's transpose bits 15 and 16).
+__host__ __device__ constexpr uint32_t idesc_make_mn(int M, int N, uint32_t fmt, uint32_t a_mn,
+                                                     uint32_t b_mn) {
+  return idesc_make(M, N, fmt) | (a_mn << 15) | (b_mn << 16);
+}
+
+// Byte offset inside a tile stored with a `swz_bytes` swizzle (128/64/32):
+// the 16-byte chunk index (bits 4..) is XORed with the row-group bits 7..,
+// the same function of the address that TMA applies when it writes a tile
+// and the tensor cores apply when they read one (tile base 1024-aligned).
+__host__ __device__ __forceinline__ uint32_t swizzle_off(uint32_t off, int swz_bytes) {
+  const uint32_t mask = swz_bytes == 128 ? 7u : (swz_bytes == 64 ? 3u : 1u);
+  return off ^ (((off >> 7) & mask) << 4);
 }
 
 __device__ __forceinline__ uint32_t tf32_round(float x) {

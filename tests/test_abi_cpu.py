@@ -71,7 +71,37 @@ def test_plan_transpose_free_swaps_roles():
     assert (info["m"], info["n"], info["k"]) == (18, 18, 18)
     assert info["m_modes"] == 2 and info["n_modes"] == 2
     assert info["a_contig"] == 1 and info["b_contig"] == 1 and info["c_contig"] == 1
-    assert info["kernel_name"] == "tc_bf16"
+    # every class has two modes and each operand is unit-stride along a free
+    # mode: the direct kernel stages its tiles from the strides (no pack)
+    assert info["kernel_name"] == "tc_bf16_direct"
+    assert P(W.transpose_free(v=6, o=3, pad=7), dtype="bf16", kernel=2)["kernel_name"] == "tc_bf16"
+
+
+def test_plan_direct_bf16_selection():
+    """The direct bf16 kernel takes a call when every class has at most two
+    modes, the batch at most one, each operand has a unit stride along a free
+    or a contracted mode and k <= 16384; otherwise the packed kernel does,
+    and asking for the direct one is an error."""
+    gemm = dict(A_shape=(64, 32), A_strides=(1, 64), la=[1, 2], B_shape=(32, 48), B_strides=(1, 32),
+                lb=[2, 3], C_shape=(64, 48), C_strides=(1, 64), lc=[1, 3], dtype="bf16")
+    assert fm.plan(**gemm)["kernel_name"] == "tc_bf16_direct"
+    long_k = dict(gemm, A_shape=(64, 20000), B_shape=(20000, 48), B_strides=(1, 20000))
+    assert fm.plan(**long_k)["kernel_name"] == "tc_bf16"
+    # three row modes that do not fuse
+    three = dict(gemm, A_shape=(4, 4, 4, 32), A_strides=(1, 5, 25, 125), la=[1, 4, 5, 2],
+                 C_shape=(4, 4, 4, 48), C_strides=(1, 4, 16, 64), lc=[1, 4, 5, 3])
+    assert fm.plan(**three)["kernel_name"] == "tc_bf16"
+    # no unit stride in A at all
+    strided = dict(gemm, A_strides=(2, 128))
+    assert fm.plan(**strided)["kernel_name"] == "tc_bf16"
+    for bad in (long_k, three, strided):
+        with pytest.raises(fm.FamliesError) as e:
+            fm.plan(**bad, kernel=4)
+        assert e.value.code == -6
+    with pytest.raises(fm.FamliesError) as e:
+        fm.plan(**dict(gemm, dtype="f32"), kernel=4)
+    assert e.value.code == -6
+    assert fm.plan(**gemm, kernel=5)["kernel_name"] == "tc_bf16_direct"
 
 
 def test_plan_batch_labels_and_extent_one_modes():
