@@ -84,6 +84,13 @@ struct BoxArgs {
   int64_t l;              // batch extent
   float* c;
   int64_t cs[5];          // C strides: m0, m1, n0, n1, batch
+  // split K of the last, partly empty round: items [0, full) are whole
+  // tiles; the `tail` tiles after them run as `splits` items each over parts
+  // of the k blocks, writing fp32 partial tiles part[split][tail tile][BN][BM]
+  // that k_box_reduce sums in split order (splits == 1: no split)
+  int64_t full, tail;
+  int splits;
+  float* part;
   float alpha, beta;
   int* status;
   int64_t wait_limit;
@@ -125,6 +132,33 @@ __device__ __forceinline__ TileIx tile_ix(const BoxArgs& a, int64_t t) {
   x.tn0 = tn % a.t0[1];
   x.tn1 = tn / a.t0[1];
   return x;
+}
+
+// Work item t: a tile and the k blocks [kb_lo, kb_hi) it covers; split >= 0
+// for a split item (ti: its index among the tail tiles).
+struct Item {
+  TileIx T;
+  int64_t kb_lo, kb_hi, ti;
+  int split;
+};
+
+__device__ __forceinline__ Item item_at(const BoxArgs& a, int64_t t, int64_t nkb) {
+  Item it;
+  int64_t tile = t;
+  it.split = -1;
+  it.ti = 0;
+  it.kb_lo = 0;
+  it.kb_hi = nkb;
+  if (a.splits > 1 && t >= a.full) {
+    const int64_t u = t - a.full;
+    it.ti = u % a.tail;
+    it.split = (int)(u / a.tail);
+    tile = a.full + it.ti;
+    it.kb_lo = nkb * it.split / a.splits;
+    it.kb_hi = nkb * (it.split + 1) / a.splits;
+  }
+  it.T = tile_ix(a, tile);
+  return it;
 }
 
 __device__ __forceinline__ uint4 ldg_nc_v4(const void* p) {
@@ -306,8 +340,8 @@ __global__ void __launch_bounds__(BoxCfg<BN, NG>::THREADS, 1)
 
   const BoxArgs& A = args;
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-  const int64_t ntiles = A.t0[0] * A.t1[0] * A.t0[1] * A.t1[1] * A.l;
   const int64_t nkb = A.nk0 * A.nk1;
+  const int64_t nitems = A.splits > 1 ? A.full + A.tail * A.splits : A.t0[0] * A.t1[0] * A.t0[1] * A.t1[1] * A.l;
   const int64_t lim = A.wait_limit;
   const bool tma0 = A.op[0].tma, tma1 = A.op[1].tma;
   const bool any_tma = tma0 || tma1;
@@ -347,14 +381,15 @@ __global__ void __launch_bounds__(BoxCfg<BN, NG>::THREADS, 1)
       int stage = 0;
       uint32_t phase = 0, pending = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const TileIx T = tile_ix(A, t);
+      for (int64_t t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
+        const Item I = item_at(A, t, nkb);
+        const TileIx& T = I.T;
         const TmaCoords ta = tile_coords(A.op[0], (int32_t)(T.tm0 * A.op[0].b0), (int32_t)(T.tm1 * A.op[0].b1),
                                          (int32_t)T.il);
         const TmaCoords tb = tile_coords(A.op[1], (int32_t)(T.tn0 * A.op[1].b0), (int32_t)(T.tn1 * A.op[1].b1),
                                          (int32_t)T.il);
-        int32_t kb0 = 0, k0s = 0, k1s = 0;
-        for (int64_t kb = 0; kb < nkb; ++kb) {
+        int32_t kb0 = (int32_t)(I.kb_lo % A.nk0), k0s = kb0 * A.bk0, k1s = (int32_t)(I.kb_lo / A.nk0) * A.bk1;
+        for (int64_t kb = I.kb_lo; kb < I.kb_hi; ++kb) {
           if (!ptx::mbar_wait(&empty[stage], phase ^ 1, lim, abort)) { ok = false; break; }
           uint8_t* st = smem + stage * Cfg::STAGE_BYTES;
           ptx::mbar_arrive_expect_tx(&full[stage], bytes);
@@ -392,17 +427,23 @@ __global__ void __launch_bounds__(BoxCfg<BN, NG>::THREADS, 1)
       uint32_t phase = 0, acc = 0, accph = 0;
       // testing: `done` completes only after this thread's last commit
       bool ok = !A.stall_test || ptx::mbar_wait(done, 0, lim, abort);
-      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int64_t t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
+        int64_t kb_lo = 0, kb_hi = nkb;
+        if (A.splits > 1 && t >= A.full) {
+          const int sp = (int)((t - A.full) / A.tail);
+          kb_lo = nkb * sp / A.splits;
+          kb_hi = nkb * (sp + 1) / A.splits;
+        }
         if (!ptx::mbar_wait(&tempty[acc], accph ^ 1, lim, abort)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t dt = tmem_base + acc * BN;
-        for (int64_t kb = 0; kb < nkb; ++kb) {
+        for (int64_t kb = kb_lo; kb < kb_hi; ++kb) {
           if (!ptx::mbar_wait(&full[stage], phase, lim, abort)) { ok = false; break; }
           ptx::tc_fence_after();
           const uint64_t so = (uint64_t)((uint32_t)(stage * Cfg::STAGE_BYTES) >> 4);
 #pragma unroll
           for (int s = 0; s < KB / 16; ++s)
-            ptx::mma_f16(dt, da[s] + so, db[s] + so, idesc, (kb | s) ? 1u : 0u);
+            ptx::mma_f16(dt, da[s] + so, db[s] + so, idesc, (kb != kb_lo || s) ? 1u : 0u);
           ptx::mma_commit(&empty[stage]);
           if (++stage == Cfg::STAGES) { stage = 0; phase ^= 1; }
         }
@@ -425,8 +466,9 @@ __global__ void __launch_bounds__(BoxCfg<BN, NG>::THREADS, 1)
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < ntiles && ok && any_gather; t += gridDim.x) {
-        const TileIx T = tile_ix(A, t);
+      for (int64_t t = blockIdx.x; t < nitems && ok && any_gather; t += gridDim.x) {
+        const Item I = item_at(A, t, nkb);
+        const TileIx& T = I.T;
         GatherCtx cx[2];
         const int64_t tr0[2] = {T.tm0, T.tn0}, tr1[2] = {T.tm1, T.tn1};
 #pragma unroll
@@ -437,8 +479,8 @@ __global__ void __launch_bounds__(BoxCfg<BN, NG>::THREADS, 1)
           cx[w].lim0 = (int)min(X.e[0] - o0, (int64_t)1 << 30);
           cx[w].lim1 = (int)min(X.e[1] - o1, (int64_t)1 << 30);
         }
-        int64_t kb0 = 0, k0s = 0, k1s = 0;
-        for (int64_t kb = 0; kb < nkb; ++kb) {
+        int64_t kb0 = I.kb_lo % A.nk0, k0s = kb0 * A.bk0, k1s = (I.kb_lo / A.nk0) * A.bk1;
+        for (int64_t kb = I.kb_lo; kb < I.kb_hi; ++kb) {
           if (!ptx::mbar_wait(&empty[stage], phase ^ 1, lim, abort)) { ok = false; break; }
           const uint32_t st = ptx::smem_u32(smem + stage * Cfg::STAGE_BYTES);
 #pragma unroll
@@ -466,14 +508,34 @@ __global__ void __launch_bounds__(BoxCfg<BN, NG>::THREADS, 1)
     const BoxOp& P = A.op[0];
     const BoxOp& Q = A.op[1];
     uint32_t acc = 0, accph = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      const TileIx T = tile_ix(A, t);
+    for (int64_t t = blockIdx.x; t < nitems; t += gridDim.x) {
+      const Item I = item_at(A, t, nkb);
+      const TileIx& T = I.T;
       if (!ptx::mbar_wait(&tfull[acc], accph, lim, abort)) {
         if (!*abort) record_timeout(abort, A.status);
         break;
       }
       ptx::tc_fence_after();
       const int lr = qd * 32 + lane;
+      if (I.split >= 0) {
+        // a split item: its fp32 partial tile, column by column (rows
+        // contiguous), summed with alpha and beta by k_box_reduce
+        float* pt = A.part + ((size_t)I.split * (size_t)A.tail + (size_t)I.ti) * BM * BN + lr;
+#pragma unroll 1
+        for (int q = 0; q < CPT / 32; ++q) {
+          uint32_t r[32];
+          ptx::tmem_ld32(tmem_base + lane_addr + acc * BN + hf * CPT + q * 32, r);
+          ptx::tmem_ld_wait();
+#pragma unroll
+          for (int i = 0; i < 32; ++i) pt[(size_t)(hf * CPT + q * 32 + i) * BM] = __uint_as_float(r[i]);
+        }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
+        acc ^= 1;
+        if (acc == 0) accph ^= 1;
+        continue;
+      }
       const int64_t r0 = T.tm0 * P.b0 + lr % P.b0, r1 = T.tm1 * P.b1 + lr / P.b0;
       const bool rv = r0 < P.e[0] && r1 < P.e[1];
       const int64_t crow = r0 * A.cs[0] + r1 * A.cs[1] + T.il * A.cs[4];
@@ -667,6 +729,31 @@ struct BoxPlan {
   int64_t tiles;
 };
 
+// Splits of the tail (the last, partly empty round of the persistent grid):
+// s items per tail tile take ceil(tail s / SMs) / s rounds instead of one;
+// s minimises that (each step up must save 2 %), up to 4 when whole rounds
+// precede the tail, else up to max(16, SMs / tiles), and each split keeps at
+// least 4 k blocks (256 k).  Returns s; *rounds gets the launch's rounds.
+int tail_splits(int64_t tiles, int64_t sms, int64_t nkb, double* rounds_out) {
+  const int64_t full = (tiles / sms) * sms, tail = tiles - full;
+  auto rounds = [&](int64_t sp) { return (double)((tail * sp + sms - 1) / sms) * (1.0 / (double)sp + 0.01); };
+  int64_t best = 1;
+  if (tail > 0) {
+    const int64_t most = full == 0 ? std::max<int64_t>(16, (sms + tail - 1) / tail) : 4;
+    const int64_t cap = std::min<int64_t>(most, nkb / 4);
+    for (int64_t sp = 2; sp <= cap; ++sp)
+      if (rounds(sp) < 0.98 * rounds(best)) best = sp;
+  }
+  if (rounds_out) *rounds_out = (double)(full / sms) + (tail > 0 ? rounds(best) : 0.0);
+  return (int)best;
+}
+
+double split_rounds(int64_t tiles, int64_t sms, int64_t nkb) {
+  double r = 0.0;
+  tail_splits(tiles, sms, nkb, &r);
+  return r;
+}
+
 // Structural plan (no device work, no tensor maps): false when the call
 // does not fit the kernel (the packed path then serves it).
 bool plan_box(const Plan& p, int tile_n, BoxPlan* out) {
@@ -723,7 +810,7 @@ bool plan_box(const Plan& p, int tile_n, BoxPlan* out) {
     pick_box(pr[1].m[0].ext, pr[1].m[1].ext, cands[c], 16, &b0, &b1);
     const int64_t tiles = t0a * t1a * ((pr[1].m[0].ext + b0 - 1) / b0) * ((pr[1].m[1].ext + b1 - 1) / b1) *
                           (p.l > 0 ? p.l : 1);
-    const double cost = (double)((tiles + sms - 1) / sms) * cands[c] * eff[c];
+    const double cost = split_rounds(tiles, sms, a.nk0 * a.nk1) * cands[c] * eff[c];
     if (best < 0 || cost < best - 1e-9) {
       best = cost;
       bn = cands[c];
@@ -783,6 +870,56 @@ bool plan_box(const Plan& p, int tile_n, BoxPlan* out) {
   return out->tiles > 0;
 }
 
+// Split K: C = alpha * (sum of the splits' partial tiles, in split order) +
+// beta * C for the tail tiles.  Grid (column chunks, tail tiles); thread t
+// owns row t % 128 and columns chunk * 16 + t / 128 + 2 j.
+__global__ void __launch_bounds__(256) k_box_reduce(const BoxArgs a, int bn) {
+  constexpr int COLS = 16, PER = COLS / 2;
+  const BoxOp& P = a.op[0];
+  const BoxOp& Q = a.op[1];
+  const int lr = threadIdx.x % BM, lq = threadIdx.x / BM;
+  const size_t per_tile = (size_t)BM * bn, per_split = (size_t)a.tail * per_tile;
+  const int64_t ti = blockIdx.y;
+  const int c0 = blockIdx.x * COLS;
+  const TileIx T = tile_ix(a, a.full + ti);
+  const int64_t r0 = T.tm0 * P.b0 + lr % P.b0, r1 = T.tm1 * P.b1 + lr / P.b0;
+  if (!(r0 < P.e[0] && r1 < P.e[1])) return;
+  const int64_t crow = r0 * a.cs[0] + r1 * a.cs[1] + T.il * a.cs[4];
+  float sum[PER], old[PER];
+  int64_t off[PER];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int lc = c0 + lq + 2 * j;
+    const int64_t n0 = T.tn0 * Q.b0 + lc % Q.b0, n1 = T.tn1 * Q.b1 + lc / Q.b0;
+    off[j] = (n0 < Q.e[0] && n1 < Q.e[1]) ? crow + n0 * a.cs[2] + n1 * a.cs[3] : -1;
+    sum[j] = 0.f;
+  }
+  const float* pt = a.part + (size_t)ti * per_tile + (size_t)(c0 + lq) * BM + lr;
+  for (int sp = 0; sp < a.splits; ++sp) {
+    float v[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) v[j] = pt[(size_t)sp * per_split + (size_t)(2 * j) * BM];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) sum[j] += v[j];
+  }
+#pragma unroll
+  for (int j = 0; j < PER; ++j) old[j] = (off[j] >= 0 && a.beta != 0.f) ? a.c[off[j]] : 0.f;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    float v = a.alpha * sum[j];
+    if (a.beta != 0.f) v = fmaf(a.beta, old[j], v);
+    if (off[j] >= 0) a.c[off[j]] = v;
+  }
+}
+
+void plan_splits(BoxPlan& bp, int64_t nkb) {
+  BoxArgs& a = bp.a;
+  const int64_t sms = num_sms();
+  a.full = (bp.tiles / sms) * sms;
+  a.tail = bp.tiles - a.full;
+  a.splits = tail_splits(bp.tiles, sms, nkb, nullptr);
+}
+
 template <int BN, int NG>
 cudaError_t launch_cfg(const CUtensorMap& ma, const CUtensorMap& mb, const BoxArgs& a, int grid, cudaStream_t s) {
   using Cfg = BoxCfg<BN, NG>;
@@ -825,32 +962,43 @@ struct RepadArgs {
   int64_t rows;   // product of the other extents
 };
 
-// One warp per row (a fixed index of every mode but u); lanes copy pairs of
-// elements along u (aligned 4-byte stores: every destination row starts on
-// a 16-byte boundary).
+// One thread per 16-byte destination chunk (8 consecutive elements along u of
+// one row: a fixed index of every mode but u), so every thread's loads are
+// independent of every other's; index arithmetic in 32 bits (the host
+// checks that the chunk count fits).  Destination rows start on 16-byte
+// boundaries, so a full chunk is one aligned 16-byte store.
 __global__ void __launch_bounds__(256) k_repad(const uint16_t* __restrict__ src, uint16_t* __restrict__ dst,
                                                const RepadArgs r) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
-  const int64_t eu = r.e[r.u], ssu = r.ss[r.u];
-  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; row < r.rows; row += warps) {
-    int64_t rest = row, so = 0, dof = 0;
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-      if (m == r.u) continue;
-      const int64_t i = rest % r.e[m];
-      rest /= r.e[m];
-      so += i * r.ss[m];
-      dof += i * r.ds[m];
+  uint32_t m4[4], e4[4];
+  int nm = 0;
+  for (int m = 0; m < 5; ++m)
+    if (m != r.u) {
+      m4[nm] = (uint32_t)m;
+      e4[nm++] = (uint32_t)r.e[m];
     }
-    for (int64_t x = 2 * lane; x < eu; x += 64) {
-      const uint32_t lo = src[so + x * ssu];
-      if (x + 1 < eu) {
-        const uint32_t hi = src[so + (x + 1) * ssu];
-        *(uint32_t*)(dst + dof + x) = lo | (hi << 16);
-      } else {
-        dst[dof + x] = (uint16_t)lo;
-      }
+  const uint32_t eu = (uint32_t)r.e[r.u], cpr = (eu + 7) / 8;
+  const int64_t ssu = r.ss[r.u];
+  const uint32_t items = (uint32_t)(r.rows * cpr);
+  for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
+    uint32_t rest = it / cpr;
+    const uint32_t x0 = (it - rest * cpr) * 8;
+    int64_t so = 0, dof = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t q = rest / e4[j], i = rest - q * e4[j];
+      rest = q;
+      so += (int64_t)i * r.ss[m4[j]];
+      dof += (int64_t)i * r.ds[m4[j]];
+    }
+    const uint32_t n = eu - x0 < 8 ? eu - x0 : 8;
+    uint32_t v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = e < (int)n ? src[so + (int64_t)(x0 + e) * ssu] : 0u;
+    if (n == 8) {
+      *(uint4*)(dst + dof + x0) = make_uint4(v[0] | (v[1] << 16), v[2] | (v[3] << 16), v[4] | (v[5] << 16),
+                                             v[6] | (v[7] << 16));
+    } else {
+      for (uint32_t e = 0; e < n; ++e) dst[dof + x0 + e] = (uint16_t)v[e];
     }
   }
 }
@@ -900,7 +1048,8 @@ bool prepare_box(const Plan& p, int force_gather, BoxLaunch* L) {
   if (!plan_box(p, p.tile_n, &L->bp)) return false;
   BoxArgs& a = L->bp.a;
   std::memset(L->maps, 0, sizeof(L->maps));
-  L->ws = 0;
+  plan_splits(L->bp, a.nk0 * a.nk1);
+  L->ws = a.splits > 1 ? ((int64_t)a.splits * a.tail * BM * L->bp.bn * 4 + 255) / 256 * 256 : 0;
   for (int w = 0; w < 2; ++w) {
     L->repad[w] = false;
     L->off[w] = 0;
@@ -913,6 +1062,7 @@ bool prepare_box(const Plan& p, int force_gather, BoxLaunch* L) {
     }
     BoxOp padded;
     const int64_t bytes = repad_layout(X, &L->rp[w], &padded);
+    if (L->rp[w].rows * ((X.e[L->rp[w].u] + 7) / 8) >= ((int64_t)1 << 32)) continue;  // gathered instead
     L->repad[w] = true;
     L->off[w] = L->ws;
     L->ws += (bytes + 255) / 256 * 256;
@@ -942,7 +1092,8 @@ cudaError_t launch_box(const Plan& p, const GemmArgs& g, void* ws, cudaStream_t 
     if (!L.repad[w]) continue;
     if (!ws) return cudaErrorInvalidValue;
     uint16_t* dst = (uint16_t*)((char*)ws + L.off[w]);
-    const int64_t blocks = std::min<int64_t>((L.rp[w].rows + 7) / 8, (int64_t)num_sms() * 16);
+    const int64_t chunks = L.rp[w].rows * ((L.rp[w].e[L.rp[w].u] + 7) / 8);
+    const int64_t blocks = std::min<int64_t>((chunks + 255) / 256, (int64_t)num_sms() * 16);
     k_repad<<<(int)std::max<int64_t>(blocks, 1), 256, 0, s>>>((const uint16_t*)a.op[w].x, dst, L.rp[w]);
     if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return e;
     ++n;
@@ -955,13 +1106,23 @@ cudaError_t launch_box(const Plan& p, const GemmArgs& g, void* ws, cudaStream_t 
   a.status = g.status;
   a.wait_limit = g.wait_limit;
   a.stall_test = g.stall_test;
-  const int grid = (int)std::min<int64_t>(L.bp.tiles, num_sms());
+  a.part = a.splits > 1 ? (float*)ws : nullptr;  // the partial tiles lead the workspace
+  if (a.splits > 1 && !ws) return cudaErrorInvalidValue;
+  const int64_t items = a.splits > 1 ? a.full + a.tail * a.splits : L.bp.tiles;
+  const int grid = (int)std::min<int64_t>(items, num_sms());
   const bool gather = !a.op[0].tma || !a.op[1].tma;
   mark_begin(g, s);
   cudaError_t e = gather ? launch_ng<NGATHER>(L.bp.bn, L.maps[0], L.maps[1], a, grid, s)
                          : launch_ng<0>(L.bp.bn, L.maps[0], L.maps[1], a, grid, s);
   mark_end(g, s);
-  if (launches) *launches = n + 1;
+  ++n;
+  if (e == cudaSuccess && a.splits > 1) {
+    // grid.y over the tail tiles (fewer than the SMs, so within its limit)
+    k_box_reduce<<<dim3((unsigned)(L.bp.bn / 16), (unsigned)a.tail), 256, 0, s>>>(a, L.bp.bn);
+    e = cudaGetLastError();
+    ++n;
+  }
+  if (launches) *launches = n;
   return e;
 }
 

@@ -153,11 +153,14 @@ def test_packed_and_direct_agree_bitwise_on_integers():
 
 def test_full_size_transpose_free_direct_sampled():
     """v=96, o=48 (M = N = K = 4608) through the default bf16 path: the direct
-    kernel after one re-pad copy of the padded operand; 512 sampled entries
-    computed one by one by the oracle."""
+    kernel after one re-pad copy of the padded operand, its last round split
+    along k; 512 sampled entries computed one by one by the oracle (tail
+    tiles and whole ones alike)."""
     p = W.transpose_free(v=96, o=48, pad=7)
     C, info = run_gpu(p, "bf16")
-    assert info["kernel_name"] == "tc_bf16_direct" and info["launches"] == 2  # re-pad of A, product
+    # re-pad of A, product (648 tiles of 128 x 256: 4 whole rounds, then the
+    # 56-tile tail split in two along k), split reduction
+    assert info["kernel_name"] == "tc_bf16_direct" and info["launches"] == 3
     assert (info["m"], info["n"], info["k"]) == (4608, 4608, 4608)
     rng = np.random.default_rng(705)
     idx = np.stack([rng.integers(0, e, 512) for e in p.C.extents], axis=1)
@@ -194,3 +197,41 @@ def test_bounded_wait_timeout_direct():
     assert info["kernel_name"] == "tc_bf16_direct"
     assert rel_frob(gpu_dense(C), run_oracle(p, in_dtype=torch.bfloat16)) <= TOL
     assert fm.device_status() == 0
+
+
+@pytest.mark.parametrize("kernel", DIRECT)
+def test_split_k_few_tiles(kernel):
+    """Two output tiles and k = 8192: the tiles' k ranges are split across the
+    SMs, every split writes an fp32 partial tile and a reduction sums them in
+    split order (deterministic) with alpha and beta."""
+    rng = np.random.default_rng(707)
+    m, n, k = 200, 64, 8192
+    A = W.uniform_operand(rng, (m, k), [1, 2])
+    B = W.uniform_operand(rng, (k, n), [2, 3])
+    C = W.uniform_operand(rng, (m, n), [1, 3])
+    p = W.Problem("split_k", 0.75, A, B, -1.5, C)
+    Cg, info = run_gpu(p, "bf16", kernel=kernel)
+    assert info["kernel_name"] == "tc_bf16_direct" and info["launches"] == 2  # product + reduction
+    want = run_oracle(p, in_dtype=torch.bfloat16, out_dtype=torch.float32)
+    assert rel_frob(gpu_dense(Cg), want) <= TOL
+    Cg2, _ = run_gpu(p, "bf16", kernel=kernel)
+    assert torch.equal(Cg, Cg2)  # the split order is fixed
+
+
+def test_split_tail_integer_exact():
+    """178 tiles on 148 SMs (tile width 256): one whole round, then the 30-tile
+    tail split along k; integer inputs make every partial sum exact, so
+    sampled entries of tail and whole tiles match the oracle exactly."""
+    rng = np.random.default_rng(708)
+    m, n, k = 89 * 128, 512, 4096
+    A = W.integer_operand(rng, (m, k), [1, 2], lo=-2, hi=2)
+    B = W.integer_operand(rng, (k, n), [2, 3], lo=-2, hi=2)
+    C = W.zeros_operand((m, n), [1, 3])
+    p = W.Problem("split_tail", 1.0, A, B, 0.0, C)
+    Cg, info = run_gpu(p, "bf16", tile_n=256)
+    assert info["kernel_name"] == "tc_bf16_direct" and info["launches"] == 2
+    got = gpu_dense(Cg)
+    rows = np.concatenate([rng.integers(74 * 128, m, 48), rng.integers(0, 74 * 128, 16)])
+    idx = np.stack([rows, rng.integers(0, n, rows.size)], axis=1)
+    want = oracle.entries(1.0, A.view(), A.labels, B.view(), B.labels, 0.0, C.view(), C.labels, idx)
+    assert np.array_equal(got[idx[:, 0], idx[:, 1]], want)
