@@ -11,6 +11,9 @@ exceeds L2, so every step streams its inputs from HBM.
 
 Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 (test infrastructure, the reference arm here) on a bounded sample instead.
+`--workload <name>` (or `all`) prints the secondary workloads instead, one
+line each with its roofline, the oracle's time on a slice of it and the
+error of sampled entries against the oracle.
 """
 from __future__ import annotations
 
@@ -278,6 +281,11 @@ def run_gpu(args):
     # ---- native fp64 on the GPU (the speedup denominator) and agreement
     Ce = C0.clone()
     step(Ce)
+    torch.cuda.synchronize()
+    # the error against the oracle: 4096 entries of the full result against
+    # the oracle's compensated (Dot2) sums, outside the timed region
+    err_oracle, err_note = sampled_error(p.alpha, p.A.view(), la, p.B.view(), lb, p.beta, p.C.view(), lc,
+                                         host64(Ce), n=4096, seed=21, dot2=True)
     Cn = C0.clone()
     fm.contract(p.alpha, V, la, T, lb, p.beta, Cn, lc, dtype="f64")  # warm-up
     Cn.copy_(C0)
@@ -321,6 +329,7 @@ def run_gpu(args):
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "speedup_vs_native_f64": native_ms / ms,
         "native_f64": {"ms": native_ms, "tflops": flops / (native_ms * 1e-3) / 1e12},
+        "rel_err_vs_oracle": err_oracle, "error_sample": err_note,
         "rel_err_vs_native_f64": rel, "rel_err_vs_native_f64_ab_term": rel_ab,
         "roofline": {"bound": "tensor", "kernel": "k_pair_gemm<bf16, fp64-split>",
                      "achieved": achieved, "peak": burst, "unit": "TFLOP/s",
@@ -367,6 +376,7 @@ def _cuda_ms(fn, steps, warmup):
 
 
 def _product_ms(fn, n=5):
+    """Mean CUDA-event time of the main product kernel (events recorded by the library around it)."""
     import torch
     evs = []
     for _ in range(n):
@@ -377,240 +387,482 @@ def _product_ms(fn, n=5):
     return statistics.mean(b.elapsed_time(e) for b, e in evs)
 
 
-def run_other(args):
-    """Secondary workloads (one JSON line each): not the headline metric."""
+# Nominal dense rates relative to bf16 (2.25 PFLOP/s): tf32 1.1 PFLOP/s.  The
+# fp64 CUDA-core rate has no measured figure here: 1.25 TFLOP/s nominal.
+TF32_OVER_BF16 = 1.1 / 2.25
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def roofline(kind, exec_flops, kernel_ms, kernel, note=None):
+    """roofline object of one kernel: executed flops per launch / its CUDA-event time
+    against the dtype's peak (bf16 measured burst; tf32 from it by the nominal ratio;
+    fp64 CUDA cores nominal)."""
+    burst, _, src = peaks()
+    if kind == "bf16":
+        peak, bound, pk = burst, "tensor", f"bf16 burst ({src})"
+    elif kind == "tf32":
+        peak, bound, pk = burst * TF32_OVER_BF16, "tensor", f"tf32 = bf16 burst ({src}) x nominal 1.1/2.25"
+    else:
+        peak, bound, pk = FP64_NOMINAL_TFLOPS, "alu", "fp64 CUDA cores, nominal 1.25 TFLOP/s"
+    achieved = exec_flops / (kernel_ms * 1e-3) / 1e12
+    r = {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+         "frac": achieved / peak, "traffic": None, "peak_kind": pk, "kernel_ms": kernel_ms,
+         "exec_flops_per_launch": exec_flops}
+    if note:
+        r["note"] = note
+    return r
+
+
+def host64(t):
+    """A device tensor's values (exactly, promoted to fp64) as a numpy array with the same strides."""
+    import torch
+    base = t.detach()
+    flat = torch.as_strided(base, (base.untyped_storage().nbytes() // base.element_size(),), (1,), 0)
+    buf = flat.to(torch.float64).cpu().numpy()
+    return np.lib.stride_tricks.as_strided(buf[base.storage_offset():], tuple(base.shape),
+                                           tuple(8 * x for x in base.stride()))
+
+
+def sampled_error(alpha, A, la, B, lb, beta, C0, lc, got, n=512, seed=11, dot2=True):
+    """Relative Frobenius error of n sampled result entries against the oracle
+    (compensated Dot2 sums, or plain fp64 sums) on the inputs as the device held them."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    idx = np.stack([rng.integers(0, e, n) for e in C0.shape], axis=1)
+    want = oracle.entries(alpha, A, la, B, lb, beta, C0, lc, idx, dot2=dot2)
+    g = np.asarray(got)[tuple(idx.T)]
+    den = np.linalg.norm(want)
+    return float(np.linalg.norm(g - want) / den) if den > 0 else float(np.linalg.norm(g)), \
+        f"{n} sampled entries vs the oracle's {'Dot2' if dot2 else 'fp64'} sums"
+
+
+def cpu_slice(alpha, A, la, B, lb, beta, C0, lc, budget_s=3.0):
+    """cpu_baseline: the oracle (all host cores) on C restricted along its largest
+    mode to a slice sized for about budget_s seconds."""
+    import oracle
+    lab = lc[int(np.argmax(C0.shape))]
+
+    def cut(x, labels, s):
+        if lab not in labels:
+            return x
+        i = list(labels).index(lab)
+        return x[(slice(None),) * i + (slice(0, s),)]
+
+    def run(s):
+        Cs = np.array(cut(C0, lc, s), copy=True)
+        As, Bs = cut(A, la, s), cut(B, lb, s)
+        ext = {}
+        for x, ls in ((As, la), (Bs, lb), (Cs, lc)):
+            ext.update(zip(ls, x.shape))
+        t0 = time.perf_counter()
+        oracle.contract(alpha, As, la, Bs, lb, beta, Cs, lc)
+        return time.perf_counter() - t0, 2.0 * float(np.prod(list(ext.values())))
+    full = C0.shape[list(lc).index(lab)]
+    dt, fl = run(1)
+    s = max(1, min(full, int(budget_s / max(dt, 1e-4))))
+    if s > 1:
+        dt, fl = run(s)
+    import oracle as _o
+    return {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": _o.default_threads(), "kind": "oracle",
+            "sample": f"C restricted to {s} of {full} along label {lab} ({fl:.3g} flop)"}
+
+
+def emit(workload, flops, ms, roof, cpu, err, err_note, **extra):
+    line = {"workload": workload, "metric": "contraction TFLOP/s", "value": flops / (ms * 1e-3) / 1e12,
+            "unit": "TFLOP/s", "ms_per_step": ms, "flops_per_step": flops, "roofline": roof,
+            "cpu_baseline": cpu, "rel_err_vs_oracle": err, "error_sample": err_note, **extra}
+    print(json.dumps(line), flush=True)
+
+
+def _put(op, dt):
+    import torch
+    buf = torch.from_numpy(op.buf).to(device="cuda", dtype=dt)
+    return torch.as_strided(buf, op.extents, op.strides)
+
+
+def wl_four_index(args):
+    """C1: C[a,b,i,j] = sum_{c,k} A[a,c,i,k] B[c,k,b,j], extents 16, fp64."""
     import torch
     import paper_2604_07311_b300 as fm
     from paper_2604_07311_b300 import inputs as W
-    torch.cuda.set_device(0)
-    burst, sustained, src = peaks()
-
-    def put(op, dt):
-        buf = torch.from_numpy(op.buf).to(device="cuda", dtype=dt)
-        return torch.as_strided(buf, op.extents, op.strides)
-
-    if args.workload == "transpose_free":
-        p = W.transpose_free(v=96, o=48, pad=7)
-        for dt, kind, pairs in (("bf16", 4, 1), ("bf16", 5, 1), ("bf16", 2, 1), ("bf16", 3, 1), ("f32", 2, 3),
-                                ("f32", 3, 3), ("f32", 1, 1)):
-            tin = torch.bfloat16 if dt == "bf16" else torch.float32
-            A, B, C = put(p.A, tin), put(p.B, tin), put(p.C, torch.float32)
-            f = lambda **kw: fm.contract(1.0, A, p.A.labels, B, p.B.labels, 0.0, C, p.C.labels,
-                                         dtype=dt, kernel=kind, **kw)
-            ms = _cuda_ms(f, args.steps, args.warmup)
-            kms = _product_ms(f)
-            print(json.dumps({"workload": "transpose_free_v96_o48_pad7", "dtype": dt,
-                              "path": {1: "cuda_cores", 2: "packed_tma", 3: "element_gather",
-                                       4: "direct", 5: "direct_all_gathered"}[kind],
-                              "ms_per_step": ms, "tflops": p.flops / ms / 1e9, "product_ms": kms,
-                              "product_exec_tflops": pairs * p.flops / kms / 1e9,
-                              "bf16_peak_sustained": sustained, "peak_source": src}), flush=True)
-    elif args.workload == "network":
-        # A CCSD-flavoured two-step network in one call: the intermediate
-        # X[c,d,i,j] = sum_{k,l} T[c,d,k,l] Y[k,l,i,j] stays on the device,
-        # then R[a,b,i,j] = sum_{c,d} V[a,b,c,d] X[c,d,i,j] + R (emulated fp64).
-        v, o = 96, 32
-        gen = torch.Generator(device="cuda")
-        gen.manual_seed(5)
-        V = torch.randn(v, v, v, v, device="cuda", dtype=torch.float64, generator=gen) / 128
-        T = torch.randn(v, v, o, o, device="cuda", dtype=torch.float64, generator=gen) * 1e-2
-        Y = torch.randn(o, o, o, o, device="cuda", dtype=torch.float64, generator=gen)
-        R = torch.zeros(v, v, o, o, device="cuda", dtype=torch.float64)
-        X = torch.empty(v, v, o, o, device="cuda", dtype=torch.float64)
-        lv, lt, ly, lx, lr = W.L("abcd"), W.L("cdkl"), W.L("klij"), W.L("cdij"), W.L("abij")
-        # the library lays an intermediate out first mode fastest: listing X's
-        # labels as (j, i, d, c) gives it the same layout as the row-major
-        # torch tensor X[c,d,i,j] of the separate calls (d fastest in V too,
-        # so the contracted pair (c, d) fuses into one mode in both operands)
-        net = [(V, lv), (T, lt), (Y, ly), ((o, o, v, v), W.L("jidc")), (R, lr)]
-        steps = [(1, 2, 3, 1.0, 0.0), (0, 3, 4, 1.0, 1.0)]
-        flops = 2 * v * v * o * o * o * o + 2 * v * v * v * v * o * o
-        ms = _cuda_ms(lambda: fm.contract_network(net, steps, dtype="f64_emu"), args.steps, args.warmup)
-
-        def separate():
-            fm.contract(1.0, T, lt, Y, ly, 0.0, X, lx, dtype="f64_emu")
-            fm.contract(1.0, V, lv, X, lx, 1.0, R, lr, dtype="f64_emu")
-        ms_sep = _cuda_ms(separate, args.steps, args.warmup)
-        print(json.dumps({"workload": "network_ladder_v96_o32_two_steps_f64_split6", "flops": flops,
-                          "network_ms": ms, "network_tflops": flops / ms / 1e9,
-                          "separate_calls_ms": ms_sep, "separate_tflops": flops / ms_sep / 1e9}),
-              flush=True)
-    elif args.workload == "ladder_sym":
-        # The ladder with V read as its packed lower triangle (V symmetric
-        # under (ab) <-> (cd)) against the same contraction on dense V;
-        # device-resident, then end to end from pinned host buffers.
-        v, o = V_EXT, O_EXT
-        n = v * v
-        gen = torch.Generator(device="cuda")
-        gen.manual_seed(6)
-        Vd = torch.randn(n, n, device="cuda", dtype=torch.float64, generator=gen) / 128
-        Vd = torch.tril(Vd) + torch.tril(Vd, -1).T
-        iu = torch.triu_indices(n, n, device="cuda")
-        Vp = Vd[iu[0], iu[1]].contiguous()  # row q of the upper triangle = column q of the lower
-        del iu
-        Vd = Vd.reshape(v, v, v, v)  # row-major flattening of a symmetric matrix is column-major
-        T = torch.randn(o, o, v, v, device="cuda", dtype=torch.float64, generator=gen).permute(3, 2, 1, 0) * 1e-2
-        C0 = torch.rand(o, o, v, v, device="cuda", dtype=torch.float64, generator=gen).permute(3, 2, 1, 0)
-        Cs, Cd = C0.clone(), C0.clone()
-        lv, lt, lc = W.L("dcba"), W.L("cdij"), W.L("abij")  # Vd's torch order is (d, c, b, a)
-        ext = (v, v, v, v)
-        flops = 2 * v ** 4 * o * o
-        f_sym = lambda: fm.contract_sym(1.0, Vp, ext, W.L("abcd"), T, lt, 1.0, Cs, lc)
-        f_den = lambda: fm.contract(1.0, Vd, lv, T, lt, 1.0, Cd, lc, dtype="f64_emu")
-        ms_sym = _cuda_ms(f_sym, args.steps, args.warmup)
-        ms_den = _cuda_ms(f_den, args.steps, args.warmup)
-        Cs.copy_(C0)
-        Cd.copy_(C0)
-        f_sym()
-        f_den()
+    p = W.four_index(ext=16)
+    A, B = _put(p.A, torch.float64), _put(p.B, torch.float64)
+    for dt, kind, kname, pairs in (("f64", "fp64", "k_simt<double>", 1),
+                                   ("f64_emu", "bf16", "k_pair_gemm<bf16, fp64-split>", 21)):
+        C = _put(p.C, torch.float64)
+        f = lambda **kw: fm.contract(p.alpha, A, p.A.labels, B, p.B.labels, p.beta, C, p.C.labels, dtype=dt, **kw)
+        ms = _cuda_ms(f, args.steps, args.warmup)
+        kms = _product_ms(f)
+        C.copy_(_put(p.C, torch.float64))
+        f()
         torch.cuda.synchronize()
-        diff = float((Cs - Cd).abs().max())
-        # end to end: V, T and C in from pinned host memory, C back, every step
-        hV, hVp = Vd.cpu().pin_memory(), Vp.cpu().pin_memory()
-        hT, hC = T.cpu().pin_memory(), C0.cpu().pin_memory()
-        out = torch.empty_like(hC).pin_memory()
+        err, note = sampled_error(p.alpha, p.A.view(), p.A.labels, p.B.view(), p.B.labels, p.beta, p.C.view(),
+                                  p.C.labels, host64(C), n=4096)
+        emit("four_index_ext16_" + dt, p.flops, ms, roofline(kind, pairs * p.flops, kms, kname),
+             cpu_slice(p.alpha, p.A.view(), p.A.labels, p.B.view(), p.B.labels, p.beta, p.C.view(), p.C.labels, 1.0),
+             err, note, dtype=dt, note="launch-latency-sized problem (3.4e7 flop)")
 
-        def e2e(packed):
-            Vdev = (Vp if packed else Vd)
-            Vdev.copy_(hVp if packed else hV, non_blocking=True)
-            T.copy_(hT, non_blocking=True)
-            Cx = Cs if packed else Cd
-            Cx.copy_(hC, non_blocking=True)
-            (f_sym if packed else f_den)()
-            out.copy_(Cx, non_blocking=True)
-        e2e_sym = _cuda_ms(lambda: e2e(True), args.steps, args.warmup)
-        e2e_den = _cuda_ms(lambda: e2e(False), args.steps, args.warmup)
-        print(json.dumps({"workload": f"ladder_v{v}_o{o}_f64_split6_packed_symmetric_V", "flops": flops,
-                          "sym_ms": ms_sym, "sym_tflops": flops / ms_sym / 1e9,
-                          "dense_ms": ms_den, "dense_tflops": flops / ms_den / 1e9,
-                          "V_bytes_packed": Vp.numel() * 8, "V_bytes_dense": Vd.numel() * 8,
-                          "max_abs_diff_sym_vs_dense": diff,
-                          "e2e_sym_ms": e2e_sym, "e2e_sym_tflops": flops / e2e_sym / 1e9,
-                          "e2e_dense_ms": e2e_den, "e2e_dense_tflops": flops / e2e_den / 1e9}),
-              flush=True)
-    elif args.workload == "gemmt":
-        # The sandwiched update C := C - A T A^T of a skew-symmetric
-        # factorisation (T tridiagonal skew-symmetric, lower triangle of C):
-        # a panel-width k and a square case, against the same update done
-        # the unfused way (T A^T formed by torch, then the full square
-        # product through the library).
+
+def wl_transpose_free(args):
+    """C3: C[b,j,a,i] = sum_{c,k} A[a,c,i,k] B[b,k,j,c], v=96, o=48, A's first mode padded by 7."""
+    import torch
+    import paper_2604_07311_b300 as fm
+    from paper_2604_07311_b300 import inputs as W
+    p = W.transpose_free(v=96, o=48, pad=7)
+    cpu = None
+    for dt, kernel, path, kind, pairs, kname in (
+            ("bf16", 0, "direct (default)", "bf16", 1, "k_box<bf16>"),
+            ("bf16", 2, "packed", "bf16", 1, "k_pair_gemm<bf16>"),
+            ("f32", 0, "packed tf32x3 (default)", "tf32", 3, "k_pair_gemm<tf32x3>"),
+            ("f32", 1, "cuda_cores", "fp32", 1, "k_simt<float>")):
+        tin = torch.bfloat16 if dt == "bf16" else torch.float32
+        A, B, C = _put(p.A, tin), _put(p.B, tin), _put(p.C, torch.float32)
+        f = lambda **kw: fm.contract(1.0, A, p.A.labels, B, p.B.labels, 0.0, C, p.C.labels, dtype=dt,
+                                     kernel=kernel, **kw)
+        ms = _cuda_ms(f, args.steps, args.warmup)
+        kms = _product_ms(f)
+        _, info = fm.contract(1.0, A, p.A.labels, B, p.B.labels, 0.0, C, p.C.labels, dtype=dt, kernel=kernel,
+                              return_info=True)
+        torch.cuda.synchronize()
+        Ah, Bh = host64(A), host64(B)
+        err, note = sampled_error(1.0, Ah, p.A.labels, Bh, p.B.labels, 0.0, np.zeros(p.C.extents), p.C.labels,
+                                  host64(C), n=512, dot2=False)
+        if cpu is None:
+            cpu = cpu_slice(1.0, Ah, p.A.labels, Bh, p.B.labels, 0.0, np.zeros(p.C.extents), p.C.labels, 3.0)
+        roof = (roofline(kind, pairs * p.flops, kms, kname) if kind != "fp32" else
+                {"bound": "alu", "kernel": kname, "achieved": p.flops / (kms * 1e-3) / 1e12, "peak": None,
+                 "unit": "TFLOP/s", "frac": None, "traffic": None, "kernel_ms": kms,
+                 "note": "fp32 CUDA cores: reference point, no fp32 peak stated"})
+        emit("transpose_free_v96_o48_pad7", p.flops, ms, roof, cpu, err, note, dtype=dt, path=path,
+             launches=info["launches"], kernel_path=info["kernel_name"])
+
+
+def wl_block_sparse(args):
+    """C4: 2000 independent four-index blocks, each extent from {8,...,96} (and a
+    small-block variant, extents 8..32), emulated fp64, grouped launch + graph vs
+    one call per block; sampled entries of at least 50 blocks against Dot2."""
+    import torch
+    import paper_2604_07311_b300 as fm
+    from paper_2604_07311_b300 import inputs as W
+    import oracle
+    for nblocks, choices in ((2000, [8, 16, 24, 32]), (2000, None)):
+        ext = W.block_sparse_extents(nblocks=nblocks, choices=choices)
         gen = torch.Generator(device="cuda")
-        gen.manual_seed(7)
-        for n, k in ((16384, 256), (8192, 8192)):
-            flops = n * (n + 1) * k  # 2k per entry of the lower triangle
-            row = {"workload": f"gemmt_skew_tridiag_n{n}_k{k}", "flops": flops}
-            for dt, tdt in (("f64_emu", torch.float64), ("f64", torch.float64), ("f32", torch.float32)):
-                A = torch.randn(k, n, device="cuda", dtype=tdt, generator=gen).t()  # column-major
-                sub = torch.randn(k - 1, device="cuda", dtype=tdt, generator=gen)
-                C = torch.randn(n, n, device="cuda", dtype=tdt, generator=gen).t()
-                f = lambda **kw: fm.gemmt_tridiag(-1.0, A, sub, None, None, 1.0, C, dtype=dt, **kw)
-                steps = args.steps if dt != "f64" else max(1, min(args.steps, 3))
-                ms = _cuda_ms(f, steps, min(args.warmup, 3) if dt == "f64" else args.warmup)
-                row[f"{dt}_ms"] = ms
-                row[f"{dt}_tflops"] = flops / ms / 1e9
-                if dt == "f64_emu":
-                    row["f64_emu_product_ms"] = _product_ms(f, 3)
-                    # unfused: B = T A^T materialised, then C := C - A B on all of C
-                    B = torch.zeros(k, n, device="cuda", dtype=tdt)
+        gen.manual_seed(3)
+        pooled = choices is None
+        pool = torch.rand(1 << 28, device="cuda", dtype=torch.float64, generator=gen) if pooled else None
+        offs = np.random.default_rng(W.SEED_BASE + 40).integers(0, (1 << 28) - 96 ** 4, size=(nblocks, 2))
+        As, Bs, Cs, la, lb, lc, flops = [], [], [], [], [], [], 0
+        for bi, (a, b, c, i, j, k) in enumerate(map(int, e) for e in ext):
+            if pooled:
+                As.append(torch.as_strided(pool, (a, c, i, k), W.colmajor_strides((a, c, i, k)), int(offs[bi, 0])))
+                Bs.append(torch.as_strided(pool, (c, k, b, j), W.colmajor_strides((c, k, b, j)), int(offs[bi, 1])))
+            else:
+                As.append(torch.rand((k, i, c, a), device="cuda", dtype=torch.float64, generator=gen).permute(3, 2, 1, 0))
+                Bs.append(torch.rand((j, b, k, c), device="cuda", dtype=torch.float64, generator=gen).permute(3, 2, 1, 0))
+            Cs.append(torch.zeros((j, i, b, a), device="cuda", dtype=torch.float64).permute(3, 2, 1, 0))
+            la.append(W.L("acik")); lb.append(W.L("ckbj")); lc.append(W.L("abij"))
+            flops += 2 * a * b * c * i * j * k
+        res = {}
+        for name, graph in (("grouped_graph", True), ("grouped_nograph", False)):
+            f = lambda: fm.contract_batched(1.0, As, la, Bs, lb, 0.0, Cs, lc, dtype="f64_emu", use_graph=graph)
+            ms = _cuda_ms(f, max(1, min(args.steps, 3)), 1)
+            res[name] = {"ms": ms, "tflops": flops / ms / 1e9}
 
-                    def unfused():
-                        B.zero_()
-                        B[1:] += sub[:, None] * A.t()[:-1]
-                        B[:-1] -= sub[:, None] * A.t()[1:]
-                        fm.contract(-1.0, A, [1, 3], B, [3, 2], 1.0, C, [1, 2], dtype="f64_emu")
-                    ms_u = _cuda_ms(unfused, args.steps, args.warmup)
-                    row["unfused_full_square_f64_emu_ms"] = ms_u
-            print(json.dumps(row), flush=True)
-    elif args.workload == "mttkrp":
-        # CP-ALS's inner contraction on a 3-way tensor: M = X_(n) (U_b kr U_c)
-        # for each mode n, the Khatri-Rao operand generated while packed.
-        gen = torch.Generator(device="cuda")
-        gen.manual_seed(8)
-        I, R = 512, 64
-        flops = 2 * I ** 3 * R
-        for dt, tdt in (("f64_emu", torch.float64), ("f64", torch.float64), ("f32", torch.float32)):
-            X = torch.randn(I, I, I, device="cuda", dtype=tdt, generator=gen).permute(2, 1, 0)  # column-major
-            U = [torch.randn(R, I, device="cuda", dtype=tdt, generator=gen).t() for _ in range(3)]
-            row = {"workload": f"mttkrp_3way_{I}_R{R}", "dtype": dt, "flops": flops,
-                   "x_bytes": X.numel() * X.element_size()}
-            for mode in range(3):
-                M = torch.zeros(R, I, device="cuda", dtype=tdt).t()
-                f = lambda **kw: fm.mttkrp(1.0, X, mode, U, 0.0, M, dtype=dt, **kw)
-                steps = args.steps if dt != "f64" else max(1, min(args.steps, 3))
-                ms = _cuda_ms(f, steps, min(args.warmup, 2) if dt == "f64" else args.warmup)
-                row[f"mode{mode}_ms"] = ms
-                row[f"mode{mode}_tflops"] = flops / ms / 1e9
-                row[f"mode{mode}_x_gbs"] = row["x_bytes"] / ms / 1e6
-            del X
-            print(json.dumps(row), flush=True)
-    elif args.workload == "autograd":
-        from paper_2604_07311_b300.autograd import contract_autograd
-        d = W.autograd_problem()
-        A = torch.from_numpy(d["A"].astype(np.float32)).cuda().requires_grad_()
-        B = torch.from_numpy(d["B"].astype(np.float32)).cuda().requires_grad_()
-        T = torch.from_numpy(d["T"].astype(np.float32)).cuda()
+        def loop():
+            for x in zip(As, la, Bs, lb, Cs, lc):
+                fm.contract(1.0, x[0], x[1], x[2], x[3], 0.0, x[4], x[5], dtype="f64_emu")
+        ms_loop = _cuda_ms(loop, max(1, min(args.steps, 3)), 1)
+        res["one_call_per_block"] = {"ms": ms_loop, "tflops": flops / ms_loop / 1e9}
+        # accuracy: the grouped result of 64 blocks (the largest one included), 32 entries each
+        for c in Cs:
+            c.zero_()
+        fm.contract_batched(1.0, As, la, Bs, lb, 0.0, Cs, lc, dtype="f64_emu", use_graph=True)
+        torch.cuda.synchronize()
+        sizes = np.array([float(np.prod(e)) for e in ext])
+        pick = sorted(set([int(np.argmax(sizes))] + list(np.random.default_rng(12).choice(nblocks, 63, replace=False))))
+        pool_h = pool.cpu().numpy() if pooled else None
+        num = den = 0.0
+        t_or, fl_or = 0.0, 0.0
+        rng = np.random.default_rng(13)
+        for bi in pick:
+            if pooled:
+                Ah = np.lib.stride_tricks.as_strided(pool_h[int(offs[bi, 0]):], As[bi].shape,
+                                                     tuple(8 * x for x in As[bi].stride()))
+                Bh = np.lib.stride_tricks.as_strided(pool_h[int(offs[bi, 1]):], Bs[bi].shape,
+                                                     tuple(8 * x for x in Bs[bi].stride()))
+            else:
+                Ah, Bh = host64(As[bi]), host64(Bs[bi])
+            got = host64(Cs[bi])
+            idx = np.stack([rng.integers(0, e, 32) for e in got.shape], axis=1)
+            z = np.zeros(got.shape)
+            want = oracle.entries(1.0, Ah, la[bi], Bh, lb[bi], 0.0, z, lc[bi], idx, dot2=True)
+            g = got[tuple(idx.T)]
+            num += float(np.sum((g - want) ** 2))
+            den += float(np.sum(want ** 2))
+        err = (num / den) ** 0.5
+        # cpu baseline: the oracle on a whole block of median size
+        mid = int(np.argsort(sizes)[len(sizes) // 2])
+        if pooled:
+            Ah = np.lib.stride_tricks.as_strided(pool_h[int(offs[mid, 0]):], As[mid].shape,
+                                                 tuple(8 * x for x in As[mid].stride()))
+            Bh = np.lib.stride_tricks.as_strided(pool_h[int(offs[mid, 1]):], Bs[mid].shape,
+                                                 tuple(8 * x for x in Bs[mid].stride()))
+        else:
+            Ah, Bh = host64(As[mid]), host64(Bs[mid])
+        cpu = cpu_slice(1.0, Ah, la[mid], Bh, lb[mid], 0.0, np.zeros(tuple(Cs[mid].shape)), lc[mid], 3.0)
+        best = res["grouped_graph"]["ms"]
+        emit(f"block_sparse_{nblocks}_ext_{'8-32' if choices else '8-96_pooled_inputs'}_f64_split{SLICES}",
+             flops, best, roofline("bf16", 21 * flops, best, "grouped k_pair_gemm<bf16, fp64-split> (+pack)",
+                                   note="whole grouped call timed (product and packs), so a lower bound"),
+             cpu, err, f"32 entries in each of {len(pick)} blocks (the largest included) vs Dot2",
+             dtype="f64_emu", **res, speedup_grouped_vs_per_block=ms_loop / best)
+        del As, Bs, Cs, pool, pool_h
+        torch.cuda.empty_cache()
 
-        def fb():
-            A.grad = B.grad = None
-            ((contract_autograd(A, d["la"], B, d["lb"], d["lc"]) - T) ** 2).sum().backward()
-        ms = _cuda_ms(fb, args.steps, args.warmup)
-        fl = 3 * 2 * 64 * 64 * 64 * 48 * 48
-        print(json.dumps({"workload": "autograd_i64_k48_fwd_bwd_fp32", "ms_per_step": ms,
-                          "tflops": fl / ms / 1e9}), flush=True)
-    elif args.workload == "block_sparse":
-        # 2000 blocks of the four-index pattern: small ones (extents 8..32, own
-        # inputs), then the full configuration (each of the six extents from
-        # {8,...,96}): its inputs would take ~350 GB, so every block's A and B
-        # are column-major views into one shared random pool at seeded offsets
-        # (read-only, so sharing is harmless); each C has its own storage
-        # (~114 GB in all).
-        for nblocks, choices in ((2000, [8, 16, 24, 32]), (2000, None)):
-            ext = W.block_sparse_extents(nblocks=nblocks, choices=choices)
-            gen = torch.Generator(device="cuda")
-            gen.manual_seed(3)
-            pooled = choices is None
-            pool = torch.rand(1 << 28, device="cuda", dtype=torch.float64, generator=gen) if pooled else None
-            offs = np.random.default_rng(W.SEED_BASE + 40).integers(0, (1 << 28) - 96 ** 4, size=(nblocks, 2))
-            As, Bs, Cs, la, lb, lc, flops = [], [], [], [], [], [], 0
-            for bi, (a, b, c, i, j, k) in enumerate(map(int, e) for e in ext):
-                if pooled:
-                    As.append(torch.as_strided(pool, (a, c, i, k), W.colmajor_strides((a, c, i, k)),
-                                               int(offs[bi, 0])))
-                    Bs.append(torch.as_strided(pool, (c, k, b, j), W.colmajor_strides((c, k, b, j)),
-                                               int(offs[bi, 1])))
-                else:
-                    As.append(torch.rand((k, i, c, a), device="cuda", dtype=torch.float64,
-                                         generator=gen).permute(3, 2, 1, 0))
-                    Bs.append(torch.rand((j, b, k, c), device="cuda", dtype=torch.float64,
-                                         generator=gen).permute(3, 2, 1, 0))
-                Cs.append(torch.zeros((j, i, b, a), device="cuda", dtype=torch.float64).permute(3, 2, 1, 0))
-                la.append(W.L("acik")); lb.append(W.L("ckbj")); lc.append(W.L("abij"))
-                flops += 2 * a * b * c * i * j * k
-            res = {}
-            for name, graph in (("grouped_graph", True), ("grouped_nograph", False)):
-                f = lambda: fm.contract_batched(1.0, As, la, Bs, lb, 0.0, Cs, lc, dtype="f64_emu",
-                                                use_graph=graph)
-                ms = _cuda_ms(f, max(1, min(args.steps, 3)), 1)
-                res[name] = {"ms": ms, "tflops": flops / ms / 1e9}
 
-            def loop():
-                for x in zip(As, la, Bs, lb, Cs, lc):
-                    fm.contract(1.0, x[0], x[1], x[2], x[3], 0.0, x[4], x[5], dtype="f64_emu")
-            ms = _cuda_ms(loop, max(1, min(args.steps, 3)), 1)
-            res["one_call_per_block"] = {"ms": ms, "tflops": flops / ms / 1e9}
-            print(json.dumps({"workload": f"block_sparse_{nblocks}_ext_"
-                              f"{'8-32' if choices else '8-96_pooled_inputs'}_f64_split{SLICES}",
-                              "flops": flops, **res}), flush=True)
-            del As, Bs, Cs, pool
+def wl_autograd(args):
+    """C5: L = ||contract(A,B) - T||^2, C[i,j,l] = sum_{k,m} A[i,k,m,l] B[k,m,j], fp32,
+    forward and both adjoints; gradients against the oracle's on sampled entries."""
+    import torch
+    import oracle
+    from paper_2604_07311_b300 import inputs as W
+    from paper_2604_07311_b300.autograd import contract_autograd
+    d = W.autograd_problem()
+    A = torch.from_numpy(d["A"].astype(np.float32)).cuda().requires_grad_()
+    B = torch.from_numpy(d["B"].astype(np.float32)).cuda().requires_grad_()
+    T = torch.from_numpy(d["T"].astype(np.float32)).cuda()
+
+    def fb():
+        A.grad = B.grad = None
+        ((contract_autograd(A, d["la"], B, d["lb"], d["lc"]) - T) ** 2).sum().backward()
+    ms = _cuda_ms(fb, args.steps, args.warmup)
+    fb()
+    torch.cuda.synchronize()
+    Ah = A.detach().double().cpu().numpy()
+    Bh = B.detach().double().cpu().numpy()
+    Th = T.double().cpu().numpy()
+    Ch = np.zeros(Th.shape)
+    t0 = time.perf_counter()
+    oracle.contract(1.0, Ah, d["la"], Bh, d["lb"], 0.0, Ch, d["lc"])
+    cdt = time.perf_counter() - t0
+    dC = 2.0 * (Ch - Th)
+    gA, gB = A.grad.double().cpu().numpy(), B.grad.double().cpu().numpy()
+    # dA[i,k,m,l] = sum_j dC[i,j,l] B[k,m,j];  dB[k,m,j] = sum_{i,l} A[i,k,m,l] dC[i,j,l]
+    eA, _ = sampled_error(1.0, dC, d["lc"], Bh, d["lb"], 0.0, np.zeros(gA.shape), d["la"], gA, n=512, dot2=False)
+    eB, _ = sampled_error(1.0, Ah, d["la"], dC, d["lc"], 0.0, np.zeros(gB.shape), d["lb"], gB, n=256, dot2=False)
+    fl = 3 * 2 * 64 * 64 * 64 * 48 * 48
+    import oracle as _o
+    cpu = {"value": (fl / 3) / cdt / 1e12, "unit": "TFLOP/s", "cores": _o.default_threads(), "kind": "oracle",
+           "sample": "the forward contraction (1.21e9 flop) in full"}
+    emit("autograd_i64_k48_fwd_bwd_fp32", fl, ms,
+         roofline("tf32", 3 * fl, ms, "forward + two adjoint contractions (tf32x3), whole step",
+                  note="the whole training step is timed (host and loss ops included), so a lower bound"),
+         cpu, max(eA, eB), "512 entries of dA and 256 of dB vs the oracle's gradient (fp64 sums)",
+         dtype="f32", rel_err_dA=eA, rel_err_dB=eB)
+
+
+def wl_network(args):
+    """f1: the two-step network X = T.Y (kept on the device), R += V.X, emulated
+    fp64, against two separate calls; sampled R entries against the oracle
+    applied step by step."""
+    import torch
+    import oracle
+    import paper_2604_07311_b300 as fm
+    from paper_2604_07311_b300 import inputs as W
+    v, o = 96, 32
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    V = torch.randn(v, v, v, v, device="cuda", dtype=torch.float64, generator=gen) / 128
+    T = torch.randn(v, v, o, o, device="cuda", dtype=torch.float64, generator=gen) * 1e-2
+    Y = torch.randn(o, o, o, o, device="cuda", dtype=torch.float64, generator=gen)
+    R = torch.zeros(v, v, o, o, device="cuda", dtype=torch.float64)
+    X = torch.empty(v, v, o, o, device="cuda", dtype=torch.float64)
+    lv, lt, ly, lx, lr = W.L("abcd"), W.L("cdkl"), W.L("klij"), W.L("cdij"), W.L("abij")
+    # the library lays an intermediate out first mode fastest: listing X's
+    # labels as (j, i, d, c) gives it the layout of the row-major tensor
+    # X[c,d,i,j] of the separate calls (d fastest in V too, so the
+    # contracted pair (c, d) fuses into one mode in both operands)
+    net = [(V, lv), (T, lt), (Y, ly), ((o, o, v, v), W.L("jidc")), (R, lr)]
+    steps = [(1, 2, 3, 1.0, 0.0), (0, 3, 4, 1.0, 1.0)]
+    flops = 2 * v * v * o * o * o * o + 2 * v * v * v * v * o * o
+    ms = _cuda_ms(lambda: fm.contract_network(net, steps, dtype="f64_emu"), args.steps, args.warmup)
+
+    def separate():
+        fm.contract(1.0, T, lt, Y, ly, 0.0, X, lx, dtype="f64_emu")
+        fm.contract(1.0, V, lv, X, lx, 1.0, R, lr, dtype="f64_emu")
+    ms_sep = _cuda_ms(separate, args.steps, args.warmup)
+    R.zero_()
+    fm.contract_network(net, steps, dtype="f64_emu")
+    torch.cuda.synchronize()
+    Vh, Th, Yh, Rh = host64(V), host64(T), host64(Y), host64(R)
+    rng = np.random.default_rng(14)
+    num = den = 0.0
+    t_cpu, fl_cpu = 0.0, 0.0
+    for _ in range(6):  # (i, j) pairs: X[:, :, i, j] by the oracle, then sampled R[a, b, i, j]
+        i, j = (int(x) for x in rng.integers(0, o, 2))
+        Xs = np.zeros((v, v, 1, 1))
+        t0 = time.perf_counter()
+        oracle.contract(1.0, Th, lt, Yh[:, :, i:i + 1, j:j + 1], ly, 0.0, Xs, lx)
+        t_cpu += time.perf_counter() - t0
+        fl_cpu += 2.0 * v * v * o * o
+        ab = np.stack([rng.integers(0, v, 64), rng.integers(0, v, 64), np.zeros(64, int), np.zeros(64, int)], 1)
+        want = oracle.entries(1.0, Vh, lv, Xs, lx, 0.0, np.zeros((v, v, 1, 1)), lr, ab, dot2=True)
+        g = Rh[ab[:, 0], ab[:, 1], i, j]
+        num += float(np.sum((g - want) ** 2))
+        den += float(np.sum(want ** 2))
+    import oracle as _o
+    cpu = {"value": fl_cpu / t_cpu / 1e12, "unit": "TFLOP/s", "cores": _o.default_threads(), "kind": "oracle",
+           "sample": f"the first step's X[:, :, i, j] for 6 (i, j) pairs ({fl_cpu:.3g} flop)"}
+    emit("network_ladder_v96_o32_two_steps_f64_split6", flops, ms,
+         roofline("bf16", 21 * flops, ms, "two k_pair_gemm<bf16, fp64-split> steps (+packs)",
+                  note="whole network call timed, so a lower bound"),
+         cpu, (num / den) ** 0.5, "64 entries of R in each of 6 (i, j) columns vs Dot2 on the oracle's X",
+         dtype="f64_emu", separate_calls_ms=ms_sep, speedup_vs_separate=ms_sep / ms)
+
+
+def wl_ladder_sym(args):
+    """f2: the ladder with V read as its packed lower triangle, against the dense call."""
+    import torch
+    import paper_2604_07311_b300 as fm
+    from paper_2604_07311_b300 import inputs as W
+    v, o = V_EXT, O_EXT
+    n = v * v
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(6)
+    Vd = torch.randn(n, n, device="cuda", dtype=torch.float64, generator=gen) / 128
+    Vd = torch.tril(Vd) + torch.tril(Vd, -1).T
+    iu = torch.triu_indices(n, n, device="cuda")
+    Vp = Vd[iu[0], iu[1]].contiguous()  # row q of the upper triangle = column q of the lower
+    del iu
+    Vd = Vd.reshape(v, v, v, v)  # row-major flattening of a symmetric matrix is column-major
+    T = torch.randn(o, o, v, v, device="cuda", dtype=torch.float64, generator=gen).permute(3, 2, 1, 0) * 1e-2
+    C0 = torch.rand(o, o, v, v, device="cuda", dtype=torch.float64, generator=gen).permute(3, 2, 1, 0)
+    Cs, Cd = C0.clone(), C0.clone()
+    lv, lt, lc = W.L("dcba"), W.L("cdij"), W.L("abij")  # Vd's torch order is (d, c, b, a)
+    ext = (v, v, v, v)
+    flops = 2 * v ** 4 * o * o
+    f_sym = lambda **kw: fm.contract_sym(1.0, Vp, ext, W.L("abcd"), T, lt, 1.0, Cs, lc, **kw)
+    f_den = lambda: fm.contract(1.0, Vd, lv, T, lt, 1.0, Cd, lc, dtype="f64_emu")
+    ms_sym = _cuda_ms(f_sym, args.steps, args.warmup)
+    kms = _product_ms(f_sym)
+    ms_den = _cuda_ms(f_den, args.steps, args.warmup)
+    Cs.copy_(C0)
+    Cd.copy_(C0)
+    f_sym()
+    f_den()
+    torch.cuda.synchronize()
+    diff = float((Cs - Cd).abs().max())
+    Vh, Th, C0h = host64(Vd), host64(T), host64(C0)
+    err, note = sampled_error(1.0, Vh, lv, Th, lt, 1.0, C0h, lc, host64(Cs), n=1024)
+    cpu = cpu_slice(1.0, Vh, lv, Th[:, :, :1, :], lt, 1.0, C0h[:, :, :1, :], lc, 3.0)
+    emit(f"ladder_v{v}_o{o}_f64_split6_packed_symmetric_V", flops, ms_sym,
+         roofline("bf16", 21 * flops, kms, "k_pair_gemm<bf16, fp64-split>"), cpu, err, note,
+         dtype="f64_emu", dense_V_ms=ms_den, V_bytes_packed=Vp.numel() * 8, V_bytes_dense=Vd.numel() * 8,
+         max_abs_diff_sym_vs_dense=diff)
+
+
+def wl_gemmt(args):
+    """f3: C := C - A T A^T (T skew-symmetric tridiagonal), lower triangle of C;
+    flops counted as n (n + 1) k."""
+    import torch
+    import oracle
+    import paper_2604_07311_b300 as fm
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    for n, k in ((16384, 256), (8192, 8192)):
+        flops = n * (n + 1) * k
+        for dt, tdt, kind, pairs, kname in (("f64_emu", torch.float64, "bf16", 21, "k_pair_gemm<bf16, fp64-split>"),
+                                            ("f32", torch.float32, "tf32", 3, "k_pair_gemm<tf32x3>"),
+                                            ("f64", torch.float64, "fp64", 1, "k_simt<double>")):
+            A = torch.randn(k, n, device="cuda", dtype=tdt, generator=gen).t()  # column-major
+            sub = torch.randn(k - 1, device="cuda", dtype=tdt, generator=gen)
+            C = torch.randn(n, n, device="cuda", dtype=tdt, generator=gen).t()
+            C0 = C.clone()
+            f = lambda **kw: fm.gemmt_tridiag(-1.0, A, sub, None, None, 1.0, C, dtype=dt, **kw)
+            steps = args.steps if dt != "f64" else max(1, min(args.steps, 3))
+            ms = _cuda_ms(f, steps, min(args.warmup, 3) if dt == "f64" else args.warmup)
+            kms = _product_ms(f, 3)
+            C.copy_(C0)
+            f()
+            torch.cuda.synchronize()
+            # oracle: B = T A^T formed on the host (the band, as the oracle's own
+            # gemmt does), then sampled entries i >= j of C0 - A B
+            Ah, sh, C0h = host64(A), host64(sub), host64(C0)
+            Bt = np.zeros((k, n))
+            Bt[1:] += sh[:, None] * Ah.T[:-1]
+            Bt[:-1] -= sh[:, None] * Ah.T[1:]
+            rng = np.random.default_rng(15)
+            i = rng.integers(0, n, 512)
+            j = (rng.random(512) * (i + 1)).astype(np.int64)
+            idx = np.stack([i, j], 1)
+            want = oracle.entries(-1.0, Ah, [1, 3], Bt, [3, 2], 1.0, C0h, [1, 2], idx, dot2=dt == "f64_emu")
+            got = host64(C)[i, j]
+            err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+            cpu = cpu_slice(-1.0, Ah, [1, 3], Bt, [3, 2], 1.0, C0h, [1, 2], 2.0)
+            emit(f"gemmt_skew_tridiag_n{n}_k{k}", flops, ms, roofline(kind, pairs * flops, kms, kname), cpu, err,
+                 "512 sampled entries i >= j vs the oracle (B = T A^T on the host, then its sums)", dtype=dt)
+            del A, C, C0
             torch.cuda.empty_cache()
+
+
+def wl_mttkrp(args):
+    """f4: CP-ALS's M = X_(n) (Khatri-Rao of the other factors), X 512^3, R = 64, every mode."""
+    import torch
+    import oracle
+    import paper_2604_07311_b300 as fm
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(8)
+    I, R = 512, 64
+    flops = 2 * I ** 3 * R
+    for dt, tdt, kind, pairs, kname in (("f64_emu", torch.float64, "bf16", 21, "k_pair_gemm<bf16, fp64-split>"),
+                                        ("f32", torch.float32, "tf32", 3, "k_pair_gemm<tf32x3>"),
+                                        ("f64", torch.float64, "fp64", 1, "k_simt<double>")):
+        X = torch.randn(I, I, I, device="cuda", dtype=tdt, generator=gen).permute(2, 1, 0)  # column-major
+        U = [torch.randn(R, I, device="cuda", dtype=tdt, generator=gen).t() for _ in range(3)]
+        Xh = host64(X)
+        Uh = [host64(u) for u in U]
+        for mode in range(3):
+            M = torch.zeros(R, I, device="cuda", dtype=tdt).t()
+            f = lambda **kw: fm.mttkrp(1.0, X, mode, U, 0.0, M, dtype=dt, **kw)
+            steps = args.steps if dt != "f64" else max(1, min(args.steps, 3))
+            ms = _cuda_ms(f, steps, min(args.warmup, 2) if dt == "f64" else args.warmup)
+            kms = _product_ms(f, 3)
+            f()
+            torch.cuda.synchronize()
+            Kt = oracle.khatri_rao(Uh, mode, 3)  # Kt[i_a, i_b, r] over the other modes a < b
+            others = [m for m in range(3) if m != mode]
+            lx = [1, 2, 3]
+            lk = [others[0] + 1, others[1] + 1, 9]
+            err, note = sampled_error(1.0, Xh, lx, Kt, lk, 0.0, np.zeros((I, R)), [mode + 1, 9], host64(M), n=256,
+                                      dot2=dt == "f64_emu")
+            cpu = cpu_slice(1.0, Xh, lx, Kt, lk, 0.0, np.zeros((I, R)), [mode + 1, 9], 2.0)
+            emit(f"mttkrp_3way_{I}_R{R}_mode{mode}", flops, ms, roofline(kind, pairs * flops, kms, kname), cpu, err,
+                 note, dtype=dt)
+        del X, U, Xh, Uh
+        torch.cuda.empty_cache()
+
+
+def run_other(args):
+    """Secondary workloads (one JSON line each): not the headline metric."""
+    import torch
+    torch.cuda.set_device(0)
+    fns = {"four_index": wl_four_index, "transpose_free": wl_transpose_free, "block_sparse": wl_block_sparse,
+           "autograd": wl_autograd, "network": wl_network, "ladder_sym": wl_ladder_sym, "gemmt": wl_gemmt,
+           "mttkrp": wl_mttkrp}
+    names = list(fns) if args.workload == "all" else [args.workload]
+    for n in names:
+        fns[n](args)
+        torch.cuda.empty_cache()
+    import paper_2604_07311_b300 as fm
     print(json.dumps({"device_status": fm.device_status()}), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="ladder",
-                    choices=["ladder", "transpose_free", "block_sparse", "autograd", "network", "ladder_sym",
-                             "gemmt", "mttkrp"],
+                    choices=["ladder", "four_index", "transpose_free", "block_sparse", "autograd", "network",
+                             "ladder_sym", "gemmt", "mttkrp", "all"],
                     help="ladder is the benchmark line; the others print secondary measurements")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
