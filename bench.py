@@ -639,6 +639,23 @@ def wl_autograd(args):
     ms = _cuda_ms(fb, args.steps, args.warmup)
     fb()
     torch.cuda.synchronize()
+    gA_eager, gB_eager = A.grad.clone(), B.grad.clone()
+    # the same training step captured once into a CUDA graph (every library
+    # call is stream-ordered, workspace included) and replayed
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            fb()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    A.grad = B.grad = None
+    with torch.cuda.graph(graph):
+        ((contract_autograd(A, d["la"], B, d["lb"], d["lc"]) - T) ** 2).sum().backward()
+    ms_graph = _cuda_ms(graph.replay, args.steps, args.warmup)
+    graph.replay()
+    torch.cuda.synchronize()
+    graph_matches_eager = bool(torch.equal(A.grad, gA_eager) and torch.equal(B.grad, gB_eager))
     Ah = A.detach().double().cpu().numpy()
     Bh = B.detach().double().cpu().numpy()
     Th = T.double().cpu().numpy()
@@ -659,7 +676,8 @@ def wl_autograd(args):
          roofline("tf32", 3 * fl, ms, "forward + two adjoint contractions (tf32x3), whole step",
                   note="the whole training step is timed (host and loss ops included), so a lower bound"),
          cpu, max(eA, eB), "512 entries of dA and 256 of dB vs the oracle's gradient (fp64 sums)",
-         dtype="f32", rel_err_dA=eA, rel_err_dB=eB)
+         dtype="f32", rel_err_dA=eA, rel_err_dB=eB, graph_step_ms=ms_graph,
+         graph_step_tflops=fl / (ms_graph * 1e-3) / 1e12, graph_grads_equal_eager=graph_matches_eager)
 
 
 def wl_network(args):

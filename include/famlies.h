@@ -159,7 +159,15 @@ typedef struct {
  * index fusion (adjacent modes whose strides chain in every operand that
  * holds them are merged); swapped = 1 when the kernel treats B as its row
  * operand so that C's unit-stride mode lies along the rows; kernel is the
- * path chosen (see FAMLIES_KERNEL_*); launches counts kernel launches. */
+ * path chosen (see FAMLIES_KERNEL_*); launches counts the kernels the call
+ * launched; cached = 1 when the call reused the workspace and offset tables
+ * of an earlier call with the same shapes, strides, dtype, knobs and stream
+ * (the plan cache; it then launched one kernel fewer: no table build).
+ * The plan cache keeps up to 16 such workspaces of at most 256 MB each,
+ * the least recently used freed (with a device-wide wait) when a new one is
+ * needed; it is bypassed while the stream is being captured into a graph
+ * and turned off by the environment variable FAMLIES_PLAN_CACHE=0.  Calls
+ * that share an entry are ordered by their (common) stream. */
 typedef struct {
   int64_t m, n, k, batch;
   int32_t m_modes, n_modes, k_modes, batch_modes;
@@ -170,7 +178,7 @@ typedef struct {
   int32_t a_contig; /* 0 none, 1 unit stride along the row class, 2 along k */
   int32_t b_contig;
   int32_t c_contig; /* 0 none, 1 along rows, 2 along columns */
-  int32_t reserved;
+  int32_t cached;   /* 1: served by the plan cache (see above) */
 } famlies_plan_info_t;
 
 #define FAMLIES_KERNEL_NONE 0      /* nothing to do (empty C) */

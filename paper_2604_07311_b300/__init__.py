@@ -7,6 +7,8 @@ imports nothing from here.
 """
 from __future__ import annotations
 
+import threading
+
 from ._lib import (BF16, DTYPES, F32, F64, F64_EMU, KERNELS, Desc, FamliesError, PlanInfo,
                    desc_numpy, desc_torch, load, options, check, error_string)
 
@@ -52,12 +54,36 @@ def contract(alpha, A, la, B, lb, beta, C, lc, dtype=None, stream=None, *, slice
     """
     lib = load()
     code = _dtype_code(dtype, A, C)
-    da, db, dc = desc_torch(A, la), desc_torch(B, lb), desc_torch(C, lc)
-    info = PlanInfo()
-    opt = options(slices, kernel, tile_n, wait_limit, events, stall_test)
+    da, db, dc = _desc_reused(0, A, la), _desc_reused(1, B, lb), _desc_reused(2, C, lc)
+    info = PlanInfo() if return_info else None
+    if slices or kernel or tile_n or wait_limit or events is not None or stall_test:
+        opt = options(slices, kernel, tile_n, wait_limit, events, stall_test)
+    else:
+        opt = None
     check(lib.famlies_contract_ex(float(alpha), da.ref, db.ref, float(beta), dc.ref, code,
                                   _stream_handle(stream), opt, info))
     return (C, info.as_dict()) if return_info else C
+
+
+_tls = threading.local()
+
+
+def _desc_reused(pos, x, labels):
+    """Descriptor of torch view x as operand `pos` of a call: the ctypes arrays of
+    a (position, shape, strides, labels) signature are built once per thread and
+    reused, only the data pointer and the size are rewritten."""
+    cache = getattr(_tls, "descs", None)
+    if cache is None:
+        cache = _tls.descs = {}
+    key = (pos, tuple(x.shape), x.stride(), tuple(int(v) for v in labels))
+    d = cache.get(key)
+    if d is None:
+        if len(cache) > 512:
+            cache.clear()
+        d = cache[key] = Desc(key[1], key[2], key[3], 0, 0)
+    d.t.data = x.data_ptr()
+    d.t.size_bytes = max(x.untyped_storage().nbytes() - x.storage_offset() * x.element_size(), 0)
+    return d
 
 
 def contract_host(alpha, A, la, B, lb, beta, C, lc, dtype="f64", stream=None, *, slices=0, kernel=0):

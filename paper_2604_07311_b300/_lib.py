@@ -64,10 +64,10 @@ class PlanInfo(ctypes.Structure):
                 ("k_modes", ctypes.c_int32), ("batch_modes", ctypes.c_int32),
                 ("swapped", ctypes.c_int32), ("kernel", ctypes.c_int32), ("launches", ctypes.c_int32),
                 ("slices", ctypes.c_int32), ("a_contig", ctypes.c_int32), ("b_contig", ctypes.c_int32),
-                ("c_contig", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("c_contig", ctypes.c_int32), ("cached", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        d = {f: getattr(self, f) for f, _ in self._fields_}
         d["kernel_name"] = KERNELS.get(self.kernel, "?")
         return d
 

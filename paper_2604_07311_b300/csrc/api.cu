@@ -90,10 +90,116 @@ const char* kernel_name(int k) {
 struct Workspace {
   void* ptr = nullptr;
   cudaStream_t s = nullptr;
+  bool owned = true;  // false: the workspace belongs to a plan-cache entry
   ~Workspace() {
-    if (ptr) cudaFreeAsync(ptr, s);
+    if (ptr && owned) cudaFreeAsync(ptr, s);
   }
 };
+
+// Plan cache.  Repeated calls with the same shapes, strides, dtype, knobs
+// and stream (a training loop, an iterative solver) keep their workspace
+// and the offset tables in it: such a call skips the allocation, the free
+// and the table kernel.  The key holds the fused label classes (extents and
+// strides of every operand), which fix the tables and the workspace layout,
+// plus the device and the stream, so that calls sharing an entry are ordered
+// by their stream.  Not used while the stream is being captured into a graph
+// (a captured call allocates its own workspace), nor for entries above
+// 256 MB; at most 16 entries, the least recently used freed (cudaFree, which
+// waits for the device) when a new one is needed.  FAMLIES_PLAN_CACHE=0
+// turns it off.
+class PlanCache {
+ public:
+  struct Entry {
+    std::vector<int64_t> key;
+    void* ws = nullptr;
+    int64_t bytes = 0;
+    uint64_t used = 0;
+    bool tables = false;  // the tables have been built in ws
+  };
+
+  static bool enabled() {
+    static int v = -1;
+    if (v < 0) {
+      const char* e = std::getenv("FAMLIES_PLAN_CACHE");
+      v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+  }
+
+  // The entry for key (created with `bytes` of workspace allocated on s when
+  // missing), or null when the cache cannot serve the call.
+  Entry* get(const std::vector<int64_t>& key, int64_t bytes, cudaStream_t s) {
+    if (bytes > kMaxBytes) return nullptr;
+    std::lock_guard<std::mutex> lk(mu_);
+    ++clock_;
+    for (Entry& e : entries_)
+      if (e.key == key && e.bytes >= bytes) {
+        e.used = clock_;
+        return &e;
+      }
+    if (entries_.size() >= kMaxEntries) {
+      size_t lru = 0;
+      for (size_t i = 1; i < entries_.size(); ++i)
+        if (entries_[i].used < entries_[lru].used) lru = i;
+      cudaFree(entries_[lru].ws);
+      cudaGetLastError();
+      entries_.erase(entries_.begin() + (long)lru);
+    }
+    Entry e;
+    e.key = key;
+    e.bytes = bytes;
+    e.used = clock_;
+    if (cudaMallocAsync(&e.ws, bytes > 0 ? bytes : 256, s) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    entries_.push_back(std::move(e));
+    return &entries_.back();
+  }
+
+ private:
+  static constexpr int64_t kMaxBytes = (int64_t)256 << 20;
+  static constexpr size_t kMaxEntries = 16;
+  std::mutex mu_;
+  std::vector<Entry> entries_;
+  uint64_t clock_ = 0;
+};
+
+PlanCache& plan_cache() {
+  static PlanCache* c = new PlanCache();  // never destroyed: entries live until exit
+  return *c;
+}
+
+// The cache key of plan p on stream s, or an empty key when p is not cached
+// (operands that carry device pointers in the plan: symmetric, banded,
+// Khatri-Rao; triangle updates).
+std::vector<int64_t> cache_key(const Plan& p, cudaStream_t s) {
+  std::vector<int64_t> k;
+  if (p.sym_n || p.band_side >= 0 || p.krp_side >= 0 || p.tri) return k;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  k = {dev, (int64_t)(intptr_t)s, (int64_t)p.dtype, p.kernel, p.slices, p.tile_n, p.force_gather,
+       (int64_t)p.swapped, p.m, p.n, p.k, p.l};
+  for (const ClassModes* cm : {&p.M, &p.N, &p.K, &p.L}) {
+    k.push_back(cm->n);
+    for (int i = 0; i < cm->n; ++i) {
+      k.push_back(cm->m[i].ext);
+      k.push_back(cm->m[i].sa);
+      k.push_back(cm->m[i].sb);
+      k.push_back(cm->m[i].sc);
+    }
+  }
+  return k;
+}
+
+bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+    cudaGetLastError();
+    return true;  // unknown: do not cache
+  }
+  return st != cudaStreamCaptureStatusNone;
+}
 
 int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
              const famlies_options_t* opt, famlies_plan_info_t* info) {
@@ -115,7 +221,15 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
     if (wsb < 0) return FAMLIES_ERR_UNSUPPORTED;
     Workspace ws;
     ws.s = s;
-    if (wsb > 0 && cudaMallocAsync(&ws.ptr, wsb, s) != cudaSuccess) {
+    PlanCache::Entry* ce = nullptr;
+    if (wsb > 0 && PlanCache::enabled() && !stream_capturing(s)) {
+      const std::vector<int64_t> key = cache_key(p, s);
+      if (!key.empty()) ce = plan_cache().get(key, wsb, s);
+    }
+    if (ce) {
+      ws.ptr = ce->ws;
+      ws.owned = false;
+    } else if (wsb > 0 && cudaMallocAsync(&ws.ptr, wsb, s) != cudaSuccess) {
       cudaGetLastError();
       ws.ptr = nullptr;
       return FAMLIES_ERR_ALLOC;
@@ -158,16 +272,32 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
   tab_bytes = (tab_bytes + 255) / 256 * 256;
   Workspace ws;
   ws.s = s;
-  if (cudaMallocAsync(&ws.ptr, tab_bytes + extra, s) != cudaSuccess) {
+  PlanCache::Entry* ce = nullptr;
+  if (PlanCache::enabled() && !stream_capturing(s)) {
+    const std::vector<int64_t> key = cache_key(p, s);
+    if (!key.empty()) ce = plan_cache().get(key, tab_bytes + extra, s);
+  }
+  if (ce) {
+    ws.ptr = ce->ws;
+    ws.owned = false;
+  } else if (cudaMallocAsync(&ws.ptr, tab_bytes + extra, s) != cudaSuccess) {
     cudaGetLastError();
     ws.ptr = nullptr;
     return FAMLIES_ERR_ALLOC;
   }
   Tables t;
   int launches = 0;
-  if (launch_tables(p, (int64_t*)((char*)ws.ptr + extra), &t, s) != cudaSuccess)
-    return FAMLIES_ERR_CUDA;
-  ++launches;
+  int64_t* tab = (int64_t*)((char*)ws.ptr + extra);
+  bool reused = false;
+  if (ce && ce->tables) {  // the cached workspace already holds this plan's tables
+    TableJob jobs[9];
+    plan_table_jobs(p, tab, jobs, &t);
+    reused = true;
+  } else {
+    if (launch_tables(p, tab, &t, s) != cudaSuccess) return FAMLIES_ERR_CUDA;
+    ++launches;
+    if (ce) ce->tables = true;
+  }
   cudaError_t err = cudaSuccess;
   if (p.kernel == FAMLIES_KERNEL_SCALE) {
     err = launch_scale(p, t, beta, s);
@@ -220,7 +350,10 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
         return FAMLIES_ERR_UNSUPPORTED;
     }
   }
-  if (info) info->launches = launches;
+  if (info) {
+    info->launches = launches;
+    info->cached = reused ? 1 : 0;
+  }
   if (err != cudaSuccess) {
     cudaGetLastError();
     return err == cudaErrorNotSupported ? FAMLIES_ERR_UNSUPPORTED : FAMLIES_ERR_CUDA;

@@ -124,6 +124,6 @@ def test_cuda_core_few_tiles_split_k(dtype, tol):
     dt = {"f64": torch.float64, "f32": torch.float32}[dtype]
     got, info = run_gpu(p, dtype, kernel=1)
     assert info["kernel_name"] == ("simt_f64" if dtype == "f64" else "simt_f32")
-    assert info["launches"] == 3  # tables, split product, reduction
+    assert info["launches"] + info["cached"] == 3  # tables, split product, reduction
     want = run_oracle(p, dt, dt)
     assert rel_frob(gpu_dense(got), want) <= tol

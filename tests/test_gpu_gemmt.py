@@ -87,7 +87,7 @@ def test_few_tiles_long_k_splits_k(dtype):
     host, devs = _case(rng, 200, 20000, dt=DT[dtype])
     info = _check(host, devs, -1.0, 1.0, dtype)
     # tables, tile list, packs (+ exponents), product, split finish (+ fix-up)
-    assert info["launches"] == {"f64_emu": 9, "f32": 6, "f64": 3}[dtype]
+    assert info["launches"] + info["cached"] == {"f64_emu": 9, "f32": 6, "f64": 3}[dtype]
 
 
 def test_nan_in_a_reaches_its_row_and_column():
