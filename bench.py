@@ -32,10 +32,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "contraction TFLOP/s, % tensor-pipe peak; split-precision vs FP64 speedup"
-# DRAM bytes per product-kernel launch from an ncu capture of a smaller ladder
-# with the same kernel, scaled by executed flops to the benchmark launch; None
-# whenever the product kernel has changed since the capture.
-PRODUCT_TRAFFIC = None
+# DRAM bytes (read + write) of one product-kernel launch from an ncu capture of
+# the v=112 ladder (the same kernel, 6.77e12 executed flops), scaled by executed
+# flops to the benchmark launch; None whenever the product kernel has changed
+# since the capture.
+PRODUCT_TRAFFIC = {"bytes": 9917750784.0 + 1656454656.0, "exec_flops": 6.767392063488e12}
 V_EXT, O_EXT, SLICES = 128, 32, 6
 WORKLOAD = f"ccsd_ladder_v128_o32_f64_split{SLICES}"
 

@@ -137,6 +137,30 @@ __device__ __forceinline__ T krp_at(const Krp& q, int64_t r, int64_t off) {
   return v;
 }
 
+// x as the nearest binary64 value (ties to even), formed with integer
+// instructions only (B300's fp64 pipe is narrow and the fp64-split epilogues
+// convert one integer sum per output): the leading set bit of |x| at
+// position p gives the biased exponent p + 1023, the 52 bits below it the
+// fraction, and the 11 bits after those decide the rounding (above half:
+// up; exactly half: up when the kept fraction is odd); a carry out of the
+// fraction raises the exponent.  Exact for |x| < 2^53.
+__device__ __forceinline__ double i64_to_f64_rn(int64_t x) {
+  if (x == 0) return 0.0;
+  const unsigned long long sign = x < 0 ? 0x8000000000000000ull : 0ull;
+  const unsigned long long u = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+  const int lz = __clzll((long long)u);
+  const unsigned long long m = u << lz;          // leading 1 at bit 63
+  unsigned long long mant = m >> 11;             // 53 bits, leading 1 at bit 52
+  const unsigned long long rem = m & 0x7FFull;   // the bits rounded away
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ++mant;
+  unsigned long long e = (unsigned long long)(63 - lz + 1023);
+  if (mant >> 53) {  // rounding carried into bit 53
+    mant >>= 1;
+    ++e;
+  }
+  return __longlong_as_double((long long)(sign | (e << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
 // Number of int64 entries the offset tables of a plan need.
 inline int64_t table_entries(const Plan& p) {
   return 2 * p.m + 2 * p.n + 2 * p.k + 3 * p.l;

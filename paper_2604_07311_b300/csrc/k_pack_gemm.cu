@@ -228,7 +228,7 @@ __device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, const
       // x * 2^e by adding e to x's exponent field (integer arithmetic: the
       // fp64 pipe is narrow) when the result stays a normal number
       // the two sums in units of 2^-xunit (lsc: an exact power of two)
-      const double x = FINE ? (double)g[j] + (double)gl[j] * lsc : (double)g[j];
+      const double x = FINE ? (double)g[j] + (double)gl[j] * lsc : i64_to_f64_rn(g[j]);
       const long long xb = __double_as_longlong(x);
       const int ex = (int)((xb >> 52) & 0x7FF);
       const double scaled = (ex != 0 && ex + e >= 1 && ex + e <= 2046)
@@ -593,12 +593,18 @@ __global__ void __launch_bounds__(256, 4) k_split_reduce(const float* __restrict
 
 // fp64 split: the splits of a tile added their int64 sums into one slot;
 // C = alpha * 2^(e_m + e_n - xunit) * sum + beta * C (rows and columns
-// holding Inf/NaN are left to the native fix-up).
+// holding Inf/NaN are left to the native fix-up).  Item: a tail tile and
+// SPLIT_COLS of its columns; thread t owns row t % BM and the columns t / BM
+// + 2 j.  Every load an item needs but C's (the row's flag, exponent and
+// offset, the columns' tables, the sums) is issued at once; only C's loads
+// wait for the column offsets: two levels of dependent loads per item.
+template <bool FINE>
 __global__ void __launch_bounds__(256, 3) k_split_finish(const int64_t* __restrict__ X, int64_t full,
-                                                     int bn, int xunit, int xlo, int nlow, Prob P) {
+                                                     int bn, int xunit, int xlo, Prob P) {
+  constexpr int PER = SPLIT_PER_THREAD;
   const int chunks = bn / SPLIT_COLS;
   const int64_t items = (prob_tiles(P, bn) - full) * chunks;
-  const size_t per = (size_t)BM * bn, slot = per * (nlow ? 2 : 1);
+  const size_t per = (size_t)BM * bn, slot = per * (FINE ? 2 : 1);
   const double lsc = ldexp(1.0, xunit - xlo);
   double* C = (double*)P.c;
   const int lr = threadIdx.x % BM, lq = threadIdx.x / BM;
@@ -608,29 +614,35 @@ __global__ void __launch_bounds__(256, 3) k_split_finish(const int64_t* __restri
     int64_t tm, tn, il;
     tile_coords(P, bn, tile, tm, tn, il);
     const int64_t row = tm * BM + lr;
-    if (row >= P.m || P.fa[il * P.m + row]) continue;
-    const int64_t crow = P.cl[il] + P.cm[row];
-    const int er = P.ea[il * P.m + row] - xunit;
-    int64_t x[SPLIT_PER_THREAD], xl[SPLIT_PER_THREAD], off[SPLIT_PER_THREAD];
-    int ec[SPLIT_PER_THREAD];
-    double old[SPLIT_PER_THREAD];
+    const bool rv = row < P.m;
+    const int32_t fa = rv ? P.fa[il * P.m + row] : 1;
+    const int64_t crow = P.cl[il] + (rv ? P.cm[row] : 0);
+    const int er = (rv ? P.ea[il * P.m + row] : 0) - xunit;
+    const int64_t* Xt = X + (size_t)ti * slot + lr;
+    int64_t x[PER], xl[PER], cn[PER];
+    int32_t fb[PER], ec[PER];
+    bool in[PER];
 #pragma unroll
-    for (int j = 0; j < SPLIT_PER_THREAD; ++j) {
+    for (int j = 0; j < PER; ++j) {
       const int lc = c0 + lq + j * (256 / BM);
       const int64_t col = tn * bn + lc;
-      const bool ok = col < P.n && !P.fb[il * P.n + col] && tri_keep(P.tri, row, col);
-      off[j] = ok ? crow + P.cn[col] : -1;
-      ec[j] = ok ? P.eb[il * P.n + col] : 0;
-      // a tile's slot: coarse sums, then fine sums (see the product's epilogue)
-      const size_t at = (size_t)ti * slot + (size_t)lc * BM + lr;
-      x[j] = X[at];
-      xl[j] = nlow ? X[at + per] : 0;
+      in[j] = rv && col < P.n && tri_keep(P.tri, row, col);
+      fb[j] = in[j] ? P.fb[il * P.n + col] : 1;
+      ec[j] = in[j] ? P.eb[il * P.n + col] : 0;
+      cn[j] = in[j] ? P.cn[col] : 0;
+      x[j] = Xt[(size_t)lc * BM];
+      xl[j] = FINE ? Xt[per + (size_t)lc * BM] : 0;
+    }
+    int64_t off[PER];
+    double old[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      off[j] = (in[j] && !fa && !fb[j]) ? crow + cn[j] : -1;
+      old[j] = (off[j] >= 0 && P.beta != 0.0) ? C[off[j]] : 0.0;
     }
 #pragma unroll
-    for (int j = 0; j < SPLIT_PER_THREAD; ++j) old[j] = (off[j] >= 0 && P.beta != 0.0) ? C[off[j]] : 0.0;
-#pragma unroll
-    for (int j = 0; j < SPLIT_PER_THREAD; ++j) {
-      const double xd = (double)x[j] + (double)xl[j] * lsc;
+    for (int j = 0; j < PER; ++j) {
+      const double xd = FINE ? (double)x[j] + (double)xl[j] * lsc : i64_to_f64_rn(x[j]);
       const int e = er + ec[j];
       const long long xb = __double_as_longlong(xd);
       const int ex = (int)((xb >> 52) & 0x7FF);
@@ -1189,9 +1201,13 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   nvtxRangePop();
   mark_end(g, s);  // the events bracket the product kernel alone
   if (e == cudaSuccess && a.tailed) {
-    if (emu)
-      k_split_finish<<<split_grid, 256, 0, s>>>(a.xtail, a.full, bn, a.sc.xunit, a.sc.xlo, a.sc.nlow,
-                                                a.single);
+    if (emu) {
+      const int fg = (int)std::min<int64_t>(spl.tail * (bn / SPLIT_COLS), (int64_t)num_sms() * 24);
+      if (a.sc.nlow)
+        k_split_finish<true><<<fg, 256, 0, s>>>(a.xtail, a.full, bn, a.sc.xunit, a.sc.xlo, a.single);
+      else
+        k_split_finish<false><<<fg, 256, 0, s>>>(a.xtail, a.full, bn, a.sc.xunit, a.sc.xlo, a.single);
+    }
     else
       k_split_reduce<<<split_grid, 256, 0, s>>>(a.part, a.splits, a.full, bn, a.single);
     e = cudaGetLastError();

@@ -162,3 +162,54 @@ def test_long_k_block_uses_exact_fine_sums_in_the_grouped_launch():
     assert rel_frob(got, want) <= 1e-13
     p2 = W.Problem("small", 1.0, A2, B2, 0.5, C2)
     assert rel_frob(gpu_dense(dev[5]), run_oracle(p2)) <= 1e-13
+
+
+def test_full_block_sparse_configuration_sampled_dot2():
+    """The full configuration: 2000 blocks of the four-index pattern, each of
+    the six extents drawn from {8, 16, ..., 96} (7.5e13 flops).  Its literal
+    inputs would take ~350 GB, so every block's A and B are column-major views
+    into one shared random pool at seeded offsets (read-only: sharing is
+    harmless); each C has its own storage (~114 GB).  One grouped call under a
+    CUDA graph; 32 entries of each of 64 blocks, the largest included, against
+    the oracle's compensated (Dot2) sums, within 1e-13 relative Frobenius."""
+    import oracle
+    torch.cuda.empty_cache()
+    nblocks = 2000
+    ext = W.block_sparse_extents(nblocks=nblocks)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(3)
+    pool = torch.rand(1 << 28, device="cuda", dtype=torch.float64, generator=gen)
+    offs = np.random.default_rng(W.SEED_BASE + 40).integers(0, (1 << 28) - 96 ** 4, size=(nblocks, 2))
+    As, Bs, Cs = [], [], []
+    la, lb, lc = W.L("acik"), W.L("ckbj"), W.L("abij")
+    for bi, (a, b, c, i, j, k) in enumerate(map(int, e) for e in ext):
+        As.append(torch.as_strided(pool, (a, c, i, k), W.colmajor_strides((a, c, i, k)), int(offs[bi, 0])))
+        Bs.append(torch.as_strided(pool, (c, k, b, j), W.colmajor_strides((c, k, b, j)), int(offs[bi, 1])))
+        Cs.append(torch.full((j, i, b, a), float("nan"), device="cuda", dtype=torch.float64).permute(3, 2, 1, 0))
+    fm.contract_batched(1.0, As, [la] * nblocks, Bs, [lb] * nblocks, 0.0, Cs, [lc] * nblocks,
+                        dtype="f64_emu", use_graph=True)
+    torch.cuda.synchronize()
+    assert fm.device_status() == 0
+    sizes = np.array([float(np.prod(e)) for e in ext])
+    pick = sorted(set([int(np.argmax(sizes))] +
+                      [int(x) for x in np.random.default_rng(960).choice(nblocks, 63, replace=False)]))
+    assert len(pick) >= 50
+    pool_h = pool.cpu().numpy()
+    rng = np.random.default_rng(961)
+    num = den = 0.0
+    for bi in pick:
+        Ah = np.lib.stride_tricks.as_strided(pool_h[int(offs[bi, 0]):], tuple(As[bi].shape),
+                                             tuple(8 * x for x in As[bi].stride()))
+        Bh = np.lib.stride_tricks.as_strided(pool_h[int(offs[bi, 1]):], tuple(Bs[bi].shape),
+                                             tuple(8 * x for x in Bs[bi].stride()))
+        got = Cs[bi].cpu().numpy()
+        idx = np.stack([rng.integers(0, e, 32) for e in got.shape], axis=1)
+        want = oracle.entries(1.0, Ah, la, Bh, lb, 0.0, np.zeros(got.shape), lc, idx, dot2=True)
+        g = got[tuple(idx.T)]
+        assert np.all(np.isfinite(g)), bi  # beta = 0: the NaN C held is overwritten
+        num += float(np.sum((g - want) ** 2))
+        den += float(np.sum(want ** 2))
+        assert rel_frob(g, want) <= 1e-13, (bi, ext[bi])
+    assert (num / den) ** 0.5 <= 1e-13
+    del As, Bs, Cs, pool
+    torch.cuda.empty_cache()
