@@ -175,7 +175,8 @@ PlanCache& plan_cache() {
 // Khatri-Rao; triangle updates).
 std::vector<int64_t> cache_key(const Plan& p, cudaStream_t s) {
   std::vector<int64_t> k;
-  if (p.sym_n || p.band_side >= 0 || p.krp_side >= 0 || p.tri) return k;
+  if (p.sym_n || p.band_side >= 0 || p.krp_side >= 0 || p.tri || p.emit_mode || p.pre_e[0] || p.pre_e[1])
+    return k;
   int dev = 0;
   cudaGetDevice(&dev);
   k = {dev, (int64_t)(intptr_t)s, (int64_t)p.dtype, p.kernel, p.slices, p.tile_n, p.force_gather,
@@ -327,6 +328,10 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
     g.tri = p.tri;
     g.krp = p.krp;
     g.krp_op = p.krp_side + 1;
+    g.emit_mode = p.emit_mode;
+    g.emit_e = p.emit_e;
+    g.emit_flag = p.emit_flag;
+    g.emit_list = p.emit_list;
     g.ev_begin = opt ? (cudaEvent_t)opt->events[0] : nullptr;
     g.ev_end = opt ? (cudaEvent_t)opt->events[1] : nullptr;
     switch (p.kernel) {
@@ -653,6 +658,75 @@ int famlies_network(const famlies_tensor_t* tensors, int32_t ntensors,
     if (rc) {
       release();
       return rc;
+    }
+  }
+  // Fused epilogues (fp64 split).  The split of a consuming step needs each
+  // of its rows' exponent bound and Inf/NaN flag, a maximum over the whole
+  // row, which a scan of the intermediate would compute.  When the
+  // intermediate is written once (beta = 0) by an fp64-split step and its
+  // first reader is an fp64-split step whose row class for it is exactly
+  // the producer's row or column class (same modes in the same order, so the
+  // two fused row indices agree; no batch labels), the producer's finish
+  // records those exponents and flags as it writes each value, and the
+  // consumer skips its exponent pass over the intermediate.  (Its digit
+  // slices cannot be written by the producer: a row's exponent is only known
+  // once every tile of that row is done.)
+  if (dtype == FAMLIES_F64_EMU && any_inter) {
+    for (int x = 0; x < ntensors; ++x) {
+      if (!inter[x] || !written[x]) continue;
+      int prod = -1, writes = 0, cons = -1;
+      for (int i = 0; i < nsteps; ++i)
+        if (steps[i].c == x) {
+          ++writes;
+          if (prod < 0) prod = i;
+        }
+      if (writes != 1) continue;
+      for (int i = prod + 1; i < nsteps && cons < 0; ++i)
+        if (steps[i].a == x || steps[i].b == x) cons = i;
+      if (cons < 0 || steps[cons].a == steps[cons].b) continue;
+      Plan& P = plans[prod];
+      Plan& Q = plans[cons];
+      auto plain = [](const Plan& q) {
+        return q.kernel == FAMLIES_KERNEL_TC_EMU && q.l == 1 && !q.sym_n && q.band_side < 0 && q.krp_side < 0 &&
+               !q.tri;
+      };
+      if (!plain(P) || !plain(Q)) continue;
+      const int side = Q.a == t[x].data ? 0 : (Q.b == t[x].data ? 1 : -1);
+      if (side < 0) continue;
+      const ClassModes& R = side == 0 ? Q.M : Q.N;
+      auto same = [&](const ClassModes& pc) {
+        if (pc.n != R.n) return false;
+        for (int d = 0; d < pc.n; ++d)
+          if (pc.m[d].ext != R.m[d].ext || pc.m[d].sc != (side == 0 ? R.m[d].sa : R.m[d].sb)) return false;
+        return true;
+      };
+      const int mode = same(P.M) ? 1 : (same(P.N) ? 2 : 0);
+      if (!mode) continue;
+      const int64_t rows = R.total();
+      void* q = nullptr;
+      const size_t eb = ((size_t)rows * 4 + 255) / 256 * 256;
+      if (cudaMallocAsync(&q, 2 * eb + (size_t)(rows + 1) * 4, s) != cudaSuccess) {
+        cudaGetLastError();
+        continue;  // unfused: the consumer scans the intermediate itself
+      }
+      owned.push_back(q);
+      int32_t* e = (int32_t*)q;
+      int32_t* flag = (int32_t*)((char*)q + eb);
+      int32_t* list = (int32_t*)((char*)q + 2 * eb);
+      // exponents start at a large negative value, flags and the list count at 0
+      if (cudaMemsetAsync(e, 0x80, (size_t)rows * 4, s) != cudaSuccess ||
+          cudaMemsetAsync(flag, 0, eb + (size_t)(rows + 1) * 4, s) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return FAMLIES_ERR_CUDA;
+      }
+      P.emit_mode = mode;
+      P.emit_e = e;
+      P.emit_flag = flag;
+      P.emit_list = list;
+      Q.pre_e[side] = e;
+      Q.pre_flag[side] = flag;
+      Q.pre_list[side] = list;
     }
   }
   for (int i = 0; i < nsteps; ++i) {

@@ -44,6 +44,10 @@ struct GemmArgs {
   Krp krp;                 // Khatri-Rao operand (see Plan) is operand krp_op - 1 (0: none)
   int krp_op;
   void* part;              // CUDA-core split K: partial results [split][l][n][m] (null: none)
+  int emit_mode;           // fp64 split in a network: consumer exponents recorded (see Plan)
+  int32_t* emit_e;
+  int32_t* emit_flag;
+  int32_t* emit_list;
   cudaEvent_t ev_begin, ev_end;  // host only: recorded around the product kernel
 };
 
@@ -159,6 +163,24 @@ __device__ __forceinline__ double i64_to_f64_rn(int64_t x) {
     ++e;
   }
   return __longlong_as_double((long long)(sign | (e << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+// A network's fused epilogue: folds output value v into the row exponent
+// bound and non-finite flag that the consuming step's split would compute
+// for its row ci (exponent max(E, 1) - 1022 over the row's biased exponents
+// E; E = 2047 flags the row and lists it once).  `e` is the largest exponent
+// already folded by this thread (or warp) for ci, so that callers can reduce
+// before the atomic; returns nothing.
+__device__ __forceinline__ int f64_row_exp(double v, bool* bad) {
+  const int E = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+  *bad = E == 0x7FF;
+  return (E > 1 ? E : 1) - 1022;
+}
+__device__ __forceinline__ void emit_mark(int32_t* flag, int32_t* list, int64_t ci) {
+  if (atomicExch(&flag[ci], 1) == 0) {
+    const int pos = atomicAdd(&list[0], 1);
+    list[1 + pos] = (int32_t)ci;
+  }
 }
 
 // Number of int64 entries the offset tables of a plan need.

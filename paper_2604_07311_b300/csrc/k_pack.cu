@@ -726,6 +726,13 @@ __device__ __forceinline__ void fixup_body(const GemmArgs& g, const int32_t* __r
     double v = g.alpha * acc;
     if (g.beta != 0.0) v = fma(g.beta, *p, v);
     *p = v;
+    if (g.emit_mode) {  // a network's fused epilogue: the consumer's exponents
+      bool bad = false;
+      const int ve = f64_row_exp(v, &bad);
+      const int64_t ci = g.emit_mode == 1 ? m : n;
+      atomicMax(&g.emit_e[ci], ve);
+      if (bad) emit_mark(g.emit_flag, g.emit_list, ci);
+    }
   }
 }
 

@@ -237,6 +237,23 @@ __device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, const
       double v = alpha == 1.0 ? scaled : alpha * scaled;
       if (beta != 0.0) v = beta == 1.0 ? v + cold[j] : fma(beta, cold[j], v);
       if (use[j]) C[crow + coff[j]] = v;
+      if (P.emit_mode) {  // a network's fused epilogue: the consumer's exponents
+        bool bad = false;
+        const int ve = use[j] ? f64_row_exp(v, &bad) : -2000;
+        const unsigned act = __activemask();  // the lanes finishing this tile
+        const int64_t ci = P.emit_mode == 1 ? row : col0 + j0 + j;
+        if (P.emit_mode == 1) {
+          if (ve > -2000) atomicMax(&P.emit_e[ci], ve);
+          if (use[j] && bad) emit_mark(P.emit_flag, P.emit_list, ci);
+        } else {
+          const int wm = __reduce_max_sync(act, ve);
+          const unsigned wb = __reduce_or_sync(act, (use[j] && bad) ? 1u : 0u);
+          if ((threadIdx.x & 31) == (unsigned)(__ffs(act) - 1) && ci < P.n) {
+            if (wm > -2000) atomicMax(&P.emit_e[ci], wm);
+            if (wb) emit_mark(P.emit_flag, P.emit_list, ci);
+          }
+        }
+      }
     }
   }
 }
@@ -640,6 +657,8 @@ __global__ void __launch_bounds__(256, 3) k_split_finish(const int64_t* __restri
       off[j] = (in[j] && !fa && !fb[j]) ? crow + cn[j] : -1;
       old[j] = (off[j] >= 0 && P.beta != 0.0) ? C[off[j]] : 0.0;
     }
+    int rmx = -2000;
+    bool rbad = false;
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
       const double xd = FINE ? (double)x[j] + (double)xl[j] * lsc : i64_to_f64_rn(x[j]);
@@ -652,6 +671,26 @@ __global__ void __launch_bounds__(256, 3) k_split_finish(const int64_t* __restri
       double v = P.alpha == 1.0 ? scaled : P.alpha * scaled;
       if (P.beta != 0.0) v = P.beta == 1.0 ? v + old[j] : fma(P.beta, old[j], v);
       if (off[j] >= 0) C[off[j]] = v;
+      if (P.emit_mode) {  // a network's fused epilogue: the consumer's exponents
+        bool bad = false;
+        const int ve = off[j] >= 0 ? f64_row_exp(v, &bad) : -2000;
+        if (P.emit_mode == 1) {
+          rmx = max(rmx, ve);
+          rbad = rbad || (off[j] >= 0 && bad);
+        } else {  // consumer row = this column: reduce over the warp's 32 rows
+          const int wm = __reduce_max_sync(0xffffffffu, ve);
+          const unsigned wb = __reduce_or_sync(0xffffffffu, (off[j] >= 0 && bad) ? 1u : 0u);
+          const int64_t col = tn * bn + c0 + lq + j * (256 / BM);
+          if ((threadIdx.x & 31) == 0 && col < P.n) {
+            if (wm > -2000) atomicMax(&P.emit_e[col], wm);
+            if (wb) emit_mark(P.emit_flag, P.emit_list, col);
+          }
+        }
+      }
+    }
+    if (P.emit_mode == 1 && rv) {
+      if (rmx > -2000) atomicMax(&P.emit_e[row], rmx);
+      if (rbad) emit_mark(P.emit_flag, P.emit_list, row);
     }
   }
 }
@@ -1120,13 +1159,27 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     pa.op[1].flag = (int32_t*)(w + L.fb);
     pa.op[0].list = (int32_t*)(w + L.la);
     pa.op[1].list = (int32_t*)(w + L.lb);
+    // an operand whose exponents, flags and list the step that produced it
+    // recorded (a network's fused epilogue): no exponent pass over it
+    bool pre_all = true;
+    for (int side = 0; side < 2; ++side) {
+      if (!p.pre_e[side]) {
+        pre_all = false;
+        continue;
+      }
+      pa.op[side].e = p.pre_e[side];
+      pa.op[side].flag = p.pre_flag[side];
+      pa.op[side].list = p.pre_list[side];
+    }
     // exponents start at a large negative value, flags and list counts at 0
     if ((e = cudaMemsetAsync(w + L.ea, 0x80, L.fa - L.ea, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w + L.fa, 0, L.G - L.fa, s)) != cudaSuccess) return e;
     PackArgs pg = pa;  // the generic kernels skip a symmetric or generated operand
     if (own >= 0) pg.op[own].rows = 0;
+    for (int side = 0; side < 2; ++side)
+      if (p.pre_e[side]) pg.op[side].rows = 0;
     nvtxRangePushA("exponents");
-    e = launch_rowexp(pg, s);
+    e = pre_all ? cudaSuccess : launch_rowexp(pg, s);
     nvtxRangePop();
     if (e != cudaSuccess) return e;
     if (sym && (e = launch_rowexp_sym(pa, p.sym_side, (int32_t*)(w + L.sym), s)) != cudaSuccess) return e;
@@ -1167,6 +1220,10 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   std::memset(&a, 0, sizeof(a));
   a.single = Prob{nullptr, nullptr, g.c, g.t.cm, g.t.cn, g.t.cl, pa.op[0].e, pa.op[1].e,
                   pa.op[0].flag, pa.op[1].flag, p.m, p.n, p.k, p.l, g.alpha, g.beta, bn};
+  a.single.emit_mode = emu ? g.emit_mode : 0;
+  a.single.emit_e = g.emit_e;
+  a.single.emit_flag = g.emit_flag;
+  a.single.emit_list = g.emit_list;
   if (p.tri) {
     if (p.l != 1) return cudaErrorNotSupported;
     const int64_t tiles_m = (p.m + BM - 1) / BM, tiles_n = (p.n + bn - 1) / bn;

@@ -60,6 +60,12 @@ struct Prob {
   int tri;
   const int2* tri_list;
   int64_t tri_tiles;
+  // Single problems in a network (fp64 split): the finish folds every
+  // output into the consuming step's row exponents and flags (see Plan).
+  int emit_mode;
+  int32_t* emit_e;
+  int32_t* emit_flag;
+  int32_t* emit_list;
 };
 
 // One entry of a grouped launch's tile list: problem, row tile, column tile, batch.

@@ -92,6 +92,19 @@ struct Plan {
   // Khatri-Rao product krp, generated while it is packed.
   Krp krp;
   int krp_side = -1;
+  // Contraction networks (fp64 split): exponents, non-finite flags and the
+  // flagged-row list of operand side w computed by the step that produced
+  // it (null: this call's exponent pass computes them) ...
+  int32_t* pre_e[2] = {nullptr, nullptr};
+  int32_t* pre_flag[2] = {nullptr, nullptr};
+  int32_t* pre_list[2] = {nullptr, nullptr};
+  // ... and, on that producing step, where its finish records them for the
+  // consumer: emit_mode 1 = the consumer's row index is this call's row
+  // index, 2 = its column index (0: nothing recorded).
+  int emit_mode = 0;
+  int32_t* emit_e = nullptr;
+  int32_t* emit_flag = nullptr;
+  int32_t* emit_list = nullptr;
 };
 
 // Validates and plans; returns FAMLIES_OK or a FAMLIES_ERR_* code.  Never

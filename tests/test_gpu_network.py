@@ -100,3 +100,43 @@ def test_empty_network_and_single_step():
     torch.cuda.synchronize()
     want = _oracle_step(2.0, A.view(), [1, 2], B.view(), [2, 3], -1.0, C.view(), [1, 3])
     assert rel_frob(gpu_dense(Cd), want) <= 1e-13
+
+
+@pytest.mark.parametrize("x_first", ["i", "k"])
+@pytest.mark.parametrize("j", [200, 600])
+@pytest.mark.parametrize("nan", [False, True])
+def test_fused_exponents_match_separate_calls_bitwise(x_first, j, nan):
+    """X = A B then D = X C - D (emulated fp64): the consumer's rows of X are
+    the producer's rows (X listed i first) or its columns (k first), so the
+    producer's finish records the consumer's row exponents and Inf/NaN flags
+    and the consumer skips its exponent scan of X.  The exponents are the
+    ones the scan would find, so the result is bit-identical to two separate
+    calls.  k = 200 finishes the producer's tiles in a separate kernel, k =
+    600 inside the product; a NaN in A sends rows through the native fix-up,
+    which records its values too."""
+    rng = np.random.default_rng(710 + j)
+    ni, nk, nl = 300, 260, 150
+    A = W.uniform_operand(rng, (ni, j), [1, 2])
+    if nan:
+        A.buf[5 + ni * 7] = np.nan
+    B = W.uniform_operand(rng, (j, nk), [2, 3])
+    Cm = W.uniform_operand(rng, (nk, nl), [3, 4])
+    D = W.uniform_operand(rng, (ni, nl), [1, 4])
+    Ad, Bd, Cd = (to_device(x, torch.float64) for x in (A, B, Cm))
+    D1, D2 = to_device(D, torch.float64), to_device(D, torch.float64)
+    lx = [1, 3] if x_first == "i" else [3, 1]
+    shape = (ni, nk) if x_first == "i" else (nk, ni)
+    tensors = [(Ad, [1, 2]), (Bd, [2, 3]), (shape, lx), (Cd, [3, 4]), (D1, [1, 4])]
+    fm.contract_network(tensors, [(0, 1, 2, 1.0, 0.0), (2, 3, 4, 1.0, -1.0)], dtype="f64_emu")
+    X = torch.empty(shape[::-1], dtype=torch.float64, device="cuda").t()  # first mode fastest, as the library lays it
+    fm.contract(1.0, Ad, [1, 2], Bd, [2, 3], 0.0, X, lx, dtype="f64_emu")
+    fm.contract(1.0, X, lx, Cd, [3, 4], -1.0, D2, [1, 4], dtype="f64_emu")
+    torch.cuda.synchronize()
+    g1, g2 = gpu_dense(D1), gpu_dense(D2)
+    assert np.array_equal(g1, g2, equal_nan=True)
+    Xo = _oracle_step(1.0, A.view(), [1, 2], B.view(), [2, 3], 0.0, np.zeros(shape), lx)
+    want = _oracle_step(1.0, Xo, lx, Cm.view(), [3, 4], -1.0, D.view(), [1, 4])
+    assert np.array_equal(np.isnan(g1), np.isnan(want))
+    fin = np.isfinite(want)
+    assert rel_frob(g1[fin], want[fin]) <= TOL["f64_emu"]
+    assert fm.device_status() == 0
