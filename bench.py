@@ -279,6 +279,27 @@ def run_gpu(args):
     burst, sustained, src = peaks()
     achieved = exec_flops / (kms * 1e-3) / 1e12
 
+    # ---- the same product on CTA pairs (cta_group::2), for comparison: step
+    # and product times, and whether the result is bit-identical
+    Cp, Cq = C0.clone(), C0.clone()
+    step(Cp)
+    _, pinfo = step(Cq, ctas_per_mma=2)
+    torch.cuda.synchronize()
+    pev = []
+    for _ in range(max(3, min(args.steps, 5))):
+        b, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        step(C, events=(b, e), ctas_per_mma=2)
+        s1.record(stream)
+        pev.append((b, e, s0, s1))
+    torch.cuda.synchronize()
+    pair_cmp = {"ctas_per_mma": pinfo["ctas_per_mma"],
+                "product_ms": statistics.mean(b.elapsed_time(e) for b, e, _, _ in pev),
+                "step_ms": statistics.mean(s0.elapsed_time(s1) for _, _, s0, s1 in pev),
+                "bit_identical": bool(torch.equal(Cp, Cq))}
+    del Cp, Cq
+
     # ---- native fp64 on the GPU (the speedup denominator) and agreement
     Ce = C0.clone()
     step(Ce)
@@ -329,6 +350,7 @@ def run_gpu(args):
                    "k": info["k"], "slices": SLICES, "beta": p.beta, "l2": "inputs larger than L2",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "speedup_vs_native_f64": native_ms / ms,
+        "cta_pairs": pair_cmp,
         "native_f64": {"ms": native_ms, "tflops": flops / (native_ms * 1e-3) / 1e12},
         "rel_err_vs_oracle": err_oracle, "error_sample": err_note,
         "rel_err_vs_native_f64": rel, "rel_err_vs_native_f64_ab_term": rel_ab,

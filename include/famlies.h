@@ -132,6 +132,14 @@ typedef struct {
  *               FAMLIES_ERR_UNSUPPORTED.
  *   tile_n      tensor-core tile width (64, 128 or 256, or 192 for the
  *               direct bf16 kernel; 0 = automatic).
+ *   ctas_per_mma 0 or 1 = one SM per tensor-core MMA (the default); 2 =
+ *               CTA pairs where the product supports them: the fp64
+ *               split's packed product with 256 x 256 tiles (cta_group::2,
+ *               each SM of a pair staging 128 rows of A and 128 columns of
+ *               B), for single problems without batch labels or triangle,
+ *               k > 512 and at least as many pair tiles as pairs of SMs
+ *               that fit at once; other calls run on one SM per MMA.
+ *               Results are the same either way (integer-exact products).
  *   wait_limit  iteration cap of every bounded wait (0 = default).
  *   stall_test  testing only (0 in normal use): nonzero makes the
  *               tensor-core product kernels first wait, bounded by
@@ -150,7 +158,9 @@ typedef struct {
   int32_t stall_test;
   int64_t wait_limit;
   void* events[2];
-  int64_t reserved[2];
+  int32_t ctas_per_mma;
+  int32_t reserved32;
+  int64_t reserved;
 } famlies_options_t;
 
 /* What the planner decided for a call (filled by famlies_plan and, when
@@ -162,7 +172,11 @@ typedef struct {
  * path chosen (see FAMLIES_KERNEL_*); launches counts the kernels the call
  * launched; cached = 1 when the call reused the workspace and offset tables
  * of an earlier call with the same shapes, strides, dtype, knobs and stream
- * (the plan cache; it then launched one kernel fewer: no table build).
+ * (the plan cache; it then launched one kernel fewer: no table build);
+ * ctas_per_mma = 2 when the product ran on CTA pairs (one tensor-core MMA
+ * over two SMs' shared memory, the fp64 split's 256 x 256 tiles; set by
+ * famlies_contract_ex when options ask for pairs and the call supports
+ * them, 1 otherwise and from famlies_plan).
  * The plan cache keeps up to 16 such workspaces of at most 256 MB each,
  * the least recently used freed (with a device-wide wait) when a new one is
  * needed; it is bypassed while the stream is being captured into a graph
@@ -179,6 +193,7 @@ typedef struct {
   int32_t b_contig;
   int32_t c_contig; /* 0 none, 1 along rows, 2 along columns */
   int32_t cached;   /* 1: served by the plan cache (see above) */
+  int32_t ctas_per_mma; /* 2: the product ran on CTA pairs (see above) */
 } famlies_plan_info_t;
 
 #define FAMLIES_KERNEL_NONE 0      /* nothing to do (empty C) */

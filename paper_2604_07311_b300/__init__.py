@@ -44,7 +44,7 @@ def _stream_handle(stream):
 
 
 def contract(alpha, A, la, B, lb, beta, C, lc, dtype=None, stream=None, *, slices=0, kernel=0,
-             tile_n=0, wait_limit=0, events=None, return_info=False, stall_test=0):
+             tile_n=0, wait_limit=0, events=None, return_info=False, stall_test=0, ctas_per_mma=0):
     """C := alpha * contract(A, B) + beta * C on the GPU, in place on C.
 
     A, B, C are CUDA torch tensors (any non-negative strides); la, lb, lc are
@@ -56,8 +56,8 @@ def contract(alpha, A, la, B, lb, beta, C, lc, dtype=None, stream=None, *, slice
     code = _dtype_code(dtype, A, C)
     da, db, dc = _desc_reused(0, A, la), _desc_reused(1, B, lb), _desc_reused(2, C, lc)
     info = PlanInfo() if return_info else None
-    if slices or kernel or tile_n or wait_limit or events is not None or stall_test:
-        opt = options(slices, kernel, tile_n, wait_limit, events, stall_test)
+    if slices or kernel or tile_n or wait_limit or events is not None or stall_test or ctas_per_mma:
+        opt = options(slices, kernel, tile_n, wait_limit, events, stall_test, ctas_per_mma)
     else:
         opt = None
     check(lib.famlies_contract_ex(float(alpha), da.ref, db.ref, float(beta), dc.ref, code,

@@ -49,7 +49,8 @@ class MatrixDesc(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("slices", ctypes.c_int32), ("kernel", ctypes.c_int32), ("tile_n", ctypes.c_int32),
                 ("stall_test", ctypes.c_int32), ("wait_limit", ctypes.c_int64),
-                ("events", ctypes.c_void_p * 2), ("reserved", ctypes.c_int64 * 2)]
+                ("events", ctypes.c_void_p * 2), ("ctas_per_mma", ctypes.c_int32), ("reserved32", ctypes.c_int32),
+                ("reserved", ctypes.c_int64)]
 
 
 class Step(ctypes.Structure):
@@ -64,7 +65,7 @@ class PlanInfo(ctypes.Structure):
                 ("k_modes", ctypes.c_int32), ("batch_modes", ctypes.c_int32),
                 ("swapped", ctypes.c_int32), ("kernel", ctypes.c_int32), ("launches", ctypes.c_int32),
                 ("slices", ctypes.c_int32), ("a_contig", ctypes.c_int32), ("b_contig", ctypes.c_int32),
-                ("c_contig", ctypes.c_int32), ("cached", ctypes.c_int32)]
+                ("c_contig", ctypes.c_int32), ("cached", ctypes.c_int32), ("ctas_per_mma", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -163,11 +164,12 @@ def desc_numpy(x, labels) -> Desc:
     return Desc(x.shape, tuple(s // es for s in x.strides), labels, x.__array_interface__["data"][0])
 
 
-def options(slices=0, kernel=0, tile_n=0, wait_limit=0, events=None, stall_test=0) -> Options:
+def options(slices=0, kernel=0, tile_n=0, wait_limit=0, events=None, stall_test=0, ctas_per_mma=0) -> Options:
     """events: optional (begin, end) torch.cuda.Event pair recorded around the product kernel."""
     o = Options()
     o.slices, o.kernel, o.tile_n, o.wait_limit = int(slices), int(kernel), int(tile_n), int(wait_limit)
     o.stall_test = int(stall_test)
+    o.ctas_per_mma = int(ctas_per_mma)
     if events is not None:
         for i, ev in enumerate(events):
             if getattr(ev, "cuda_event", 0) == 0:

@@ -180,7 +180,7 @@ std::vector<int64_t> cache_key(const Plan& p, cudaStream_t s) {
   int dev = 0;
   cudaGetDevice(&dev);
   k = {dev, (int64_t)(intptr_t)s, (int64_t)p.dtype, p.kernel, p.slices, p.tile_n, p.force_gather,
-       (int64_t)p.swapped, p.m, p.n, p.k, p.l};
+       p.cta_pair, (int64_t)p.swapped, p.m, p.n, p.k, p.l};
   for (const ClassModes* cm : {&p.M, &p.N, &p.K, &p.L}) {
     k.push_back(cm->n);
     for (int i = 0; i < cm->n; ++i) {
@@ -358,6 +358,7 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
   if (info) {
     info->launches = launches;
     info->cached = reused ? 1 : 0;
+    info->ctas_per_mma = p.kernel == FAMLIES_KERNEL_TC_EMU ? packed_ctas_per_mma(p) : 1;
   }
   if (err != cudaSuccess) {
     cudaGetLastError();

@@ -102,6 +102,8 @@ int64_t packed_workspace_bytes(const Plan& p);
 cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream_t s);
 // Kernel launches launch_packed makes for plan p.
 int packed_launches(const Plan& p);
+// CTAs per tensor-core MMA of the packed product (2: CTA pairs).
+int packed_ctas_per_mma(const Plan& p);
 
 // Whether C's element (row r, column c) of the kernel's indices is updated
 // under triangle mode tri (see Plan::tri).

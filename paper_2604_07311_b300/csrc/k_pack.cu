@@ -6,6 +6,7 @@
 // the operand's unit-stride index into shared memory and written as 16-byte
 // K-major chunks, so both the reads and the writes are full-width.  All of
 // it is bound by HBM bandwidth.
+#include <algorithm>
 #include <cstdint>
 
 #include <cuda_bf16.h>
@@ -736,6 +737,102 @@ __device__ __forceinline__ void fixup_body(const GemmArgs& g, const int32_t* __r
   }
 }
 
+// ------------------------------------------------------------ one-pass split
+// An fp64-split operand whose k is one unit-stride mode (each row a run of k
+// consecutive values, k <= kRowPackMaxK): its row exponents, flags and slices
+// in one read.  tpr threads hold a row in registers, 8 consecutive values
+// per group, RP_G groups each (value 8 (g tpr + t) + j in v[g][j]), reduce
+// its exponent bound and flag, then split it from the registers.  The next
+// row's loads go out group by group as the current row's slices are
+// written, so they are in flight while it is split.  512 / tpr rows per
+// block at a time; one block per SM.
+constexpr int RP_THREADS = 512;
+constexpr int RP_G = 4;
+
+template <int S>
+__global__ void __launch_bounds__(RP_THREADS, 1) k_rowpack(const __grid_constant__ PackArgs pa, int side,
+                                                           int tpr) {
+  const PackOp& o = pa.op[side];
+  const double* __restrict__ X = (const double*)o.x;
+  const int64_t K = pa.k, total = pa.l * o.rows;
+  const int rpb = RP_THREADS / tpr;
+  const int slot = threadIdx.x / tpr, t = threadIdx.x % tpr;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t slice_stride = (size_t)pa.l * o.rows * pa.kp;  // elements per slice
+  __shared__ int smx[2][RP_THREADS / 32], sbad[2][RP_THREADS / 32];
+  double v[RP_G][8];
+  auto row_src = [&](int64_t ri) {
+    const int64_t il = pa.l == 1 ? 0 : ri / o.rows;
+    return X + o.loff[il] + row_off(o, ri - il * o.rows);
+  };
+  // group g of this thread's share of the row at p (zeros past k or for no row)
+  auto load = [&](const double* p, int g, bool ok) {
+    const int64_t k0 = 8 * ((int64_t)g * tpr + t);
+    if (ok && k0 + 8 <= K) {
+      if (((uintptr_t)p & 15) == 0) {
+        const double2* q = (const double2*)(p + k0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const double2 d = __ldg(q + j);
+          v[g][2 * j] = d.x;
+          v[g][2 * j + 1] = d.y;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[g][j] = __ldg(p + k0 + j);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[g][j] = ok && k0 + j < K ? __ldg(p + k0 + j) : 0.0;
+    }
+  };
+  const int64_t step = (int64_t)gridDim.x * rpb;
+  int64_t base = (int64_t)blockIdx.x * rpb;  // the block's first row this round
+  {
+    const bool ok = base + slot < total;
+    const double* p = ok ? row_src(base + slot) : X;
+#pragma unroll
+    for (int g = 0; g < RP_G; ++g) load(p, g, ok);
+  }
+  for (int par = 0; base < total; base += step, par ^= 1) {
+    const int64_t ri = base + slot, rn = ri + step;
+    const bool ok = ri < total, okn = rn < total;
+    // values past k were loaded as zeros: their bound, -1021, is the least
+    // any value gives, so they change neither result
+    int mx = -1100, bad = 0;
+#pragma unroll
+    for (int g = 0; g < RP_G; ++g)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) exp_update(v[g][j], mx, bad);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (tpr > 32) {  // across the row's warps (parity-double-buffered: one barrier per round)
+      if (lane == 0) {
+        smx[par][warp] = mx;
+        sbad[par][warp] = bad;
+      }
+      __syncthreads();
+      const int w0 = slot * (tpr >> 5);
+      for (int w = w0; w < w0 + (tpr >> 5); ++w) {
+        mx = max(mx, smx[par][w]);
+        bad |= sbad[par][w];
+      }
+    }
+    if (ok && t == 0) {
+      o.e[ri] = mx;
+      if (bad) mark_row(o, ri);
+    }
+    const double* pn = okn ? row_src(rn) : X;
+    uint16_t* out = (uint16_t*)o.out + (size_t)(ok ? ri : 0) * pa.kp;
+#pragma unroll
+    for (int g = 0; g < RP_G; ++g) {
+      const int64_t k0 = 8 * ((int64_t)g * tpr + t);
+      if (ok && k0 < K) split8<S>(v[g], mx, bad != 0, out + k0, slice_stride);
+      load(pn, g, okn);
+    }
+  }
+}
+
 int grid_for(int64_t blocks) {
   const int64_t cap = (int64_t)num_sms() * 8;
   return (int)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
@@ -922,6 +1019,27 @@ static cudaError_t configure_pack_kernels() {
   e = cudaGetLastError();
   if (e == cudaSuccess && dev < kMaxDev) done[dev] = true;
   return e;
+}
+
+cudaError_t launch_rowpack(const PackArgs& pa, int side, cudaStream_t s) {
+  const PackOp& o = pa.op[side];
+  if (pa.k < kRowPackMinK || pa.k > kRowPackMaxK || !(o.affine & 2) || o.ks != 1) return cudaErrorInvalidValue;
+  static_assert(kRowPackMaxK <= (int64_t)RP_THREADS * RP_G * 8, "a row must fit the block's registers");
+  int tpr = 32;  // threads per row: the fewest that hold k in RP_G groups of 8
+  while ((int64_t)tpr * RP_G * 8 < pa.k) tpr *= 2;
+  const int64_t rows = pa.l * o.rows;
+  if (rows <= 0) return cudaSuccess;
+  const int64_t per = RP_THREADS / tpr;
+  const int grid = (int)std::min<int64_t>((rows + per - 1) / per, num_sms());
+  switch (pa.slices) {
+    case 2: k_rowpack<2><<<grid, RP_THREADS, 0, s>>>(pa, side, tpr); break;
+    case 3: k_rowpack<3><<<grid, RP_THREADS, 0, s>>>(pa, side, tpr); break;
+    case 4: k_rowpack<4><<<grid, RP_THREADS, 0, s>>>(pa, side, tpr); break;
+    case 5: k_rowpack<5><<<grid, RP_THREADS, 0, s>>>(pa, side, tpr); break;
+    case 6: k_rowpack<6><<<grid, RP_THREADS, 0, s>>>(pa, side, tpr); break;
+    default: k_rowpack<7><<<grid, RP_THREADS, 0, s>>>(pa, side, tpr); break;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pack(int pmode, const PackArgs& pa, cudaStream_t s) {

@@ -81,20 +81,26 @@ struct PairArgs {
   int64_t wait_limit;
 };
 
-template <int KIND, int BN, int MODE = PAIR_MODE_F32OUT>
+// CG: CTAs per MMA.  With 2 (a cluster pair, cta_group::2) a tile is
+// 2 BM x BN: each CTA stages its BM rows of A and BN / 2 of B's columns and
+// holds its BM rows of the accumulator; the MMA reads both CTAs' halves.
+template <int KIND, int BN, int MODE = PAIR_MODE_F32OUT, int CG = 1>
 struct PCfg {
   static constexpr int KB = pair_stage_k(KIND);            // k per stage
   static constexpr int ROWB = pair_row_bytes(KIND);        // bytes of one tile row in a stage
   static constexpr int MMA_K = KIND == PAIR_KIND_BF16 ? 16 : 8;
   static constexpr int KSTEPS = KB / MMA_K;
+  static constexpr int TM = BM * CG;                       // rows of an output tile
+  static constexpr int B_ROWS = BN / CG;                   // this CTA's columns of B per stage
   static constexpr int A_BYTES = BM * ROWB;
-  static constexpr int B_BYTES = BN * ROWB;
+  static constexpr int B_BYTES = B_ROWS * ROWB;
   // Ring stages (as many as ~200 KB holds, at most 8).  The row operand's
   // tiles fill one region and the column operand's another, stage s of each
   // guarded by one barrier pair.  (Separate producers and rings of different
   // depth per operand measured slower on both the fp64 split and bf16.)
-  static constexpr int STAGES =
-      (200 * 1024) / (A_BYTES + B_BYTES) > 8 ? 8 : (200 * 1024) / (A_BYTES + B_BYTES);
+  // (A pair's 32 KB stages take the whole 227 KB: seven of them.)
+  static constexpr int RING = CG == 2 ? 227 * 1024 - 1536 : 200 * 1024;
+  static constexpr int STAGES = RING / (A_BYTES + B_BYTES) > 8 ? 8 : RING / (A_BYTES + B_BYTES);
   static constexpr int B_OFF = STAGES * A_BYTES;
   static constexpr int BAR_OFF = B_OFF + STAGES * B_BYTES;
   // Accumulator buffers in tensor memory: two of 256 columns, or four of
@@ -102,7 +108,7 @@ struct PCfg {
   // while the next ones accumulate.
   static constexpr int NACC = BN == 256 ? 2 : 4;
   static constexpr uint32_t TMEM_COLS = NACC * BN;
-  static constexpr uint32_t IDESC = ptx::idesc_make(BM, BN, KIND == PAIR_KIND_BF16 ? 1u : 2u);
+  static constexpr uint32_t IDESC = ptx::idesc_make(TM, BN, KIND == PAIR_KIND_BF16 ? 1u : 2u);
   static constexpr int SMEM_BYTES = BAR_OFF + 1024 + 512;
   static_assert(STAGES >= 2 && SMEM_BYTES <= 227 * 1024, "shared memory budget");
 };
@@ -125,11 +131,12 @@ struct TileRef {
 // Output tiles of a single problem: the whole grid of bn-wide tiles, or
 // those of its triangle list; and the coordinates of tile number `tile`
 // (column tiles fastest, then row tiles, then the batch).
-__host__ __device__ __forceinline__ int64_t prob_tiles(const Prob& P, int bn) {
-  return P.tri_list ? P.tri_tiles : ((P.m + BM - 1) / BM) * ((P.n + bn - 1) / bn) * P.l;
+// rm: rows of a tile (BM, or 2 BM for a CTA pair).
+__host__ __device__ __forceinline__ int64_t prob_tiles(const Prob& P, int bn, int rm = BM) {
+  return P.tri_list ? P.tri_tiles : ((P.m + rm - 1) / rm) * ((P.n + bn - 1) / bn) * P.l;
 }
 __device__ __forceinline__ void tile_coords(const Prob& P, int bn, int64_t tile, int64_t& tm, int64_t& tn,
-                                            int64_t& il) {
+                                            int64_t& il, int rm = BM) {
   if (P.tri_list) {
     const int2 e = P.tri_list[tile];
     tm = e.x;
@@ -137,17 +144,17 @@ __device__ __forceinline__ void tile_coords(const Prob& P, int bn, int64_t tile,
     il = 0;
     return;
   }
-  const int64_t tiles_m = (P.m + BM - 1) / BM, tiles_n = (P.n + bn - 1) / bn;
+  const int64_t tiles_m = (P.m + rm - 1) / rm, tiles_n = (P.n + bn - 1) / bn;
   tn = tile % tiles_n;
   const int64_t rest = tile / tiles_n;
   tm = rest % tiles_m;
   il = rest / tiles_m;
 }
 
-template <int BN, bool GROUPED, bool SPLITK>
+template <int BN, bool GROUPED, bool SPLITK, int RM = BM>
 __device__ __forceinline__ int64_t tile_count(const PairArgs& a) {
   if (GROUPED) return a.ntiles;
-  const int64_t ntile = prob_tiles(a.single, BN);
+  const int64_t ntile = prob_tiles(a.single, BN, RM);
   return SPLITK ? a.full + (ntile - a.full) * a.splits : ntile;
 }
 
@@ -158,7 +165,7 @@ __device__ __forceinline__ int64_t tile_count(const PairArgs& a) {
 // splits the slowest index (concurrent CTAs read the same k range).  A split
 // covers whole units of the fp32-output schedule, or any k blocks for the
 // fp64 split (each diagonal forms its units inside the range).
-template <int BN, bool GROUPED, int KB, bool SPLITK>
+template <int BN, bool GROUPED, int KB, bool SPLITK, int RM = BM>
 __device__ __forceinline__ TileRef tile_at(const PairArgs& a, int64_t t) {
   if (GROUPED) {
     const TileEntry e = a.tiles[t];
@@ -170,7 +177,7 @@ __device__ __forceinline__ TileRef tile_at(const PairArgs& a, int64_t t) {
   int64_t tile = t;
   int split = -1, lo = 0, hi = nkb;
   if (SPLITK && t >= a.full) {
-    const int64_t tail = prob_tiles(P, BN) - a.full, u = t - a.full;
+    const int64_t tail = prob_tiles(P, BN, RM) - a.full, u = t - a.full;
     tile = a.full + u % tail;
     split = (int)(u / tail);
     const int kcb = a.sc.ndiag > 1 ? 1 : a.sc.kcb[0];
@@ -180,7 +187,7 @@ __device__ __forceinline__ TileRef tile_at(const PairArgs& a, int64_t t) {
     hi = hi < nkb ? hi : nkb;
   }
   int64_t tm, tn, il;
-  tile_coords(P, BN, tile, tm, tn, il);
+  tile_coords(P, BN, tile, tm, tn, il, RM);
   return TileRef{&a.single, tm, tn, il, tile, split, lo, hi};
 }
 
@@ -258,16 +265,30 @@ __device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, const
   }
 }
 
+// Items of a CTA: its own for CG = 1, its cluster's for a pair (both CTAs
+// of a cluster walk the same items; CTAs of a cluster have consecutive
+// numbers).
+template <int CG>
+__device__ __forceinline__ int64_t first_item() { return CG == 2 ? blockIdx.x >> 1 : blockIdx.x; }
+template <int CG>
+__device__ __forceinline__ int64_t item_step() { return CG == 2 ? gridDim.x >> 1 : gridDim.x; }
+
 // The TMA producer: walks the CTA's unit sequence (tiles, diagonals, units,
 // pairs, k blocks, exactly as the MMA issuer consumes it) and fills stage s
 // of both operand regions per k block.  On a timeout it sets the abort flag;
 // before returning it waits (bounded) for its copies still in flight.
-template <class Cfg, int BN, bool GROUPED, bool SPLITK>
+// A CTA pair: each CTA loads its own rows of A and columns of B, and both
+// count their bytes on the even CTA's stage barrier (the one the MMA issuer
+// waits on); the stage is free again once the issuer's commit reaches this
+// CTA's own empty barrier.
+template <class Cfg, int BN, bool GROUPED, bool SPLITK, int CG>
 __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap* map_a,
                                         const CUtensorMap* map_b, uint8_t* ring_a, uint8_t* ring_b,
                                         uint64_t* full, uint64_t* empty, int64_t ntiles,
                                         int64_t lim, volatile int* abort) {
   constexpr int S = Cfg::STAGES;
+  const uint32_t rank = CG == 2 ? ptx::cluster_rank() : 0;
+  const uint32_t full0 = CG == 2 ? ptx::mapa(full, 0) : 0;  // the even CTA's barriers
   const Sched& sc = args.sc;
   if (!GROUPED) {
     ptx::prefetch_tmap(map_a);
@@ -277,14 +298,14 @@ __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap*
   uint32_t phase = 0;
   uint32_t pending = 0;  // bit s: stage s holds a copy issued in phase bit (s+8)
   bool ok = true;
-  for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-    const TileRef T = tile_at<BN, GROUPED, Cfg::KB, SPLITK>(args, t);
+  for (int64_t t = first_item<CG>(); t < ntiles && ok; t += item_step<CG>()) {
+    const TileRef T = tile_at<BN, GROUPED, Cfg::KB, SPLITK, Cfg::TM>(args, t);
     const CUtensorMap* ma = GROUPED ? T.P->map_a : map_a;
     const CUtensorMap* mb = GROUPED ? T.P->map_b : map_b;
     const int l = (int)T.P->l;
     const int bnp = GROUPED ? T.P->bn : BN;  // this tile's width
-    const uint32_t bytes = (uint32_t)(Cfg::A_BYTES + bnp * Cfg::ROWB);
-    const int row_a = (int)(T.tm * BM), row_b = (int)(T.tn * bnp);
+    const uint32_t bytes = (uint32_t)(CG * Cfg::A_BYTES + bnp * Cfg::ROWB);  // both CTAs' for a pair
+    const int row_a = (int)(T.tm * Cfg::TM + rank * BM), row_b = (int)(T.tn * bnp + rank * Cfg::B_ROWS);
     for (int di = 0; di < sc.ndiag && ok; ++di) {
       const int kcb = sc.kcb[di];
       for (int kb0 = T.kb_lo; kb0 < T.kb_hi && ok; kb0 += kcb) {
@@ -294,10 +315,18 @@ __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap*
           const int za = sc.pa[di][p] * l + (int)T.il;
           const int zb = sc.pb[di][p] * l + (int)T.il;
           for (int kb = kb0; kb < kb1; ++kb) {
-            if (!ptx::mbar_wait(&empty[stage], phase ^ 1, lim, abort)) { ok = false; break; }
-            ptx::mbar_arrive_expect_tx(&full[stage], bytes);
-            ptx::tma_load_3d(ring_a + stage * Cfg::A_BYTES, ma, &full[stage], kb * Cfg::KB, row_a, za);
-            ptx::tma_load_3d(ring_b + stage * Cfg::B_BYTES, mb, &full[stage], kb * Cfg::KB, row_b, zb);
+            if constexpr (CG == 2) {
+              if (!ptx::mbar_wait(&empty[stage], phase ^ 1, lim, abort)) { ok = false; break; }
+              if (rank == 0) ptx::mbar_arrive_expect_tx(&full[stage], bytes);
+              const uint32_t fb = full0 + 8u * (uint32_t)stage;
+              ptx::tma_load_3d_pair(ring_a + stage * Cfg::A_BYTES, ma, fb, kb * Cfg::KB, row_a, za);
+              ptx::tma_load_3d_pair(ring_b + stage * Cfg::B_BYTES, mb, fb, kb * Cfg::KB, row_b, zb);
+            } else {
+              if (!ptx::mbar_wait(&empty[stage], phase ^ 1, lim, abort)) { ok = false; break; }
+              ptx::mbar_arrive_expect_tx(&full[stage], bytes);
+              ptx::tma_load_3d(ring_a + stage * Cfg::A_BYTES, ma, &full[stage], kb * Cfg::KB, row_a, za);
+              ptx::tma_load_3d(ring_b + stage * Cfg::B_BYTES, mb, &full[stage], kb * Cfg::KB, row_b, zb);
+            }
             pending = (pending & ~(0x101u << stage)) | (1u << stage) | (phase << (stage + 8));
             if (++stage == S) { stage = 0; phase ^= 1; }
           }
@@ -307,7 +336,11 @@ __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap*
   }
   if (!ok && !*abort) record_timeout(abort, args.status);
   // Copies still in flight must land before the CTA leaves: wait (bounded)
-  // for the phase each stage was last filled in.
+  // for the phase each stage was last filled in.  (The odd CTA of a pair
+  // cannot wait on the even CTA's barriers: the pair's closing cluster
+  // barrier follows the issuer's wait for its last MMA, which read every
+  // stage both CTAs filled.)
+  if (CG == 2 && rank != 0) return;
   for (int s = 0; s < S; ++s) {
     if (!(pending & (1u << s))) continue;
     const uint32_t ph = (pending >> (s + 8)) & 1u;
@@ -316,11 +349,12 @@ __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap*
   }
 }
 
-template <int KIND, int MODE, int BN, bool GROUPED, bool SPLITK>
+template <int KIND, int MODE, int BN, bool GROUPED, bool SPLITK, int CG = 1>
 __global__ void __launch_bounds__(THREADS, 1)
     k_pair_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                 const __grid_constant__ PairArgs args) {
-  using Cfg = PCfg<KIND, BN, MODE>;
+  static_assert(CG == 1 || (CG == 2 && KIND == PAIR_KIND_BF16 && !GROUPED), "CTA pairs: bf16 single problems");
+  using Cfg = PCfg<KIND, BN, MODE, CG>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + Cfg::BAR_OFF);
@@ -333,8 +367,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const Sched& sc = args.sc;
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-  const int64_t ntiles = tile_count<BN, GROUPED, SPLITK>(args);
+  const int64_t ntiles = tile_count<BN, GROUPED, SPLITK, Cfg::TM>(args);
   const int64_t lim = args.wait_limit;
+  const uint32_t rank = CG == 2 ? ptx::cluster_rank() : 0;  // 0: the CTA that issues the MMAs
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < Cfg::STAGES; ++s) {
@@ -343,36 +378,52 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int b = 0; b < Cfg::NACC; ++b) {
       ptx::mbar_init(&tfull[b], 1);
-      ptx::mbar_init(&tempty[b], EPI_WARPS);
+      ptx::mbar_init(&tempty[b], EPI_WARPS * CG);  // a pair: both CTAs' epilogue warps
     }
     ptx::mbar_init(done, 1);
     *abort = 0;
     ptx::fence_mbar_init();
   }
   if (warp == EPI_WARPS + 1) {
-    ptx::tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
-    ptx::tmem_relinquish();
+    if constexpr (CG == 2) {
+      ptx::tmem_alloc_pair(tmem_slot, Cfg::TMEM_COLS);
+      ptx::tmem_relinquish_pair();
+    } else {
+      ptx::tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+      ptx::tmem_relinquish();
+    }
   }
   ptx::tc_fence_before();
-  __syncthreads();
+  // a pair: the other CTA's barriers are initialised before anything reaches them
+  if constexpr (CG == 2) {
+    __syncwarp();
+    ptx::cluster_sync();
+  } else {
+    __syncthreads();
+  }
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
   if (warp == EPI_WARPS) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0)
-      produce<Cfg, BN, GROUPED, SPLITK>(args, &map_a, &map_b, smem, smem + Cfg::B_OFF, full, empty, ntiles,
-                                lim, abort);
+      produce<Cfg, BN, GROUPED, SPLITK, CG>(args, &map_a, &map_b, smem, smem + Cfg::B_OFF, full, empty,
+                                            ntiles, lim, abort);
     __syncwarp();
   } else if (warp == EPI_WARPS + 1) {
     // ------------------------------------------------------------ MMA issue
-    if (lane == 0) {
+    // (a pair: the even CTA's thread issues for both; each commit is sent
+    // to the barrier of each CTA, one commit per CTA)
+    if (lane == 0 && rank == 0) {
       int stage = 0;
       uint32_t phase = 0, acc = 0, accph = 0;
+      const uint32_t empty0 = CG == 2 ? ptx::mapa(empty, 0) : 0, empty1 = CG == 2 ? ptx::mapa(empty, 1) : 0;
+      const uint32_t tfull0 = CG == 2 ? ptx::mapa(tfull, 0) : 0, tfull1 = CG == 2 ? ptx::mapa(tfull, 1) : 0;
+      auto wait = [&](uint64_t* bar, uint32_t par) { return ptx::mbar_wait(bar, par, lim, abort); };
       // testing: `done` completes only after this thread's last commit
       bool ok = !args.stall_test || ptx::mbar_wait(done, 0, lim, abort);
-      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const TileRef T = tile_at<BN, GROUPED, Cfg::KB, SPLITK>(args, t);
+      for (int64_t t = first_item<CG>(); t < ntiles && ok; t += item_step<CG>()) {
+        const TileRef T = tile_at<BN, GROUPED, Cfg::KB, SPLITK, Cfg::TM>(args, t);
         // the MMA's N is this tile's width (the instruction descriptor's N field)
         const uint32_t idesc =
             GROUPED ? ptx::idesc_make(BM, T.P->bn, KIND == PAIR_KIND_BF16 ? 1u : 2u) : Cfg::IDESC;
@@ -380,37 +431,50 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int kcb = sc.kcb[di];
           for (int kb0 = T.kb_lo; kb0 < T.kb_hi && ok; kb0 += kcb) {
             const int kb1 = kb0 + kcb < T.kb_hi ? kb0 + kcb : T.kb_hi;
-            if (!ptx::mbar_wait(&tempty[acc], accph ^ 1, lim, abort)) { ok = false; break; }
+            if (!wait(&tempty[acc], accph ^ 1)) { ok = false; break; }
             ptx::tc_fence_after();
             const uint32_t dt = tmem_base + acc * BN;
             uint32_t accumulate = 0;
             for (int p = 0; p < sc.npairs[di] && ok; ++p) {
               for (int kb = kb0; kb < kb1; ++kb) {
-                if (!ptx::mbar_wait(&full[stage], phase, lim, abort)) { ok = false; break; }
+                if (!wait(&full[stage], phase)) { ok = false; break; }
                 ptx::tc_fence_after();
                 const uint64_t da = ptx::sdesc_kmajor<Cfg::ROWB>(ptx::smem_u32(smem + stage * Cfg::A_BYTES));
                 const uint64_t db =
                     ptx::sdesc_kmajor<Cfg::ROWB>(ptx::smem_u32(smem + Cfg::B_OFF + stage * Cfg::B_BYTES));
 #pragma unroll
                 for (int kk = 0; kk < Cfg::KSTEPS; ++kk) {
-                  if (KIND == PAIR_KIND_BF16)
+                  if (CG == 2)
+                    ptx::mma_f16_pair(dt, da + 2 * kk, db + 2 * kk, idesc, accumulate);
+                  else if (KIND == PAIR_KIND_BF16)
                     ptx::mma_f16(dt, da + 2 * kk, db + 2 * kk, idesc, accumulate);
                   else
                     ptx::mma_tf32(dt, da + 2 * kk, db + 2 * kk, idesc, accumulate);
                   accumulate = 1;
                 }
-                ptx::mma_commit(&empty[stage]);
+                if constexpr (CG == 2) {
+                  ptx::mma_commit_pair(empty0 + 8u * (uint32_t)stage);
+                  ptx::mma_commit_pair(empty1 + 8u * (uint32_t)stage);
+                } else {
+                  ptx::mma_commit(&empty[stage]);
+                }
                 if (++stage == Cfg::STAGES) { stage = 0; phase ^= 1; }
               }
             }
             if (!ok) break;
-            ptx::mma_commit(&tfull[acc]);
+            if constexpr (CG == 2) {
+              ptx::mma_commit_pair(tfull0 + 8u * acc);
+              ptx::mma_commit_pair(tfull1 + 8u * acc);
+            } else {
+              ptx::mma_commit(&tfull[acc]);
+            }
             if (++acc == Cfg::NACC) { acc = 0; accph ^= 1; }
           }
         }
       }
       if (!ok && !*abort) record_timeout(abort, args.status);
-      ptx::mma_commit(done);
+      if constexpr (CG == 2) ptx::mma_commit_pair(ptx::mapa(done, 0));
+      else ptx::mma_commit(done);
       for (int64_t i = 0; i < ((int64_t)1 << 24); ++i)
         if (ptx::mbar_try_wait(done, 0)) break;
     }
@@ -422,12 +486,19 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t lane_addr = (uint32_t)(qd * 32) << 16;
     uint32_t acc = 0, accph = 0;
     bool ok = true;
-    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const TileRef T = tile_at<BN, GROUPED, Cfg::KB, SPLITK>(args, t);
+    // a pair: the accumulator buffer is released to the even CTA's issuer
+    const uint32_t tempty0 = CG == 2 ? ptx::mapa(tempty, 0) : 0;
+    auto wait_full = [&](uint32_t b, uint32_t par) { return ptx::mbar_wait(&tfull[b], par, lim, abort); };
+    auto release = [&](uint32_t b) {
+      if (CG == 2 && rank != 0) ptx::mbar_arrive_cluster(tempty0 + 8u * b);
+      else ptx::mbar_arrive(&tempty[b]);
+    };
+    for (int64_t t = first_item<CG>(); t < ntiles && ok; t += item_step<CG>()) {
+      const TileRef T = tile_at<BN, GROUPED, Cfg::KB, SPLITK, Cfg::TM>(args, t);
       const Prob& P = *T.P;
       const int nkb = T.kb_hi - T.kb_lo;  // k blocks of this item
       const int64_t il = T.il;
-      const int64_t row = T.tm * BM + qd * 32 + lane;
+      const int64_t row = T.tm * Cfg::TM + rank * BM + qd * 32 + lane;
       const int bnp = GROUPED ? P.bn : BN;  // this tile's width
       const int lc0 = hf * CPT;             // first tile-local column of this thread
       const int64_t col0 = T.tn * bnp + lc0;
@@ -441,7 +512,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int kcb = sc.kcb[0];
         const int nunits = (nkb + kcb - 1) / kcb;
         for (int u = 0; u < nunits; ++u) {
-          if (!ptx::mbar_wait(&tfull[acc], accph, lim, abort)) { ok = false; break; }
+          if (!wait_full(acc, accph)) { ok = false; break; }
           ptx::tc_fence_after();
 #pragma unroll
           for (int q = 0; q < CPT / 32; ++q) {
@@ -455,7 +526,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           ptx::tc_fence_before();
           __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
+          if (lane == 0) release(acc);
           if (++acc == Cfg::NACC) { acc = 0; accph ^= 1; }
         }
         if (!ok) break;
@@ -498,7 +569,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         const bool part_item = SPLITK && T.split >= 0;
         constexpr bool FINE = MODE == PAIR_MODE_EMU_FINE;
         constexpr size_t slot = (size_t)BM * BN * (FINE ? 2 : 1);
-        int64_t* Xt = (part_item ? args.xtail + (size_t)(T.tile - args.full) * slot
+        // a pair's tail tiles (every tile split, no batch): each CTA's half
+        // has the slot of its BM-row tile, numbered as k_split_finish numbers them
+        const int64_t xi = CG == 2 ? (2 * T.tm + rank) * ((P.n + BN - 1) / BN) + T.tn : T.tile - args.full;
+        int64_t* Xt = (part_item ? args.xtail + (size_t)xi * slot
                                  : (int64_t*)args.G + (size_t)blockIdx.x * slot) +
                       (size_t)(hf * CPT) * BM + qd * 32 + lane;
         bool first_flush = true;
@@ -507,7 +581,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int nunits = (nkb + kcb - 1) / kcb;
           if (FINE && di == sc.nlow) first_flush = true;  // the first diagonal of the coarse sums
           for (int u = 0; u < nunits; ++u) {
-            if (!ptx::mbar_wait(&tfull[acc], accph, lim, abort)) { ok = false; break; }
+            if (!wait_full(acc, accph)) { ok = false; break; }
             ptx::tc_fence_after();
             const bool last_unit = (u == nunits - 1);
             const bool flush = last_unit || ((u + 1) % sc.flush_every[di]) == 0;
@@ -522,7 +596,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             ptx::tc_fence_before();
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
+            if (lane == 0) release(acc);
             if (++acc == Cfg::NACC) { acc = 0; accph ^= 1; }
             if (!flush) continue;
             // sum += S * 2^xshift in int64 (exact, order-free): the first
@@ -552,10 +626,18 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 
   ptx::tc_fence_before();
-  __syncthreads();
+  // a pair: neither CTA leaves (nor frees its tensor memory) while the
+  // issuer's MMAs may still read its shared memory or write its tensor memory
+  if constexpr (CG == 2) {
+    __syncwarp();
+    ptx::cluster_sync();
+  } else {
+    __syncthreads();
+  }
   if (warp == EPI_WARPS + 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
+    if constexpr (CG == 2) ptx::tmem_dealloc_pair(tmem_base, Cfg::TMEM_COLS);
+    else ptx::tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
   }
 }
 
@@ -839,6 +921,111 @@ int grid_of(const Plan& p, int bn) {
   return (int)(items < num_sms() ? items : num_sms());
 }
 
+// ------------------------------------------------------------- CTA pairs
+// The fp64 split's product on CTA pairs (cta_group::2, 256 x 256 tiles):
+// per SM, each MMA reads 128 rows of A and 128 columns of B from shared
+// memory instead of 128 rows and all 256 columns, so the operand traffic
+// through shared memory (TMA writes plus MMA reads) drops by a third for
+// the same tensor work.
+
+template <int MODE, bool SPLITK>
+cudaError_t pair2_attr() {
+  using Cfg = PCfg<PAIR_KIND_BF16, 256, MODE, 2>;
+  constexpr int kMaxDev = 64;
+  static bool attr[kMaxDev] = {};
+  int dev = 0;
+  if (cudaError_t e = cudaGetDevice(&dev); e != cudaSuccess) return e;
+  if (dev < kMaxDev && attr[dev]) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_pair_gemm<PAIR_KIND_BF16, MODE, 256, false, SPLITK, 2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
+  if (e == cudaSuccess && dev < kMaxDev) attr[dev] = true;
+  return e;
+}
+
+cudaLaunchConfig_t pair2_config(int grid, int smem, cudaStream_t s, cudaLaunchAttribute* at) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = s;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Clusters of two CTAs of the pair kernel that fit on the device at once (0
+// when the query fails: pairs are then not used).  Once per device.
+int pair_clusters() {
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static int known[kMaxDev] = {};  // clusters + 1; 0: not asked yet
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    return 0;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (known[dev]) return known[dev] - 1;
+  int n = 0;
+  using Cfg = PCfg<PAIR_KIND_BF16, 256, PAIR_MODE_EMU, 2>;
+  cudaLaunchAttribute at[1];
+  const cudaLaunchConfig_t cfg = pair2_config(2 * (num_sms() / 2), Cfg::SMEM_BYTES, nullptr, at);
+  if (pair2_attr<PAIR_MODE_EMU, false>() != cudaSuccess ||
+      cudaOccupancyMaxActiveClusters(&n, k_pair_gemm<PAIR_KIND_BF16, PAIR_MODE_EMU, 256, false, false, 2>,
+                                     &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  known[dev] = n + 1;
+  return n;
+}
+
+// The product's schedule: CTAs per MMA, the split of its tiles (in tiles of
+// cg * BM rows), its grid, and the int64 slots of the tail tiles' sums
+// (BM x bn each).
+struct ProductPlan {
+  int cg;
+  SplitPlan sp;
+  int grid;
+  int64_t xslots;
+};
+
+// Pairs (when the options ask for them) run the fp64 split's single
+// problems with 256-wide tiles, no batch, no triangle and K past the
+// deferred-finish range, when there is at least one whole round of pair
+// tiles.  Either no tile is split (each finishes in the product) or every
+// tile is split in s and k_split_finish finishes them, whichever takes
+// fewer rounds.  (On the ladder product the pairs halve each SM's operand
+// traffic through shared memory but measured a few per cent slower than one
+// SM per MMA: that kernel waits on operand latency, not on bandwidth, so
+// one SM per MMA stays the default.)
+ProductPlan product_plan(const Plan& p, int bn) {
+  const SplitPlan sp1 = split_plan(p, bn);
+  ProductPlan r{1, sp1, grid_of(p, bn), sp1.tail};
+  if (!p.cta_pair || p.kernel != FAMLIES_KERNEL_TC_EMU || bn != 256 || p.tri || p.l != 1 || p.k <= 512) return r;
+  const int nc = pair_clusters();
+  const int64_t tm2 = (p.m + 2 * BM - 1) / (2 * BM), pt = tm2 * ((p.n + bn - 1) / bn);
+  if (nc < 1 || pt < nc) return r;
+  int best = 1;
+  double cost = 1e30;
+  for (int s = 1; s <= 4; ++s) {  // rounds of the persistent grid, a little more per split
+    const double c = (double)((pt * s + nc - 1) / nc) / (double)s + 0.01 * (s - 1);
+    if (c < cost - 1e-9) {
+      cost = c;
+      best = s;
+    }
+  }
+  r.cg = 2;
+  r.sp = best == 1 ? SplitPlan{1, pt, 0} : SplitPlan{best, 0, pt};
+  r.grid = 2 * (int)std::min<int64_t>(r.sp.full + r.sp.tail * r.sp.splits, nc);
+  r.xslots = best == 1 ? 0 : 2 * pt;  // both halves of every pair tile
+  return r;
+}
+
 struct Layout {
   size_t a, b, ea, eb, fa, fb, la, lb, G, xtail, part, tri, sym, total;
 };
@@ -865,10 +1052,10 @@ Layout layout_of(const Plan& p) {
     // per-CTA tile sums for the tiles that run whole; split K (and the
     // deferred finish) adds one slot per tail tile; one int64 sum per
     // element, two when the fine diagonals keep their own
-    const SplitPlan sp = split_plan(p, bn);
-    const size_t sums = make_pair_sched(p.kernel, p.slices, kSplitBits, p.k, sp.splits).nlow ? 2 : 1;
-    L.G = off; off += sp.full > 0 ? up(sums * grid_of(p, bn) * BM * bn * 8) : 0;
-    L.xtail = off; off += up(sums * sp.tail * BM * bn * 8);
+    const ProductPlan pp = product_plan(p, bn);
+    const size_t sums = make_pair_sched(p.kernel, p.slices, kSplitBits, p.k, pp.sp.splits).nlow ? 2 : 1;
+    L.G = off; off += pp.sp.full > 0 ? up(sums * pp.grid * BM * bn * 8) : 0;
+    L.xtail = off; off += up(sums * pp.xslots * BM * bn * 8);
   } else {
     const int bn = pair_bn_for(p.n, p.tile_n);
     const SplitPlan sp = split_plan(p, bn);
@@ -923,6 +1110,26 @@ cudaError_t launch_pair_bn(int bn, const CUtensorMap& ma, const CUtensorMap& mb,
   if (bn == 64) return launch_pair<KIND, MODE, 64, GROUPED>(ma, mb, a, grid, s);
   if (bn == 128) return launch_pair<KIND, MODE, 128, GROUPED>(ma, mb, a, grid, s);
   return launch_pair<KIND, MODE, 256, GROUPED>(ma, mb, a, grid, s);
+}
+
+// The pair kernel (fp64 split, 256-wide tiles) as clusters of two.
+template <int MODE, bool SPLITK>
+cudaError_t launch_pair2_k(const CUtensorMap& ma, const CUtensorMap& mb, const PairArgs& a, int grid,
+                           cudaStream_t s) {
+  using Cfg = PCfg<PAIR_KIND_BF16, 256, MODE, 2>;
+  if (cudaError_t e = pair2_attr<MODE, SPLITK>(); e != cudaSuccess) return e;
+  cudaLaunchAttribute at[1];
+  const cudaLaunchConfig_t cfg = pair2_config(grid, Cfg::SMEM_BYTES, s, at);
+  return cudaLaunchKernelEx(&cfg, k_pair_gemm<PAIR_KIND_BF16, MODE, 256, false, SPLITK, 2>, ma, mb, a);
+}
+
+cudaError_t launch_pair2(int mode, const CUtensorMap& ma, const CUtensorMap& mb, const PairArgs& a, int grid,
+                         cudaStream_t s) {
+  if (mode == PAIR_MODE_EMU_FINE)
+    return a.tailed ? launch_pair2_k<PAIR_MODE_EMU_FINE, true>(ma, mb, a, grid, s)
+                    : launch_pair2_k<PAIR_MODE_EMU_FINE, false>(ma, mb, a, grid, s);
+  return a.tailed ? launch_pair2_k<PAIR_MODE_EMU, true>(ma, mb, a, grid, s)
+                  : launch_pair2_k<PAIR_MODE_EMU, false>(ma, mb, a, grid, s);
 }
 
 template <bool GROUPED>
@@ -1107,12 +1314,37 @@ cudaError_t launch_pair_grouped(int kind, int mode, int bn, const Prob* probs,
 
 int64_t packed_workspace_bytes(const Plan& p) { return (int64_t)layout_of(p).total; }
 
+int packed_ctas_per_mma(const Plan& p) { return product_plan(p, pair_bn_for(p.n, p.tile_n)).cg; }
+
+// fp64 split: the operands (bit 0: A, bit 1: B) split in one pass by
+// k_rowpack (k one unit-stride mode of a length it holds in registers;
+// neither symmetric nor generated).
+static int rowpack_sides(const Plan& p) {
+  if (p.kernel != FAMLIES_KERNEL_TC_EMU || p.k < kRowPackMinK || p.k > kRowPackMaxK || p.K.n != 1) return 0;
+  int mask = 0;
+  for (int side = 0; side < 2; ++side) {
+    const bool own = (p.sym_n > 0 && p.sym_side == side) || p.band_side == side || p.krp_side == side;
+    if (!own && (side == 0 ? p.K.m[0].sa : p.K.m[0].sb) == 1) mask |= 1 << side;
+  }
+  return mask;
+}
+
 int packed_launches(const Plan& p) {
   const int tri = p.tri ? 1 : 0;  // the triangle's tile list
-  if (p.kernel == FAMLIES_KERNEL_TC_EMU)  // exponents + pack + product (+ split finish) + fix-up
-    return 4 + (split_plan(p, pair_bn_for(p.n, p.tile_n)).tail > 0 ? 1 : 0) + tri +
-           (p.band_side >= 0 || p.krp_side >= 0 ? 2 : 0) +  // (+ a generated operand's own)
+  if (p.kernel == FAMLIES_KERNEL_TC_EMU) {
+    // exponents + pack of the generic operands (one launch each for both),
+    // one launch per one-pass operand, product (+ split finish) + fix-up
+    const int rp = rowpack_sides(p);
+    const int own = p.sym_n > 0 ? p.sym_side : (p.band_side >= 0 ? p.band_side : p.krp_side);
+    int generic = 0, one_pass = 0;
+    for (int side = 0; side < 2; ++side) {
+      if (rp >> side & 1) ++one_pass;
+      else if (side != own) ++generic;
+    }
+    return (generic ? 2 : 0) + one_pass + 2 + (product_plan(p, pair_bn_for(p.n, p.tile_n)).sp.tail > 0 ? 1 : 0) +
+           tri + (p.band_side >= 0 || p.krp_side >= 0 ? 2 : 0) +  // (+ a generated operand's own)
            (p.sym_n > 0 ? 3 : 0);  // (+ a symmetric operand's exponents, their reduction, pack)
+  }
   DirectView v;
   const bool tf32 = p.kernel == FAMLIES_KERNEL_TC_TF32X3;
   const bool da = !tf32 && direct_view(p.M, p.K, p.L, 0, p.a, &v);
@@ -1151,6 +1383,7 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     o.krp = p.krp;
   }
   const int own = sym ? p.sym_side : gside;  // packed by its own kernels (-1: none)
+  const int rp = rowpack_sides(p);           // split in one pass
   cudaError_t e;
   if (emu) {
     pa.op[0].e = (int32_t*)(w + L.ea);
@@ -1160,13 +1393,10 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     pa.op[0].list = (int32_t*)(w + L.la);
     pa.op[1].list = (int32_t*)(w + L.lb);
     // an operand whose exponents, flags and list the step that produced it
-    // recorded (a network's fused epilogue): no exponent pass over it
-    bool pre_all = true;
+    // recorded (a network's fused epilogue): no exponent pass over it (a
+    // one-pass split stores the same values again)
     for (int side = 0; side < 2; ++side) {
-      if (!p.pre_e[side]) {
-        pre_all = false;
-        continue;
-      }
+      if (!p.pre_e[side]) continue;
       pa.op[side].e = p.pre_e[side];
       pa.op[side].flag = p.pre_flag[side];
       pa.op[side].list = p.pre_list[side];
@@ -1174,12 +1404,14 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     // exponents start at a large negative value, flags and list counts at 0
     if ((e = cudaMemsetAsync(w + L.ea, 0x80, L.fa - L.ea, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w + L.fa, 0, L.G - L.fa, s)) != cudaSuccess) return e;
-    PackArgs pg = pa;  // the generic kernels skip a symmetric or generated operand
+    // the generic kernels skip a symmetric or generated operand and one
+    // split in one pass
+    PackArgs pg = pa;
     if (own >= 0) pg.op[own].rows = 0;
     for (int side = 0; side < 2; ++side)
-      if (p.pre_e[side]) pg.op[side].rows = 0;
+      if (p.pre_e[side] || (rp >> side & 1)) pg.op[side].rows = 0;
     nvtxRangePushA("exponents");
-    e = pre_all ? cudaSuccess : launch_rowexp(pg, s);
+    e = pg.op[0].rows || pg.op[1].rows ? launch_rowexp(pg, s) : cudaSuccess;
     nvtxRangePop();
     if (e != cudaSuccess) return e;
     if (sym && (e = launch_rowexp_sym(pa, p.sym_side, (int32_t*)(w + L.sym), s)) != cudaSuccess) return e;
@@ -1205,7 +1437,13 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     } range;
     PackArgs pg = pa;
     if (own >= 0) pg.op[own].rows = 0;
-    if ((e = launch_pack(emu ? PACK_F64 : (tf32 ? PACK_TF32 : PACK_BF16), pg, s)) != cudaSuccess)
+    for (int side = 0; side < 2; ++side) {
+      if (!(rp >> side & 1)) continue;
+      if ((e = launch_rowpack(pa, side, s)) != cudaSuccess) return e;
+      pg.op[side].rows = 0;
+    }
+    if ((pg.op[0].rows || pg.op[1].rows) &&
+        (e = launch_pack(emu ? PACK_F64 : (tf32 ? PACK_TF32 : PACK_BF16), pg, s)) != cudaSuccess)
       return e;
     if (sym && (e = launch_pack_sym(pa, p.sym_side, s)) != cudaSuccess) return e;
     if (gen && (e = launch_pack_gen(emu ? PACK_F64 : PACK_TF32, pa, gside, s)) != cudaSuccess)
@@ -1213,8 +1451,10 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   }
   const bool ok_a = da ? make_view_map(&ma, va, p.k, p.m, p.l, kbk, BM)
                        : make_slice_map(&ma, w + L.a, tf32, p.k, kp, p.m, (int64_t)S * p.l, kbk, BM);
+  // the product's schedule (a CTA pair stages half of B's tile columns per CTA)
+  const ProductPlan pp = emu ? product_plan(p, bn) : ProductPlan{1, split_plan(p, bn), grid_of(p, bn), 0};
   const bool ok_b = db ? make_view_map(&mb, vb, p.k, p.n, p.l, kbk, bn)
-                       : make_slice_map(&mb, w + L.b, tf32, p.k, kp, p.n, (int64_t)S * p.l, kbk, bn);
+                       : make_slice_map(&mb, w + L.b, tf32, p.k, kp, p.n, (int64_t)S * p.l, kbk, bn / pp.cg);
   if (!ok_a || !ok_b) return cudaErrorInvalidValue;
   PairArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -1235,7 +1475,7 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     a.single.tri_list = list;
     a.single.tri_tiles = tri_tile_count(p, bn);
   }
-  const SplitPlan spl = split_plan(p, bn);
+  const SplitPlan spl = pp.sp;
   a.sc = make_pair_sched(p.kernel, p.slices, bits, p.k, spl.splits);
   a.G = emu ? (double*)(w + L.G) : nullptr;
   a.splits = spl.splits;
@@ -1246,20 +1486,22 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
   a.status = g.status;
   a.wait_limit = g.wait_limit;
   a.stall_test = g.stall_test;
-  const int grid = grid_of(p, bn);
+  const int grid = pp.grid;
   const int split_grid = (int)std::min<int64_t>(spl.tail * (bn / SPLIT_COLS), (int64_t)num_sms() * 16);
   if (emu && a.tailed &&
-      (e = cudaMemsetAsync(a.xtail, 0, (size_t)(a.sc.nlow ? 2 : 1) * spl.tail * BM * bn * 8, s)) != cudaSuccess)
+      (e = cudaMemsetAsync(a.xtail, 0, (size_t)(a.sc.nlow ? 2 : 1) * pp.xslots * BM * bn * 8, s)) != cudaSuccess)
     return e;
   mark_begin(g, s);
   nvtxRangePushA("product");
   const int mode = emu ? (a.sc.nlow ? PAIR_MODE_EMU_FINE : PAIR_MODE_EMU) : PAIR_MODE_F32OUT;
-  e = launch_pair_any<false>(kind, mode, bn, ma, mb, a, grid, s);
+  e = pp.cg == 2 ? launch_pair2(mode, ma, mb, a, grid, s) : launch_pair_any<false>(kind, mode, bn, ma, mb, a, grid, s);
   nvtxRangePop();
   mark_end(g, s);  // the events bracket the product kernel alone
   if (e == cudaSuccess && a.tailed) {
     if (emu) {
-      const int fg = (int)std::min<int64_t>(spl.tail * (bn / SPLIT_COLS), (int64_t)num_sms() * 24);
+      // finished per BM-row tile (a pair's split tiles: every tile, full = 0)
+      const int64_t ftiles = pp.cg == 2 ? ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) : spl.tail;
+      const int fg = (int)std::min<int64_t>(ftiles * (bn / SPLIT_COLS), (int64_t)num_sms() * 24);
       if (a.sc.nlow)
         k_split_finish<true><<<fg, 256, 0, s>>>(a.xtail, a.full, bn, a.sc.xunit, a.sc.xlo, a.single);
       else

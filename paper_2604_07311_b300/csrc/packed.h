@@ -60,6 +60,12 @@ struct PackArgs {
 cudaError_t launch_rowexp(const PackArgs& pa, cudaStream_t s);
 // Writes the slices of both operands.
 cudaError_t launch_pack(int pmode, const PackArgs& pa, cudaStream_t s);
+// fp64 split in one pass over operand pa.op[side] (row exponents, flags and
+// slices) when its k is one unit-stride mode and kRowPackMinK <= k <=
+// kRowPackMaxK (each row is then held in registers while it is split).
+constexpr int64_t kRowPackMinK = 512;
+constexpr int64_t kRowPackMaxK = 16384;
+cudaError_t launch_rowpack(const PackArgs& pa, int side, cudaStream_t s);
 // Symmetric packed operand pa.op[side] (fp64 split): row exponents and flags
 // (every stored element bounds its row and, by symmetry, its column) and its
 // slices, both from one read of the lower triangle.

@@ -273,6 +273,8 @@ int make_plan(double alpha, const famlies_tensor_t* A, const famlies_tensor_t* B
     return e ? std::atoi(e) : 0;
   };
   p.tile_n = opt && opt->tile_n ? opt->tile_n : env_int("FAMLIES_FORCE_TILE");
+  if (opt && (opt->ctas_per_mma < 0 || opt->ctas_per_mma > 2)) return FAMLIES_ERR_INVALID_ARG;
+  p.cta_pair = opt && opt->ctas_per_mma == 2 ? 1 : 0;
   if (p.tile_n != 0 && p.tile_n != 64 && p.tile_n != 128 && p.tile_n != 192 && p.tile_n != 256)
     return FAMLIES_ERR_INVALID_ARG;
   // bf16: the direct kernel (tiles staged from the caller's strides) when
@@ -306,6 +308,7 @@ void fill_info(const Plan& p, famlies_plan_info_t* info) {
   info->batch_modes = p.L.n;
   info->swapped = p.swapped;
   info->kernel = p.kernel;
+  info->ctas_per_mma = 1;
   info->slices = p.dtype == FAMLIES_F64_EMU ? p.slices : 0;
   info->a_contig = p.a_contig;
   info->b_contig = p.b_contig;

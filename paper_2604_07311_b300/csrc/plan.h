@@ -75,6 +75,7 @@ struct Plan {
   int kernel = FAMLIES_KERNEL_NONE;
   int slices = 6;
   int tile_n = 0;  // tensor-core tile width request (0 = automatic)
+  int cta_pair = 0;  // fp64 split: run the product on CTA pairs where it supports them
   int force_gather = 0;  // direct bf16 kernel: operands staged by gather warps (bit 0 row, bit 1 column)
   // Symmetric packed operand (famlies_contract_sym): n > 0 when the row
   // (side 0) or column (side 1) operand is stored as the lower triangle of

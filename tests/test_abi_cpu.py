@@ -302,3 +302,30 @@ def test_environment_defaults_for_slices_and_tile_width():
     env = dict(os.environ, FAMLIES_FORCE_TILE="96")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=120)
     assert "famlies error -1" in r.stderr
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """Every struct the binding marshals has the header's size and field
+    offsets (a C program compiled against include/famlies.h prints them)."""
+    pairs = [("famlies_tensor_t", _lib.TensorDesc), ("famlies_symtensor_t", _lib.SymTensorDesc),
+             ("famlies_matrix_t", _lib.MatrixDesc), ("famlies_options_t", _lib.Options),
+             ("famlies_step_t", _lib.Step), ("famlies_plan_info_t", _lib.PlanInfo)]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "famlies.h"', "int main(void) {"]
+    for cname, cls in pairs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", f"-I{os.path.join(ROOT, 'include')}", str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)]).decode().splitlines():
+        name, field, val = line.split()
+        got[(name, field)] = int(val)
+    import ctypes
+    for cname, cls in pairs:
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)

@@ -192,7 +192,9 @@ def test_split_k_few_tiles_with_nonfinite_row():
     C = W.uniform_operand(rng, (m, n), [1, 3])
     p = W.Problem("split_k_emu", -0.5, Aop, B, 2.0, C)
     Cg, info = run_gpu(p, "f64_emu")
-    assert info["launches"] + info["cached"] == 6  # tables, exponents, pack, product, split finish, fix-up
+    # tables, A's exponents and pack, B's one-pass split (k unit-stride),
+    # product, split finish, fix-up
+    assert info["launches"] + info["cached"] == 7
     got, want = gpu_dense(Cg), run_oracle(p)
     assert np.array_equal(np.isnan(got), np.isnan(want))
     fin = ~np.isnan(want)
@@ -211,7 +213,8 @@ def test_split_every_tile_over_several_rounds():
     C = W.uniform_operand(rng, (m, n), [1, 3])
     p = W.Problem("split_tail_emu", 1.0, A, B, -1.0, C)
     Cg, info = run_gpu(p, "f64_emu", tile_n=256)
-    assert info["launches"] + info["cached"] == 6  # tables, exponents, pack, product, split finish, fix-up
+    # tables, A's exponents and pack, B's one-pass split, product, split finish, fix-up
+    assert info["launches"] + info["cached"] == 7
     got = gpu_dense(Cg)
     rows = np.concatenate([rng.integers(74 * 128, m, 48), rng.integers(0, 74 * 128, 16)])
     idx = np.stack([rows, rng.integers(0, n, rows.size)], axis=1)
@@ -223,9 +226,9 @@ def test_split_every_tile_over_several_rounds():
 @pytest.mark.parametrize("k,deferred", [(512, True), (513, False)])
 def test_short_k_finish_boundary_integer_exact(k, deferred):
     """m = n = 2048 (128 tiles of 128 x 256): up to K = 512 every tile's int64
-    sums go to its own slot and a separate kernel finishes them (six launches:
-    tables, exponents, pack, product, finish, fix-up); from K = 513 the tiles
-    finish inside the product (five).  Integer-valued inputs, alpha and beta
+    sums go to its own slot and a separate kernel finishes them (seven
+    launches: tables, A's exponents and pack, B's one-pass split, product,
+    finish, fix-up); from K = 513 the tiles finish inside the product (six).  Integer-valued inputs, alpha and beta
     that are not 0 or 1 and a row holding Inf: both sides exact."""
     rng = np.random.default_rng(408 + k)
     m = n = 2048
@@ -236,7 +239,7 @@ def test_short_k_finish_boundary_integer_exact(k, deferred):
     C = W.Operand(rng.integers(-4, 5, m * n).astype(np.float64), (m, n), (1, m), [1, 3])
     p = W.Problem("short_k_boundary", 0.5, Aop, B, -2.0, C)
     Cg, info = run_gpu(p, "f64_emu", tile_n=256)
-    assert info["launches"] + info["cached"] == (6 if deferred else 5), info
+    assert info["launches"] + info["cached"] == (7 if deferred else 6), info
     got, want = gpu_dense(Cg), run_oracle(p)
     assert np.array_equal(np.isnan(got), np.isnan(want))
     assert np.array_equal(np.isinf(got), np.isinf(want))
