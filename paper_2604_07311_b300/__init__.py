@@ -98,7 +98,7 @@ def contract_host(alpha, A, la, B, lb, beta, C, lc, dtype="f64", stream=None, *,
 
 
 def plan(A_shape, A_strides, la, B_shape, B_strides, lb, C_shape, C_strides, lc, dtype="f64",
-         pointers=(0x10000, 0x20000000, 0x40000000), slices=0, kernel=0):
+         pointers=(0x10000, 0x20000000, 0x40000000), slices=0, kernel=0, tile_n=0, ctas_per_mma=0):
     """Host-only plan report (no device needed): classes, fusion, role swap."""
     lib = load()
     code = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
@@ -106,7 +106,8 @@ def plan(A_shape, A_strides, la, B_shape, B_strides, lb, C_shape, C_strides, lc,
     db = Desc(B_shape, B_strides, lb, pointers[1])
     dc = Desc(C_shape, C_strides, lc, pointers[2])
     info = PlanInfo()
-    check(lib.famlies_plan(da.ref, db.ref, dc.ref, code, options(slices, kernel), info))
+    check(lib.famlies_plan(da.ref, db.ref, dc.ref, code,
+                           options(slices, kernel, tile_n=tile_n, ctas_per_mma=ctas_per_mma), info))
     return info.as_dict()
 
 

@@ -329,3 +329,18 @@ def test_ctypes_structs_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_ctas_per_mma_option_is_validated():
+    """ctas_per_mma takes 0, 1 or 2; anything else is an invalid argument.  The
+    host-only plan reports one CTA per MMA (pairs are decided with the device)."""
+    A = ((64, 96), (1, 64), [1, 2])
+    B = ((96, 80), (1, 96), [2, 3])
+    C = ((64, 80), (1, 64), [1, 3])
+    for v in (0, 1, 2):
+        info = fm.plan(*A, *B, *C, dtype="f64_emu", ctas_per_mma=v)
+        assert info["ctas_per_mma"] == 1
+    for v in (-1, 3):
+        with pytest.raises(fm.FamliesError) as e:
+            fm.plan(*A, *B, *C, dtype="f64_emu", ctas_per_mma=v)
+        assert e.value.code == -1  # FAMLIES_ERR_INVALID_ARG
