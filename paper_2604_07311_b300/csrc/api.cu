@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <list>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -104,9 +105,12 @@ struct Workspace {
 // plus the device and the stream, so that calls sharing an entry are ordered
 // by their stream.  Not used while the stream is being captured into a graph
 // (a captured call allocates its own workspace), nor for entries above
-// 256 MB; at most 16 entries, the least recently used freed (cudaFree, which
-// waits for the device) when a new one is needed.  FAMLIES_PLAN_CACHE=0
-// turns it off.
+// 256 MB; at most 16 entries, the least recently used one not held by a call
+// in progress freed when a new one is needed.  Each call that used an entry
+// records an event on its stream after its last kernel; eviction waits for
+// that event before it frees the workspace (in stream order: it came from
+// the stream-ordered allocator, whose memory a plain free may unmap under
+// kernels still queued).  FAMLIES_PLAN_CACHE=0 turns it off.
 class PlanCache {
  public:
   struct Entry {
@@ -114,7 +118,9 @@ class PlanCache {
     void* ws = nullptr;
     int64_t bytes = 0;
     uint64_t used = 0;
-    bool tables = false;  // the tables have been built in ws
+    bool tables = false;         // the tables have been built in ws
+    cudaEvent_t done = nullptr;  // after the last kernel of the last call that used ws
+    int holders = 0;             // calls between get() and release()
   };
 
   static bool enabled() {
@@ -128,6 +134,8 @@ class PlanCache {
 
   // The entry for key (created with `bytes` of workspace allocated on s when
   // missing), or null when the cache cannot serve the call.
+  // A returned entry is held until release(entry, stream), which the caller
+  // makes once the call's kernels are enqueued.
   Entry* get(const std::vector<int64_t>& key, int64_t bytes, cudaStream_t s) {
     if (bytes > kMaxBytes) return nullptr;
     std::lock_guard<std::mutex> lk(mu_);
@@ -135,20 +143,30 @@ class PlanCache {
     for (Entry& e : entries_)
       if (e.key == key && e.bytes >= bytes) {
         e.used = clock_;
+        ++e.holders;
         return &e;
       }
     if (entries_.size() >= kMaxEntries) {
-      size_t lru = 0;
-      for (size_t i = 1; i < entries_.size(); ++i)
-        if (entries_[i].used < entries_[lru].used) lru = i;
-      cudaFree(entries_[lru].ws);
+      auto lru = entries_.end();
+      for (auto it = entries_.begin(); it != entries_.end(); ++it)
+        if (it->holders == 0 && (lru == entries_.end() || it->used < lru->used)) lru = it;
+      if (lru == entries_.end()) return nullptr;  // every entry is in use: no caching
+      // the last call that used it may still be queued on its stream
+      if (lru->done) {
+        cudaEventSynchronize(lru->done);
+        cudaEventDestroy(lru->done);
+      } else {
+        cudaDeviceSynchronize();
+      }
+      cudaFreeAsync(lru->ws, s);
       cudaGetLastError();
-      entries_.erase(entries_.begin() + (long)lru);
+      entries_.erase(lru);
     }
     Entry e;
     e.key = key;
     e.bytes = bytes;
     e.used = clock_;
+    e.holders = 1;
     if (cudaMallocAsync(&e.ws, bytes > 0 ? bytes : 256, s) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
@@ -157,11 +175,26 @@ class PlanCache {
     return &entries_.back();
   }
 
+  // The call holding e has enqueued its kernels on s.
+  void release(Entry* e, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(mu_);
+    if (!e->done && cudaEventCreateWithFlags(&e->done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      e->done = nullptr;
+    }
+    if (e->done && cudaEventRecord(e->done, s) != cudaSuccess) {
+      cudaGetLastError();
+      cudaEventDestroy(e->done);
+      e->done = nullptr;  // eviction then waits for the whole device
+    }
+    --e->holders;
+  }
+
  private:
   static constexpr int64_t kMaxBytes = (int64_t)256 << 20;
   static constexpr size_t kMaxEntries = 16;
   std::mutex mu_;
-  std::vector<Entry> entries_;
+  std::list<Entry> entries_;  // stable addresses: entries are held across a call
   uint64_t clock_ = 0;
 };
 
@@ -169,6 +202,17 @@ PlanCache& plan_cache() {
   static PlanCache* c = new PlanCache();  // never destroyed: entries live until exit
   return *c;
 }
+
+// Releases a held plan-cache entry when the call's scope ends (after its
+// kernels are enqueued, on every return path).
+struct CacheHold {
+  PlanCache::Entry* e = nullptr;
+  cudaStream_t s = nullptr;
+  ~CacheHold() {
+    if (e) plan_cache().release(e, s);
+  }
+};
+
 
 // The cache key of plan p on stream s, or an empty key when p is not cached
 // (operands that carry device pointers in the plan: symmetric, banded,
@@ -227,6 +271,7 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
       const std::vector<int64_t> key = cache_key(p, s);
       if (!key.empty()) ce = plan_cache().get(key, wsb, s);
     }
+    CacheHold hold{ce, s};
     if (ce) {
       ws.ptr = ce->ws;
       ws.owned = false;
@@ -278,6 +323,7 @@ int run_plan(const Plan& p, double alpha, double beta, cudaStream_t s,
     const std::vector<int64_t> key = cache_key(p, s);
     if (!key.empty()) ce = plan_cache().get(key, tab_bytes + extra, s);
   }
+  CacheHold hold{ce, s};
   if (ce) {
     ws.ptr = ce->ws;
     ws.owned = false;

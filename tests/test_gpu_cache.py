@@ -83,3 +83,34 @@ def test_capture_bypasses_the_cache_and_replays():
     torch.cuda.synchronize()
     want = 2.0 * run_oracle(p)
     assert rel_frob(gpu_dense(Cd), want) <= 1e-13
+
+
+def test_eviction_waits_for_queued_calls():
+    """More distinct shapes than the cache holds (16), each call a few
+    milliseconds of work, all enqueued before any finishes: an entry is
+    evicted while the call that last used its workspace may still be queued,
+    so the eviction must wait for that call (the entry's event) before the
+    workspace is freed.  Every result against the oracle's compensated sums
+    on sampled entries."""
+    import oracle
+    rng = np.random.default_rng(953)
+    probs, outs = [], []
+    for t in range(20):
+        m, n, k = 1024 + 8 * t, 1024, 8192 + 8 * t  # distinct shapes: distinct entries (< 256 MB each)
+        A = W.uniform_operand(rng, (m, k), [1, 2])
+        B = W.uniform_operand(rng, (k, n), [2, 3])
+        C = W.uniform_operand(rng, (m, n), [1, 3])
+        p = W.Problem(f"evict{t}", 1.0, A, B, -1.0, C)
+        Ad, Bd, Cd = (to_device(x, torch.float64) for x in (p.A, p.B, p.C))
+        probs.append((p, Ad, Bd, Cd))
+    torch.cuda.synchronize()
+    for p, Ad, Bd, Cd in probs:  # no synchronisation between calls
+        fm.contract(p.alpha, Ad, p.A.labels, Bd, p.B.labels, p.beta, Cd, p.C.labels, dtype="f64_emu")
+    torch.cuda.synchronize()
+    assert fm.device_status() == 0
+    for p, _, _, Cd in probs:
+        got = gpu_dense(Cd)
+        idx = np.stack([rng.integers(0, e, 64) for e in got.shape], axis=1)
+        want = oracle.entries(p.alpha, p.A.view(), p.A.labels, p.B.view(), p.B.labels, p.beta, p.C.view(),
+                              p.C.labels, idx, dot2=True)
+        assert rel_frob(got[tuple(idx.T)], want) <= 1e-13, p.name
