@@ -178,8 +178,11 @@ typedef struct {
  * famlies_contract_ex when options ask for pairs and the call supports
  * them, 1 otherwise and from famlies_plan).
  * The plan cache keeps up to 16 such workspaces of at most 256 MB each,
- * the least recently used freed (with a device-wide wait) when a new one is
- * needed; it is bypassed while the stream is being captured into a graph
+ * the least recently used one that no call is holding freed when a new one
+ * is needed, once the last call that used it has finished on its stream (an
+ * event recorded after that call's kernels; a host wait when the eviction
+ * happens while it is still queued); it is bypassed while the stream is
+ * being captured into a graph
  * and turned off by the environment variable FAMLIES_PLAN_CACHE=0.  Calls
  * that share an entry are ordered by their (common) stream. */
 typedef struct {
