@@ -32,11 +32,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "contraction TFLOP/s, % tensor-pipe peak; split-precision vs FP64 speedup"
-# DRAM bytes (read + write) of one product-kernel launch from an ncu capture of
-# the v=112 ladder (the same kernel, 6.77e12 executed flops), scaled by executed
-# flops to the benchmark launch; None whenever the product kernel has changed
-# since the capture.
-PRODUCT_TRAFFIC = {"bytes": 9917750784.0 + 1656454656.0, "exec_flops": 6.767392063488e12}
+# DRAM bytes (read + write) of one product-kernel launch of this benchmark
+# (v=128, 1.154e13 executed flops) from an ncu capture of its dram byte
+# counters; None whenever the product kernel has changed since the capture.
+PRODUCT_TRAFFIC = {"bytes": 15693139456.0 + 1611676928.0, "exec_flops": 1.1544872091648e13}
 V_EXT, O_EXT, SLICES = 128, 32, 6
 WORKLOAD = f"ccsd_ladder_v128_o32_f64_split{SLICES}"
 
@@ -359,7 +358,7 @@ def run_gpu(args):
                      "frac": achieved / burst,
                      "traffic": (PRODUCT_TRAFFIC["bytes"] * exec_flops / PRODUCT_TRAFFIC["exec_flops"]
                                  if PRODUCT_TRAFFIC else None),
-                     "traffic_note": "ncu dram bytes of the v=112 capture scaled by executed flops",
+                     "traffic_note": "ncu dram bytes of one launch of this workload (read + write)",
                      "peak_kind": (f"bf16 burst ({src}): the timed region is ~0.1 s and the SM "
                                    f"clock stays near its maximum, unlike the power-capped "
                                    f"seconds-long loop behind the sustained figure"),

@@ -284,8 +284,9 @@ __global__ void __launch_bounds__(256) k_simt_reduce(GemmArgs g, int splits) {
 namespace {
 
 // Tile shape and grid of the CUDA-core kernel, and its K splits: a launch
-// with fewer tiles than SMs splits K (at least 256 per split) so that every
-// SM gets work.
+// with fewer tiles than SMs splits K (at least 32 per split, two of the
+// kernel's 16-deep k steps) so that every SM gets work: at B300's fp64 rate
+// (~8 GFLOP/s per SM) a 64 x 64 tile with k = 256 alone takes ~0.25 ms.
 struct SimtShape {
   int bm, bn, blocks_per_sm;
   int64_t tiles;
@@ -301,7 +302,7 @@ SimtShape simt_shape(const Plan& p) {
   int64_t sp = 1;
   if (sh.tiles < sms) {
     sp = (2 * sms + sh.tiles - 1) / sh.tiles;
-    const int64_t kmax = p.k / 256;
+    const int64_t kmax = p.k / 32;
     if (sp > kmax) sp = kmax;
     if (sp > 64) sp = 64;
     if (sp < 1) sp = 1;
