@@ -167,6 +167,31 @@ __device__ __forceinline__ double i64_to_f64_rn(int64_t x) {
   return __longlong_as_double((long long)(sign | (e << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
+// How the end of an fp64-split tile applies alpha and beta, classified once
+// per thread: alpha = +-2^p (p in the normal range) goes into the int64
+// sum's sign and the scaling exponent in integer arithmetic (one rounding in
+// all), any other alpha takes one fp64 multiply; beta = 0 leaves C unread,
+// beta = 1 costs one fp64 add, any other beta one fma.  The fp64 pipe is
+// narrow on this GPU (one warp instruction occupies it for ~16 cycles): a
+// finish that compared and multiplied in fp64 per output was bound by it.
+struct FinishScale {
+  bool a_neg;  // alpha = -2^p
+  bool a_gen;  // alpha is not a power of two: multiply
+  int a_p;     // alpha = +-2^p
+  int b_kind;  // 0: beta = 0, 1: beta = 1, 2: other
+};
+__device__ __forceinline__ FinishScale finish_scale(double alpha, double beta) {
+  FinishScale f;
+  const unsigned long long u = (unsigned long long)__double_as_longlong(alpha);
+  const int E = (int)((u >> 52) & 0x7FF);
+  const bool pow2 = (u & 0xFFFFFFFFFFFFFull) == 0 && E >= 1 && E <= 2046;
+  f.a_gen = !pow2;
+  f.a_neg = pow2 && (u >> 63) != 0;
+  f.a_p = pow2 ? E - 1023 : 0;
+  f.b_kind = beta == 0.0 ? 0 : (beta == 1.0 ? 1 : 2);
+  return f;
+}
+
 // A network's fused epilogue: folds output value v into the row exponent
 // bound and non-finite flag that the consuming step's split would compute
 // for its row ci (exponent max(E, 1) - 1022 over the row's biased exponents

@@ -194,17 +194,20 @@ __device__ __forceinline__ TileRef tile_at(const PairArgs& a, int64_t t) {
 // The end of an fp64-split tile: C = alpha * 2^(e_m + e_n - xunit) * X + beta
 // * C for this thread's row and CPT columns (X: the int64 tile sums), in
 // groups of columns whose table entries, X and C are loaded together.  X is
-// read from L2 (the reductions that built it ran there).  Not inlined: it
-// runs once per tile and keeps its registers out of the drain loop's budget.
-template <int CPT, bool FINE>
-__device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, const Sched& sc, int64_t il,
+// read from L2 (the reductions that built it ran there).  AK, BK: alpha and
+// beta classified as FinishScale does (AK 0: alpha = +-2^p, applied in
+// integer arithmetic; BK: beta 0, 1 or other), fixed at compile time so that
+// no fp64 instruction of an untaken choice runs.
+template <int CPT, bool FINE, int AK, int BK>
+__device__ __forceinline__ void finish_cols(const Prob& P, const int64_t* Xt, const Sched& sc, int64_t il,
                                          int64_t row, int64_t crow, int64_t col0, int lc0, int bnp) {
   // the fine sums follow the coarse ones in the tile's slot (tiles 2 CPT wide)
   const int64_t* Lt = Xt + (size_t)BM * (2 * CPT);
   const int xunit = sc.xunit, xlo = sc.xlo;
   double* C = (double*)P.c;
   const double alpha = P.alpha, beta = P.beta;
-  const int er = P.ea[il * P.m + row] - xunit;
+  const FinishScale fs = finish_scale(P.alpha, P.beta);
+  const int er = P.ea[il * P.m + row] - xunit + fs.a_p;
   const int32_t* ebl = P.eb + il * P.n;
   const int32_t* fbl = P.fb + il * P.n;
   const double lsc = ldexp(1.0, xunit - xlo);
@@ -227,22 +230,26 @@ __device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, const
       gl[j] = FINE ? __ldcg(Lt + (size_t)(j0 + j) * BM) : 0;
     }
 #pragma unroll
-    for (int j = 0; j < FG; ++j) cold[j] = (use[j] && beta != 0.0) ? C[crow + coff[j]] : 0.0;
+    for (int j = 0; j < FG; ++j) cold[j] = (use[j] && BK) ? C[crow + coff[j]] : 0.0;
 #pragma unroll
     for (int j = 0; j < FG; ++j) {
       const int e = er + ecol[j];
-      // 2^e built from its bits when it is a normal number
+      // the two sums in units of 2^-xunit (lsc: an exact power of two),
+      // alpha's sign applied to them; converted with integer instructions
+      const int64_t g0 = fs.a_neg ? -g[j] : g[j], g1 = fs.a_neg ? -gl[j] : gl[j];
+      const double x = FINE ? fma(i64_to_f64_rn(g1), lsc, i64_to_f64_rn(g0)) : i64_to_f64_rn(g0);
       // x * 2^e by adding e to x's exponent field (integer arithmetic: the
       // fp64 pipe is narrow) when the result stays a normal number
-      // the two sums in units of 2^-xunit (lsc: an exact power of two)
-      const double x = FINE ? (double)g[j] + (double)gl[j] * lsc : i64_to_f64_rn(g[j]);
       const long long xb = __double_as_longlong(x);
       const int ex = (int)((xb >> 52) & 0x7FF);
       const double scaled = (ex != 0 && ex + e >= 1 && ex + e <= 2046)
                                 ? __longlong_as_double(xb + ((long long)e << 52))
                                 : ldexp(x, e);
-      double v = alpha == 1.0 ? scaled : alpha * scaled;
-      if (beta != 0.0) v = beta == 1.0 ? v + cold[j] : fma(beta, cold[j], v);
+      // (compile-time choices: no fp64 instruction for a branch not taken)
+      double v = scaled;
+      if constexpr (AK == 1) v = alpha * scaled;
+      if constexpr (BK == 1) v = v + cold[j];
+      if constexpr (BK == 2) v = fma(beta, cold[j], v);
       if (use[j]) C[crow + coff[j]] = v;
       if (P.emit_mode) {  // a network's fused epilogue: the consumer's exponents
         bool bad = false;
@@ -262,6 +269,25 @@ __device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, const
         }
       }
     }
+  }
+}
+
+// finish_cols for the problem's alpha and beta (the same for every tile of
+// a single problem; per problem in a grouped launch): the choice is made once
+// per call, outside the loops over columns.  Not inlined: one call site in
+// the product kernel keeps its registers out of the drain loop's budget.
+template <int CPT, bool FINE>
+__device__ __noinline__ void finish_tile(const Prob& P, const int64_t* Xt, const Sched& sc, int64_t il,
+                                         int64_t row, int64_t crow, int64_t col0, int lc0, int bnp) {
+  const FinishScale fs = finish_scale(P.alpha, P.beta);
+  if (!fs.a_gen) {
+    if (fs.b_kind == 0) finish_cols<CPT, FINE, 0, 0>(P, Xt, sc, il, row, crow, col0, lc0, bnp);
+    else if (fs.b_kind == 1) finish_cols<CPT, FINE, 0, 1>(P, Xt, sc, il, row, crow, col0, lc0, bnp);
+    else finish_cols<CPT, FINE, 0, 2>(P, Xt, sc, il, row, crow, col0, lc0, bnp);
+  } else {
+    if (fs.b_kind == 0) finish_cols<CPT, FINE, 1, 0>(P, Xt, sc, il, row, crow, col0, lc0, bnp);
+    else if (fs.b_kind == 1) finish_cols<CPT, FINE, 1, 1>(P, Xt, sc, il, row, crow, col0, lc0, bnp);
+    else finish_cols<CPT, FINE, 1, 2>(P, Xt, sc, il, row, crow, col0, lc0, bnp);
   }
 }
 
@@ -697,7 +723,8 @@ __global__ void __launch_bounds__(256, 4) k_split_reduce(const float* __restrict
 // + 2 j.  Every load an item needs but C's (the row's flag, exponent and
 // offset, the columns' tables, the sums) is issued at once; only C's loads
 // wait for the column offsets: two levels of dependent loads per item.
-template <bool FINE>
+// AK, BK: alpha and beta classified on the host (see FinishScale).
+template <bool FINE, int AK, int BK>
 __global__ void __launch_bounds__(256, 3) k_split_finish(const int64_t* __restrict__ X, int64_t full,
                                                      int bn, int xunit, int xlo, Prob P) {
   constexpr int PER = SPLIT_PER_THREAD;
@@ -705,6 +732,7 @@ __global__ void __launch_bounds__(256, 3) k_split_finish(const int64_t* __restri
   const int64_t items = (prob_tiles(P, bn) - full) * chunks;
   const size_t per = (size_t)BM * bn, slot = per * (FINE ? 2 : 1);
   const double lsc = ldexp(1.0, xunit - xlo);
+  const FinishScale fs = finish_scale(P.alpha, P.beta);
   double* C = (double*)P.c;
   const int lr = threadIdx.x % BM, lq = threadIdx.x / BM;
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
@@ -716,7 +744,7 @@ __global__ void __launch_bounds__(256, 3) k_split_finish(const int64_t* __restri
     const bool rv = row < P.m;
     const int32_t fa = rv ? P.fa[il * P.m + row] : 1;
     const int64_t crow = P.cl[il] + (rv ? P.cm[row] : 0);
-    const int er = (rv ? P.ea[il * P.m + row] : 0) - xunit;
+    const int er = (rv ? P.ea[il * P.m + row] : 0) - xunit + fs.a_p;
     const int64_t* Xt = X + (size_t)ti * slot + lr;
     int64_t x[PER], xl[PER], cn[PER];
     int32_t fb[PER], ec[PER];
@@ -737,21 +765,27 @@ __global__ void __launch_bounds__(256, 3) k_split_finish(const int64_t* __restri
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
       off[j] = (in[j] && !fa && !fb[j]) ? crow + cn[j] : -1;
-      old[j] = (off[j] >= 0 && P.beta != 0.0) ? C[off[j]] : 0.0;
+      old[j] = (off[j] >= 0 && BK) ? C[off[j]] : 0.0;
     }
     int rmx = -2000;
     bool rbad = false;
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
-      const double xd = FINE ? (double)x[j] + (double)xl[j] * lsc : i64_to_f64_rn(x[j]);
+      // alpha's sign on the sums, their conversion and scaling in integer
+      // instructions (see FinishScale)
+      const int64_t x0 = fs.a_neg ? -x[j] : x[j], x1 = fs.a_neg ? -xl[j] : xl[j];
+      const double xd = FINE ? fma(i64_to_f64_rn(x1), lsc, i64_to_f64_rn(x0)) : i64_to_f64_rn(x0);
       const int e = er + ec[j];
       const long long xb = __double_as_longlong(xd);
       const int ex = (int)((xb >> 52) & 0x7FF);
       const double scaled = (ex != 0 && ex + e >= 1 && ex + e <= 2046)
                                 ? __longlong_as_double(xb + ((long long)e << 52))
                                 : ldexp(xd, e);
-      double v = P.alpha == 1.0 ? scaled : P.alpha * scaled;
-      if (P.beta != 0.0) v = P.beta == 1.0 ? v + old[j] : fma(P.beta, old[j], v);
+      // (compile-time choices: no fp64 instruction for a branch not taken)
+      double v = scaled;
+      if constexpr (AK == 1) v = P.alpha * scaled;
+      if constexpr (BK == 1) v = v + old[j];
+      if constexpr (BK == 2) v = fma(P.beta, old[j], v);
       if (off[j] >= 0) C[off[j]] = v;
       if (P.emit_mode) {  // a network's fused epilogue: the consumer's exponents
         bool bad = false;
@@ -775,6 +809,35 @@ __global__ void __launch_bounds__(256, 3) k_split_finish(const int64_t* __restri
       if (rbad) emit_mark(P.emit_flag, P.emit_list, row);
     }
   }
+}
+
+// k_split_finish for the problem's alpha and beta (classified as FinishScale
+// does on the device): power-of-two alpha and beta 0 or 1 take no fp64
+// multiply.
+template <bool FINE>
+cudaError_t launch_split_finish_a(bool agen, int bk, int grid, const int64_t* X, int64_t full, int bn, int xunit,
+                                  int xlo, const Prob& P, cudaStream_t s) {
+  if (!agen) {
+    if (bk == 0) k_split_finish<FINE, 0, 0><<<grid, 256, 0, s>>>(X, full, bn, xunit, xlo, P);
+    else if (bk == 1) k_split_finish<FINE, 0, 1><<<grid, 256, 0, s>>>(X, full, bn, xunit, xlo, P);
+    else k_split_finish<FINE, 0, 2><<<grid, 256, 0, s>>>(X, full, bn, xunit, xlo, P);
+  } else {
+    if (bk == 0) k_split_finish<FINE, 1, 0><<<grid, 256, 0, s>>>(X, full, bn, xunit, xlo, P);
+    else if (bk == 1) k_split_finish<FINE, 1, 1><<<grid, 256, 0, s>>>(X, full, bn, xunit, xlo, P);
+    else k_split_finish<FINE, 1, 2><<<grid, 256, 0, s>>>(X, full, bn, xunit, xlo, P);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_finish(bool fine, int grid, const int64_t* X, int64_t full, int bn, int xunit, int xlo,
+                                const Prob& P, cudaStream_t s) {
+  uint64_t u;
+  std::memcpy(&u, &P.alpha, sizeof(u));
+  const int E = (int)((u >> 52) & 0x7FF);
+  const bool agen = !((u & 0xFFFFFFFFFFFFFull) == 0 && E >= 1 && E <= 2046);
+  const int bk = P.beta == 0.0 ? 0 : (P.beta == 1.0 ? 1 : 2);
+  return fine ? launch_split_finish_a<true>(agen, bk, grid, X, full, bn, xunit, xlo, P, s)
+              : launch_split_finish_a<false>(agen, bk, grid, X, full, bn, xunit, xlo, P, s);
 }
 
 // The tiles of a triangle of C (tri 1: row >= col, 2: row <= col): row tile
@@ -913,7 +976,6 @@ SplitPlan split_plan(const Plan& p, int bn) {
   return SplitPlan{(int)best, full, tail};
 }
 
-int split_count(const Plan& p, int bn) { return split_plan(p, bn).splits; }
 
 int grid_of(const Plan& p, int bn) {
   const SplitPlan sp = split_plan(p, bn);
@@ -1502,10 +1564,7 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
       // finished per BM-row tile (a pair's split tiles: every tile, full = 0)
       const int64_t ftiles = pp.cg == 2 ? ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) : spl.tail;
       const int fg = (int)std::min<int64_t>(ftiles * (bn / SPLIT_COLS), (int64_t)num_sms() * 24);
-      if (a.sc.nlow)
-        k_split_finish<true><<<fg, 256, 0, s>>>(a.xtail, a.full, bn, a.sc.xunit, a.sc.xlo, a.single);
-      else
-        k_split_finish<false><<<fg, 256, 0, s>>>(a.xtail, a.full, bn, a.sc.xunit, a.sc.xlo, a.single);
+      e = launch_split_finish(a.sc.nlow != 0, fg, a.xtail, a.full, bn, a.sc.xunit, a.sc.xlo, a.single, s);
     }
     else
       k_split_reduce<<<split_grid, 256, 0, s>>>(a.part, a.splits, a.full, bn, a.single);
