@@ -245,3 +245,28 @@ def test_short_k_finish_boundary_integer_exact(k, deferred):
     assert np.array_equal(np.isinf(got), np.isinf(want))
     fin = np.isfinite(want)
     assert np.array_equal(got[fin], want[fin])
+
+
+@pytest.mark.parametrize("alpha", [2.0 ** -40, -(2.0 ** 30), 2.0 ** -1040, 3.0, -1.0])
+@pytest.mark.parametrize("beta", [0.0, 1.0, -0.25])
+@pytest.mark.parametrize("k", [200, 520, 4096])
+def test_alpha_beta_kinds_exact(alpha, beta, k):
+    """alpha = +-2^p goes into the int64 sums' sign and the scaling exponent
+    (integer arithmetic), any other alpha (3, or the subnormal 2^-1040) takes
+    one multiply; beta 0, 1 and -0.25 each have their own finish.  Integer
+    inputs keep every product, sum and scaling exact, so the result equals
+    the oracle's bit for bit.  k = 200: the deferred finish (a separate
+    kernel); k = 520: whole tiles finished inside the product; k = 4096: K
+    split across the SMs, the separate kernel again."""
+    rng = np.random.default_rng(420 + k)
+    m, n = 300, 200
+    A = W.Operand(rng.integers(-6, 7, m * k).astype(np.float64), (m, k), (1, m), [1, 2])
+    B = W.Operand(rng.integers(-6, 7, k * n).astype(np.float64), (k, n), (1, k), [2, 3])
+    C = W.Operand(rng.integers(-6, 7, m * n).astype(np.float64), (m, n), (1, m), [1, 3])
+    p = W.Problem("alpha_beta_kinds", alpha, A, B, beta, C)
+    Cg, info = run_gpu(p, "f64_emu")
+    assert np.array_equal(gpu_dense(Cg), run_oracle(p))
+    # in-product finish: no separate finishing launch (tables, exponents,
+    # pack, B's one-pass split, product, fix-up)
+    if k == 520:
+        assert info["launches"] + info["cached"] == 6
