@@ -324,6 +324,10 @@ __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap*
   uint32_t phase = 0;
   uint32_t pending = 0;  // bit s: stage s holds a copy issued in phase bit (s+8)
   bool ok = true;
+  // the row operand's tiles are read by the CTAs of one row of tiles at
+  // about the same time, the column operand's by every row of tiles: keep
+  // the latter in L2
+  const uint64_t pol_a = ptx::policy_evict_first(), pol_b = ptx::policy_evict_last();
   for (int64_t t = first_item<CG>(); t < ntiles && ok; t += item_step<CG>()) {
     const TileRef T = tile_at<BN, GROUPED, Cfg::KB, SPLITK, Cfg::TM>(args, t);
     const CUtensorMap* ma = GROUPED ? T.P->map_a : map_a;
@@ -350,8 +354,8 @@ __device__ __forceinline__ void produce(const PairArgs& args, const CUtensorMap*
             } else {
               if (!ptx::mbar_wait(&empty[stage], phase ^ 1, lim, abort)) { ok = false; break; }
               ptx::mbar_arrive_expect_tx(&full[stage], bytes);
-              ptx::tma_load_3d(ring_a + stage * Cfg::A_BYTES, ma, &full[stage], kb * Cfg::KB, row_a, za);
-              ptx::tma_load_3d(ring_b + stage * Cfg::B_BYTES, mb, &full[stage], kb * Cfg::KB, row_b, zb);
+              ptx::tma_load_3d_hint(ring_a + stage * Cfg::A_BYTES, ma, &full[stage], kb * Cfg::KB, row_a, za, pol_a);
+              ptx::tma_load_3d_hint(ring_b + stage * Cfg::B_BYTES, mb, &full[stage], kb * Cfg::KB, row_b, zb, pol_b);
             }
             pending = (pending & ~(0x101u << stage)) | (1u << stage) | (phase << (stage + 8));
             if (++stage == S) { stage = 0; phase ^= 1; }
