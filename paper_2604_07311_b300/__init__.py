@@ -119,12 +119,10 @@ def contract_batched(alpha, As, las, Bs, lbs, beta, Cs, lcs, dtype=None, stream=
     if not (len(Bs) == len(Cs) == len(las) == len(lbs) == len(lcs) == n):
         raise ValueError("one entry per problem")
     code = _dtype_code(dtype, As[0], Cs[0]) if n else F64
-    descs = [(desc_torch(a, x), desc_torch(b, y), desc_torch(c, z))
-             for a, x, b, y, c, z in zip(As, las, Bs, lbs, Cs, lcs)]
-    from ._lib import TensorDesc
-    ta = (TensorDesc * max(n, 1))(*[d[0].t for d in descs])
-    tb = (TensorDesc * max(n, 1))(*[d[1].t for d in descs])
-    tc = (TensorDesc * max(n, 1))(*[d[2].t for d in descs])
+    from ._lib import desc_array_torch
+    ta, keep_a = desc_array_torch(As, las)
+    tb, keep_b = desc_array_torch(Bs, lbs)
+    tc, keep_c = desc_array_torch(Cs, lcs)
     al = [alpha] * n if not hasattr(alpha, "__len__") else list(alpha)
     be = [beta] * n if not hasattr(beta, "__len__") else list(beta)
     aa = (ctypes.c_double * max(n, 1))(*al)

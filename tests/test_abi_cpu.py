@@ -344,3 +344,29 @@ def test_ctas_per_mma_option_is_validated():
         with pytest.raises(fm.FamliesError) as e:
             fm.plan(*A, *B, *C, dtype="f64_emu", ctas_per_mma=v)
         assert e.value.code == -1  # FAMLIES_ERR_INVALID_ARG
+
+
+def test_bulk_batch_descriptors_match_single_ones():
+    # The grouped call marshals its descriptors in bulk; each must read as the
+    # per-tensor descriptor of the same view (any strides, storage offsets,
+    # a 0-mode tensor, mixed ranks).
+    import torch
+    from paper_2604_07311_b300 import _lib
+    base = torch.zeros(4000, dtype=torch.float64)
+    xs = [base[:24].view(2, 3, 4).permute(2, 0, 1),
+          base[100:100 + 60].view(5, 12)[:, 1:7],
+          base[7:8].view(()),
+          base[1000:].view(-1, 30)[:, ::3],
+          torch.zeros(3, 1, 5, dtype=torch.float64).transpose(0, 2)]
+    labels = [[1, 2, 3], [4, 5], [], [6, 7], [8, 9, 10]]
+    p, keep = _lib.desc_array_torch(xs, labels)
+    for i, (x, la) in enumerate(zip(xs, labels)):
+        d = _lib.desc_torch(x, la).t
+        q = p[i]
+        assert (q.ndim, q.data, q.size_bytes) == (d.ndim, d.data, d.size_bytes)
+        for m in range(d.ndim):
+            assert (q.extents[m], q.strides[m], q.labels[m]) == (d.extents[m], d.strides[m], d.labels[m])
+    with pytest.raises(ValueError):
+        _lib.desc_array_torch(xs[:2], [[1, 2, 3], [4]])
+    with pytest.raises(ValueError):
+        _lib.desc_array_torch(xs[:2], [[1, 2], [3, 4, 5]])
