@@ -752,16 +752,26 @@ __global__ void __launch_bounds__(256, 4) k_split_reduce(const float* __restrict
 // fp64 split: the splits of a tile added their int64 sums into one slot;
 // C = alpha * 2^(e_m + e_n - xunit) * sum + beta * C (rows and columns
 // holding Inf/NaN are left to the native fix-up).  Item: a tail tile and
-// SPLIT_COLS of its columns; thread t owns row t % BM and the columns t / BM
-// + 2 j.  Every load an item needs but C's (the row's flag, exponent and
-// offset, the columns' tables, the sums) is issued at once; only C's loads
-// wait for the column offsets: two levels of dependent loads per item.
-// AK, BK: alpha and beta classified on the host (see FinishScale).
+// FIN_COLS of its columns.  The item's column tables (C offset, exponent;
+// offset -1 for a column left to the fix-up or past the edge) are staged in
+// shared memory once, beside each thread's row tables; thread t then owns
+// row t % BM and the item's columns t / BM + 2 j, a group at a time, with
+// the sums and the C entries of a group loaded together.  An item thus waits on
+// the tables once and then on one level of loads per group (a 16-column
+// item that fetched its own tables waited on three levels and kept the
+// kernel at ~2.8 TB/s).  AK, BK: alpha and beta classified on the host (see
+// FinishScale).
+constexpr int FIN_COLS = 64;
+
 template <bool FINE, int AK, int BK>
 __global__ void __launch_bounds__(256, 3) k_split_finish(const int64_t* __restrict__ X, int64_t full,
                                                      int bn, int xunit, int xlo, Prob P) {
-  constexpr int PER = SPLIT_PER_THREAD;
-  const int chunks = bn / SPLIT_COLS;
+  // columns per group: 8, or 4 with the second (fine) sums, whose loads
+  // and converts would not fit the register budget at 8
+  constexpr int FIN_G = FINE ? 4 : 8;
+  __shared__ int64_t s_cn[FIN_COLS];
+  __shared__ int32_t s_ec[FIN_COLS];
+  const int chunks = (bn + FIN_COLS - 1) / FIN_COLS;
   const int64_t items = (prob_tiles(P, bn) - full) * chunks;
   const size_t per = (size_t)BM * bn, slot = per * (FINE ? 2 : 1);
   const double lsc = ldexp(1.0, xunit - xlo);
@@ -770,69 +780,78 @@ __global__ void __launch_bounds__(256, 3) k_split_finish(const int64_t* __restri
   const int lr = threadIdx.x % BM, lq = threadIdx.x / BM;
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
     const int64_t ti = it / chunks, tile = full + ti;  // ti: index among the tail tiles
-    const int c0 = (int)(it % chunks) * SPLIT_COLS;
+    const int c0 = (int)(it % chunks) * FIN_COLS;
     int64_t tm, tn, il;
     tile_coords(P, bn, tile, tm, tn, il);
     const int64_t row = tm * BM + lr;
     const bool rv = row < P.m;
-    const int32_t fa = rv ? P.fa[il * P.m + row] : 1;
+    __syncthreads();  // the previous item's reads of the column tables are done
+    if (threadIdx.x < FIN_COLS) {
+      const int lc = c0 + (int)threadIdx.x;
+      const int64_t col = tn * bn + lc;
+      const bool ok = lc < bn && col < P.n;
+      const int32_t fb = ok ? P.fb[il * P.n + col] : 1;
+      const int64_t cn = ok ? P.cn[col] : 0;
+      const int32_t ec = ok ? P.eb[il * P.n + col] : 0;
+      s_cn[threadIdx.x] = (ok && !fb) ? cn : -1;
+      s_ec[threadIdx.x] = ec;
+    }
+    const bool rskip = !rv || P.fa[il * P.m + (rv ? row : 0)];
     const int64_t crow = P.cl[il] + (rv ? P.cm[row] : 0);
     const int er = (rv ? P.ea[il * P.m + row] : 0) - xunit + fs.a_p;
+    __syncthreads();
     const int64_t* Xt = X + (size_t)ti * slot + lr;
-    int64_t x[PER], xl[PER], cn[PER];
-    int32_t fb[PER], ec[PER];
-    bool in[PER];
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-      const int lc = c0 + lq + j * (256 / BM);
-      const int64_t col = tn * bn + lc;
-      in[j] = rv && col < P.n && tri_keep(P.tri, row, col);
-      fb[j] = in[j] ? P.fb[il * P.n + col] : 1;
-      ec[j] = in[j] ? P.eb[il * P.n + col] : 0;
-      cn[j] = in[j] ? P.cn[col] : 0;
-      x[j] = Xt[(size_t)lc * BM];
-      xl[j] = FINE ? Xt[per + (size_t)lc * BM] : 0;
-    }
-    int64_t off[PER];
-    double old[PER];
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-      off[j] = (in[j] && !fa && !fb[j]) ? crow + cn[j] : -1;
-      old[j] = (off[j] >= 0 && BK) ? C[off[j]] : 0.0;
-    }
     int rmx = -2000;
     bool rbad = false;
+#pragma unroll 1
+    for (int g0 = 0; g0 < FIN_COLS / 2; g0 += FIN_G) {
+      int64_t x[FIN_G], xl[FIN_G], off[FIN_G];
+      int32_t ec[FIN_G];
+      double old[FIN_G];
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-      // alpha's sign on the sums, their conversion and scaling in integer
-      // instructions (see FinishScale)
-      const int64_t x0 = fs.a_neg ? -x[j] : x[j], x1 = fs.a_neg ? -xl[j] : xl[j];
-      const double xd = FINE ? fma(i64_to_f64_rn(x1), lsc, i64_to_f64_rn(x0)) : i64_to_f64_rn(x0);
-      const int e = er + ec[j];
-      const long long xb = __double_as_longlong(xd);
-      const int ex = (int)((xb >> 52) & 0x7FF);
-      const double scaled = (ex != 0 && ex + e >= 1 && ex + e <= 2046)
-                                ? __longlong_as_double(xb + ((long long)e << 52))
-                                : ldexp(xd, e);
-      // (compile-time choices: no fp64 instruction for a branch not taken)
-      double v = scaled;
-      if constexpr (AK == 1) v = P.alpha * scaled;
-      if constexpr (BK == 1) v = v + old[j];
-      if constexpr (BK == 2) v = fma(P.beta, old[j], v);
-      if (off[j] >= 0) C[off[j]] = v;
-      if (P.emit_mode) {  // a network's fused epilogue: the consumer's exponents
-        bool bad = false;
-        const int ve = off[j] >= 0 ? f64_row_exp(v, &bad) : -2000;
-        if (P.emit_mode == 1) {
-          rmx = max(rmx, ve);
-          rbad = rbad || (off[j] >= 0 && bad);
-        } else {  // consumer row = this column: reduce over the warp's 32 rows
-          const int wm = __reduce_max_sync(0xffffffffu, ve);
-          const unsigned wb = __reduce_or_sync(0xffffffffu, (off[j] >= 0 && bad) ? 1u : 0u);
-          const int64_t col = tn * bn + c0 + lq + j * (256 / BM);
-          if ((threadIdx.x & 31) == 0 && col < P.n) {
-            if (wm > -2000) atomicMax(&P.emit_e[col], wm);
-            if (wb) emit_mark(P.emit_flag, P.emit_list, col);
+      for (int j = 0; j < FIN_G; ++j) {
+        const int cc = lq + 2 * (g0 + j);  // column within the item
+        const int lc = c0 + cc;            // column within the tile
+        const int64_t cn = s_cn[cc];
+        off[j] = (!rskip && cn >= 0 && tri_keep(P.tri, row, tn * bn + lc)) ? crow + cn : -1;
+        ec[j] = s_ec[cc];
+        x[j] = lc < bn ? Xt[(size_t)lc * BM] : 0;
+        xl[j] = (FINE && lc < bn) ? Xt[per + (size_t)lc * BM] : 0;
+      }
+#pragma unroll
+      for (int j = 0; j < FIN_G; ++j) old[j] = (off[j] >= 0 && BK) ? C[off[j]] : 0.0;
+#pragma unroll
+      for (int j = 0; j < FIN_G; ++j) {
+        // alpha's sign on the sums, their conversion and scaling in integer
+        // instructions (see FinishScale)
+        const int64_t x0 = fs.a_neg ? -x[j] : x[j], x1 = fs.a_neg ? -xl[j] : xl[j];
+        const double xd = FINE ? fma(i64_to_f64_rn(x1), lsc, i64_to_f64_rn(x0)) : i64_to_f64_rn(x0);
+        const int e = er + ec[j];
+        const long long xb = __double_as_longlong(xd);
+        const int ex = (int)((xb >> 52) & 0x7FF);
+        const double scaled = (ex != 0 && ex + e >= 1 && ex + e <= 2046)
+                                  ? __longlong_as_double(xb + ((long long)e << 52))
+                                  : ldexp(xd, e);
+        // (compile-time choices: no fp64 instruction for a branch not taken)
+        double v = scaled;
+        if constexpr (AK == 1) v = P.alpha * scaled;
+        if constexpr (BK == 1) v = v + old[j];
+        if constexpr (BK == 2) v = fma(P.beta, old[j], v);
+        if (off[j] >= 0) C[off[j]] = v;
+        if (P.emit_mode) {  // a network's fused epilogue: the consumer's exponents
+          bool bad = false;
+          const int ve = off[j] >= 0 ? f64_row_exp(v, &bad) : -2000;
+          if (P.emit_mode == 1) {
+            rmx = max(rmx, ve);
+            rbad = rbad || (off[j] >= 0 && bad);
+          } else {  // consumer row = this column: reduce over the warp's 32 rows
+            const int wm = __reduce_max_sync(0xffffffffu, ve);
+            const unsigned wb = __reduce_or_sync(0xffffffffu, (off[j] >= 0 && bad) ? 1u : 0u);
+            const int64_t col = tn * bn + c0 + lq + 2 * (g0 + j);
+            if ((threadIdx.x & 31) == 0 && col < P.n) {
+              if (wm > -2000) atomicMax(&P.emit_e[col], wm);
+              if (wb) emit_mark(P.emit_flag, P.emit_list, col);
+            }
           }
         }
       }
@@ -1596,7 +1615,7 @@ cudaError_t launch_packed(const Plan& p, const GemmArgs& g, void* ws, cudaStream
     if (emu) {
       // finished per BM-row tile (a pair's split tiles: every tile, full = 0)
       const int64_t ftiles = pp.cg == 2 ? ((p.m + BM - 1) / BM) * ((p.n + bn - 1) / bn) : spl.tail;
-      const int fg = (int)std::min<int64_t>(ftiles * (bn / SPLIT_COLS), (int64_t)num_sms() * 24);
+      const int fg = (int)std::min<int64_t>(ftiles * ((bn + FIN_COLS - 1) / FIN_COLS), (int64_t)num_sms() * 24);
       e = launch_split_finish(a.sc.nlow != 0, fg, a.xtail, a.full, bn, a.sc.xunit, a.sc.xlo, a.single, s);
     }
     else
