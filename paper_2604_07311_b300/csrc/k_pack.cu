@@ -787,7 +787,7 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpack(const __grid_constant
     }
   };
   const int64_t step = (int64_t)gridDim.x * rpb;
-  int64_t base = (int64_t)blockIdx.x * rpb;  // the block's first row this round
+  int64_t base = (int64_t)blockIdx.x * rpb;  // the block's first row in this pass of the grid
   {
     const bool ok = base + slot < total;
     const double* p = ok ? row_src(base + slot) : X;
