@@ -242,7 +242,10 @@ FAMLIES_API int famlies_contract_host(double alpha, const famlies_tensor_t* A, c
  * one after the other.  F64 problems, and problems with alpha == 0 or an
  * empty contracted extent, run one by one.  The tile width is tuned on the
  * first call for a shape class by timing the candidates with C redirected
- * to scratch (FAMLIES_AUTOTUNE=0 disables this).  Every C[i] must be
+ * to scratch (FAMLIES_AUTOTUNE=0 disables this) and kept for the process;
+ * FAMLIES_TUNE_CACHE=<path> also keeps the tuned widths in that JSON file
+ * (one object, shape-class key -> width), read on the first grouped call
+ * and rewritten whenever a new class is tuned.  Every C[i] must be
  * disjoint from every A[j], B[j] and from every other C[j] (not checked
  * across problems).  When use_graph is non-zero the whole call is captured
  * once into a CUDA graph, cached by the problem set (device, pointers,

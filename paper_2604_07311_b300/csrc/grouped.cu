@@ -11,7 +11,8 @@
 // balance the uneven blocks.  With use_graph the launches are captured once
 // into a CUDA graph per problem set and replayed.  The tile width of the
 // product is picked by timing the candidates on the first call for a given
-// shape class (the autotuner) and remembered for the process.
+// shape class (the autotuner) and remembered for the process, or across
+// processes in the file FAMLIES_TUNE_CACHE names.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -249,6 +250,71 @@ cudaError_t enqueue_finish(const GroupSetup& G, const DevPtrs& d, cudaStream_t s
 // ------------------------------------------------------------ autotuner
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune;
+bool g_tune_loaded = false;
+
+// FAMLIES_LOG=1: one line per grouped call on stderr (problems, chunks, the
+// product's tile width and where it came from).
+bool grouped_log() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("FAMLIES_LOG");
+    v = (e && e[0] && e[0] != '0') ? 1 : 0;
+  }
+  return v == 1;
+}
+
+// Tuned widths kept across processes: FAMLIES_TUNE_CACHE names a JSON file,
+// one object mapping each shape-class key to its width ({"sm148 k2 ...": 128,
+// ...}).  It is read on the first lookup (entries whose width is not 64, 128
+// or 256 are ignored) and rewritten, through a temporary file and a rename,
+// whenever this process tunes a new class; two processes tuning at once
+// keep the last writer's set.  The keys hold the SM count, so a file moved
+// to another kind of GPU is not taken for it.
+const char* tune_cache_path() {
+  const char* e = std::getenv("FAMLIES_TUNE_CACHE");
+  return (e && e[0]) ? e : nullptr;
+}
+
+void load_tune_cache_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = tune_cache_path();
+  if (!path) return;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return;
+  std::string text;
+  char buf[4096];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+  std::fclose(f);
+  size_t i = 0;
+  while ((i = text.find('"', i)) != std::string::npos) {
+    const size_t j = text.find('"', i + 1);
+    if (j == std::string::npos) break;
+    const size_t c = text.find(':', j);
+    if (c == std::string::npos) break;
+    char* end = nullptr;
+    const long w = std::strtol(text.c_str() + c + 1, &end, 10);
+    if (w == 64 || w == 128 || w == 256) g_tune.emplace(text.substr(i + 1, j - i - 1), (int)w);
+    i = end && end > text.c_str() + c + 1 ? (size_t)(end - text.c_str()) : c + 1;
+  }
+}
+
+void save_tune_cache_locked() {
+  const char* path = tune_cache_path();
+  if (!path) return;
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return;
+  std::fputs("{\n", f);
+  size_t n = 0;
+  for (const auto& kv : g_tune)
+    std::fprintf(f, "  \"%s\": %d%s\n", kv.first.c_str(), kv.second, ++n < g_tune.size() ? "," : "");
+  std::fputs("}\n", f);
+  const bool ok = std::fclose(f) == 0;
+  if (ok) std::rename(tmp.c_str(), path);
+  else std::remove(tmp.c_str());
+}
 
 std::string tune_key(const std::vector<const Plan*>& ps) {
   std::vector<int64_t> m, n, k;
@@ -259,7 +325,7 @@ std::string tune_key(const std::vector<const Plan*>& ps) {
   };
   auto lg = [](int64_t x) { int b = 0; while ((int64_t)1 << (b + 1) <= x) ++b; return b; };
   char buf[160];
-  std::snprintf(buf, sizeof(buf), "k%d s%d m%d n%d k%d c%d", ps[0]->kernel, ps[0]->slices,
+  std::snprintf(buf, sizeof(buf), "sm%d k%d s%d m%d n%d k%d c%d", num_sms(), ps[0]->kernel, ps[0]->slices,
                 lg(med(m)), lg(med(n)), lg(med(k)), lg((int64_t)ps.size()));
   return buf;
 }
@@ -337,16 +403,24 @@ int pick_bn(const std::vector<const Plan*>& ps, const double* alpha, const doubl
             GroupSetup& G, char* d_ws, int* status, int64_t wait_limit, cudaStream_t s,
             bool can_tune) {
   const std::string key = tune_key(ps);
+  auto log = [&](int bn, const char* how) {
+    if (grouped_log())
+      std::fprintf(stderr, "famlies: grouped %zu problems [%s]: tile width %d (%s)\n", ps.size(), key.c_str(), bn,
+                   how);
+    return bn;
+  };
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
+    load_tune_cache_locked();
     auto it = g_tune.find(key);
-    if (it != g_tune.end()) return it->second;
+    if (it != g_tune.end()) return log(it->second, "tuned");
   }
-  if (!can_tune || !autotune_enabled()) return heuristic_bn(ps);
+  if (!can_tune || !autotune_enabled()) return log(heuristic_bn(ps), "heuristic");
   const int bn = tune_bn(ps, alpha, beta, G, d_ws, status, wait_limit, s);
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = bn;
-  return bn;
+  save_tune_cache_locked();
+  return log(bn, "timed now");
 }
 
 // ------------------------------------------------------------ graph cache
@@ -498,10 +572,14 @@ int run_grouped(const std::vector<const Plan*>& all, const std::vector<double>& 
     bool tuned;
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
+      load_tune_cache_locked();
       auto it = g_tune.find(tk);
       tuned = it != g_tune.end();
       r.bn = tuned ? it->second : heuristic_bn(r.ps);
     }
+    if (tuned && grouped_log())
+      std::fprintf(stderr, "famlies: grouped %zu problems [%s]: tile width %d (tuned)\n", r.ps.size(), tk.c_str(),
+                   r.bn);
     const bool need_prepare = !use_graph || !tuned;
     if (!need_prepare) continue;
     if (!build_blob(r.ps, r.alpha, r.beta, r.G, r.bn, ws, r.d_blob, status, wait_limit, r.blob)) {
