@@ -23,6 +23,8 @@
 #include <string>
 #include <vector>
 
+#include <unistd.h>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -267,8 +269,9 @@ bool grouped_log() {
 // one object mapping each shape-class key to its width ({"sm148 k2 ...": 128,
 // ...}).  It is read on the first lookup (entries whose width is not 64, 128
 // or 256 are ignored) and rewritten, through a temporary file and a rename,
-// whenever this process tunes a new class; two processes tuning at once
-// keep the last writer's set.  The keys hold the SM count, so a file moved
+// whenever this process tunes a new class (each process through a
+// temporary file of its own); two processes tuning at once keep the last
+// writer's set.  The keys hold the SM count, so a file moved
 // to another kind of GPU is not taken for it.
 const char* tune_cache_path() {
   const char* e = std::getenv("FAMLIES_TUNE_CACHE");
@@ -303,7 +306,7 @@ void load_tune_cache_locked() {
 void save_tune_cache_locked() {
   const char* path = tune_cache_path();
   if (!path) return;
-  const std::string tmp = std::string(path) + ".tmp";
+  const std::string tmp = std::string(path) + ".tmp" + std::to_string((long long)getpid());
   FILE* f = std::fopen(tmp.c_str(), "wb");
   if (!f) return;
   std::fputs("{\n", f);
