@@ -594,8 +594,11 @@ def wl_block_sparse(args):
         def loop():
             for x in zip(As, la, Bs, lb, Cs, lc):
                 fm.contract(1.0, x[0], x[1], x[2], x[3], 0.0, x[4], x[5], dtype="f64_emu")
-        ms_loop = _cuda_ms(loop, max(1, min(args.steps, 3)), 1)
-        res["one_call_per_block"] = {"ms": ms_loop, "tflops": flops / ms_loop / 1e9}
+        if args.no_per_block:  # profiling captures: the grouped calls' launches only
+            ms_loop = None
+        else:
+            ms_loop = _cuda_ms(loop, max(1, min(args.steps, 3)), 1)
+            res["one_call_per_block"] = {"ms": ms_loop, "tflops": flops / ms_loop / 1e9}
         # accuracy: the grouped result of 64 blocks (the largest one included), 32 entries each
         for c in Cs:
             c.zero_()
@@ -638,7 +641,7 @@ def wl_block_sparse(args):
              flops, best, roofline("bf16", 21 * flops, best, "grouped k_pair_gemm<bf16, fp64-split> (+pack)",
                                    note="whole grouped call timed (product and packs), so a lower bound"),
              cpu, err, f"32 entries in each of {len(pick)} blocks (the largest included) vs Dot2",
-             dtype="f64_emu", **res, speedup_grouped_vs_per_block=ms_loop / best)
+             dtype="f64_emu", **res, speedup_grouped_vs_per_block=ms_loop / best if ms_loop else None)
         del As, Bs, Cs, pool, pool_h
         torch.cuda.empty_cache()
 
@@ -912,6 +915,8 @@ def main():
                     help="output columns (i,j pairs) in the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-per-block", action="store_true",
+                    help="block_sparse: skip the one-call-per-block comparison (profiling captures only)")
     ap.add_argument("--v", type=int, default=128, help="virtual extent (profiling captures only)")
     ap.add_argument("--o", type=int, default=32, help="occupied extent (profiling captures only)")
     args = ap.parse_args()
