@@ -39,6 +39,9 @@ namespace {
 
 auto up256 = [](size_t x) { return (x + 255) / 256 * 256; };
 
+// Most workspace the deferred finish of a grouped set's tiles may take.
+constexpr size_t kGroupDeferBytes = (size_t)2 << 30;
+
 struct ProbLayout {
   size_t tab, a, b;    // in the per-problem region
   size_t ea, eb;       // in the exponent region
@@ -48,7 +51,8 @@ struct ProbLayout {
 struct GroupSetup {
   int n = 0;
   int kernel = 0, kind = 0, mode = 0, slices = 1;
-  size_t ws_main = 0, ws_exp = 0, ws_flag = 0, ws_g = 0, ws_total = 0;
+  size_t ws_main = 0, ws_exp = 0, ws_flag = 0, ws_g = 0, ws_defer = 0, ws_total = 0;
+  bool fine = false;  // fp64 split: the schedule keeps the fine diagonals' second sums
   std::vector<ProbLayout> lay;
   int64_t ntiles = 0, max_table = 1, rowexp_total = 0, pack_total = 0, kmax = 1;
   size_t blob_probs = 0, blob_gargs = 0, blob_pargs = 0, blob_jobs = 0, blob_tiles = 0,
@@ -90,7 +94,25 @@ GroupSetup layout_group(const std::vector<const Plan*>& ps, int bn_max) {
     G.c_bytes += up256((size_t)p.span_c * p.es_c);
   }
   if (emu) G.ws_g = up256((size_t)2 * num_sms() * kPairBM * bn_max * 8);  // two sums per element
-  G.ws_total = G.ws_main + G.ws_exp + G.ws_flag + G.ws_g;
+  if (emu) {
+    // Deferred finish: a slot of int64 sums per tile (bn_max columns, two
+    // sums with the fine diagonals), sized for the widest tile list any
+    // candidate width gives; above kGroupDeferBytes the tiles finish inside
+    // the product instead.
+    G.fine = make_pair_sched(G.kernel, G.slices, kSplitBits, G.kmax).nlow != 0;
+    size_t most = 0;
+    for (int bw = 64; bw <= bn_max; bw *= 2) {
+      size_t tiles = 0;
+      for (const Plan* p : ps) {
+        const int w = std::min(pair_bn_for(p->n, 0), bw);
+        tiles += (size_t)p->l * (size_t)((p->m + kPairBM - 1) / kPairBM) * (size_t)((p->n + w - 1) / w);
+      }
+      most = std::max(most, tiles * kPairBM * bw);
+    }
+    const size_t bytes = up256(most * 8 * (G.fine ? 2 : 1));
+    if (bytes <= kGroupDeferBytes) G.ws_defer = bytes;
+  }
+  G.ws_total = G.ws_main + G.ws_exp + G.ws_flag + G.ws_g + G.ws_defer;
   return G;
 }
 
@@ -240,12 +262,23 @@ cudaError_t enqueue_product(const GroupSetup& G, int bn, const Prob* probs, cons
   const int grid = (int)std::min<int64_t>(G.ntiles, num_sms());
   const Sched sc = make_pair_sched(G.kernel, G.slices, kSplitBits, G.kmax);
   double* Gsum = G.mode == PAIR_MODE_EMU ? (double*)(d_ws + G.ws_main + G.ws_exp + G.ws_flag) : nullptr;
-  return launch_pair_grouped(G.kind, G.mode, bn, probs, tiles, G.ntiles, sc, Gsum, grid, status,
+  int64_t* slots = G.ws_defer ? (int64_t*)(d_ws + G.ws_main + G.ws_exp + G.ws_flag + G.ws_g) : nullptr;
+  return launch_pair_grouped(G.kind, G.mode, bn, probs, tiles, G.ntiles, sc, Gsum, slots, grid, status,
                              wait_limit, s);
 }
 
-cudaError_t enqueue_finish(const GroupSetup& G, const DevPtrs& d, cudaStream_t s) {
+// After the product: the deferred finish of every tile (when the product
+// left its sums in slots), then the native recomputation of the rows and
+// columns that hold Inf/NaN.
+cudaError_t enqueue_finish(const GroupSetup& G, const DevPtrs& d, char* d_ws, int bn, cudaStream_t s) {
   if (G.mode != PAIR_MODE_EMU) return cudaSuccess;
+  if (G.ws_defer) {
+    const Sched sc = make_pair_sched(G.kernel, G.slices, kSplitBits, G.kmax);
+    const cudaError_t e =
+        launch_group_finish(sc.nlow != 0, (const int64_t*)(d_ws + G.ws_main + G.ws_exp + G.ws_flag + G.ws_g),
+                            d.probs, d.tiles, G.ntiles, bn, sc.xunit, sc.xlo, s);
+    if (e != cudaSuccess) return e;
+  }
   return launch_fixup_grouped(d.gargs, d.pargs, G.n, s);
 }
 
@@ -603,7 +636,7 @@ int run_grouped(const std::vector<const Plan*>& all, const std::vector<double>& 
     }
     if (!use_graph) {
       if (enqueue_product(r.G, r.bn, d.probs, d.tiles, ws, status, wait_limit, s) != cudaSuccess ||
-          enqueue_finish(r.G, d, s) != cudaSuccess) {
+          enqueue_finish(r.G, d, ws, r.bn, s) != cudaSuccess) {
         rc = FAMLIES_ERR_CUDA;
         break;
       }
@@ -633,7 +666,7 @@ int run_grouped(const std::vector<const Plan*>& all, const std::vector<double>& 
       const DevPtrs d = dev_ptrs(r.G, r.d_blob);
       if (ek == cudaSuccess) ek = enqueue_prepare(r.G, ws, d, cs);
       if (ek == cudaSuccess) ek = enqueue_product(r.G, r.bn, d.probs, d.tiles, ws, status, wait_limit, cs);
-      if (ek == cudaSuccess) ek = enqueue_finish(r.G, d, cs);
+      if (ek == cudaSuccess) ek = enqueue_finish(r.G, d, ws, r.bn, cs);
     }
     e = cudaStreamEndCapture(cs, &graph);
     if (e == cudaSuccess && ek != cudaSuccess) e = ek;

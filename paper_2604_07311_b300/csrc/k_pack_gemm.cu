@@ -74,7 +74,9 @@ struct PairArgs {
   int tailed;            // single problem: tail items write tile slots finished by k_split_finish /
                          // k_split_reduce (K splits, or the deferred finish of short-K tiles)
   int64_t full;          // splits > 1: the leading tiles that run whole (the rest is the tail)
-  int64_t* xtail;        // fp64 split, splits > 1: int64 sums of the tail tiles [tail][BN][BM]
+  int64_t* xtail;        // fp64 split, splits > 1: int64 sums of the tail tiles [tail][BN][BM];
+                         // grouped with defer: the sums of every tile of the list [tile][BN][BM]
+  int defer;             // grouped, fp64 split: tiles leave their sums in xtail for k_group_finish
   int stall_test;        // testing: the MMA issuer first waits on a barrier nothing completes
   float* part;           // fp32 output, splits > 1: partial tail tiles [split][tail][BN][BM]
   int* status;
@@ -631,8 +633,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         // a pair's tail tiles (every tile split, no batch): each CTA's half
         // has the slot of its BM-row tile, numbered as k_split_finish numbers them
         const int64_t xi = CG == 2 ? (2 * T.tm + rank) * ((P.n + BN - 1) / BN) + T.tn : T.tile - args.full;
-        int64_t* Xt = (part_item ? args.xtail + (size_t)xi * slot
-                                 : (int64_t*)args.G + (size_t)blockIdx.x * slot) +
+        // a deferred grouped tile (one CTA owns it, so its first flush
+        // stores) keeps its sums in its own slot for k_group_finish
+        const bool deferred = GROUPED && args.defer;
+        int64_t* Xt = (part_item  ? args.xtail + (size_t)xi * slot
+                       : deferred ? args.xtail + (size_t)t * slot
+                                  : (int64_t*)args.G + (size_t)blockIdx.x * slot) +
                       (size_t)(hf * CPT) * BM + qd * 32 + lane;
         bool first_flush = true;
         for (int di = 0; di < sc.ndiag && ok; ++di) {
@@ -675,7 +681,8 @@ __global__ void __launch_bounds__(THREADS, 1)
               }
               first_flush = false;
             }
-            if (part_item || !(last_unit && di == sc.ndiag - 1) || !rv || P.fa[il * P.m + row]) continue;
+            if (part_item || deferred || !(last_unit && di == sc.ndiag - 1) || !rv || P.fa[il * P.m + row])
+              continue;
             finish_tile<CPT, FINE>(P, Xt, sc, il, row, crow, col0, lc0, bnp);
           }
         }
@@ -891,6 +898,90 @@ cudaError_t launch_split_finish(bool fine, int grid, const int64_t* X, int64_t f
   return fine ? launch_split_finish_a<true>(agen, bk, grid, X, full, bn, xunit, xlo, P, s)
               : launch_split_finish_a<false>(agen, bk, grid, X, full, bn, xunit, xlo, P, s);
 }
+
+// Grouped, fp64 split, deferred: every tile of the list left its int64 sums
+// in its slot (xtail [tile][bn][BM], bn the launch's widest tile); this
+// finishes them all after the product, like k_split_finish, per item a tile
+// and FIN_COLS of its columns, with the tile's own problem (tables, width,
+// alpha and beta, classified per item at run time; the branches are uniform
+// across an item) and no fp64 instruction for alpha = +-2^p or beta 0.
+template <bool FINE>
+__global__ void __launch_bounds__(256, 3) k_group_finish(const int64_t* __restrict__ X, const Prob* __restrict__ probs,
+                                                     const TileEntry* __restrict__ tiles, int64_t ntiles, int bn,
+                                                     int xunit, int xlo) {
+  constexpr int FIN_G = FINE ? 4 : 8;
+  __shared__ int64_t s_cn[FIN_COLS];
+  __shared__ int32_t s_ec[FIN_COLS];
+  const int chunks = (bn + FIN_COLS - 1) / FIN_COLS;
+  const int64_t items = ntiles * chunks;
+  const size_t per = (size_t)BM * bn, slot = per * (FINE ? 2 : 1);
+  const double lsc = ldexp(1.0, xunit - xlo);
+  const int lr = threadIdx.x % BM, lq = threadIdx.x / BM;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int64_t ti = it / chunks;
+    const int c0 = (int)(it % chunks) * FIN_COLS;
+    const TileEntry te = tiles[ti];
+    const Prob& P = probs[te.p];
+    const int bnp = P.bn;  // this tile's width
+    if (c0 >= bnp) continue;  // the whole block skips the item together
+    const int64_t tm = te.tm, tn = te.tn, il = te.il;
+    const FinishScale fs = finish_scale(P.alpha, P.beta);
+    double* C = (double*)P.c;
+    const int64_t row = tm * BM + lr;
+    const bool rv = row < P.m;
+    __syncthreads();  // the previous item's reads of the column tables are done
+    if (threadIdx.x < FIN_COLS) {
+      const int lc = c0 + (int)threadIdx.x;
+      const int64_t col = tn * bnp + lc;
+      const bool ok = lc < bnp && col < P.n;
+      const int32_t fb = ok ? P.fb[il * P.n + col] : 1;
+      const int64_t cn = ok ? P.cn[col] : 0;
+      const int32_t ec = ok ? P.eb[il * P.n + col] : 0;
+      s_cn[threadIdx.x] = (ok && !fb) ? cn : -1;
+      s_ec[threadIdx.x] = ec;
+    }
+    const bool rskip = !rv || P.fa[il * P.m + (rv ? row : 0)];
+    const int64_t crow = P.cl[il] + (rv ? P.cm[row] : 0);
+    const int er = (rv ? P.ea[il * P.m + row] : 0) - xunit + fs.a_p;
+    __syncthreads();
+    const int64_t* Xt = X + (size_t)ti * slot + lr;
+#pragma unroll 1
+    for (int g0 = 0; g0 < FIN_COLS / 2; g0 += FIN_G) {
+      int64_t x[FIN_G], xl[FIN_G], off[FIN_G];
+      int32_t ec[FIN_G];
+      double old[FIN_G];
+#pragma unroll
+      for (int j = 0; j < FIN_G; ++j) {
+        const int cc = lq + 2 * (g0 + j);  // column within the item
+        const int lc = c0 + cc;            // column within the tile
+        const int64_t cn = s_cn[cc];
+        off[j] = (!rskip && cn >= 0) ? crow + cn : -1;
+        ec[j] = s_ec[cc];
+        x[j] = off[j] >= 0 ? Xt[(size_t)lc * BM] : 0;
+        xl[j] = (FINE && off[j] >= 0) ? Xt[per + (size_t)lc * BM] : 0;
+      }
+#pragma unroll
+      for (int j = 0; j < FIN_G; ++j) old[j] = (off[j] >= 0 && fs.b_kind != 0) ? C[off[j]] : 0.0;
+#pragma unroll
+      for (int j = 0; j < FIN_G; ++j) {
+        if (off[j] < 0) continue;
+        const int64_t x0 = fs.a_neg ? -x[j] : x[j], x1 = fs.a_neg ? -xl[j] : xl[j];
+        const double xd = FINE ? fma(i64_to_f64_rn(x1), lsc, i64_to_f64_rn(x0)) : i64_to_f64_rn(x0);
+        const int e = er + ec[j];
+        const long long xb = __double_as_longlong(xd);
+        const int ex = (int)((xb >> 52) & 0x7FF);
+        const double scaled = (ex != 0 && ex + e >= 1 && ex + e <= 2046)
+                                  ? __longlong_as_double(xb + ((long long)e << 52))
+                                  : ldexp(xd, e);
+        double v = fs.a_gen ? P.alpha * scaled : scaled;
+        if (fs.b_kind == 1) v = v + old[j];
+        else if (fs.b_kind == 2) v = fma(P.beta, old[j], v);
+        C[off[j]] = v;
+      }
+    }
+  }
+}
+
 
 // The tiles of a triangle of C (tri 1: row >= col, 2: row <= col): row tile
 // tm meets it in the column tiles [lo, hi).
@@ -1407,9 +1498,19 @@ Sched make_pair_sched(int kernel, int slices, int bits, int64_t k, int64_t parts
   return sc;
 }
 
+cudaError_t launch_group_finish(bool fine, const int64_t* X, const Prob* probs, const TileEntry* tiles,
+                                int64_t ntiles, int bn, int xunit, int xlo, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  const int64_t items = ntiles * ((bn + FIN_COLS - 1) / FIN_COLS);
+  const int grid = (int)std::min<int64_t>(items, (int64_t)num_sms() * 24);
+  if (fine) k_group_finish<true><<<grid, 256, 0, s>>>(X, probs, tiles, ntiles, bn, xunit, xlo);
+  else k_group_finish<false><<<grid, 256, 0, s>>>(X, probs, tiles, ntiles, bn, xunit, xlo);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pair_grouped(int kind, int mode, int bn, const Prob* probs,
                                 const TileEntry* tiles, int64_t ntiles, const Sched& sc,
-                                double* G, int grid, int* status, int64_t wait_limit,
+                                double* G, int64_t* slots, int grid, int* status, int64_t wait_limit,
                                 cudaStream_t s) {
   PairArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -1418,6 +1519,8 @@ cudaError_t launch_pair_grouped(int kind, int mode, int bn, const Prob* probs,
   a.ntiles = ntiles;
   a.sc = sc;
   a.G = G;
+  a.xtail = slots;
+  a.defer = slots != nullptr;
   a.status = status;
   a.wait_limit = wait_limit;
   CUtensorMap unused;

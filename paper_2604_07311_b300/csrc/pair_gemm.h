@@ -81,10 +81,16 @@ int pair_bn_for(int64_t n, int request);
 bool make_slice_map(CUtensorMap* map, void* base, bool f32, int64_t k, int64_t kp, int64_t rows,
                     int64_t z, int box_k, int box_rows);
 // Grouped product over a device tile list; probs/tiles are device arrays.
+// slots (fp64 split, may be null): every tile leaves its int64 sums in its
+// slot [tile][bn][BM] (two sums per element with the fine diagonals) for
+// launch_group_finish instead of finishing inside the product.
 cudaError_t launch_pair_grouped(int kind, int mode, int bn, const Prob* probs,
                                 const TileEntry* tiles, int64_t ntiles, const Sched& sc,
-                                double* G, int grid, int* status, int64_t wait_limit,
+                                double* G, int64_t* slots, int grid, int* status, int64_t wait_limit,
                                 cudaStream_t s);
+// C of every tile of the list from its slot (after a product with slots).
+cudaError_t launch_group_finish(bool fine, const int64_t* X, const Prob* probs, const TileEntry* tiles,
+                                int64_t ntiles, int bn, int xunit, int xlo, cudaStream_t s);
 // k per ring stage.  bf16 stages hold rows of kBf16StageK values (64 bytes at
 // 32, read through the 64-byte swizzle; 128 bytes at 64, the 128-byte one);
 // tf32 stages rows of 32 values (128 bytes).  Smaller stages of the same
