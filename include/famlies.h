@@ -245,7 +245,11 @@ FAMLIES_API int famlies_contract_host(double alpha, const famlies_tensor_t* A, c
  * to scratch (FAMLIES_AUTOTUNE=0 disables this) and kept for the process;
  * FAMLIES_TUNE_CACHE=<path> also keeps the tuned widths in that JSON file
  * (one object, shape-class key -> width), read on the first grouped call
- * and rewritten whenever a new class is tuned.  Every C[i] must be
+ * and rewritten whenever a new class is tuned.  fp64-split tiles leave
+ * their int64 sums in per-tile slots (at most 2 GB per chunk, counted in its
+ * workspace) that a finishing kernel converts after the chunk's product
+ * (FAMLIES_GROUP_DEFER=0, or slots above that size: each tile finishes
+ * inside the product instead).  Every C[i] must be
  * disjoint from every A[j], B[j] and from every other C[j] (not checked
  * across problems).  When use_graph is non-zero the whole call is captured
  * once into a CUDA graph, cached by the problem set (device, pointers,

@@ -42,6 +42,17 @@ auto up256 = [](size_t x) { return (x + 255) / 256 * 256; };
 // Most workspace the deferred finish of a grouped set's tiles may take.
 constexpr size_t kGroupDeferBytes = (size_t)2 << 30;
 
+// FAMLIES_GROUP_DEFER=0: grouped tiles finish inside the product (as they
+// do anyway when their slots would pass kGroupDeferBytes).
+bool group_defer_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("FAMLIES_GROUP_DEFER");
+    v = (e && e[0] == '0') ? 0 : 1;
+  }
+  return v == 1;
+}
+
 struct ProbLayout {
   size_t tab, a, b;    // in the per-problem region
   size_t ea, eb;       // in the exponent region
@@ -110,7 +121,7 @@ GroupSetup layout_group(const std::vector<const Plan*>& ps, int bn_max) {
       most = std::max(most, tiles * kPairBM * bw);
     }
     const size_t bytes = up256(most * 8 * (G.fine ? 2 : 1));
-    if (bytes <= kGroupDeferBytes) G.ws_defer = bytes;
+    if (bytes <= kGroupDeferBytes && group_defer_enabled()) G.ws_defer = bytes;
   }
   G.ws_total = G.ws_main + G.ws_exp + G.ws_flag + G.ws_g + G.ws_defer;
   return G;

@@ -78,6 +78,15 @@ print("grouped child ok")
 """
 
 
+def test_grouped_tiles_finished_inside_the_product():
+    # FAMLIES_GROUP_DEFER=0: the path a chunk takes when its tile slots would
+    # pass their size cap
+    r = subprocess.run([sys.executable, "-c", GROUPED_CHILD], cwd=ROOT,
+                       env=dict(os.environ, FAMLIES_GROUP_DEFER="0"), capture_output=True, text=True,
+                       timeout=900)
+    assert r.returncode == 0 and "grouped child ok" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]
+
+
 def _grouped_child(cache_path):
     env = dict(os.environ, FAMLIES_TUNE_CACHE=str(cache_path), FAMLIES_LOG="1")
     r = subprocess.run([sys.executable, "-c", GROUPED_CHILD], cwd=ROOT, env=env, capture_output=True,
