@@ -516,17 +516,19 @@ std::vector<std::pair<size_t, size_t>> make_chunks(const std::vector<const Plan*
   const char* env = std::getenv("FAMLIES_BATCH_WORKSPACE_MB");
   size_t budget = env ? (size_t)std::atoll(env) << 20 : (size_t)4096 << 20;
   if (budget < ((size_t)16 << 20)) budget = (size_t)16 << 20;
+  // each problem's own workspace, laid out once: all of it, and without the
+  // per-CTA sums, which the problems of a chunk share
+  std::vector<size_t> whole(ps.size()), shared(ps.size());
+  for (size_t i = 0; i < ps.size(); ++i) {
+    const GroupSetup one = layout_group({ps[i]}, 256);
+    whole[i] = one.ws_total;
+    shared[i] = one.ws_total - one.ws_g;
+  }
   std::vector<std::pair<size_t, size_t>> out;
   size_t i0 = 0;
   while (i0 < ps.size()) {
-    size_t i1 = i0 + 1, used = layout_group({ps[i0]}, 256).ws_total;
-    while (i1 < ps.size()) {
-      const GroupSetup one = layout_group({ps[i1]}, 256);
-      const size_t w = one.ws_total - one.ws_g;  // the per-CTA sums are shared
-      if (used + w > budget) break;
-      used += w;
-      ++i1;
-    }
+    size_t i1 = i0 + 1, used = whole[i0];
+    while (i1 < ps.size() && used + shared[i1] <= budget) used += shared[i1++];
     out.emplace_back(i0, i1);
     i0 = i1;
   }
@@ -560,6 +562,17 @@ int run_grouped(const std::vector<const Plan*>& all, const std::vector<double>& 
   if (all.empty()) return FAMLIES_OK;
   int dev = 0;
   cudaGetDevice(&dev);
+  // a set captured before replays its graph: no chunking or layout needed
+  uint64_t key = 0;
+  if (use_graph) {
+    key = set_key(all, alpha.data(), beta.data(), dev);
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {
+      if (it->key != key) continue;
+      g_graphs.splice(g_graphs.begin(), g_graphs, it);
+      return cudaGraphLaunch(g_graphs.front().exec, s) == cudaSuccess ? FAMLIES_OK : FAMLIES_ERR_CUDA;
+    }
+  }
   const auto ranges = make_chunks(all);
   std::vector<ChunkRun> chunks(ranges.size());
   size_t ws_max = 0;
@@ -570,16 +583,6 @@ int run_grouped(const std::vector<const Plan*>& all, const std::vector<double>& 
     r.beta = beta.data() + ranges[c].first;
     r.G = layout_group(r.ps, 256);
     ws_max = std::max(ws_max, r.G.ws_total);
-  }
-  uint64_t key = 0;
-  if (use_graph) {
-    key = set_key(all, alpha.data(), beta.data(), dev);
-    std::lock_guard<std::mutex> lk(g_graph_mu);
-    for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {
-      if (it->key != key) continue;
-      g_graphs.splice(g_graphs.begin(), g_graphs, it);
-      return cudaGraphLaunch(g_graphs.front().exec, s) == cudaSuccess ? FAMLIES_OK : FAMLIES_ERR_CUDA;
-    }
   }
   // workspace (one, reused by the chunks in turn) and descriptor blocks
   char* ws = nullptr;
