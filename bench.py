@@ -35,7 +35,7 @@ METRIC = "contraction TFLOP/s, % tensor-pipe peak; split-precision vs FP64 speed
 # DRAM bytes (read + write) of one product-kernel launch of this benchmark
 # (v=128, 1.154e13 executed flops) from an ncu capture of its dram byte
 # counters; None whenever the product kernel has changed since the capture.
-PRODUCT_TRAFFIC = {"bytes": 14594137856.0 + 1263772160.0, "exec_flops": 1.1544872091648e13}
+PRODUCT_TRAFFIC = {"bytes": 14593853696.0 + 1262723840.0, "exec_flops": 1.1544872091648e13}
 V_EXT, O_EXT, SLICES = 128, 32, 6
 WORKLOAD = f"ccsd_ladder_v128_o32_f64_split{SLICES}"
 
